@@ -1,0 +1,212 @@
+"""FP64 oracle of the RX detector (test infrastructure; never called by the library).
+
+What it computes, and where the paper says so:
+
+* Calibration, Sec. 3.2 ("Data Acquisition"): raw values are gain-corrected and
+  radiometrically calibrated before detection. Reading: a per-band affine map
+  x_b = (v_b - offset_b) * gain_b.
+* Statistics, Sec. 3.3 ("Detection Algorithm"): each band is a variable and each
+  pixel a sample; the mean is the per-band average and the covariance uses
+  "standard statistical methods". Reading: the unbiased sample covariance with
+  denominator N-1, computed two-pass (mean first, then the centred sum).
+* Score, Sec. 3.3, Eq. 1: delta = (s - mu)^T Sigma^{-1} (s - mu), evaluated by
+  the textbook Cholesky factorisation Sigma = L L^T, forward substitution
+  z = L^{-1}(s - mu) and delta = z^T z.
+* Normalisation and threshold, Sec. 3.3 (last paragraph): scores are divided by
+  the cube maximum so the highest is 1; a pixel is anomalous when its score is
+  above a configurable value. Reading: strict ">" on delta (ABS) or on
+  delta / delta_max (REL).
+* Statistics window. Global RX uses every pixel of the 1000-line cube,
+  including the scored pixel (Sec. 3.3, first paragraph). A line-based detector
+  is proposed in Sec. 6.1. Readings for the streamed forms: EXCLUSIVE scores
+  line t against lines [r, t) and INCLUSIVE against [r, t], where r is the last
+  reset (every ``cube_lines`` lines, or never when it is 0). A line whose
+  statistics hold fewer than max(B+1, warmup_pixels) pixels is not ready
+  (NaN score).
+
+Pins (tests/test_oracle_*.py): exact rational brute force on tiny inputs, the
+in-sample identity mean(delta) = B (N-1)/N, invariance under invertible affine
+band maps, closed forms for B = 1 and B = 2, delta(mu) = 0, the Hotelling T^2
+expectation for out-of-sample scores, the leave-one-out identity linking
+EXCLUSIVE and INCLUSIVE scores, LAPACK's Cholesky and triangular solve, and
+ranking of implanted anomalies.
+"""
+from __future__ import annotations
+
+import math
+from typing import Callable, Union
+
+import numpy as np
+
+EXCLUSIVE, INCLUSIVE, CUBE = "exclusive", "inclusive", "cube"
+ABS, REL = "abs", "rel"
+
+# per-line status codes returned by stream_rx
+OK, NOT_READY, NOT_PD = 0, 1, 2
+
+
+class NotPositiveDefinite(ArithmeticError):
+    """The covariance has a non-positive pivot, so Eq. 1 is undefined."""
+
+
+def calibrate(v, gain=None, offset=None) -> np.ndarray:
+    """x_b = (v_b - offset_b) * gain_b in FP64 (Sec. 3.2; per-band affine reading)."""
+    x = np.asarray(v, dtype=np.float64)
+    if offset is not None:
+        x = x - np.asarray(offset, dtype=np.float64)
+    if gain is not None:
+        x = x * np.asarray(gain, dtype=np.float64)
+    return x
+
+
+def sample_mean(X: np.ndarray) -> np.ndarray:
+    """Per-band average over all N pixels of X [N, B] (Sec. 3.3)."""
+    X = np.asarray(X, dtype=np.float64)
+    return X.sum(axis=0) / X.shape[0]
+
+
+def sample_covariance(X: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    """Sigma = sum_p (x_p - mu)(x_p - mu)^T / (N - 1), second pass of two (Sec. 3.3)."""
+    X = np.asarray(X, dtype=np.float64)
+    D = X - mu
+    return (D.T @ D) / (X.shape[0] - 1)
+
+
+def cholesky_lower(S: np.ndarray) -> np.ndarray:
+    """Textbook Cholesky factor L (lower, positive diagonal) with S = L L^T.
+
+    Column j: L_jj = sqrt(S_jj - sum_{k<j} L_jk^2), then
+    L_ij = (S_ij - sum_{k<j} L_ik L_jk) / L_jj for i > j.
+    Raises NotPositiveDefinite when a pivot is not positive.
+    """
+    S = np.asarray(S, dtype=np.float64)
+    n = S.shape[0]
+    L = np.zeros_like(S)
+    for j in range(n):
+        pivot = S[j, j] - L[j, :j] @ L[j, :j]
+        if not (pivot > 0.0) or not math.isfinite(pivot):
+            raise NotPositiveDefinite(f"pivot {j} = {pivot!r}")
+        L[j, j] = math.sqrt(pivot)
+        L[j + 1:, j] = (S[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return L
+
+
+def forward_substitution(L: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """Z with L Z = R for lower-triangular L [B, B] and right-hand sides R [B, n]."""
+    L = np.asarray(L, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    Z = np.zeros_like(R)
+    for i in range(L.shape[0]):
+        Z[i] = (R[i] - L[i, :i] @ Z[:i]) / L[i, i]
+    return Z
+
+
+def rx_scores(S: np.ndarray, mu: np.ndarray, Sigma: np.ndarray) -> np.ndarray:
+    """Eq. 1 for every row s of S [n, B]: (s - mu)^T Sigma^{-1} (s - mu) via Cholesky."""
+    S = np.asarray(S, dtype=np.float64)
+    L = cholesky_lower(Sigma)
+    Z = forward_substitution(L, (S - mu).T)
+    return (Z * Z).sum(axis=0)
+
+
+def threshold_mask(delta: np.ndarray, tau: float, mode: str = ABS, delta_max=None) -> np.ndarray:
+    """Anomaly mask: delta > tau (ABS) or delta / delta_max > tau (REL). NaN -> False."""
+    delta = np.asarray(delta, dtype=np.float64)
+    with np.errstate(invalid="ignore"):
+        if mode == REL:
+            dmax = np.nanmax(delta) if delta_max is None else delta_max
+            return (delta / dmax) > tau
+        return delta > tau
+
+
+def global_rx(cube: np.ndarray, gain=None, offset=None):
+    """Global RX of one cube [L, W, B] (Sec. 3.3): statistics over all its pixels.
+
+    Returns ``(delta [L, W], delta / max(delta))``.
+    """
+    L_, W, B = cube.shape
+    X = calibrate(cube.reshape(-1, B), gain, offset)
+    mu = sample_mean(X)
+    Sigma = sample_covariance(X, mu)
+    d = rx_scores(X, mu, Sigma).reshape(L_, W)
+    return d, d / d.max()
+
+
+# ---------------------------------------------------------------- streamed forms
+LineSource = Union[np.ndarray, Callable[[int, int], np.ndarray]]
+
+
+def _fetch(lines: LineSource, t0: int, n: int) -> np.ndarray:
+    if callable(lines):
+        return lines(t0, n)
+    return lines[t0:t0 + n]
+
+
+def statistics_lines(t: int, mode: str, cube_lines: int, n_lines: int) -> tuple[int, int]:
+    """Half-open line range [a, b) whose pixels form the statistics for scoring line t."""
+    r = (t // cube_lines) * cube_lines if cube_lines > 0 else 0
+    if mode == EXCLUSIVE:
+        return r, t
+    if mode == INCLUSIVE:
+        return r, t + 1
+    if mode == CUBE:
+        if cube_lines <= 0:
+            return 0, n_lines
+        return r, min(r + cube_lines, n_lines)
+    raise ValueError(mode)
+
+
+def _stats_over_lines(lines: LineSource, a: int, b: int, gain, offset, chunk: int):
+    """Two-pass mean and N-1 covariance over the pixels of lines [a, b).
+
+    The sums run over line chunks only to bound host memory; each pass is the
+    same sum as the unchunked definition, in a different rounding order.
+    """
+    s1, n = None, 0
+    for t0 in range(a, b, chunk):
+        X = calibrate(_fetch(lines, t0, min(chunk, b - t0)), gain, offset)
+        X = X.reshape(-1, X.shape[-1])
+        s1 = X.sum(axis=0) if s1 is None else s1 + X.sum(axis=0)
+        n += X.shape[0]
+    mu = s1 / n
+    m2 = None
+    for t0 in range(a, b, chunk):
+        X = calibrate(_fetch(lines, t0, min(chunk, b - t0)), gain, offset)
+        D = X.reshape(-1, X.shape[-1]) - mu
+        m2 = D.T @ D if m2 is None else m2 + D.T @ D
+    return mu, m2 / (n - 1), n
+
+
+def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines: int = 0,
+                   warmup_pixels: int = 0, gain=None, offset=None, n_lines: int | None = None,
+                   chunk: int = 64):
+    """Scores of line t under the given statistics window.
+
+    Returns ``(delta [W], status)`` with status OK, NOT_READY (too few pixels;
+    delta is NaN) or NOT_PD (covariance not positive definite; delta is NaN).
+    """
+    line = calibrate(_fetch(lines, t, 1), gain, offset)[0]
+    W, B = line.shape
+    if n_lines is None:
+        n_lines = (t + 1) if callable(lines) else lines.shape[0]
+    a, b = statistics_lines(t, mode, cube_lines, n_lines)
+    n_pix = (b - a) * W
+    if n_pix < max(B + 1, int(warmup_pixels)):
+        return np.full(W, np.nan), NOT_READY
+    mu, Sigma, _ = _stats_over_lines(lines, a, b, gain, offset, chunk)
+    try:
+        return rx_scores(line, mu, Sigma), OK
+    except NotPositiveDefinite:
+        return np.full(W, np.nan), NOT_PD
+
+
+def stream_rx(lines: np.ndarray, mode: str = EXCLUSIVE, cube_lines: int = 0, warmup_pixels: int = 0,
+              gain=None, offset=None):
+    """Scores of every line of ``lines`` [T, W, B]: ``(delta [T, W], status [T])``."""
+    T, W, B = lines.shape
+    delta = np.full((T, W), np.nan)
+    status = np.zeros(T, dtype=np.int32)
+    for t in range(T):
+        delta[t], status[t] = stream_rx_line(lines, t, mode, cube_lines, warmup_pixels,
+                                             gain, offset, n_lines=T)
+    return delta, status

@@ -1,0 +1,73 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin catches each.
+
+A pin that passes a broken oracle pins nothing; each mutant below must be
+rejected by at least one of the independent checks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rx as orx
+from tests._exact import exact_scores
+
+
+def _cov_biased(X, mu):                       # denominator N instead of N-1
+    D = np.asarray(X, dtype=np.float64) - mu
+    return (D.T @ D) / X.shape[0]
+
+
+def _cov_no_centering(X, mu):                 # dropped mean subtraction
+    X = np.asarray(X, dtype=np.float64)
+    return (X.T @ X) / (X.shape[0] - 1)
+
+
+def _fsub_transposed(L, R):                   # solves with L^T instead of L
+    return np.linalg.solve(L.T, R)
+
+
+def _chol_sign(S):                            # wrong sign in the pivot update
+    S = np.asarray(S, dtype=np.float64)
+    n = S.shape[0]
+    L = np.zeros_like(S)
+    for j in range(n):
+        piv = S[j, j] + L[j, :j] @ L[j, :j]
+        L[j, j] = np.sqrt(piv)
+        L[j + 1:, j] = (S[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return L
+
+
+def _mean_off_by_one(X):                      # divides by N-1
+    X = np.asarray(X, dtype=np.float64)
+    return X.sum(axis=0) / (X.shape[0] - 1)
+
+
+def _checks_fail():
+    """Return True if at least one independent pin rejects the current oracle."""
+    rng = np.random.default_rng(5)
+    X = rng.integers(-20, 21, size=(9, 3)).astype(np.float64)
+    ex = np.array([float(v) for v in exact_scores(X.tolist(), X.tolist())])
+    try:
+        mu = oracle.sample_mean(X)
+        d = oracle.rx_scores(X, mu, oracle.sample_covariance(X, mu))
+    except Exception:
+        return True
+    if not np.all(np.isfinite(d)):
+        return True
+    if np.max(np.abs(d - ex) / np.maximum(ex, 1e-12)) > 1e-11:
+        return True
+    N, B = X.shape
+    return abs(d.mean() - B * (N - 1) / N) > 1e-10
+
+
+@pytest.mark.parametrize("target,mutant", [
+    ("sample_covariance", _cov_biased),
+    ("sample_covariance", _cov_no_centering),
+    ("forward_substitution", _fsub_transposed),
+    ("cholesky_lower", _chol_sign),
+    ("sample_mean", _mean_off_by_one),
+])
+def test_pins_reject_mutant(monkeypatch, target, mutant):
+    assert not _checks_fail(), "pins must accept the unmodified oracle"
+    monkeypatch.setattr(orx, target, mutant)
+    monkeypatch.setattr(oracle, target, mutant)
+    assert _checks_fail(), f"mutant {mutant.__name__} of {target} was not caught"
