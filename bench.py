@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Throughput / latency benchmark of streaming RX on one GB300 (or N replicas).
+
+Workload (default): the 640-pixel x 270-band push-broom stream, 4000 lines of
+uint16 12-bit DN, EXCLUSIVE running statistics (each line scored against all
+earlier lines, Sec. 6.1's line-based form of the global RX of Sec. 3.3), ABS
+threshold. One step = restart the stream and push all 4000 lines (resident in
+HBM) through the C ABI, then read every score and mask back into device memory.
+
+Printed: one JSON line with pixel-spectra scored / s (whole job), the same
+metric end to end from pinned host memory, p50/p99 single-line latency, a
+roofline entry for the dominant kernel timed live with CUDA events on the
+launching stream, the FP32 path next to the BF16 path, clocks sampled during
+the timed region, and the FP64 oracle timed on a bounded sample on the host.
+
+``--impl reference`` times the oracle itself (the only reference that exists).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "stream_640x270": dict(width=640, bands=270, lines=4000, batch=1024),
+    "precision_1024x448": dict(width=1024, bands=448, lines=8000, batch=1024),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d.get("hbm_gbs", 6800.0), bf16_tflops=d.get("bf16_tflops", 1900.0),
+                    bf16_tflops_sustained=d.get("bf16_tflops_sustained", 1700.0), source="measured",
+                    sm_max_mhz=d.get("sm_max_mhz", 2070.0))
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, source="fallback",
+                sm_max_mhz=2070.0)
+
+
+# FP64 and FP32 SIMT peaks derived from unit counts x clock (no measured figure exists):
+# 152 SMs x 2070 MHz x (4 FP64 flops / clk / SM, i.e. the 1.25 TF/s nominal) and
+# x (128 FP32 lanes x 2 flops / clk / SM).
+def fp64_peak_tflops(mhz):
+    return 152 * mhz * 1e6 * 4 / 1e12
+
+
+def fp32_peak_tflops(mhz):
+    return 152 * mhz * 1e6 * 256 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def oracle_sample(lines, t_list, gain, offset):
+    """Time the FP64 oracle scoring the given lines of the stream (EXCLUSIVE)."""
+    import oracle
+    from oracle import rx as orx
+    t0 = time.perf_counter()
+    px = 0
+    for t in t_list:
+        d, st = orx.stream_rx_line(lines, t, oracle.EXCLUSIVE, gain=gain, offset=offset)
+        px += d.size
+    return px, time.perf_counter() - t0
+
+
+def make_inputs(wl, rank):
+    import numpy as np
+    from gen import PushbroomScene, SEED_BASE
+    seed = SEED_BASE + (2 if wl["bands"] == 270 else 3) + 1000 * rank
+    sc = PushbroomScene(wl["width"], wl["bands"], seed=seed)
+    lines = sc.lines(0, wl["lines"])
+    return sc, lines
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    sc, lines = make_inputs(wl, 0)
+    T = wl["lines"]
+    cores = len(os.sched_getaffinity(0))
+    mid = T // 2
+    for i in range(args.warmup):
+        oracle_sample(lines, [mid - 1 - i], sc.gain, sc.offset)
+    px_total, secs = 0, 0.0
+    for i in range(args.steps):
+        px, s = oracle_sample(lines, [mid + i], sc.gain, sc.offset)
+        px_total += px
+        secs += s
+    v = px_total / secs
+    out = {
+        "metric": "pixel-spectra scored/s", "value": v, "unit": "pixel-spectra/s", "impl": "reference",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "width": wl["width"], "bands": wl["bands"], "lines": T,
+                   "stats": "exclusive", "parallelism": "none (host oracle)"},
+        "cpu_baseline": {"value": v, "unit": "pixel-spectra/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one line per step at the stream midpoint (t = {mid}..{mid + args.steps - 1}),"
+                                   " whose cost equals the stream average"},
+        "e2e": {"value": v, "unit": "pixel-spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stream_640x270", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--batch", type=int, default=0, help="lines per internal batch (0 = workload default)")
+    ap.add_argument("--latency-lines", type=int, default=200)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp32-arm", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = dict(WORKLOADS[args.workload])
+    if args.batch:
+        wl["batch"] = args.batch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2602_13509_gb300 as hs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    peaks = load_peaks()
+    sc, lines = make_inputs(wl, rank)
+    T, W, B = wl["lines"], wl["width"], wl["bands"]
+    x_dev = torch.from_numpy(lines.view(np.int16)).to(f"cuda:{local}")
+    x_host = torch.from_numpy(lines.view(np.int16)).pin_memory()
+    s_dev = torch.empty((T, W), dtype=torch.float32, device=f"cuda:{local}")
+    m_dev = torch.empty((T, W), dtype=torch.uint8, device=f"cuda:{local}")
+    s_host = torch.empty((T, W), dtype=torch.float32).pin_memory()
+    m_host = torch.empty((T, W), dtype=torch.uint8).pin_memory()
+
+    def detector(prec):
+        return hs.Detector(width=W, bands=B, stats_mode="exclusive", precision=prec, gain=sc.gain,
+                           offset=sc.offset, max_batch_lines=wl["batch"], result_lines=T, device=local)
+
+    def step(det, host=False):
+        det.reset()
+        if host:
+            rc, first = hs.hsad_push_lines(det.ctx, x_host, T, hs.HSAD_HOST)
+            assert rc == hs.HSAD_OK, hs.hsad_last_error(det.ctx)
+            rc = hs.hsad_scores(det.ctx, first, T, s_host, m_host, hs.HSAD_HOST, -1)
+        else:
+            rc, first = hs.hsad_push_lines(det.ctx, x_dev, T, hs.HSAD_DEVICE)
+            assert rc == hs.HSAD_OK, hs.hsad_last_error(det.ctx)
+            rc = hs.hsad_scores(det.ctx, first, T, s_dev, m_dev, hs.HSAD_DEVICE, -1)
+        assert rc in (hs.HSAD_OK, hs.HSAD_E_NOT_READY), hs.hsad_status_string(rc)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(det, host=False, clocks=None):
+        for _ in range(args.warmup):
+            step(det, host)
+        stream = torch.cuda.ExternalStream(det.stream)
+        barrier()
+        n0 = det.kernel_launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(det, host)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        if dist is not None:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, det.kernel_launches - n0
+
+    px_step = T * W
+    det = detector(args.precision)
+    with ClockSampler(local) as clk:
+        ms, launches = timed(det)
+    value = px_step * world / (ms / 1e3)
+
+    # per-kernel times, CUDA events on the library's stream (separate pass)
+    det.profile(True)
+    det.profile_reset()
+    for _ in range(2):
+        step(det)
+    prof = det.profile_totals()
+    det.profile(False)
+    per_kernel = {k: {"launches_per_step": n / 2, "ms_per_step": t / 2} for k, (n, t) in prof.items()}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+
+    lat = {}
+    if rank == 0 and args.latency_lines > 0:
+        det.reset()
+        warm = (B + 1 + W - 1) // W + 2 + 64
+        hs.hsad_push_lines(det.ctx, x_host[:warm], warm, hs.HSAD_HOST)
+        det.synchronize()
+        one_s = torch.empty((1, W), dtype=torch.float32).pin_memory()
+        one_m = torch.empty((1, W), dtype=torch.uint8).pin_memory()
+        samples = []
+        for t in range(warm, min(T, warm + args.latency_lines)):
+            t0 = time.perf_counter()
+            rc, first = hs.hsad_push_lines(det.ctx, x_host[t:t + 1], 1, hs.HSAD_HOST)
+            rc = hs.hsad_scores(det.ctx, first, 1, one_s, one_m, hs.HSAD_HOST, -1)
+            samples.append((time.perf_counter() - t0) * 1e3)
+        samples.sort()
+        lat = {"p50_ms": samples[len(samples) // 2], "p99_ms": samples[min(len(samples) - 1, int(0.99 * len(samples)))],
+               "lines": len(samples), "line_period_ms": 1e3 / 249.0,
+               "what": "one line pushed from host memory to its scores on the host, single stream"}
+
+    # end to end through the public API from pinned host memory
+    e2e_ms, _ = timed(det, host=True)
+    e2e = {"value": px_step * world / (e2e_ms / 1e3), "unit": "pixel-spectra/s",
+           "h2d_bytes_per_step": int(x_host.numel() * 2), "d2h_bytes_per_step": int(T * W * 5)}
+    det.close()
+
+    fp32_arm = None
+    if args.precision != "fp32" and not args.skip_fp32_arm:
+        d32 = detector("fp32")
+        ms32, _ = timed(d32)
+        d32.close()
+        fp32_arm = {"value": px_step * world / (ms32 / 1e3), "ms_per_step": ms32}
+
+    # roofline of the dominant kernel
+    roof = None
+    if dom is not None:
+        n, tot = prof[dom]
+        avg_ms = tot / n
+        mhz = peaks["sm_max_mhz"]
+        if dom == "factor":
+            lines_per_launch = px_step / W / n
+            work = lines_per_launch * 2.0 * B ** 3 / 3.0
+            ach = work / (avg_ms / 1e3) / 1e12
+            pk = fp64_peak_tflops(mhz)
+            roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "kernel": "factor (FP64 Cholesky + triangular inverse)",
+                    "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk (nominal 1.25 TF/s)"}
+        else:
+            per_launch_px = px_step / n
+            byts = per_launch_px * (2 * B + (5 if dom == "whiten_score" else 0))
+            ach = byts / (avg_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
+                    "peak_source": peaks["source"]}
+        roof["avg_launch_ms"] = avg_ms
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        mid = T // 2
+        px, secs = oracle_sample(lines, [mid], sc.gain, sc.offset)
+        cpu = {"value": px / secs, "unit": "pixel-spectra/s", "cores": len(os.sched_getaffinity(0)),
+               "kind": "oracle", "sample": f"line {mid} of the stream ({W} pixels) scored against lines "
+                                           f"0..{mid - 1}; its cost equals the stream average"}
+
+    out = {
+        "metric": "pixel-spectra scored/s", "value": value, "unit": "pixel-spectra/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": args.workload, "width": W, "bands": B, "lines": T, "stats": "exclusive",
+                   "input": "uint16 12-bit DN", "batch_lines": wl["batch"],
+                   "parallelism": f"replicas x{world} (independent streams)" if world > 1 else "single stream",
+                   "l2": "inputs larger than L2 (%.2f GB per step)" % (x_dev.numel() * 2 / 1e9)},
+        "latency": lat, "e2e": e2e, "gpu_launches": launches, "fp32_path": fp32_arm,
+        "roofline": roof, "kernels": per_kernel, "cpu_baseline": cpu, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

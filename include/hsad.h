@@ -1,0 +1,192 @@
+/*
+ * hsad.h -- C ABI of the GB300 streaming RX hyperspectral anomaly detector.
+ *
+ * The detector is the global RX algorithm of Sec. 3.3 ("Detection Algorithm"):
+ * per-band mean mu and covariance Sigma of a set of pixel spectra, and for every
+ * scored pixel s the squared Mahalanobis distance of Eq. 1,
+ *     delta = (s - mu)^T Sigma^{-1} (s - mu),
+ * optionally divided by the cube maximum and thresholded into an anomaly mask
+ * (Sec. 3.3, last paragraph). Lines of W samples x B bands arrive continuously
+ * from a push-broom imager (Sec. 2.1, Sec. 3.2); Sec. 6.1 proposes scoring them
+ * line by line, which the EXCLUSIVE and INCLUSIVE statistics modes provide.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an hsad_status (0 = HSAD_OK, negative = error).
+ *  - The caller owns every buffer it passes. Nothing is retained after return
+ *    except as documented for HSAD_DEVICE input (stream-ordered reads).
+ *  - Calls on one context must be serialised by the caller. Different contexts
+ *    may be used from different threads.
+ *  - A context that hits a CUDA error becomes sticky-failed: every later call
+ *    except hsad_destroy / hsad_last_error returns HSAD_E_CUDA.
+ *  - Scores are FP32, one per pixel, line-major [n_lines][width]; the mask is one
+ *    byte per pixel (1 = anomalous), same layout.
+ *  - Input lines are band-interleaved-by-pixel (BIP): [n_lines][width][bands],
+ *    bands contiguous, uint16 DN (12-bit sensor values) or float32.
+ */
+#ifndef HSAD_H
+#define HSAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hsad_ctx hsad_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  HSAD_OK = 0,
+  HSAD_E_INVALID = -1,      /* bad argument, size or state; nothing was done */
+  HSAD_E_NOMEM = -2,        /* device budget or allocation exhausted */
+  HSAD_E_NOT_READY = -3,    /* warm-up lines (NaN scores), or not yet computed with timeout 0 */
+  HSAD_E_NOT_PD = -4,       /* covariance not positive definite for some requested line (NaN scores) */
+  HSAD_E_TIMEOUT = -5,      /* a bounded wait expired */
+  HSAD_E_CUDA = -6,         /* CUDA error; the context is now failed */
+  HSAD_E_BUSY = -7,         /* no admission slot (serving); retry later */
+  HSAD_E_INVALID_DATA = -8  /* non-finite input values in a float32 push */
+} hsad_status;
+
+/* input element type */
+enum { HSAD_U16 = 0, HSAD_F32 = 1 };
+/* working precision of the whitening contraction (the covariance sums are exact
+ * for HSAD_U16 input in every mode; the Cholesky factorisation and triangular
+ * inverse are always FP64) */
+enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
+/* statistics window (which pixels form mu and Sigma for a scored line t) */
+enum {
+  HSAD_EXCLUSIVE = 0, /* lines [r, t): line t scored against earlier lines only */
+  HSAD_INCLUSIVE = 1, /* lines [r, t] */
+  HSAD_CUBE = 2       /* the whole cube of cube_lines lines containing t (global RX, Sec. 3.3) */
+};
+/* threshold form */
+enum { HSAD_ABS = 0 /* delta > threshold */, HSAD_REL = 1 /* delta / cube max > threshold (CUBE only) */ };
+/* memory space of a caller buffer */
+enum { HSAD_HOST = 0, HSAD_DEVICE = 1 };
+/* flags */
+enum {
+  HSAD_CREATE_WAIT = 1,      /* hsad_create blocks (bounded) until the device budget admits the context */
+  HSAD_NORMALIZE_SCORES = 2  /* CUBE mode: report delta / cube max instead of delta (Sec. 3.3) */
+};
+
+typedef struct {
+  int32_t width;               /* W >= 1 samples per line */
+  int32_t bands;               /* 1 <= B <= 512 */
+  int32_t in_dtype;            /* HSAD_U16 | HSAD_F32 */
+  int32_t precision;           /* HSAD_FP32 | HSAD_BF16 | HSAD_FP16 */
+  int32_t stats_mode;          /* HSAD_EXCLUSIVE | HSAD_INCLUSIVE | HSAD_CUBE */
+  int32_t cube_lines;          /* statistics reset period in lines; 0 = never (stream modes).
+                                  Required > 0 in CUBE mode (the paper uses 1000). */
+  const float* gain;           /* length B host array or NULL (all 1); copied at create; non-zero */
+  const float* offset;         /* length B host array or NULL (all 0); copied at create */
+  int32_t threshold_mode;      /* HSAD_ABS | HSAD_REL */
+  float threshold;             /* tau; the paper's display value 0.110 is relative (REL) */
+  int64_t warmup_pixels;       /* a line is scored only once its statistics hold at least
+                                  max(B + 1, warmup_pixels) pixels */
+  int64_t device_budget_bytes; /* 0 = no cap for this context */
+  int32_t flags;               /* HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES */
+  int32_t device;              /* CUDA device ordinal */
+  int32_t max_batch_lines;     /* lines processed per internal batch (0 = default 256) */
+  int32_t result_lines;        /* lines of scores kept for hsad_scores (0 = default) */
+} hsad_config;
+
+/* Fill *cfg with defaults: U16, FP32, EXCLUSIVE, cube_lines 0, ABS threshold
+ * B + 6 sqrt(2B) once bands is known (threshold 0 here means "use that default"),
+ * device 0. Returns HSAD_E_INVALID for NULL. */
+int hsad_config_init(hsad_config* cfg);
+
+/* Create a detector context on cfg->device. Validates every field (HSAD_E_INVALID),
+ * allocates its device state and checks it against device_budget_bytes and the
+ * device-wide budget (HSAD_E_NOMEM, or HSAD_E_BUSY when admission would succeed
+ * later; with HSAD_CREATE_WAIT the call waits up to 10 s for admission).
+ * On success *out owns the context; release it with hsad_destroy. */
+int hsad_create(const hsad_config* cfg, hsad_ctx** out);
+
+/* Append n_lines lines (BIP, in_dtype) to the stream and enqueue their work.
+ * mem = HSAD_HOST: the data are copied into library staging before return, so the
+ *   buffer may be reused at once.
+ * mem = HSAD_DEVICE: the lines are read in place, stream-ordered: the buffer must
+ *   stay unchanged until hsad_scores has returned for these lines (or
+ *   hsad_synchronize). In CUBE mode device lines are copied into the cube buffer
+ *   unless the push holds exactly one whole cube starting at its first line.
+ * *first_line_id (optional) receives the id of the first pushed line; ids count
+ * lines from 0 in push order. n_lines = 0 is a no-op. Returns HSAD_E_INVALID for
+ * NULL data, a negative count, a pointer in the wrong memory space, or a push
+ * larger than the result ring; HSAD_E_INVALID_DATA when a float32 push holds NaN
+ * or Inf (the whole push is rejected and nothing is enqueued). */
+int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem,
+                    uint64_t* first_line_id);
+
+/* CUBE mode: close the current partial cube (fewer than cube_lines lines) and score
+ * it as a cube of its own. No-op when no partial cube is open or in stream modes. */
+int hsad_flush(hsad_ctx* ctx);
+
+/* Copy scores and/or mask of lines [first_line_id, first_line_id + n_lines) into
+ * caller memory (mem = HSAD_HOST or HSAD_DEVICE; scores/mask may be NULL).
+ * Waits up to timeout_ms for the lines to be computed (0 = poll: HSAD_E_NOT_READY if
+ * not yet done; negative = wait without limit). Lines that were never pushed or have
+ * left the result ring give HSAD_E_INVALID. Lines still in warm-up get NaN scores
+ * and mask 0 and the call returns HSAD_E_NOT_READY; lines whose covariance was not
+ * positive definite likewise return HSAD_E_NOT_PD (which takes precedence). */
+int hsad_scores(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, float* scores,
+                uint8_t* mask, int32_t mem, int32_t timeout_ms);
+
+/* Per-line status of computed lines: 0 = scored, 1 = warm-up (not ready),
+ * 2 = covariance not positive definite, 3 = invalid data. Host array of n_lines.
+ * Same waiting rules as hsad_scores. */
+int hsad_line_status(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines,
+                     int32_t* status, int32_t timeout_ms);
+
+/* Restart the stream: the running statistics, the open cube and the result ring are
+ * cleared and line ids start again at 0. Work already enqueued completes first
+ * (stream order); no allocation happens. */
+int hsad_reset(hsad_ctx* ctx);
+
+/* Block until all work enqueued on the context has finished (bounded by timeout_ms,
+ * negative = no limit). */
+int hsad_synchronize(hsad_ctx* ctx, int32_t timeout_ms);
+
+/* The CUDA stream (cudaStream_t) the context launches on, for event timing. */
+void* hsad_stream(hsad_ctx* ctx);
+
+/* Number of kernel launches the context has issued so far. */
+int64_t hsad_kernel_launches(const hsad_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded around every kernel on the context's
+ * stream (off by default; costs two event records per launch when on). */
+int hsad_profile_enable(hsad_ctx* ctx, int32_t enable);
+
+/* Totals of kernel class `index` (0-based, in first-launch order) since the last
+ * reset: its name (copied into name[name_len], NUL-terminated), launches and total
+ * milliseconds. Synchronises the context's stream. HSAD_E_INVALID past the last
+ * class. */
+int hsad_profile_read(hsad_ctx* ctx, int32_t index, char* name, int32_t name_len,
+                      int64_t* launches, double* total_ms);
+
+/* Clear the per-kernel totals. */
+int hsad_profile_reset(hsad_ctx* ctx);
+
+/* Bytes of device memory the context holds. */
+int64_t hsad_device_bytes(const hsad_ctx* ctx);
+
+/* Device-wide admission budget in bytes shared by every context on `device`
+ * (0 = unlimited, the default). Contexts already admitted are not affected. */
+int hsad_set_device_budget(int device, int64_t bytes);
+
+/* Bytes currently charged against the device-wide budget of `device`. */
+int64_t hsad_device_budget_used(int device);
+
+/* Release the context. NULL-safe. Waits (up to 10 s) for in-flight work first. */
+int hsad_destroy(hsad_ctx* ctx);
+
+/* Detail string of the last error on this context (or of the last failed
+ * hsad_create on this thread when ctx is NULL). Never NULL. */
+const char* hsad_last_error(const hsad_ctx* ctx);
+
+/* Static name of a status code. */
+const char* hsad_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSAD_H */

@@ -1,0 +1,900 @@
+// Host engine behind the C ABI declared in include/hsad.h.
+//
+// One context = one sensor stream: its running statistics (shift c, S1, S2, N) live on
+// the device, pushed lines are processed in batches of up to max_batch_lines on the
+// context's stream, and per-line scores / mask / status land in a result ring that
+// hsad_scores copies out once the batch's completion event has fired.
+//
+// Per batch in the stream modes (Sec. 6.1's line-based detector; EXCLUSIVE scores line t
+// against lines [r, t), INCLUSIVE against [r, t]):
+//   K1 shift (first line after a reset) -> K1 column sums -> K2 per-line SYRK
+//   -> K3 running mean / covariance per line -> K4+K5 FP64 Cholesky + inverse per line
+//   -> K6 whitening + score + threshold.
+// In CUBE mode (global RX per cube of cube_lines lines, Sec. 3.3) the cube's lines are
+// kept on the device; when the cube is complete: K1, K2 over the whole cube, K3 once,
+// K4+K5 once, K6 over every line, K7 maximum / normalisation / threshold.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hsad.h"
+#include "hsad_internal.h"
+
+using namespace hsad;
+
+namespace {
+
+thread_local std::string g_thread_error = "";
+
+struct Record {
+  uint64_t first, n;
+  cudaEvent_t ev;
+};
+
+// Device-wide admission budget shared by all contexts of the process.
+struct Budget {
+  std::mutex mu;
+  std::map<int, int64_t> limit, used;
+};
+Budget& budget() {
+  static Budget b;
+  return b;
+}
+
+using Clock = std::chrono::steady_clock;
+
+}  // namespace
+
+struct hsad_ctx {
+  hsad_config cfg{};
+  int W = 0, B = 0, Bp = 0, in_type = 0, prec = 0, mode = 0;
+  int64_t min_pix = 0, elem = 2, line_elems = 0, line_bytes = 0;
+  float tau = 0.f;
+  int Lmax = 256;
+  int64_t ring = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr, copy_stream = nullptr;
+  std::string err;
+  bool failed = false;
+  LaunchCounter lc;
+  std::vector<void*> dev_allocs;
+  std::vector<void*> host_allocs;
+  int64_t dev_bytes = 0;
+  bool budget_charged = false;
+
+  // device state
+  int32_t* c_int = nullptr;
+  float* c_flt = nullptr;
+  double* dgain = nullptr;
+  double* state_s1 = nullptr;
+  double* state_s2 = nullptr;
+  // per-batch workspace
+  double* s1_line = nullptr;
+  double* m_line = nullptr;
+  double* sigma = nullptr;
+  double* inv = nullptr;
+  void* wmat = nullptr;
+  float* y0 = nullptr;
+  float* inv_s2 = nullptr;
+  int32_t* status = nullptr;
+  unsigned int* dmax_bits = nullptr;
+  int32_t* bad_flag = nullptr;
+  // result ring
+  float* r_scores = nullptr;
+  uint8_t* r_mask = nullptr;
+  int32_t* r_status = nullptr;
+  // input staging (host pushes) and cube buffer
+  void* h_stage[2] = {nullptr, nullptr};
+  void* d_stage[2] = {nullptr, nullptr};
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  int stage_idx = 0;
+  void* cube_buf = nullptr;
+  int32_t* h_small = nullptr;  // pinned scratch for small host->device values
+
+  // host-side stream state
+  uint64_t next_line = 0;   // id of the next line to be pushed
+  int64_t n_stats = 0;      // pixels in the running statistics (stream modes)
+  int64_t cube_fill = 0;    // lines in the open cube (CUBE mode)
+  uint64_t cube_first = 0;  // id of the open cube's first line
+  std::deque<Record> records;
+  std::vector<cudaEvent_t> event_pool;
+
+  // profiling: pending (name, begin, end) event triples and per-name totals
+  bool prof_on = false;
+  cudaEvent_t prof_open = nullptr;
+  struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> prof_pending;
+  std::vector<std::string> prof_names;
+  std::map<std::string, std::pair<int64_t, double>> prof_tot;
+  std::vector<cudaEvent_t> prof_pool;
+};
+
+// ------------------------------------------------------------------------------ helpers
+namespace {
+
+int fail(hsad_ctx* c, int code, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (code == HSAD_E_CUDA) c->failed = true;
+  } else {
+    g_thread_error = msg;
+  }
+  return code;
+}
+
+#define CK(expr)                                                                        \
+  do {                                                                                  \
+    cudaError_t _e = (expr);                                                            \
+    if (_e != cudaSuccess)                                                              \
+      return fail(ctx, HSAD_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// Per-kernel CUDA-event timing on the launching stream (off unless enabled).
+void prof_begin(hsad_ctx* ctx);
+void prof_end(hsad_ctx* ctx, const char* name);
+
+#define KL(name, expr)    \
+  do {                    \
+    prof_begin(ctx);      \
+    CK(expr);             \
+    prof_end(ctx, name);  \
+  } while (0)
+
+cudaEvent_t get_event(hsad_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  return e;
+}
+
+cudaEvent_t prof_event(hsad_ctx* ctx) {
+  if (!ctx->prof_pool.empty()) {
+    cudaEvent_t e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void prof_begin(hsad_ctx* ctx) {
+  if (!ctx->prof_on) return;
+  ctx->prof_open = prof_event(ctx);
+  if (ctx->prof_open) cudaEventRecord(ctx->prof_open, ctx->stream);
+}
+
+void prof_end(hsad_ctx* ctx, const char* name) {
+  if (!ctx->prof_on || !ctx->prof_open) return;
+  cudaEvent_t b = prof_event(ctx);
+  if (!b) return;
+  cudaEventRecord(b, ctx->stream);
+  ctx->prof_pending.push_back({name, ctx->prof_open, b});
+  ctx->prof_open = nullptr;
+}
+
+// Wait (bounded) for an event. timeout_ms < 0: no limit; 0: single poll.
+int wait_event(hsad_ctx* ctx, cudaEvent_t ev, int32_t timeout_ms) {
+  const auto t0 = Clock::now();
+  for (;;) {
+    cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) return HSAD_OK;
+    if (q != cudaErrorNotReady) return fail(ctx, HSAD_E_CUDA, std::string("event: ") + cudaGetErrorString(q));
+    if (timeout_ms == 0) return HSAD_E_NOT_READY;
+    if (timeout_ms > 0 &&
+        std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count() >= timeout_ms)
+      return fail(ctx, HSAD_E_TIMEOUT, "timed out waiting for device work");
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+void* dalloc(hsad_ctx* ctx, int64_t bytes, bool* ok) {
+  if (bytes <= 0) return nullptr;
+  void* p = nullptr;
+  if (cudaMalloc(&p, (size_t)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ok = false;
+    return nullptr;
+  }
+  ctx->dev_allocs.push_back(p);
+  ctx->dev_bytes += bytes;
+  return p;
+}
+
+int64_t plan_bytes(const hsad_ctx* c) {
+  const int64_t B = c->B, Bp = c->Bp, L = c->Lmax;
+  const int64_t Lf = (c->mode == HSAD_CUBE) ? 1 : L;            // factors per batch
+  const int64_t Ls = (c->mode == HSAD_CUBE) ? c->cfg.cube_lines : L;  // lines per batch
+  int64_t b = 0;
+  b += B * 4 + B * 4 + B * 8 + B * 8 + B * B * 8;                // c, dgain, S1, S2
+  b += Ls * B * 8 * 2;                                           // s1_line, m_line
+  b += Lf * B * B * 8 * 2;                                       // sigma, inv
+  b += Lf * Bp * Bp * 4 + Lf * Bp * 4 + Lf * 4 + Ls * 4;        // wmat, y0, inv_s2, status
+  b += c->ring * c->W * 5 + c->ring * 4 + 64;                    // result ring
+  if (c->mode == HSAD_CUBE) b += (int64_t)c->cfg.cube_lines * c->line_bytes;
+  else b += 2 * L * c->line_bytes;                               // device staging
+  return b;
+}
+
+int validate(const hsad_config* cfg, std::string* why) {
+  auto bad = [&](const char* m) { *why = m; return HSAD_E_INVALID; };
+  if (!cfg) return bad("cfg is NULL");
+  if (cfg->width < 1) return bad("width must be >= 1");
+  if (cfg->bands < 1 || cfg->bands > 512) return bad("bands must be in [1, 512]");
+  if (cfg->in_dtype != HSAD_U16 && cfg->in_dtype != HSAD_F32) return bad("in_dtype must be HSAD_U16 or HSAD_F32");
+  if (cfg->precision < HSAD_FP32 || cfg->precision > HSAD_FP16) return bad("unknown precision");
+  if (cfg->stats_mode < HSAD_EXCLUSIVE || cfg->stats_mode > HSAD_CUBE) return bad("unknown stats_mode");
+  if (cfg->cube_lines < 0) return bad("cube_lines must be >= 0");
+  if (cfg->stats_mode == HSAD_CUBE && cfg->cube_lines <= 0) return bad("CUBE mode needs cube_lines > 0");
+  if (cfg->threshold_mode != HSAD_ABS && cfg->threshold_mode != HSAD_REL) return bad("unknown threshold_mode");
+  if (cfg->threshold_mode == HSAD_REL && cfg->stats_mode != HSAD_CUBE) return bad("REL threshold needs CUBE mode");
+  if (!std::isfinite(cfg->threshold) || cfg->threshold < 0.f) return bad("threshold must be finite and >= 0");
+  if (cfg->warmup_pixels < 0) return bad("warmup_pixels must be >= 0");
+  if (cfg->device_budget_bytes < 0) return bad("device_budget_bytes must be >= 0");
+  if (cfg->max_batch_lines < 0 || cfg->max_batch_lines > 65535) return bad("max_batch_lines must be in [0, 65535]");
+  if (cfg->result_lines < 0) return bad("result_lines must be >= 0");
+  if (cfg->flags & ~(HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES)) return bad("unknown flags");
+  if ((cfg->flags & HSAD_NORMALIZE_SCORES) && cfg->stats_mode != HSAD_CUBE) return bad("HSAD_NORMALIZE_SCORES needs CUBE mode");
+  if (cfg->gain)
+    for (int b = 0; b < cfg->bands; ++b)
+      if (!std::isfinite(cfg->gain[b]) || cfg->gain[b] == 0.f) return bad("gain must be finite and non-zero");
+  if (cfg->offset)
+    for (int b = 0; b < cfg->bands; ++b)
+      if (!std::isfinite(cfg->offset[b])) return bad("offset must be finite");
+  if ((int64_t)cfg->width * cfg->bands > (int64_t)1 << 31) return bad("line too large");
+  return HSAD_OK;
+}
+
+void release(hsad_ctx* ctx) {
+  if (!ctx) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& r : ctx->records) cudaEventDestroy(r.ev);
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+  for (auto& p : ctx->prof_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (int i = 0; i < 2; ++i)
+    if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
+  for (void* p : ctx->dev_allocs) cudaFree(p);
+  for (void* p : ctx->host_allocs) cudaFreeHost(p);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->budget_charged) {
+    std::lock_guard<std::mutex> g(budget().mu);
+    budget().used[ctx->device] -= ctx->dev_bytes;
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  delete ctx;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ ABI
+extern "C" {
+
+const char* hsad_status_string(int s) {
+  switch (s) {
+    case HSAD_OK: return "HSAD_OK";
+    case HSAD_E_INVALID: return "HSAD_E_INVALID";
+    case HSAD_E_NOMEM: return "HSAD_E_NOMEM";
+    case HSAD_E_NOT_READY: return "HSAD_E_NOT_READY";
+    case HSAD_E_NOT_PD: return "HSAD_E_NOT_PD";
+    case HSAD_E_TIMEOUT: return "HSAD_E_TIMEOUT";
+    case HSAD_E_CUDA: return "HSAD_E_CUDA";
+    case HSAD_E_BUSY: return "HSAD_E_BUSY";
+    case HSAD_E_INVALID_DATA: return "HSAD_E_INVALID_DATA";
+    default: return "unknown status";
+  }
+}
+
+int hsad_config_init(hsad_config* cfg) {
+  if (!cfg) return HSAD_E_INVALID;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->in_dtype = HSAD_U16;
+  cfg->precision = HSAD_FP32;
+  cfg->stats_mode = HSAD_EXCLUSIVE;
+  cfg->threshold_mode = HSAD_ABS;
+  return HSAD_OK;
+}
+
+int hsad_set_device_budget(int device, int64_t bytes) {
+  if (bytes < 0) return HSAD_E_INVALID;
+  std::lock_guard<std::mutex> g(budget().mu);
+  budget().limit[device] = bytes;
+  return HSAD_OK;
+}
+
+int64_t hsad_device_budget_used(int device) {
+  std::lock_guard<std::mutex> g(budget().mu);
+  return budget().used[device];
+}
+
+int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
+  hsad_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, HSAD_E_INVALID, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (validate(cfg, &why) != HSAD_OK) return fail(nullptr, HSAD_E_INVALID, why);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return fail(nullptr, HSAD_E_CUDA, "no CUDA device");
+  }
+  if (cfg->device < 0 || cfg->device >= ndev) return fail(nullptr, HSAD_E_INVALID, "device ordinal out of range");
+
+  ctx = new hsad_ctx();
+  ctx->cfg = *cfg;
+  ctx->cfg.gain = nullptr;
+  ctx->cfg.offset = nullptr;
+  ctx->device = cfg->device;
+  ctx->W = cfg->width;
+  ctx->B = cfg->bands;
+  ctx->Bp = pad64(cfg->bands);
+  ctx->in_type = cfg->in_dtype == HSAD_U16 ? IN_U16 : IN_F32;
+  ctx->prec = cfg->precision == HSAD_FP32 ? P_FP32 : (cfg->precision == HSAD_BF16 ? P_BF16 : P_FP16);
+  ctx->mode = cfg->stats_mode;
+  ctx->elem = ctx->in_type == IN_U16 ? 2 : 4;
+  ctx->line_elems = (int64_t)ctx->W * ctx->B;
+  ctx->line_bytes = ctx->line_elems * ctx->elem;
+  ctx->min_pix = std::max<int64_t>((int64_t)ctx->B + 1, cfg->warmup_pixels);
+  ctx->tau = cfg->threshold > 0.f
+                 ? cfg->threshold
+                 : (cfg->threshold_mode == HSAD_ABS ? (float)(ctx->B + 6.0 * std::sqrt(2.0 * ctx->B)) : 0.f);
+  ctx->cfg.threshold = ctx->tau;
+  ctx->Lmax = cfg->max_batch_lines > 0 ? cfg->max_batch_lines : 256;
+  {
+    int64_t r = cfg->result_lines > 0 ? cfg->result_lines : std::max<int64_t>(4096, 2 * (int64_t)ctx->Lmax);
+    if (ctx->mode == HSAD_CUBE) r = std::max<int64_t>(r, 2 * (int64_t)cfg->cube_lines);
+    ctx->ring = r;
+  }
+  DeviceGuard dg(ctx->device);
+
+  // admission
+  const int64_t need = plan_bytes(ctx);
+  if (cfg->device_budget_bytes > 0 && need > cfg->device_budget_bytes) {
+    delete ctx;
+    return fail(nullptr, HSAD_E_NOMEM, "context needs " + std::to_string(need) + " bytes, above its budget");
+  }
+  {
+    const auto t0 = Clock::now();
+    for (;;) {
+      std::unique_lock<std::mutex> g(budget().mu);
+      const int64_t lim = budget().limit.count(ctx->device) ? budget().limit[ctx->device] : 0;
+      const int64_t used = budget().used[ctx->device];
+      if (lim == 0 || used + need <= lim) {
+        budget().used[ctx->device] += need;
+        ctx->budget_charged = true;
+        break;
+      }
+      g.unlock();
+      if (need > lim) {
+        delete ctx;
+        return fail(nullptr, HSAD_E_NOMEM, "context larger than the device budget");
+      }
+      if (!(cfg->flags & HSAD_CREATE_WAIT) ||
+          std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count() > 10000) {
+        delete ctx;
+        return fail(nullptr, HSAD_E_BUSY, "device budget exhausted; retry when contexts are released");
+      }
+      std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
+  }
+  // the charge is recorded as dev_bytes once allocated; start from the planned amount
+  const int64_t charged = need;
+
+  bool ok = true;
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    ok = false;
+  }
+  const int64_t B = ctx->B, Bp = ctx->Bp, L = ctx->Lmax;
+  const int64_t Lf = ctx->mode == HSAD_CUBE ? 1 : L;
+  const int64_t Ls = ctx->mode == HSAD_CUBE ? cfg->cube_lines : L;
+  ctx->c_int = (int32_t*)dalloc(ctx, B * 4, &ok);
+  ctx->c_flt = (float*)dalloc(ctx, B * 4, &ok);
+  ctx->dgain = (double*)dalloc(ctx, B * 8, &ok);
+  ctx->state_s1 = (double*)dalloc(ctx, B * 8, &ok);
+  ctx->state_s2 = (double*)dalloc(ctx, B * B * 8, &ok);
+  ctx->s1_line = (double*)dalloc(ctx, Ls * B * 8, &ok);
+  ctx->m_line = (double*)dalloc(ctx, Ls * B * 8, &ok);
+  ctx->sigma = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
+  ctx->inv = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
+  ctx->wmat = dalloc(ctx, Lf * Bp * Bp * 4, &ok);
+  ctx->y0 = (float*)dalloc(ctx, Lf * Bp * 4, &ok);
+  ctx->inv_s2 = (float*)dalloc(ctx, Lf * 4, &ok);
+  ctx->status = (int32_t*)dalloc(ctx, Ls * 4, &ok);
+  ctx->dmax_bits = (unsigned int*)dalloc(ctx, 64, &ok);
+  ctx->bad_flag = (int32_t*)((char*)ctx->dmax_bits + 32);
+  ctx->r_scores = (float*)dalloc(ctx, ctx->ring * ctx->W * 4, &ok);
+  ctx->r_mask = (uint8_t*)dalloc(ctx, ctx->ring * ctx->W, &ok);
+  ctx->r_status = (int32_t*)dalloc(ctx, ctx->ring * 4, &ok);
+  if (ctx->mode == HSAD_CUBE) {
+    ctx->cube_buf = dalloc(ctx, (int64_t)cfg->cube_lines * ctx->line_bytes, &ok);
+  } else {
+    for (int i = 0; i < 2; ++i) ctx->d_stage[i] = dalloc(ctx, L * ctx->line_bytes, &ok);
+  }
+  for (int i = 0; i < 2 && ok; ++i) {
+    void* h = nullptr;
+    const int64_t hb = (ctx->mode == HSAD_CUBE ? std::min<int64_t>(L, cfg->cube_lines) : L) * ctx->line_bytes;
+    if (cudaHostAlloc(&h, (size_t)hb, cudaHostAllocDefault) != cudaSuccess) ok = false;
+    else ctx->host_allocs.push_back(h);
+    ctx->h_stage[i] = h;
+    if (cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming) != cudaSuccess) ok = false;
+  }
+  if (ok) {
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, 64, cudaHostAllocDefault) != cudaSuccess) ok = false;
+    else ctx->host_allocs.push_back(h);
+    ctx->h_small = (int32_t*)h;
+  }
+  {
+    std::lock_guard<std::mutex> g(budget().mu);
+    budget().used[ctx->device] += ctx->dev_bytes - charged;  // settle planned vs actual
+  }
+  if (!ok) {
+    cudaGetLastError();
+    release(ctx);
+    return fail(nullptr, HSAD_E_NOMEM, "device allocation failed");
+  }
+  // calibration gain as FP64 (the offset cancels in the centring)
+  std::vector<double> g(B, 1.0);
+  if (cfg->gain)
+    for (int b = 0; b < B; ++b) g[b] = (double)cfg->gain[b];
+  if (cudaMemcpy(ctx->dgain, g.data(), B * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemsetAsync(ctx->state_s1, 0, B * 8, ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->state_s2, 0, B * B * 8, ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->r_status, 0xff, ctx->ring * 4, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    release(ctx);
+    return fail(nullptr, HSAD_E_CUDA, "device initialisation failed");
+  }
+  *out = ctx;
+  return HSAD_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------ engine
+namespace {
+
+ScoreOut score_out(hsad_ctx* ctx, uint64_t first_line, bool write_mask) {
+  ScoreOut o;
+  o.scores = ctx->r_scores;
+  o.mask = ctx->r_mask;
+  o.ring_status = ctx->r_status;
+  o.slot0 = (int64_t)(first_line % (uint64_t)ctx->ring);
+  o.ring = ctx->ring;
+  o.tau = ctx->tau;
+  o.write_mask = write_mask ? 1 : 0;
+  return o;
+}
+
+int add_record(hsad_ctx* ctx, uint64_t first, uint64_t n) {
+  cudaEvent_t ev = get_event(ctx);
+  if (!ev) return fail(ctx, HSAD_E_CUDA, "event creation failed");
+  CK(cudaEventRecord(ev, ctx->stream));
+  ctx->records.push_back({first, n, ev});
+  // drop records whose lines have left the ring
+  while (!ctx->records.empty()) {
+    const Record& r = ctx->records.front();
+    if (r.first + r.n + (uint64_t)ctx->ring > ctx->next_line) break;
+    if (cudaEventQuery(r.ev) != cudaSuccess) break;
+    ctx->event_pool.push_back(r.ev);
+    ctx->records.pop_front();
+  }
+  return HSAD_OK;
+}
+
+// One batch of L lines of a stream-mode context, all inside one statistics segment.
+int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
+  const int W = ctx->W, B = ctx->B;
+  cudaStream_t st = ctx->stream;
+  const int incl = ctx->mode == HSAD_INCLUSIVE ? 1 : 0;
+  if (ctx->n_stats == 0) KL("shift_init", launch_shift_init(x, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, st, &ctx->lc));
+  CK(cudaMemsetAsync(ctx->status, 0, (size_t)L * 4, st));
+  KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
+  KL("syrk", launch_syrk_simt(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->sigma, (int64_t)B * B, 0,
+                      st, &ctx->lc));
+  KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, incl,
+                        ctx->min_pix, ctx->status, st, &ctx->lc));
+  KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->m_line, ctx->state_s2, ctx->dgain, ctx->n_stats, W, L, B, incl,
+                       ctx->min_pix, st, &ctx->lc));
+  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, L, B, ctx->prec, ctx->wmat, ctx->y0,
+                   ctx->inv_s2, ctx->status, st, &ctx->lc));
+  KL("whiten_score", launch_whiten_score_simt(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec, ctx->wmat,
+                              ctx->y0, ctx->inv_s2, ctx->status, 1, score_out(ctx, first, true), st,
+                              &ctx->lc));
+  ctx->n_stats += (int64_t)L * W;
+  return add_record(ctx, first, (uint64_t)L);
+}
+
+// Score the open cube (lines [cube_first, cube_first + n) held in x).
+int cube_score(hsad_ctx* ctx, const void* x, int64_t n) {
+  const int W = ctx->W, B = ctx->B;
+  cudaStream_t st = ctx->stream;
+  const int64_t N = n * W;
+  KL("shift_init", launch_shift_init(x, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, st, &ctx->lc));
+  CK(cudaMemsetAsync(ctx->state_s1, 0, (size_t)B * 8, st));
+  CK(cudaMemsetAsync(ctx->state_s2, 0, (size_t)B * B * 8, st));
+  KL("colsum", launch_colsum(x, n, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
+  CK(cudaMemsetAsync(ctx->status, 0, (size_t)n * 4, st));
+  KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, 0, W, (int)n, B, 1, 0, ctx->status, st,
+                        &ctx->lc));
+  KL("syrk", launch_syrk_simt(x, 1, N, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->state_s2, 0, 1, st,
+                      &ctx->lc));
+  KL("finalize_cov", launch_finalize_cov(ctx->state_s1, ctx->state_s2, ctx->dgain, N, B, ctx->sigma, ctx->m_line,
+                         ctx->min_pix, ctx->status, st, &ctx->lc));
+  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, 1, B, ctx->prec, ctx->wmat, ctx->y0,
+                   ctx->inv_s2, ctx->status, st, &ctx->lc));
+  const bool rel = ctx->cfg.threshold_mode == HSAD_REL;
+  const bool norm = (ctx->cfg.flags & HSAD_NORMALIZE_SCORES) != 0;
+  ScoreOut o = score_out(ctx, ctx->cube_first, !(rel || norm));
+  KL("whiten_score", launch_whiten_score_simt(x, (int)n, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec, ctx->wmat,
+                              ctx->y0, ctx->inv_s2, ctx->status, 0, o, st, &ctx->lc));
+  if (rel || norm)
+    KL("cube_normalize", launch_cube_normalize(o, n, W, rel ? 1 : 0, norm ? 1 : 0, ctx->dmax_bits, st, &ctx->lc));
+  const uint64_t first = ctx->cube_first;
+  ctx->cube_first += (uint64_t)n;
+  ctx->cube_fill = 0;
+  return add_record(ctx, first, (uint64_t)n);
+}
+
+bool is_device_ptr(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice && a.device == device) || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem, uint64_t* first_line_id) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  if (n_lines < 0) return fail(ctx, HSAD_E_INVALID, "n_lines < 0");
+  if (mem != HSAD_HOST && mem != HSAD_DEVICE) return fail(ctx, HSAD_E_INVALID, "mem must be HSAD_HOST or HSAD_DEVICE");
+  if (first_line_id) *first_line_id = ctx->next_line;
+  if (n_lines == 0) return HSAD_OK;
+  if (!lines) return fail(ctx, HSAD_E_INVALID, "lines is NULL");
+  if (n_lines > ctx->ring) return fail(ctx, HSAD_E_INVALID, "push larger than the result ring");
+  DeviceGuard dg(ctx->device);
+  if (mem == HSAD_DEVICE && !is_device_ptr(lines, ctx->device))
+    return fail(ctx, HSAD_E_INVALID, "lines is not device memory of this context's device");
+  if (mem == HSAD_HOST && is_device_ptr(lines, ctx->device))
+    return fail(ctx, HSAD_E_INVALID, "lines is device memory but mem = HSAD_HOST");
+
+  // float input: reject non-finite values before anything is enqueued
+  if (ctx->in_type == IN_F32) {
+    const int64_t n = n_lines * ctx->line_elems;
+    if (mem == HSAD_HOST) {
+      const float* f = (const float*)lines;
+      for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(f[i])) return fail(ctx, HSAD_E_INVALID_DATA, "non-finite value in float32 push");
+    } else {
+      CK(cudaMemsetAsync(ctx->bad_flag, 0, 4, ctx->stream));
+      KL("check_finite", launch_check_finite((const float*)lines, n, ctx->bad_flag, ctx->stream, &ctx->lc));
+      CK(cudaMemcpyAsync(ctx->h_small + 1, ctx->bad_flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (ctx->h_small[1]) return fail(ctx, HSAD_E_INVALID_DATA, "non-finite value in float32 push");
+    }
+  }
+
+  const char* src = (const char*)lines;
+  int64_t done = 0;
+  if (ctx->mode == HSAD_CUBE) {
+    const int64_t CL = ctx->cfg.cube_lines;
+    while (done < n_lines) {
+      // zero-copy: a device push that holds one whole cube from its first line
+      if (mem == HSAD_DEVICE && ctx->cube_fill == 0 && n_lines - done >= CL) {
+        ctx->next_line += (uint64_t)CL;
+        int rc = cube_score(ctx, src + done * ctx->line_bytes, CL);
+        if (rc != HSAD_OK) return rc;
+        done += CL;
+        continue;
+      }
+      const int64_t take = std::min<int64_t>(n_lines - done, CL - ctx->cube_fill);
+      char* dst = (char*)ctx->cube_buf + ctx->cube_fill * ctx->line_bytes;
+      if (mem == HSAD_DEVICE) {
+        CK(cudaMemcpyAsync(dst, src + done * ctx->line_bytes, (size_t)(take * ctx->line_bytes),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+      } else {
+        // through pinned staging, in pieces of the staging size
+        const int64_t cap = std::min<int64_t>(ctx->Lmax, CL);
+        for (int64_t o = 0; o < take; o += cap) {
+          const int64_t k = std::min<int64_t>(cap, take - o);
+          const int s = ctx->stage_idx;
+          int rc = wait_event(ctx, ctx->stage_ev[s], 10000);
+          if (rc != HSAD_OK) return rc == HSAD_E_NOT_READY ? fail(ctx, HSAD_E_TIMEOUT, "staging busy") : rc;
+          memcpy(ctx->h_stage[s], src + (done + o) * ctx->line_bytes, (size_t)(k * ctx->line_bytes));
+          CK(cudaMemcpyAsync(dst + o * ctx->line_bytes, ctx->h_stage[s], (size_t)(k * ctx->line_bytes),
+                             cudaMemcpyHostToDevice, ctx->stream));
+          CK(cudaEventRecord(ctx->stage_ev[s], ctx->stream));
+          ctx->stage_idx ^= 1;
+        }
+      }
+      ctx->cube_fill += take;
+      ctx->next_line += (uint64_t)take;
+      done += take;
+      if (ctx->cube_fill == CL) {
+        int rc = cube_score(ctx, ctx->cube_buf, CL);
+        if (rc != HSAD_OK) return rc;
+      }
+    }
+    return HSAD_OK;
+  }
+
+  // stream modes: batches of <= Lmax lines, never across a statistics reset
+  const int64_t CLr = ctx->cfg.cube_lines;
+  while (done < n_lines) {
+    int64_t take = std::min<int64_t>(n_lines - done, ctx->Lmax);
+    if (CLr > 0) {
+      const int64_t into = (int64_t)(ctx->next_line % (uint64_t)CLr);
+      take = std::min<int64_t>(take, CLr - into);
+    }
+    const void* x;
+    if (mem == HSAD_DEVICE) {
+      x = src + done * ctx->line_bytes;
+    } else {
+      const int s = ctx->stage_idx;
+      int rc = wait_event(ctx, ctx->stage_ev[s], 10000);
+      if (rc != HSAD_OK) return rc == HSAD_E_NOT_READY ? fail(ctx, HSAD_E_TIMEOUT, "staging busy") : rc;
+      memcpy(ctx->h_stage[s], src + done * ctx->line_bytes, (size_t)(take * ctx->line_bytes));
+      CK(cudaMemcpyAsync(ctx->d_stage[s], ctx->h_stage[s], (size_t)(take * ctx->line_bytes),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaEventRecord(ctx->stage_ev[s], ctx->stream));
+      ctx->stage_idx ^= 1;
+      x = ctx->d_stage[s];
+    }
+    const uint64_t first = ctx->next_line;
+    ctx->next_line += (uint64_t)take;
+    int rc = stream_batch(ctx, x, (int)take, first);
+    if (rc != HSAD_OK) return rc;
+    done += take;
+    if (CLr > 0 && ctx->next_line % (uint64_t)CLr == 0) {  // statistics reset
+      CK(cudaMemsetAsync(ctx->state_s1, 0, (size_t)ctx->B * 8, ctx->stream));
+      CK(cudaMemsetAsync(ctx->state_s2, 0, (size_t)ctx->B * ctx->B * 8, ctx->stream));
+      ctx->n_stats = 0;
+    }
+  }
+  return HSAD_OK;
+}
+
+int hsad_flush(hsad_ctx* ctx) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  if (ctx->mode != HSAD_CUBE || ctx->cube_fill == 0) return HSAD_OK;
+  DeviceGuard dg(ctx->device);
+  return cube_score(ctx, ctx->cube_buf, ctx->cube_fill);
+}
+
+static int find_ready(hsad_ctx* ctx, uint64_t first, int64_t n, int32_t timeout_ms) {
+  if (n <= 0) return HSAD_OK;
+  const uint64_t last = first + (uint64_t)n - 1;
+  if (last >= ctx->next_line) return fail(ctx, HSAD_E_INVALID, "lines not pushed yet");
+  if (first + (uint64_t)ctx->ring < ctx->next_line) return fail(ctx, HSAD_E_INVALID, "lines have left the result ring");
+  for (auto it = ctx->records.rbegin(); it != ctx->records.rend(); ++it) {
+    if (last >= it->first && last < it->first + it->n) return wait_event(ctx, it->ev, timeout_ms);
+  }
+  // pushed but not yet scored (the open cube in CUBE mode)
+  return HSAD_E_NOT_READY;
+}
+
+static int copy_ring(hsad_ctx* ctx, void* dst, const void* ring_base, int64_t elem_bytes, uint64_t first,
+                     int64_t n, int32_t mem) {
+  const int64_t per_line = (int64_t)ctx->W * elem_bytes;
+  const cudaMemcpyKind kind = mem == HSAD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  int64_t done = 0;
+  while (done < n) {
+    const int64_t slot = (int64_t)((first + (uint64_t)done) % (uint64_t)ctx->ring);
+    const int64_t k = std::min<int64_t>(n - done, ctx->ring - slot);
+    CK(cudaMemcpyAsync((char*)dst + done * per_line, (const char*)ring_base + slot * per_line,
+                       (size_t)(k * per_line), kind, ctx->copy_stream));
+    done += k;
+  }
+  return HSAD_OK;
+}
+
+int hsad_line_status(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, int32_t* status,
+                     int32_t timeout_ms) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  if (n_lines < 0 || (n_lines > 0 && !status)) return fail(ctx, HSAD_E_INVALID, "bad status arguments");
+  if (n_lines > ctx->ring) return fail(ctx, HSAD_E_INVALID, "request larger than the result ring");
+  DeviceGuard dg(ctx->device);
+  int rc = find_ready(ctx, first_line_id, n_lines, timeout_ms);
+  if (rc != HSAD_OK) return rc;
+  int64_t done = 0;
+  while (done < n_lines) {
+    const int64_t slot = (int64_t)((first_line_id + (uint64_t)done) % (uint64_t)ctx->ring);
+    const int64_t k = std::min<int64_t>(n_lines - done, ctx->ring - slot);
+    CK(cudaMemcpyAsync(status + done, ctx->r_status + slot, (size_t)k * 4, cudaMemcpyDeviceToHost,
+                       ctx->copy_stream));
+    done += k;
+  }
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  return HSAD_OK;
+}
+
+int hsad_scores(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, float* scores, uint8_t* mask,
+                int32_t mem, int32_t timeout_ms) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  if (n_lines < 0) return fail(ctx, HSAD_E_INVALID, "n_lines < 0");
+  if (mem != HSAD_HOST && mem != HSAD_DEVICE) return fail(ctx, HSAD_E_INVALID, "mem must be HSAD_HOST or HSAD_DEVICE");
+  if (n_lines > ctx->ring) return fail(ctx, HSAD_E_INVALID, "request larger than the result ring");
+  if (n_lines == 0) return HSAD_OK;
+  DeviceGuard dg(ctx->device);
+  int rc = find_ready(ctx, first_line_id, n_lines, timeout_ms);
+  if (rc != HSAD_OK) return rc;
+  if (scores) {
+    rc = copy_ring(ctx, scores, ctx->r_scores, 4, first_line_id, n_lines, mem);
+    if (rc != HSAD_OK) return rc;
+  }
+  if (mask) {
+    rc = copy_ring(ctx, mask, ctx->r_mask, 1, first_line_id, n_lines, mem);
+    if (rc != HSAD_OK) return rc;
+  }
+  std::vector<int32_t> st((size_t)n_lines);
+  int64_t done = 0;
+  while (done < n_lines) {
+    const int64_t slot = (int64_t)((first_line_id + (uint64_t)done) % (uint64_t)ctx->ring);
+    const int64_t k = std::min<int64_t>(n_lines - done, ctx->ring - slot);
+    CK(cudaMemcpyAsync(st.data() + done, ctx->r_status + slot, (size_t)k * 4, cudaMemcpyDeviceToHost,
+                       ctx->copy_stream));
+    done += k;
+  }
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  bool nr = false, npd = false;
+  for (int32_t s : st) {
+    if (s == LS_NOT_PD) npd = true;
+    else if (s != LS_OK) nr = true;
+  }
+  if (npd) return fail(ctx, HSAD_E_NOT_PD, "covariance not positive definite for some requested lines");
+  if (nr) return HSAD_E_NOT_READY;
+  return HSAD_OK;
+}
+
+int hsad_reset(hsad_ctx* ctx) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  DeviceGuard dg(ctx->device);
+  CK(cudaMemsetAsync(ctx->state_s1, 0, (size_t)ctx->B * 8, ctx->stream));
+  CK(cudaMemsetAsync(ctx->state_s2, 0, (size_t)ctx->B * ctx->B * 8, ctx->stream));
+  CK(cudaMemsetAsync(ctx->r_status, 0xff, (size_t)ctx->ring * 4, ctx->stream));
+  // completion events may still be pending; re-recording a pooled event later is fine
+  for (auto& r : ctx->records) ctx->event_pool.push_back(r.ev);
+  ctx->records.clear();
+  ctx->next_line = 0;
+  ctx->n_stats = 0;
+  ctx->cube_fill = 0;
+  ctx->cube_first = 0;
+  return HSAD_OK;
+}
+
+int hsad_synchronize(hsad_ctx* ctx, int32_t timeout_ms) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  DeviceGuard dg(ctx->device);
+  cudaEvent_t ev = get_event(ctx);
+  if (!ev) return fail(ctx, HSAD_E_CUDA, "event creation failed");
+  CK(cudaEventRecord(ev, ctx->stream));
+  int rc = wait_event(ctx, ev, timeout_ms < 0 ? -1 : (timeout_ms == 0 ? 1 : timeout_ms));
+  ctx->event_pool.push_back(ev);
+  return rc;
+}
+
+int hsad_profile_enable(hsad_ctx* ctx, int32_t enable) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  ctx->prof_on = enable != 0;
+  return HSAD_OK;
+}
+
+int hsad_profile_read(hsad_ctx* ctx, int32_t index, char* name, int32_t name_len, int64_t* launches,
+                      double* total_ms) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  DeviceGuard dg(ctx->device);
+  if (!ctx->prof_pending.empty()) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& p : ctx->prof_pending) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, p.a, p.b));
+      auto& t = ctx->prof_tot[p.name];
+      if (t.first == 0 && t.second == 0.0) ctx->prof_names.push_back(p.name);
+      t.first += 1;
+      t.second += ms;
+      ctx->prof_pool.push_back(p.a);
+      ctx->prof_pool.push_back(p.b);
+    }
+    ctx->prof_pending.clear();
+  }
+  if (index < 0 || index >= (int32_t)ctx->prof_names.size()) return HSAD_E_INVALID;
+  const std::string& nm = ctx->prof_names[index];
+  const auto& t = ctx->prof_tot[nm];
+  if (name && name_len > 0) {
+    strncpy(name, nm.c_str(), (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = t.first;
+  if (total_ms) *total_ms = t.second;
+  return HSAD_OK;
+}
+
+int hsad_profile_reset(hsad_ctx* ctx) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  int64_t l;
+  double ms;
+  hsad_profile_read(ctx, -1, nullptr, 0, &l, &ms);  // drains pending events
+  ctx->prof_tot.clear();
+  ctx->prof_names.clear();
+  return HSAD_OK;
+}
+
+void* hsad_stream(hsad_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int64_t hsad_kernel_launches(const hsad_ctx* ctx) { return ctx ? ctx->lc.n : 0; }
+
+int64_t hsad_device_bytes(const hsad_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+int hsad_destroy(hsad_ctx* ctx) {
+  if (!ctx) return HSAD_OK;
+  if (ctx->stream) {
+    DeviceGuard dg(ctx->device);
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(ev, ctx->stream);
+      const auto t0 = Clock::now();
+      while (cudaEventQuery(ev) == cudaErrorNotReady &&
+             std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count() < 10000)
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+      cudaEventDestroy(ev);
+    }
+  }
+  release(ctx);
+  return HSAD_OK;
+}
+
+const char* hsad_last_error(const hsad_ctx* ctx) {
+  if (!ctx) return g_thread_error.c_str();
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

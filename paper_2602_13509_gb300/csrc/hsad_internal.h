@@ -1,0 +1,102 @@
+// Internal kernel launchers of the hsad library (not part of the C ABI).
+//
+// Data layout in HBM (all row-major):
+//   input lines     [L][W][B]   uint16 DN or float32 (BIP, bands contiguous)
+//   shift c         [B]         int32 (u16 input: integer DN) or float (f32 input)
+//   per-line sums   [L][B]      double   s1_t = sum_p (x_p - c)
+//   per-line SYRK   [L][B][B]   double   s2_t = sum_p (x_p - c)(x_p - c)^T, then Sigma_t in place
+//   factor          [L][Bp][Bp] whitening operand G_t = s_t L_t^{-1} D, row n = output coordinate
+//                               (FP32: float; FP16/BF16: hi plane then lo plane, 16-bit)
+//   y0              [L][Bp]     float   s_t G_t (mu_t - c)
+//   inv_s2          [L]         float   1 / s_t^2 (s_t: power-of-two scale of G_t)
+//   line status     [L]         int32   LS_*
+//   result ring     [R][W]      float scores, uint8 mask, [R] int32 status
+// Bp = B rounded up to a multiple of 64 (zero padded).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hsad {
+
+enum LineStatus : int32_t { LS_OK = 0, LS_NOT_READY = 1, LS_NOT_PD = 2, LS_INVALID_DATA = 3 };
+enum InType : int32_t { IN_U16 = 0, IN_F32 = 1 };
+enum Prec : int32_t { P_FP32 = 0, P_BF16 = 1, P_FP16 = 2 };
+
+__host__ __device__ inline int pad64(int b) { return (b + 63) / 64 * 64; }
+
+// Counts every kernel this library launches (per context, host side).
+struct LaunchCounter {
+  int64_t n = 0;
+};
+
+// K1a: integer (u16) or float (f32) centring shift from one line: c_b = rint(mean_b).
+cudaError_t launch_shift_init(const void* line, int W, int B, int in_type, int32_t* c_int,
+                              float* c_flt, cudaStream_t st, LaunchCounter* lc);
+
+// K1b: per-line column sums s1[t][b] = sum_p (x[t][p][b] - c_b), FP64 (exact for u16).
+cudaError_t launch_colsum(const void* x, int64_t n_lines, int W, int B, int in_type,
+                          const int32_t* c_int, const float* c_flt, double* s1, cudaStream_t st,
+                          LaunchCounter* lc);
+
+// K2 (SIMT): s2 = sum (x - c)(x - c)^T over the pixels of each group of
+// lines_per_group lines; out[g] is a full B x B FP64 matrix (row stride B).
+// accumulate != 0 adds into out with atomics (split over pixel slices).
+cudaError_t launch_syrk_simt(const void* x, int64_t n_groups, int64_t pix_per_group, int B,
+                             int in_type, const int32_t* c_int, const float* c_flt, double* out,
+                             int64_t out_stride, int accumulate, cudaStream_t st,
+                             LaunchCounter* lc);
+
+// K3a: running per-band sums -> per-line mean offset m_t = S1_t / N_t (FP64), line
+// readiness, and the updated state S1.
+cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
+                               int W, int L, int B, int inclusive, int64_t min_pixels,
+                               int32_t* status, cudaStream_t st, LaunchCounter* lc);
+
+// K3b: per-line covariance Sigma_t = D (S2_t - N_t m_t m_t^T) D / (N_t - 1) written in
+// place over the per-line SYRK results, and the updated state S2.
+cudaError_t launch_prefix_cov(double* buf, const double* m, double* state_s2, const double* dgain,
+                              int64_t n0, int W, int L, int B, int inclusive, int64_t min_pixels,
+                              cudaStream_t st, LaunchCounter* lc);
+
+// K3c (cube): Sigma = D (S2 - N m m^T) D / (N - 1), m = S1 / N from the state; status[0]
+// becomes LS_OK or LS_NOT_READY (fewer than min_pixels pixels).
+cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, const double* dgain,
+                                int64_t n, int B, double* sigma, double* m, int64_t min_pixels,
+                                int32_t* status, cudaStream_t st, LaunchCounter* lc);
+
+// K4+K5: FP64 Cholesky and triangular inverse of each ready line's Sigma_t (in place),
+// then G_t = s_t L^{-1} D cast to the working precision, y0 and 1/s_t^2.
+// scratch: [L][B][B] FP64.
+cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
+                          int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
+                          int32_t* status, cudaStream_t st, LaunchCounter* lc);
+
+// K6 (SIMT): delta_p = inv_s2 * || G (x_p - c) - y0 ||^2 for every pixel of every line,
+// threshold, and scatter into the result ring. factor_stride = 0 makes every line
+// use factor 0 (cube mode).
+struct ScoreOut {
+  float* scores;
+  uint8_t* mask;
+  int32_t* ring_status;
+  int64_t slot0;     // ring slot of line 0
+  int64_t ring;      // ring capacity in lines
+  float tau;
+  int write_mask;    // 1: mask = delta > tau here; 0: left to the cube normaliser
+};
+cudaError_t launch_whiten_score_simt(const void* x, int L, int W, int B, int in_type,
+                                     const int32_t* c_int, const float* c_flt, int prec,
+                                     const void* wmat, const float* y0, const float* inv_s2,
+                                     const int32_t* status, int factor_stride, ScoreOut out,
+                                     cudaStream_t st, LaunchCounter* lc);
+
+// K7: cube maximum of delta over n_lines ring lines, then optional normalisation and
+// the REL / ABS mask.
+cudaError_t launch_cube_normalize(ScoreOut out, int64_t n_lines, int W, int rel, int normalize,
+                                  unsigned int* dmax_bits, cudaStream_t st, LaunchCounter* lc);
+
+// f32 input validation: sets *bad = 1 if any value is NaN or Inf.
+cudaError_t launch_check_finite(const float* x, int64_t n, int32_t* bad, cudaStream_t st,
+                                LaunchCounter* lc);
+
+}  // namespace hsad

@@ -1,0 +1,266 @@
+// K6 (SIMT form) whitening + score, and K7 cube normalisation / threshold.
+//
+// Eq. 1 (Sec. 3.3): delta = (x - mu)^T Sigma^{-1} (x - mu) = || G x' - y0 ||^2 / s^2 with
+// the whitening operand G, offset y0 and scale s built by the factor kernel. The
+// contraction Y = X' G^T (pixels x bands times bands x bands, G lower triangular so the
+// k loop of output tile n stops at the tile's last row) is followed in registers by the
+// row norm, so Y is never written. The mask marks scores above the threshold
+// (Sec. 3.3, last paragraph; strict ">").
+//
+// Operand terms per working precision (products exact in FP32, FP32 accumulation):
+//   FP32 : x' (exact for uint16) times G (float)
+//   FP16 : h(x') times G_hi, h(x') times G_lo           (h: round to FP16)
+//   BF16 : H times G_hi, H times G_lo, R times G_hi      (x' = H + R, both exact in BF16:
+//          integer input H = 64 rint(x'/64); float input H = bf16(x'), R = bf16(x' - H))
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hsad_internal.h"
+
+namespace hsad {
+
+namespace {
+constexpr int WS_P = 64, WS_N = 64, WS_K = 16;
+
+template <typename In>
+__device__ __forceinline__ float centred(In v, const int32_t* ci, const float* cf, int b);
+template <>
+__device__ __forceinline__ float centred<uint16_t>(uint16_t v, const int32_t* ci, const float*, int b) {
+  return (float)((int)v - ci[b]);
+}
+template <>
+__device__ __forceinline__ float centred<float>(float v, const int32_t*, const float* cf, int b) {
+  return v - cf[b];
+}
+
+template <typename In, int PREC>
+__device__ __forceinline__ void split_x(float x, float& a0, float& a1) {
+  if (PREC == P_FP32) {
+    a0 = x;
+    a1 = 0.f;
+  } else if (PREC == P_FP16) {
+    a0 = __half2float(__float2half_rn(x));
+    a1 = 0.f;
+  } else {
+    if (sizeof(In) == 2) {
+      const float h = 64.f * rintf(x * (1.f / 64.f));
+      a0 = h;
+      a1 = x - h;
+    } else {
+      const float h = __bfloat162float(__float2bfloat16_rn(x));
+      a0 = h;
+      a1 = __bfloat162float(__float2bfloat16_rn(x - h));
+    }
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void load_w(const void* w, int64_t plane, int64_t idx, float& b0, float& b1) {
+  if (PREC == P_FP32) {
+    b0 = ((const float*)w)[idx];
+    b1 = 0.f;
+  } else if (PREC == P_FP16) {
+    b0 = __half2float(((const __half*)w)[idx]);
+    b1 = __half2float(((const __half*)w)[plane + idx]);
+  } else {
+    b0 = __bfloat162float(((const __nv_bfloat16*)w)[idx]);
+    b1 = __bfloat162float(((const __nv_bfloat16*)w)[plane + idx]);
+  }
+}
+}  // namespace
+
+template <typename In, int PREC>
+__global__ void __launch_bounds__(256) whiten_score_kernel(
+    const In* __restrict__ x, int W, int B, const int32_t* __restrict__ c_int,
+    const float* __restrict__ c_flt, const void* __restrict__ wmat, const float* __restrict__ y0_all,
+    const float* __restrict__ inv_s2_all, const int32_t* __restrict__ status, int factor_stride,
+    ScoreOut out) {
+  // rows padded by 4 floats: the staging stores walk k fastest
+  __shared__ __align__(16) float As[2][WS_K][WS_P + 4];
+  __shared__ __align__(16) float Bs[2][WS_K][WS_N + 4];
+  const int t = blockIdx.y;
+  const int p0 = blockIdx.x * WS_P;
+  const int f = factor_stride ? t : 0;
+  const int64_t slot = (out.slot0 + t) % out.ring;
+  const int st = status[f];
+  if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;
+  if (st != LS_OK) {
+    for (int p = p0 + threadIdx.x; p < p0 + WS_P && p < W; p += blockDim.x) {
+      out.scores[slot * W + p] = __int_as_float(0x7fc00000);
+      out.mask[slot * W + p] = 0;
+    }
+    return;
+  }
+  const int Bp = pad64(B);
+  const int64_t plane = (int64_t)Bp * Bp;
+  const void* w = (const char*)wmat + (size_t)f * plane * 4;
+  const float* y0 = y0_all + (int64_t)f * Bp;
+  const In* xl = x + (int64_t)t * W * B;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+
+  float dsum[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int n0 = 0; n0 < B; n0 += WS_N) {
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) acc[r][s] = 0.f;
+    const int kmax = min(B, n0 + WS_N);
+    for (int k0 = 0; k0 < kmax; k0 += WS_K) {
+      // stage: element e -> (row e/16, k e%16) for both operands
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = threadIdx.x + q * 256;
+        const int rr = e >> 4, kk = e & 15;
+        const int k = k0 + kk;
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+        const int p = p0 + rr;
+        if (p < W && k < B) {
+          const float xc = centred<In>(xl[(int64_t)p * B + k], c_int, c_flt, k);
+          split_x<In, PREC>(xc, a0, a1);
+        }
+        const int n = n0 + rr;
+        if (n < B && k < Bp) load_w<PREC>(w, plane, (int64_t)n * Bp + k, b0, b1);
+        As[0][kk][rr] = a0;
+        As[1][kk][rr] = a1;
+        Bs[0][kk][rr] = b0;
+        Bs[1][kk][rr] = b1;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < WS_K; ++kk) {
+        float a0[4], b0[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          a0[r] = As[0][kk][ty * 4 + r];
+          b0[r] = Bs[0][kk][tx * 4 + r];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int s = 0; s < 4; ++s) acc[r][s] = fmaf(a0[r], b0[s], acc[r][s]);
+        if (PREC != P_FP32) {
+          float b1[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) b1[r] = Bs[1][kk][tx * 4 + r];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) acc[r][s] = fmaf(a0[r], b1[s], acc[r][s]);
+        }
+        if (PREC == P_BF16) {
+          float a1[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) a1[r] = As[1][kk][ty * 4 + r];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) acc[r][s] = fmaf(a1[r], b0[s], acc[r][s]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int n = n0 + tx * 4 + s;
+      if (n < B) {
+        const float yn = y0[n];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float v = acc[r][s] - yn;
+          dsum[r] = fmaf(v, v, dsum[r]);
+        }
+      }
+    }
+  }
+  // row norm: reduce over the 16 lanes sharing ty (lanes tx = 0..15 are contiguous)
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) dsum[r] += __shfl_xor_sync(0xffffffffu, dsum[r], o);
+  if (tx == 0) {
+    const float is2 = inv_s2_all[f];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int p = p0 + ty * 4 + r;
+      if (p < W) {
+        const float d = dsum[r] * is2;
+        out.scores[slot * W + p] = d;
+        if (out.write_mask) out.mask[slot * W + p] = d > out.tau ? 1 : 0;
+      }
+    }
+  }
+}
+
+cudaError_t launch_whiten_score_simt(const void* x, int L, int W, int B, int in_type,
+                                     const int32_t* c_int, const float* c_flt, int prec,
+                                     const void* wmat, const float* y0, const float* inv_s2,
+                                     const int32_t* status, int factor_stride, ScoreOut out,
+                                     cudaStream_t st, LaunchCounter* lc) {
+  if (L <= 0) return cudaSuccess;
+  dim3 grid((W + WS_P - 1) / WS_P, L), block(256);
+#define HSAD_WS(IN, P)                                                                          \
+  whiten_score_kernel<IN, P><<<grid, block, 0, st>>>((const IN*)x, W, B, c_int, c_flt, wmat, y0, \
+                                                     inv_s2, status, factor_stride, out)
+  if (in_type == IN_U16) {
+    if (prec == P_FP32) HSAD_WS(uint16_t, P_FP32);
+    else if (prec == P_FP16) HSAD_WS(uint16_t, P_FP16);
+    else HSAD_WS(uint16_t, P_BF16);
+  } else {
+    if (prec == P_FP32) HSAD_WS(float, P_FP32);
+    else if (prec == P_FP16) HSAD_WS(float, P_FP16);
+    else HSAD_WS(float, P_BF16);
+  }
+#undef HSAD_WS
+  if (lc) lc->n += 1;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// K7: cube maximum (delta >= 0, so the float bit pattern orders like an unsigned int),
+// then delta / max and the mask (REL: delta / max > tau; ABS: delta > tau).
+__global__ void cube_max_kernel(ScoreOut out, int64_t n_lines, int W, unsigned int* dmax_bits) {
+  const int64_t n = n_lines * W;
+  float mx = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t line = i / W, p = i % W;
+    const float v = out.scores[((out.slot0 + line) % out.ring) * W + p];
+    if (v > mx) mx = v;  // NaN compares false
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dmax_bits, __float_as_uint(mx));
+}
+
+__global__ void cube_norm_kernel(ScoreOut out, int64_t n_lines, int W, int rel, int normalize,
+                                 const unsigned int* dmax_bits) {
+  const float dmax = __uint_as_float(*dmax_bits);
+  const int64_t n = n_lines * W;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t line = i / W, p = i % W;
+    const int64_t at = ((out.slot0 + line) % out.ring) * W + p;
+    const float v = out.scores[at];
+    const float r = v / dmax;
+    out.mask[at] = (rel ? (r > out.tau) : (v > out.tau)) ? 1 : 0;
+    if (normalize) out.scores[at] = r;
+  }
+}
+
+cudaError_t launch_cube_normalize(ScoreOut out, int64_t n_lines, int W, int rel, int normalize,
+                                  unsigned int* dmax_bits, cudaStream_t st, LaunchCounter* lc) {
+  if (n_lines <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(dmax_bits, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (n_lines * W + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  cube_max_kernel<<<(unsigned)blocks, 256, 0, st>>>(out, n_lines, W, dmax_bits);
+  cube_norm_kernel<<<(unsigned)blocks, 256, 0, st>>>(out, n_lines, W, rel, normalize, dmax_bits);
+  if (lc) lc->n += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace hsad

@@ -1,0 +1,359 @@
+// Statistics kernels of the RX detector: centring shift, column sums, covariance
+// rank-k update and the running (prefix) mean / covariance per line.
+//
+// Sec. 3.3 ("Detection Algorithm"): each band is a variable and each pixel a
+// sample; mu is the per-band mean and Sigma the covariance of the statistics set.
+// The data are shifted by an integer per-band value c (the rounded mean of the
+// first line after a reset), so for uint16 input every sum below is an exact
+// integer: s1 = sum (x - c), s2 = sum (x - c)(x - c)^T. The covariance then
+// follows as Sigma = (S2 - S1 S1^T / N) / (N - 1) (N-1 sample covariance), scaled
+// by the calibration gain D on both sides: Sigma_cal = D Sigma D, because the
+// calibrated spectrum is D (DN - offset) (Sec. 3.2, gain and radiometric
+// correction); the offset cancels in the centring.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hsad_internal.h"
+
+namespace hsad {
+
+#define HSAD_LAUNCH_CHECK(lc) \
+  do {                        \
+    if (lc) (lc)->n += 1;     \
+    return cudaGetLastError(); \
+  } while (0)
+
+// ---------------------------------------------------------------------------------
+// K1a shift_init: c_b = rint(mean over the W pixels of one line).
+template <typename In>
+__global__ void shift_init_kernel(const In* __restrict__ line, int W, int B, int32_t* c_int,
+                                  float* c_flt) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int p = 0; p < W; ++p) s += (double)line[(int64_t)p * B + b];
+  double mean = s / (double)W;
+  if (c_int) c_int[b] = (int32_t)rint(mean);
+  if (c_flt) c_flt[b] = isfinite(mean) ? (float)mean : 0.0f;
+}
+
+cudaError_t launch_shift_init(const void* line, int W, int B, int in_type, int32_t* c_int,
+                              float* c_flt, cudaStream_t st, LaunchCounter* lc) {
+  dim3 grid((B + 127) / 128), block(128);
+  if (in_type == IN_U16)
+    shift_init_kernel<uint16_t><<<grid, block, 0, st>>>((const uint16_t*)line, W, B, c_int, nullptr);
+  else
+    shift_init_kernel<float><<<grid, block, 0, st>>>((const float*)line, W, B, nullptr, c_flt);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// ---------------------------------------------------------------------------------
+// K1b colsum: one CTA per line, threads over bands (coalesced along the band axis).
+__global__ void colsum_u16_kernel(const uint16_t* __restrict__ x, int W, int B,
+                                  const int32_t* __restrict__ c, double* __restrict__ s1) {
+  const int64_t t = blockIdx.x;
+  const uint16_t* line = x + t * (int64_t)W * B;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    int64_t acc = 0;
+    const int cb = c[b];
+    for (int p = 0; p < W; ++p) acc += (int64_t)((int)line[(int64_t)p * B + b] - cb);
+    s1[t * B + b] = (double)acc;
+  }
+}
+
+__global__ void colsum_f32_kernel(const float* __restrict__ x, int W, int B,
+                                  const float* __restrict__ c, double* __restrict__ s1) {
+  const int64_t t = blockIdx.x;
+  const float* line = x + t * (int64_t)W * B;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    double acc = 0.0;
+    const float cb = c[b];
+    for (int p = 0; p < W; ++p) acc += (double)(line[(int64_t)p * B + b] - cb);
+    s1[t * B + b] = acc;
+  }
+}
+
+cudaError_t launch_colsum(const void* x, int64_t n_lines, int W, int B, int in_type,
+                          const int32_t* c_int, const float* c_flt, double* s1, cudaStream_t st,
+                          LaunchCounter* lc) {
+  if (n_lines <= 0) return cudaSuccess;
+  dim3 grid((unsigned)n_lines), block(B >= 256 ? 256 : (B + 31) / 32 * 32);
+  if (in_type == IN_U16)
+    colsum_u16_kernel<<<grid, block, 0, st>>>((const uint16_t*)x, W, B, c_int, s1);
+  else
+    colsum_f32_kernel<<<grid, block, 0, st>>>((const float*)x, W, B, c_flt, s1);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// ---------------------------------------------------------------------------------
+// K2 (SIMT) syrk: 64 x 64 output tiles of the upper block triangle, 256 threads with
+// 4 x 4 micro-tiles, pixels staged through shared memory 16 at a time.
+// u16: (x - c) is an integer with |x - c| <= 4095, so each product is below 2^24 and
+// 64 of them fit in int32; partial sums flush into int64 every 64 pixels (exact).
+// f32: products of two floats are exact in FP64 and accumulate in FP64.
+namespace {
+constexpr int SY_T = 64, SY_K = 16;
+
+template <typename In>
+struct SyrkTraits;
+template <>
+struct SyrkTraits<uint16_t> {
+  using Stage = int32_t;
+  using Acc = int32_t;
+  using Wide = long long;
+  __device__ static Stage load(uint16_t v, const int32_t* ci, const float*, int b) {
+    return (int32_t)v - ci[b];
+  }
+};
+template <>
+struct SyrkTraits<float> {
+  using Stage = float;
+  using Acc = double;
+  using Wide = double;
+  __device__ static Stage load(float v, const int32_t*, const float* cf, int b) { return v - cf[b]; }
+};
+}  // namespace
+
+template <typename In>
+__global__ void __launch_bounds__(256) syrk_simt_kernel(const In* __restrict__ x,
+                                                        int64_t pix_per_group, int B,
+                                                        const int32_t* __restrict__ c_int,
+                                                        const float* __restrict__ c_flt,
+                                                        double* __restrict__ out,
+                                                        int64_t out_stride, int64_t pix_per_slice,
+                                                        int accumulate) {
+  using Tr = SyrkTraits<In>;
+  using Stage = typename Tr::Stage;
+  using Acc = typename Tr::Acc;
+  using Wide = typename Tr::Wide;
+  __shared__ Stage As[SY_K][SY_T];
+  __shared__ Stage Bs[SY_K][SY_T];
+
+  // decode the upper-triangle tile (ti <= tj)
+  const int nt = (B + SY_T - 1) / SY_T;
+  int tile = blockIdx.x, ti = 0;
+  while (tile >= nt - ti) {
+    tile -= nt - ti;
+    ++ti;
+  }
+  const int tj = ti + tile;
+  const int i0 = ti * SY_T, j0 = tj * SY_T;
+  const int64_t g = blockIdx.y;
+  const int64_t p_begin = (int64_t)blockIdx.z * pix_per_slice;
+  int64_t p_end = p_begin + pix_per_slice;
+  if (p_end > pix_per_group) p_end = pix_per_group;
+  const In* xg = x + g * pix_per_group * (int64_t)B;
+
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  Acc acc[4][4];
+  Wide wide[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc[a][b] = 0;
+      wide[a][b] = 0;
+    }
+
+  int since_flush = 0;
+  for (int64_t p0 = p_begin; p0 < p_end; p0 += SY_K) {
+    // stage 16 pixels x 64 bands of each operand; element e -> (pixel e/64, band e%64)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * 256;
+      const int pp = e >> 6, bb = e & 63;
+      const int64_t p = p0 + pp;
+      Stage va = 0, vb = 0;
+      if (p < p_end) {
+        const In* row = xg + p * B;
+        if (i0 + bb < B) va = Tr::load(row[i0 + bb], c_int, c_flt, i0 + bb);
+        if (j0 + bb < B) vb = Tr::load(row[j0 + bb], c_int, c_flt, j0 + bb);
+      }
+      As[pp][bb] = va;
+      Bs[pp][bb] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SY_K; ++k) {
+      Stage a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        a[r] = As[k][ty * 4 + r];
+        b[r] = Bs[k][tx * 4 + r];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc[r][s] += (Acc)a[r] * (Acc)b[s];
+    }
+    __syncthreads();
+    since_flush += SY_K;
+    if (since_flush >= 64) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          wide[r][s] += (Wide)acc[r][s];
+          acc[r][s] = 0;
+        }
+      since_flush = 0;
+    }
+  }
+  double* o = out + g * out_stride;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = i0 + ty * 4 + r, j = j0 + tx * 4 + s;
+      if (i >= B || j >= B) continue;
+      const double v = (double)(wide[r][s] + (Wide)acc[r][s]);
+      if (accumulate) {
+        atomicAdd(&o[(int64_t)i * B + j], v);
+        if (ti != tj) atomicAdd(&o[(int64_t)j * B + i], v);
+      } else {
+        o[(int64_t)i * B + j] = v;
+        if (ti != tj) o[(int64_t)j * B + i] = v;
+      }
+    }
+}
+
+cudaError_t launch_syrk_simt(const void* x, int64_t n_groups, int64_t pix_per_group, int B,
+                             int in_type, const int32_t* c_int, const float* c_flt, double* out,
+                             int64_t out_stride, int accumulate, cudaStream_t st,
+                             LaunchCounter* lc) {
+  if (n_groups <= 0 || pix_per_group <= 0) return cudaSuccess;
+  const int nt = (B + SY_T - 1) / SY_T;
+  const int tiles = nt * (nt + 1) / 2;
+  // split large groups over pixel slices (only when accumulating)
+  int64_t slices = 1, per = pix_per_group;
+  if (accumulate) {
+    const int64_t target = 1024;  // pixels per slice
+    slices = (pix_per_group + target - 1) / target;
+    if (slices > 65535) slices = 65535;
+    per = (pix_per_group + slices - 1) / slices;
+    per = (per + SY_K - 1) / SY_K * SY_K;
+    slices = (pix_per_group + per - 1) / per;
+  }
+  dim3 grid(tiles, (unsigned)n_groups, (unsigned)slices), block(256);
+  if (in_type == IN_U16)
+    syrk_simt_kernel<uint16_t><<<grid, block, 0, st>>>((const uint16_t*)x, pix_per_group, B, c_int,
+                                                       nullptr, out, out_stride, per, accumulate);
+  else
+    syrk_simt_kernel<float><<<grid, block, 0, st>>>((const float*)x, pix_per_group, B, nullptr,
+                                                    c_flt, out, out_stride, per, accumulate);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// ---------------------------------------------------------------------------------
+// K3a prefix_mean: thread per band walks the lines of the batch in order.
+// EXCLUSIVE (inclusive = 0): line t uses the lines before it; INCLUSIVE: through it.
+__global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* __restrict__ m_out,
+                                   double* __restrict__ state_s1, int64_t n0, int W, int L, int B,
+                                   int inclusive, int64_t min_pixels, int32_t* __restrict__ status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) {
+    double run = state_s1[b];
+    for (int t = 0; t < L; ++t) {
+      const double s = s1_line[(int64_t)t * B + b];
+      if (inclusive) run += s;
+      const int64_t n = n0 + (int64_t)(t + inclusive) * W;
+      m_out[(int64_t)t * B + b] = n > 0 ? run / (double)n : 0.0;
+      if (!inclusive) run += s;
+    }
+    state_s1[b] = run;
+  }
+  if (b == 0) {
+    for (int t = 0; t < L; ++t) {
+      const int64_t n = n0 + (int64_t)(t + inclusive) * W;
+      if (n < min_pixels && status[t] == LS_OK) status[t] = LS_NOT_READY;
+    }
+  }
+}
+
+cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
+                               int W, int L, int B, int inclusive, int64_t min_pixels,
+                               int32_t* status, cudaStream_t st, LaunchCounter* lc) {
+  prefix_mean_kernel<<<(B + 127) / 128, 128, 0, st>>>(s1_line, m_out, state_s1, n0, W, L, B,
+                                                      inclusive, min_pixels, status);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// K3b prefix_cov: thread per matrix entry walks the lines; in place over the per-line s2.
+__global__ void prefix_cov_kernel(double* __restrict__ buf, const double* __restrict__ m,
+                                  double* __restrict__ state_s2, const double* __restrict__ dgain,
+                                  int64_t n0, int W, int L, int B, int inclusive,
+                                  int64_t min_pixels) {
+  const int64_t BB = (int64_t)B * B;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= BB) return;
+  const int i = (int)(e / B), j = (int)(e % B);
+  const double dd = dgain[i] * dgain[j];
+  double run = state_s2[e];
+  for (int t = 0; t < L; ++t) {
+    double* slot = buf + (int64_t)t * BB + e;
+    const double v = *slot;
+    if (inclusive) run += v;
+    const int64_t n = n0 + (int64_t)(t + inclusive) * W;
+    if (n >= min_pixels && n > 1) {
+      const double mi = m[(int64_t)t * B + i], mj = m[(int64_t)t * B + j];
+      *slot = dd * (run - (double)n * mi * mj) / (double)(n - 1);
+    } else {
+      *slot = 0.0;
+    }
+    if (!inclusive) run += v;
+  }
+  state_s2[e] = run;
+}
+
+cudaError_t launch_prefix_cov(double* buf, const double* m, double* state_s2, const double* dgain,
+                              int64_t n0, int W, int L, int B, int inclusive, int64_t min_pixels,
+                              cudaStream_t st, LaunchCounter* lc) {
+  const int64_t BB = (int64_t)B * B;
+  prefix_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(buf, m, state_s2, dgain, n0, W,
+                                                                  L, B, inclusive, min_pixels);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// K3c finalize_cov (cube mode): statistics of the whole cube from the state.
+__global__ void finalize_cov_kernel(const double* __restrict__ s1, const double* __restrict__ s2,
+                                    const double* __restrict__ dgain, int64_t n, int B,
+                                    double* __restrict__ sigma, double* __restrict__ m,
+                                    int64_t min_pixels, int32_t* __restrict__ status) {
+  const int64_t BB = (int64_t)B * B;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= BB) return;
+  const int i = (int)(e / B), j = (int)(e % B);
+  const double mi = s1[i] / (double)n, mj = s1[j] / (double)n;
+  sigma[e] = dgain[i] * dgain[j] * (s2[e] - (double)n * mi * mj) / (double)(n - 1);
+  if (j == 0) m[i] = mi;
+  if (e == 0) status[0] = (n >= min_pixels && n > 1) ? LS_OK : LS_NOT_READY;
+}
+
+cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, const double* dgain,
+                                int64_t n, int B, double* sigma, double* m, int64_t min_pixels,
+                                int32_t* status, cudaStream_t st, LaunchCounter* lc) {
+  const int64_t BB = (int64_t)B * B;
+  finalize_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(state_s1, state_s2, dgain, n,
+                                                                    B, sigma, m, min_pixels, status);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// ---------------------------------------------------------------------------------
+__global__ void check_finite_kernel(const float* __restrict__ x, int64_t n, int32_t* bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int found = 0;
+  for (; i < n; i += stride) found |= !isfinite(x[i]);
+  if (__syncthreads_or(found) && threadIdx.x == 0) atomicExch(bad, 1);
+}
+
+cudaError_t launch_check_finite(const float* x, int64_t n, int32_t* bad, cudaStream_t st,
+                                LaunchCounter* lc) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  check_finite_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, bad);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+}  // namespace hsad

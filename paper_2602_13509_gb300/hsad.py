@@ -1,0 +1,336 @@
+"""Thin ctypes binding of the hsad C ABI (include/hsad.h).
+
+Every function here has the same name as its C entry point and only marshals
+arguments: numpy arrays and torch tensors become raw pointers, status codes
+come back unchanged. All computation happens in the CUDA library
+``libhsad.so``; if that library is missing, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhsad.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hsad.h")
+
+# status codes
+HSAD_OK, HSAD_E_INVALID, HSAD_E_NOMEM, HSAD_E_NOT_READY = 0, -1, -2, -3
+HSAD_E_NOT_PD, HSAD_E_TIMEOUT, HSAD_E_CUDA, HSAD_E_BUSY, HSAD_E_INVALID_DATA = -4, -5, -6, -7, -8
+# enums
+HSAD_U16, HSAD_F32 = 0, 1
+HSAD_FP32, HSAD_BF16, HSAD_FP16 = 0, 1, 2
+HSAD_EXCLUSIVE, HSAD_INCLUSIVE, HSAD_CUBE = 0, 1, 2
+HSAD_ABS, HSAD_REL = 0, 1
+HSAD_HOST, HSAD_DEVICE = 0, 1
+HSAD_CREATE_WAIT, HSAD_NORMALIZE_SCORES = 1, 2
+# per-line status
+LS_OK, LS_NOT_READY, LS_NOT_PD, LS_INVALID_DATA = 0, 1, 2, 3
+
+
+class hsad_config(C.Structure):
+    _fields_ = [
+        ("width", C.c_int32), ("bands", C.c_int32), ("in_dtype", C.c_int32),
+        ("precision", C.c_int32), ("stats_mode", C.c_int32), ("cube_lines", C.c_int32),
+        ("gain", C.POINTER(C.c_float)), ("offset", C.POINTER(C.c_float)),
+        ("threshold_mode", C.c_int32), ("threshold", C.c_float),
+        ("warmup_pixels", C.c_int64), ("device_budget_bytes", C.c_int64),
+        ("flags", C.c_int32), ("device", C.c_int32),
+        ("max_batch_lines", C.c_int32), ("result_lines", C.c_int32),
+    ]
+
+
+class HsadError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{hsad_status_string(code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"hsad CUDA library not built ({LIB_PATH} missing); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first. There is no fallback.")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "hsad_config_init": (C.c_int, [C.POINTER(hsad_config)]),
+        "hsad_create": (C.c_int, [C.POINTER(hsad_config), C.POINTER(P)]),
+        "hsad_push_lines": (C.c_int, [P, P, C.c_int64, C.c_int32, C.POINTER(C.c_uint64)]),
+        "hsad_flush": (C.c_int, [P]),
+        "hsad_scores": (C.c_int, [P, C.c_uint64, C.c_int64, P, P, C.c_int32, C.c_int32]),
+        "hsad_line_status": (C.c_int, [P, C.c_uint64, C.c_int64, P, C.c_int32]),
+        "hsad_synchronize": (C.c_int, [P, C.c_int32]),
+        "hsad_reset": (C.c_int, [P]),
+        "hsad_stream": (P, [P]),
+        "hsad_kernel_launches": (C.c_int64, [P]),
+        "hsad_device_bytes": (C.c_int64, [P]),
+        "hsad_set_device_budget": (C.c_int, [C.c_int, C.c_int64]),
+        "hsad_device_budget_used": (C.c_int64, [C.c_int]),
+        "hsad_profile_enable": (C.c_int, [P, C.c_int32]),
+        "hsad_profile_read": (C.c_int, [P, C.c_int32, C.c_char_p, C.c_int32, C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_double)]),
+        "hsad_profile_reset": (C.c_int, [P]),
+        "hsad_destroy": (C.c_int, [P]),
+        "hsad_last_error": (C.c_char_p, [P]),
+        "hsad_status_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/hsad.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hsad_[a-z_0-9]+)\s*\(", txt)))
+
+
+def library():
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    """Raw address of a numpy array or torch tensor (None stays None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+# ---------------------------------------------------------------- C entry points
+def hsad_status_string(code: int) -> str:
+    return _lib.hsad_status_string(int(code)).decode()
+
+
+def hsad_last_error(ctx=None) -> str:
+    return (_lib.hsad_last_error(ctx) or b"").decode()
+
+
+def hsad_config_init(cfg: hsad_config | None = None) -> hsad_config:
+    cfg = cfg or hsad_config()
+    _lib.hsad_config_init(C.byref(cfg))
+    return cfg
+
+
+def hsad_create(cfg: hsad_config):
+    """Returns ``(status, ctx)``; ctx is an opaque handle (int) or None."""
+    out = C.c_void_p()
+    rc = _lib.hsad_create(C.byref(cfg), C.byref(out))
+    return rc, (out.value if rc == HSAD_OK else None)
+
+
+def hsad_push_lines(ctx, lines, n_lines: int, mem: int):
+    """Returns ``(status, first_line_id)``."""
+    first = C.c_uint64(0)
+    rc = _lib.hsad_push_lines(ctx, _ptr(lines), int(n_lines), int(mem), C.byref(first))
+    return rc, first.value
+
+
+def hsad_flush(ctx) -> int:
+    return _lib.hsad_flush(ctx)
+
+
+def hsad_scores(ctx, first_line_id: int, n_lines: int, scores, mask, mem: int, timeout_ms: int) -> int:
+    return _lib.hsad_scores(ctx, int(first_line_id), int(n_lines), _ptr(scores), _ptr(mask), int(mem),
+                            int(timeout_ms))
+
+
+def hsad_line_status(ctx, first_line_id: int, n_lines: int, status, timeout_ms: int) -> int:
+    return _lib.hsad_line_status(ctx, int(first_line_id), int(n_lines), _ptr(status), int(timeout_ms))
+
+
+def hsad_synchronize(ctx, timeout_ms: int = -1) -> int:
+    return _lib.hsad_synchronize(ctx, int(timeout_ms))
+
+
+def hsad_reset(ctx) -> int:
+    return _lib.hsad_reset(ctx)
+
+
+def hsad_stream(ctx) -> int:
+    return _lib.hsad_stream(ctx) or 0
+
+
+def hsad_kernel_launches(ctx) -> int:
+    return int(_lib.hsad_kernel_launches(ctx))
+
+
+def hsad_device_bytes(ctx) -> int:
+    return int(_lib.hsad_device_bytes(ctx))
+
+
+def hsad_set_device_budget(device: int, nbytes: int) -> int:
+    return _lib.hsad_set_device_budget(int(device), int(nbytes))
+
+
+def hsad_device_budget_used(device: int) -> int:
+    return int(_lib.hsad_device_budget_used(int(device)))
+
+
+def hsad_profile_enable(ctx, enable: bool) -> int:
+    return _lib.hsad_profile_enable(ctx, 1 if enable else 0)
+
+
+def hsad_profile_read(ctx, index: int):
+    """Returns ``(status, name, launches, total_ms)``."""
+    buf = C.create_string_buffer(64)
+    n, ms = C.c_int64(0), C.c_double(0.0)
+    rc = _lib.hsad_profile_read(ctx, int(index), buf, 64, C.byref(n), C.byref(ms))
+    return rc, buf.value.decode(), n.value, ms.value
+
+
+def hsad_profile_reset(ctx) -> int:
+    return _lib.hsad_profile_reset(ctx)
+
+
+def hsad_destroy(ctx) -> int:
+    return _lib.hsad_destroy(ctx)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+_NAMES = {
+    "u16": HSAD_U16, "f32": HSAD_F32,
+    "fp32": HSAD_FP32, "bf16": HSAD_BF16, "fp16": HSAD_FP16,
+    "exclusive": HSAD_EXCLUSIVE, "inclusive": HSAD_INCLUSIVE, "cube": HSAD_CUBE,
+    "abs": HSAD_ABS, "rel": HSAD_REL,
+}
+
+
+def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="exclusive", cube_lines=0,
+                gain=None, offset=None, threshold_mode="abs", threshold=0.0, warmup_pixels=0,
+                device_budget_bytes=0, flags=0, device=0, max_batch_lines=0, result_lines=0):
+    """Build an hsad_config; ``gain``/``offset`` arrays are kept alive on the struct."""
+    import numpy as np
+    cfg = hsad_config_init()
+    cfg.width, cfg.bands = int(width), int(bands)
+    cfg.in_dtype = _NAMES.get(in_dtype, in_dtype)
+    cfg.precision = _NAMES.get(precision, precision)
+    cfg.stats_mode = _NAMES.get(stats_mode, stats_mode)
+    cfg.cube_lines = int(cube_lines)
+    cfg.threshold_mode = _NAMES.get(threshold_mode, threshold_mode)
+    cfg.threshold = float(threshold)
+    cfg.warmup_pixels, cfg.device_budget_bytes = int(warmup_pixels), int(device_budget_bytes)
+    cfg.flags, cfg.device = int(flags), int(device)
+    cfg.max_batch_lines, cfg.result_lines = int(max_batch_lines), int(result_lines)
+    keep = []
+    for name, arr in (("gain", gain), ("offset", offset)):
+        if arr is not None:
+            a = np.ascontiguousarray(np.asarray(arr, dtype=np.float32))
+            keep.append(a)
+            setattr(cfg, name, a.ctypes.data_as(C.POINTER(C.c_float)))
+    cfg._keep = keep
+    return cfg
+
+
+class Detector:
+    """Owns one hsad context; raises HsadError on hard failures."""
+
+    def __init__(self, **kw):
+        self.cfg = make_config(**kw)
+        rc, self.ctx = hsad_create(self.cfg)
+        if rc != HSAD_OK:
+            raise HsadError(rc, hsad_last_error(None))
+        self.width, self.bands = self.cfg.width, self.cfg.bands
+
+    def push(self, lines, mem=None) -> int:
+        """Push lines ([n, W, B] numpy array or contiguous tensor); returns the first line id."""
+        if mem is None:
+            mem = HSAD_DEVICE if (hasattr(lines, "is_cuda") and lines.is_cuda) else HSAD_HOST
+        rc, first = hsad_push_lines(self.ctx, lines, lines.shape[0], mem)
+        if rc != HSAD_OK:
+            raise HsadError(rc, hsad_last_error(self.ctx))
+        return first
+
+    def flush(self):
+        rc = hsad_flush(self.ctx)
+        if rc != HSAD_OK:
+            raise HsadError(rc, hsad_last_error(self.ctx))
+
+    def scores(self, first, n, timeout_ms=-1):
+        """Host copies: ``(status, scores float32 [n, W], mask uint8 [n, W], line_status int32 [n])``."""
+        import numpy as np
+        s = np.empty((n, self.width), dtype=np.float32)
+        m = np.empty((n, self.width), dtype=np.uint8)
+        rc = hsad_scores(self.ctx, first, n, s, m, HSAD_HOST, timeout_ms)
+        if rc in (HSAD_E_INVALID, HSAD_E_CUDA, HSAD_E_TIMEOUT):
+            raise HsadError(rc, hsad_last_error(self.ctx))
+        st = np.empty(n, dtype=np.int32)
+        rc2 = hsad_line_status(self.ctx, first, n, st, 0)
+        if rc2 not in (HSAD_OK,):
+            raise HsadError(rc2, hsad_last_error(self.ctx))
+        return rc, s, m, st
+
+    def scores_device(self, first, n, scores, mask, timeout_ms=-1) -> int:
+        return hsad_scores(self.ctx, first, n, scores, mask, HSAD_DEVICE, timeout_ms)
+
+    def reset(self):
+        rc = hsad_reset(self.ctx)
+        if rc != HSAD_OK:
+            raise HsadError(rc, hsad_last_error(self.ctx))
+
+    def synchronize(self, timeout_ms=-1):
+        rc = hsad_synchronize(self.ctx, timeout_ms)
+        if rc != HSAD_OK:
+            raise HsadError(rc, hsad_last_error(self.ctx))
+
+    @property
+    def stream(self) -> int:
+        return hsad_stream(self.ctx)
+
+    def profile(self, enable=True):
+        hsad_profile_enable(self.ctx, enable)
+
+    def profile_totals(self) -> dict:
+        """{kernel class: (launches, total_ms)} since the last reset."""
+        out, i = {}, 0
+        while True:
+            rc, name, n, ms = hsad_profile_read(self.ctx, i)
+            if rc != HSAD_OK:
+                break
+            out[name] = (n, ms)
+            i += 1
+        return out
+
+    def profile_reset(self):
+        hsad_profile_reset(self.ctx)
+
+    @property
+    def kernel_launches(self) -> int:
+        return hsad_kernel_launches(self.ctx)
+
+    @property
+    def device_bytes(self) -> int:
+        return hsad_device_bytes(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            hsad_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

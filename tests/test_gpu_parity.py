@@ -1,0 +1,188 @@
+"""CUDA path vs the FP64 oracle on seeded inputs (needs a GB300).
+
+Every call goes through the C ABI (via the ctypes binding). Sizes span several
+64-wide tiles with ragged tails; the edge cases cover B = 1..3, W = 1, warm-up,
+statistics resets, partial cubes and a non positive definite covariance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import rx as orx
+from tests._parity import MARGIN, TOL, mask_mismatch, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_13509_gb300 as hs
+    return hs
+
+
+def _scene_lines(T, W, B, seed):
+    from gen import PushbroomScene
+    sc = PushbroomScene(W, B, seed=seed)
+    return sc, sc.lines(0, T)
+
+
+def _run(hs, lines, **kw):
+    det = hs.Detector(width=lines.shape[1], bands=lines.shape[2], **kw)
+    first = det.push(lines)
+    if kw.get("stats_mode") == "cube":
+        det.flush()
+    rc, s, m, st = det.scores(first, lines.shape[0])
+    launches = det.kernel_launches
+    det.close()
+    return rc, s, m, st, launches
+
+
+# ------------------------------------------------------------------ global RX (cube mode)
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_config1_cube_global_rx(hs, prec):
+    """64 x 128 x 64 float32 mixture cube, global RX, REL threshold 0.110 (Sec. 3.3)."""
+    from gen import config1_cube
+    cube, anom, _ = config1_cube()
+    dref, dnorm = oracle.global_rx(cube)
+    rc, s, m, st, nl = _run(hs, cube, in_dtype="f32", precision=prec, stats_mode="cube", cube_lines=64,
+                            threshold_mode="rel", threshold=0.110)
+    assert rc == hs.HSAD_OK and (st == 0).all() and nl > 0
+    emax, _ = rel_err(s, dref)
+    if prec == "fp32":
+        assert emax <= TOL["fp32"], emax
+        assert mask_mismatch(m, dnorm, 0.110, 2 * MARGIN["fp32"]) == 0
+    else:
+        # float input is not integer, so the BF16/FP16 operand split is approximate:
+        # only the ranking property is required here
+        assert np.median(s[anom]) > np.percentile(s[~anom], 99)
+
+
+def test_config1_normalized_scores(hs):
+    from gen import config1_cube
+    cube, _, _ = config1_cube()
+    _, dnorm = oracle.global_rx(cube)
+    rc, s, m, st, _ = _run(hs, cube, in_dtype="f32", stats_mode="cube", cube_lines=64, threshold_mode="rel",
+                           threshold=0.110, flags=hs.HSAD_NORMALIZE_SCORES)
+    assert rc == hs.HSAD_OK
+    assert abs(np.nanmax(s) - 1.0) < 1e-6
+    assert np.max(np.abs(s - dnorm)) < 2e-4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_cube_mode_u16_with_partial_cube(hs, prec):
+    sc, lines = _scene_lines(52, 70, 33, seed=7)   # two cubes of 20 lines + a partial of 12
+    rc, s, m, st, _ = _run(hs, lines, stats_mode="cube", cube_lines=20, precision=prec,
+                           gain=sc.gain, offset=sc.offset)
+    assert rc == hs.HSAD_OK
+    ref, _ = orx.stream_rx(lines, oracle.CUBE, cube_lines=20, gain=sc.gain, offset=sc.offset)
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL[prec], emax
+    tau = 33 + 6 * np.sqrt(66)
+    assert mask_mismatch(m, ref, tau, MARGIN[prec]) == 0
+
+
+# ------------------------------------------------------------------ streamed forms
+@pytest.mark.parametrize("mode", ["exclusive", "inclusive"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_stream_modes_small(hs, mode, prec):
+    sc, lines = _scene_lines(40, 96, 24, seed=3)
+    rc, s, m, st, _ = _run(hs, lines, stats_mode=mode, precision=prec, gain=sc.gain, offset=sc.offset,
+                           max_batch_lines=16)
+    ref, rst = orx.stream_rx(lines, getattr(oracle, mode.upper()), gain=sc.gain, offset=sc.offset)
+    assert rc in (hs.HSAD_OK, hs.HSAD_E_NOT_READY)
+    np.testing.assert_array_equal(st, rst)
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL[prec], emax
+    tau = 24 + 6 * np.sqrt(48)
+    assert mask_mismatch(m, ref, tau, MARGIN[prec]) == 0
+
+
+@pytest.mark.parametrize("W,B", [(1, 1), (7, 1), (3, 2), (9, 3), (65, 64), (33, 127), (64, 128),
+                                 (17, 129), (130, 200)])
+def test_stream_ragged_shapes(hs, W, B):
+    sc, lines = _scene_lines(max(6, (B + 1) // W + 4), W, B, seed=W * 1000 + B)
+    rc, s, m, st, _ = _run(hs, lines, stats_mode="exclusive", gain=sc.gain, offset=sc.offset)
+    ref, rst = orx.stream_rx(lines, oracle.EXCLUSIVE, gain=sc.gain, offset=sc.offset)
+    np.testing.assert_array_equal(st, rst)
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL["fp32"], emax
+
+
+def test_stream_resets_and_warmup(hs):
+    sc, lines = _scene_lines(50, 40, 20, seed=11)
+    kw = dict(stats_mode="exclusive", cube_lines=16, warmup_pixels=100, gain=sc.gain, offset=sc.offset,
+              max_batch_lines=7)
+    rc, s, m, st, _ = _run(hs, lines, **kw)
+    ref, rst = orx.stream_rx(lines, oracle.EXCLUSIVE, cube_lines=16, warmup_pixels=100, gain=sc.gain,
+                             offset=sc.offset)
+    np.testing.assert_array_equal(st, rst)
+    assert (rst == orx.NOT_READY).sum() >= 9     # 3 lines after each reset
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL["fp32"], emax
+
+
+def test_host_and_device_push_agree(hs):
+    import torch
+    sc, lines = _scene_lines(30, 64, 32, seed=5)
+    a = _run(hs, lines, stats_mode="exclusive")
+    det = hs.Detector(width=64, bands=32, stats_mode="exclusive")
+    first = det.push(torch.from_numpy(lines.view(np.int16)).cuda())   # same bytes as uint16
+    rc, s, m, st = det.scores(first, 30)
+    det.close()
+    np.testing.assert_array_equal(np.isnan(a[1]), np.isnan(s))
+    np.testing.assert_array_equal(np.nan_to_num(a[1]), np.nan_to_num(s))
+    np.testing.assert_array_equal(a[2], m)
+
+
+def test_pushes_of_one_line_match_one_batch(hs):
+    sc, lines = _scene_lines(24, 48, 16, seed=9)
+    a = _run(hs, lines, stats_mode="exclusive")
+    det = hs.Detector(width=48, bands=16, stats_mode="exclusive")
+    ids = [det.push(lines[t:t + 1]) for t in range(24)]
+    assert ids == list(range(24))
+    rc, s, m, st = det.scores(0, 24)
+    det.close()
+    np.testing.assert_allclose(np.nan_to_num(s), np.nan_to_num(a[1]), rtol=1e-6, atol=1e-6)
+
+
+def test_not_positive_definite_is_reported(hs):
+    sc, lines = _scene_lines(12, 40, 8, seed=2)
+    lines = lines.copy()
+    lines[..., 3] = 1000                          # constant band: singular covariance
+    det = hs.Detector(width=40, bands=8, stats_mode="exclusive")
+    first = det.push(lines)
+    rc, s, m, st = det.scores(first, 12)
+    det.close()
+    assert rc == hs.HSAD_E_NOT_PD
+    assert (st[1:] == hs.LS_NOT_PD).all() and np.isnan(s[1:]).all() and (m == 0).all()
+
+
+def test_float_push_with_nan_is_rejected(hs):
+    x = np.random.default_rng(0).normal(size=(4, 10, 5)).astype(np.float32)
+    x[2, 3, 1] = np.nan
+    det = hs.Detector(width=10, bands=5, in_dtype="f32", stats_mode="exclusive")
+    rc, _ = hs.hsad_push_lines(det.ctx, x, 4, hs.HSAD_HOST)
+    assert rc == hs.HSAD_E_INVALID_DATA
+    import torch
+    rc, _ = hs.hsad_push_lines(det.ctx, torch.from_numpy(x).cuda(), 4, hs.HSAD_DEVICE)
+    assert rc == hs.HSAD_E_INVALID_DATA
+    det.close()
+
+
+def test_scores_poll_and_ring_eviction(hs):
+    sc, lines = _scene_lines(20, 32, 8, seed=4)
+    det = hs.Detector(width=32, bands=8, stats_mode="exclusive", result_lines=8, max_batch_lines=4)
+    rc, _ = hs.hsad_push_lines(det.ctx, lines[:8], 8, hs.HSAD_HOST)
+    assert rc == hs.HSAD_OK
+    rc, _ = hs.hsad_push_lines(det.ctx, lines[8:16], 8, hs.HSAD_HOST)
+    assert rc == hs.HSAD_OK
+    s = np.empty((4, 32), np.float32)
+    assert hs.hsad_scores(det.ctx, 0, 4, s, None, hs.HSAD_HOST, -1) == hs.HSAD_E_INVALID  # evicted
+    assert hs.hsad_scores(det.ctx, 12, 4, s, None, hs.HSAD_HOST, -1) == hs.HSAD_OK
+    assert hs.hsad_scores(det.ctx, 16, 1, s, None, hs.HSAD_HOST, -1) == hs.HSAD_E_INVALID  # not pushed
+    rc, _ = hs.hsad_push_lines(det.ctx, lines[:9], 9, hs.HSAD_HOST)
+    assert rc == hs.HSAD_E_INVALID                                                   # above the ring
+    det.close()
