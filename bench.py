@@ -165,6 +165,7 @@ def main():
     ap.add_argument("--workload", default="stream_640x270", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--batch", type=int, default=0, help="lines per internal batch (0 = workload default)")
+    ap.add_argument("--lines", type=int, default=0, help="override the stream length (profiling captures)")
     ap.add_argument("--latency-lines", type=int, default=200)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32-arm", action="store_true")
@@ -173,6 +174,8 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
         wl["batch"] = args.batch
+    if args.lines:
+        wl["lines"] = args.lines
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
