@@ -175,6 +175,33 @@ int hsad_set_device_budget(int device, int64_t bytes);
 /* Bytes currently charged against the device-wide budget of `device`. */
 int64_t hsad_device_budget_used(int device);
 
+/* Global RX of one cube already in device memory, with no device allocation.
+ * The paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory (flight or embedded code that forbids the allocator after
+ * start-up, or hosts whose external memory manager owns the whole device pool).
+ * Same arithmetic and kernels as a CUBE-mode context scoring one cube:
+ *   cube    device [n_lines][width][bands], in_dtype (HSAD_U16 | HSAD_F32)
+ *   gain    host array of `bands` floats or NULL (all 1), finite and non-zero
+ *   threshold_mode / threshold / flags (HSAD_NORMALIZE_SCORES only) as in hsad_config
+ *           (threshold 0 with HSAD_ABS means B + 6 sqrt(2B))
+ *   scores  device float [n_lines][width], mask device uint8 [n_lines][width]
+ *   stream  cudaStream_t to run on (NULL = legacy default stream), device = ordinal
+ * Every intermediate lives in one static device array of 16 MiB that each GPU loading
+ * the library keeps until exit; the cube must fit it: roughly
+ *   16 n_lines B + 24 B^2 + 4 pad64(B)^2 + 8 n_lines bytes <= 16 MiB
+ * (e.g. B = 270 up to ~3300 lines, B = 70 up to ~14000 lines), else HSAD_E_INVALID
+ * before anything runs. The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current) and loads the module: make it
+ * before any stream capture. Calls share the array and keep its last contents (the
+ * sums and status words are cleared at the start of each call): calls that overlap
+ * on the GPU, from any thread or stream, race and must not be issued. The call
+ * returns after the cube is scored: HSAD_OK, HSAD_E_NOT_PD, HSAD_E_NOT_READY (fewer
+ * than bands + 1 pixels), HSAD_E_INVALID or HSAD_E_CUDA. No error string is kept. */
+int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int32_t bands,
+                           int32_t in_dtype, int32_t precision, const float* gain,
+                           int32_t threshold_mode, float threshold, int32_t flags, float* scores,
+                           uint8_t* mask, void* stream, int32_t device);
+
 /* Release the context. NULL-safe. Waits (up to 10 s) for in-flight work first. */
 int hsad_destroy(hsad_ctx* ctx);
 

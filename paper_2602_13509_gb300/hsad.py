@@ -72,6 +72,9 @@ def _load():
         "hsad_profile_read": (C.c_int, [P, C.c_int32, C.c_char_p, C.c_int32, C.POINTER(C.c_int64),
                                         C.POINTER(C.c_double)]),
         "hsad_profile_reset": (C.c_int, [P]),
+        "hsad_global_rx_noalloc": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                             C.POINTER(C.c_float), C.c_int32, C.c_float, C.c_int32, P, P, P,
+                                             C.c_int32]),
         "hsad_destroy": (C.c_int, [P]),
         "hsad_last_error": (C.c_char_p, [P]),
         "hsad_status_string": (C.c_char_p, [C.c_int]),
@@ -197,6 +200,19 @@ def hsad_profile_read(ctx, index: int):
 
 def hsad_profile_reset(ctx) -> int:
     return _lib.hsad_profile_reset(ctx)
+
+
+def hsad_global_rx_noalloc(cube, n_lines, width, bands, in_dtype, precision, gain, threshold_mode,
+                           threshold, flags, scores, mask, stream=None, device=0) -> int:
+    """Allocation-free global RX of one device cube (see include/hsad.h)."""
+    g = None
+    if gain is not None:
+        import numpy as np
+        keep = np.ascontiguousarray(np.asarray(gain, dtype=np.float32))
+        g = keep.ctypes.data_as(C.POINTER(C.c_float))
+    return _lib.hsad_global_rx_noalloc(_ptr(cube), int(n_lines), int(width), int(bands), int(in_dtype),
+                                       int(precision), g, int(threshold_mode), float(threshold), int(flags),
+                                       _ptr(scores), _ptr(mask), stream, int(device))
 
 
 def hsad_destroy(ctx) -> int:
