@@ -31,8 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "stream_640x270": dict(width=640, bands=270, lines=4000, batch=1024),
-    "precision_1024x448": dict(width=1024, bands=448, lines=8000, batch=1024),
+    # the whole stream is one batch: one launch per kernel, one wave tail per step
+    "stream_640x270": dict(width=640, bands=270, lines=4000, batch=4000),
+    "precision_1024x448": dict(width=1024, bands=448, lines=8000, batch=2000),
 }
 
 

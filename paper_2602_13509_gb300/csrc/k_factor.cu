@@ -73,15 +73,30 @@ __device__ double block_max(double v, double* red) {
 }
 }  // namespace
 
+constexpr int NB = 16;      // Cholesky panel width = inverse block height
+constexpr int PS = NB + 1;  // padded panel row stride (doubles): rows fall in different banks
+
+__host__ __device__ inline int factor_smem_doubles(int B) {
+  const int a = B * PS, b = NB * (B + 1);
+  return a > b ? a : b;
+}
+
+// One CTA per line. Sigma (full B x B, lower triangle used) is factored in place in
+// global memory with a blocked right-looking Cholesky: the NB-column panel is staged in
+// shared memory and factored there, and the trailing lower triangle is updated with
+// 4 x 4 register tiles (NB DFMA per element loaded and stored). The inverse X = L^{-1}
+// is then built NB rows at a time: the contribution of earlier block rows is a
+// register-tiled product, and the within-block forward substitution runs per column,
+// each thread owning whole columns, so it needs no synchronisation.
 template <int PREC>
-__global__ void __launch_bounds__(FT) factor_kernel(double* __restrict__ sigma_all,
-                                                    double* __restrict__ inv_all,
-                                                    const double* __restrict__ m_all,
-                                                    const double* __restrict__ dgain, int B,
-                                                    void* __restrict__ wmat,
-                                                    float* __restrict__ y0_all,
-                                                    float* __restrict__ inv_s2_all,
-                                                    int32_t* __restrict__ status) {
+__global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigma_all,
+                                                       double* __restrict__ inv_all,
+                                                       const double* __restrict__ m_all,
+                                                       const double* __restrict__ dgain, int B,
+                                                       void* __restrict__ wmat,
+                                                       float* __restrict__ y0_all,
+                                                       float* __restrict__ inv_s2_all,
+                                                       int32_t* __restrict__ status) {
   const int t = blockIdx.x;
   if (status[t] != LS_OK) return;
   const int64_t BB = (int64_t)B * B;
@@ -89,63 +104,131 @@ __global__ void __launch_bounds__(FT) factor_kernel(double* __restrict__ sigma_a
   double* Inv = inv_all + t * BB;
   const double* m = m_all + (int64_t)t * B;
   const int Bp = pad64(B);
-  __shared__ double col[512];
+  extern __shared__ double smem[];
   __shared__ double red[FT / 32];
-  __shared__ int s_fail;
-  __shared__ double s_l;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // ---- Cholesky (right-looking, lower triangle in place) -------------------------
-  for (int j = 0; j < B; ++j) {
-    if (tid == 0) {
-      const double piv = A[(int64_t)j * B + j];
-      const int fail = !(piv > 0.0) || !isfinite(piv);
-      s_fail = fail;
-      const double l = fail ? 1.0 : sqrt(piv);
-      s_l = l;
-      A[(int64_t)j * B + j] = l;
+  // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
+  double* P = smem;  // panel: P[r * PS + j] = A[p + r][p + j]
+  for (int p = 0; p < B; p += NB) {
+    const int kb = min(NB, B - p), rows = B - p;
+    for (int e = tid; e < rows * kb; e += FT) {
+      const int r = e / kb, j = e - r * kb;
+      P[r * PS + j] = A[(int64_t)(p + r) * B + p + j];
     }
     __syncthreads();
-    if (s_fail) {
-      if (tid == 0) status[t] = LS_NOT_PD;
-      return;
+    for (int j = 0; j < kb; ++j) {
+      const double piv = P[j * PS + j];
+      if (!(piv > 0.0) || !isfinite(piv)) {  // same value in every thread: uniform exit
+        if (tid == 0) status[t] = LS_NOT_PD;
+        return;
+      }
+      const double l = sqrt(piv);
+      for (int r = j + 1 + tid; r < rows; r += FT) P[r * PS + j] /= l;
+      __syncthreads();
+      if (tid == 0) P[j * PS + j] = l;
+      const int nc = kb - j - 1;
+      if (nc > 0) {
+        for (int e = tid; e < (rows - j - 1) * nc; e += FT) {
+          const int r = j + 1 + e / nc, k = j + 1 + e % nc;
+          if (k <= r) P[r * PS + k] = fma(-P[r * PS + j], P[k * PS + j], P[r * PS + k]);
+        }
+      }
+      __syncthreads();
     }
-    const double ljj = s_l;
-    for (int i = j + 1 + tid; i < B; i += FT) {
-      const double v = A[(int64_t)i * B + j] / ljj;
-      A[(int64_t)i * B + j] = v;
-      col[i] = v;
+    for (int e = tid; e < rows * kb; e += FT) {
+      const int r = e / kb, j = e - r * kb;
+      if (r >= j) A[(int64_t)(p + r) * B + p + j] = P[r * PS + j];
     }
-    __syncthreads();
-    // trailing lower triangle: one warp per row, lanes along the row
-    for (int i = j + 1 + warp; i < B; i += FT / 32) {
-      const double ci = col[i];
-      double* row = A + (int64_t)i * B;
-      for (int k = j + 1 + lane; k <= i; k += 32) row[k] -= ci * col[k];
+    // trailing update: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B
+    const int mrem = rows - kb;
+    if (mrem > 0) {
+      const int mt = (mrem + 3) >> 2;
+      const int ntiles = mt * (mt + 1) / 2;
+      for (int idx = tid; idx < ntiles; idx += FT) {
+        int ti = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+        while (ti * (ti + 1) / 2 > idx) --ti;
+        while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
+        const int tk = idx - ti * (ti + 1) / 2;
+        const int r0 = kb + 4 * ti, c0 = kb + 4 * tk;  // panel-relative
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = r0 + a, c = c0 + b;
+            acc[a][b] = (r < rows && c <= r) ? A[(int64_t)(p + r) * B + p + c] : 0.0;
+          }
+        for (int j = 0; j < kb; ++j) {
+          double x[4], y[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            x[a] = (r0 + a < rows) ? P[(r0 + a) * PS + j] : 0.0;
+            y[a] = (c0 + a < rows) ? P[(c0 + a) * PS + j] : 0.0;
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(-x[a], y[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = r0 + a, c = c0 + b;
+            if (r < rows && c <= r) A[(int64_t)(p + r) * B + p + c] = acc[a][b];
+          }
+      }
     }
     __syncthreads();
   }
 
-  // ---- triangular inverse Inv = L^{-1} (lower) -------------------------------------
-  // Thread owns columns c = tid and tid + FT; column c needs only its own earlier
-  // entries, so no synchronisation is needed between rows. Entries above the
-  // diagonal are stored as zeros so the k loop can start at the warp's first column.
-  for (int i = 0; i < B; ++i) {
-    const double* Li = A + (int64_t)i * B;
-    const double lii = Li[i];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int c = tid + q * FT;
-      const int kstart = (c & ~31);
-      if (c >= B && kstart >= B) continue;
-      double acc = (c == i) ? 1.0 : 0.0;
-      if (kstart <= i) {
-        for (int k = kstart; k < i; ++k) acc -= Li[k] * (c < B ? Inv[(int64_t)k * B + c] : 0.0);
-      }
-      if (c < B) Inv[(int64_t)i * B + c] = (c <= i) ? acc / lii : 0.0;
+  // ---- blocked triangular inverse X = L^{-1} (lower; zeros stored above) -----------
+  double* Lb = smem;  // Lb[r * (B + 1) + k] = L[r0 + r][k]
+  const int LS = B + 1;
+  for (int r0 = 0; r0 < B; r0 += NB) {
+    const int rb = min(NB, B - r0), ncols = r0 + rb;
+    for (int e = tid; e < rb * ncols; e += FT) {
+      const int r = e / ncols, k = e - r * ncols;
+      Lb[r * LS + k] = A[(int64_t)(r0 + r) * B + k];
     }
+    __syncthreads();
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+      const int c = q == 0 ? tid : 2 * FT - 1 - tid;  // paired columns balance the work
+      const bool active = c < ncols;
+      const int kstart = __reduce_min_sync(0xffffffffu, active ? c : 0x7fffffff);
+      if (active) {
+        double acc[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) acc[r] = 0.0;
+        // earlier block rows: X[k][c] = 0 for k < c, so a warp-uniform start is exact
+        for (int k = kstart; k < r0; ++k) {
+          const double xk = Inv[(int64_t)k * B + c];
+#pragma unroll
+          for (int r = 0; r < NB; ++r)
+            if (r < rb) acc[r] = fma(Lb[r * LS + k], xk, acc[r]);
+        }
+        double xn[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+          if (r < rb) {
+            double v = ((r0 + r) == c ? 1.0 : 0.0) - acc[r];
+#pragma unroll
+            for (int q2 = 0; q2 < r; ++q2) v = fma(-Lb[r * LS + r0 + q2], xn[q2], v);
+            v /= Lb[r * LS + r0 + r];
+            xn[r] = v;
+            Inv[(int64_t)(r0 + r) * B + c] = v;
+          } else {
+            xn[r] = 0.0;
+          }
+        }
+      } else if (c < B) {
+        for (int r = 0; r < rb; ++r) Inv[(int64_t)(r0 + r) * B + c] = 0.0;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   // ---- G = Inv D, power-of-two scale, cast, y0 ------------------------------------
   double mx = 0.0;
@@ -179,15 +262,23 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const
                           int32_t* status, cudaStream_t st, LaunchCounter* lc) {
   if (L <= 0) return cudaSuccess;
   dim3 grid(L), block(FT);
+  const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
+  cudaError_t e = cudaSuccess;
   switch (prec) {
     case P_FP32:
-      factor_kernel<P_FP32><<<grid, block, 0, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
+      e = cudaFuncSetAttribute(factor_kernel<P_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      factor_kernel<P_FP32><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
       break;
     case P_FP16:
-      factor_kernel<P_FP16><<<grid, block, 0, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
+      e = cudaFuncSetAttribute(factor_kernel<P_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      factor_kernel<P_FP16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
       break;
     default:
-      factor_kernel<P_BF16><<<grid, block, 0, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
+      e = cudaFuncSetAttribute(factor_kernel<P_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      factor_kernel<P_BF16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
       break;
   }
   if (lc) lc->n += 1;

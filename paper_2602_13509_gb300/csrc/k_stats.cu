@@ -247,34 +247,45 @@ cudaError_t launch_syrk_simt(const void* x, int64_t n_groups, int64_t pix_per_gr
 // ---------------------------------------------------------------------------------
 // K3a prefix_mean: thread per band walks the lines of the batch in order.
 // EXCLUSIVE (inclusive = 0): line t uses the lines before it; INCLUSIVE: through it.
+// One warp per band scans 32 lines at a time with shuffles (u16 sums are exact
+// integers, so the scan order does not change them).
 __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* __restrict__ m_out,
                                    double* __restrict__ state_s1, int64_t n0, int W, int L, int B,
                                    int inclusive, int64_t min_pixels, int32_t* __restrict__ status) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (b < B) {
-    double run = state_s1[b];
-    for (int t = 0; t < L; ++t) {
-      const double s = s1_line[(int64_t)t * B + b];
-      if (inclusive) run += s;
-      const int64_t n = n0 + (int64_t)(t + inclusive) * W;
-      m_out[(int64_t)t * B + b] = n > 0 ? run / (double)n : 0.0;
-      if (!inclusive) run += s;
+    double carry = state_s1[b];
+    for (int t0 = 0; t0 < L; t0 += 32) {
+      const int t = t0 + lane;
+      const double v = t < L ? s1_line[(int64_t)t * B + b] : 0.0;
+      double x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const double incl = carry + x;
+      const double run = inclusive ? incl : incl - v;
+      if (t < L) {
+        const int64_t n = n0 + (int64_t)(t + inclusive) * W;
+        m_out[(int64_t)t * B + b] = n > 0 ? run / (double)n : 0.0;
+      }
+      carry = __shfl_sync(0xffffffffu, incl, 31);
     }
-    state_s1[b] = run;
+    if (lane == 0) state_s1[b] = carry;
   }
-  if (b == 0) {
-    for (int t = 0; t < L; ++t) {
-      const int64_t n = n0 + (int64_t)(t + inclusive) * W;
-      if (n < min_pixels && status[t] == LS_OK) status[t] = LS_NOT_READY;
-    }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L; t += gridDim.x * blockDim.x) {
+    const int64_t n = n0 + (int64_t)(t + inclusive) * W;
+    if (n < min_pixels && status[t] == LS_OK) status[t] = LS_NOT_READY;
   }
 }
 
 cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
                                int W, int L, int B, int inclusive, int64_t min_pixels,
                                int32_t* status, cudaStream_t st, LaunchCounter* lc) {
-  prefix_mean_kernel<<<(B + 127) / 128, 128, 0, st>>>(s1_line, m_out, state_s1, n0, W, L, B,
-                                                      inclusive, min_pixels, status);
+  prefix_mean_kernel<<<(B + 7) / 8, 256, 0, st>>>(s1_line, m_out, state_s1, n0, W, L, B, inclusive,
+                                                  min_pixels, status);
   HSAD_LAUNCH_CHECK(lc);
 }
 
@@ -289,18 +300,25 @@ __global__ void prefix_cov_kernel(double* __restrict__ buf, const double* __rest
   const int i = (int)(e / B), j = (int)(e % B);
   const double dd = dgain[i] * dgain[j];
   double run = state_s2[e];
-  for (int t = 0; t < L; ++t) {
-    double* slot = buf + (int64_t)t * BB + e;
-    const double v = *slot;
-    if (inclusive) run += v;
-    const int64_t n = n0 + (int64_t)(t + inclusive) * W;
-    if (n >= min_pixels && n > 1) {
-      const double mi = m[(int64_t)t * B + i], mj = m[(int64_t)t * B + j];
-      *slot = dd * (run - (double)n * mi * mj) / (double)(n - 1);
-    } else {
-      *slot = 0.0;
+  constexpr int U = 8;  // lines whose loads are in flight together
+  for (int t0 = 0; t0 < L; t0 += U) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = (t0 + u < L) ? buf[(int64_t)(t0 + u) * BB + e] : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u;
+      if (t >= L) break;
+      if (inclusive) run += v[u];
+      const int64_t n = n0 + (int64_t)(t + inclusive) * W;
+      double out = 0.0;
+      if (n >= min_pixels && n > 1) {
+        const double mi = m[(int64_t)t * B + i], mj = m[(int64_t)t * B + j];
+        out = dd * (run - (double)n * mi * mj) / (double)(n - 1);
+      }
+      buf[(int64_t)t * BB + e] = out;
+      if (!inclusive) run += v[u];
     }
-    if (!inclusive) run += v;
   }
   state_s2[e] = run;
 }
