@@ -141,6 +141,15 @@ int hsad_line_status(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines,
  * (stream order); no allocation happens. */
 int hsad_reset(hsad_ctx* ctx);
 
+/* Export the running statistics (Sec. 3.3: the per-band sums behind mu and Sigma) after
+ * all enqueued work: *n_pixels = pixels since the last reset (stream modes) or in the
+ * last scored cube (CUBE mode); shift[B] = the per-band centring c (rounded DN for
+ * uint16 input, cast to double; float input: the float shift); s1[B] = sum (x - c);
+ * s2[B*B] = sum (x - c)(x - c)^T, row-major, lower triangle (row >= column) valid.
+ * All arguments are host arrays and may be NULL. For uint16 input every value is an
+ * exact integer. Synchronises the context's stream (bounded, 10 s). */
+int hsad_get_stats(hsad_ctx* ctx, int64_t* n_pixels, double* shift, double* s1, double* s2);
+
 /* Block until all work enqueued on the context has finished (bounded by timeout_ms,
  * negative = no limit). */
 int hsad_synchronize(hsad_ctx* ctx, int32_t timeout_ms);
@@ -201,6 +210,47 @@ int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int
                            int32_t in_dtype, int32_t precision, const float* gain,
                            int32_t threshold_mode, float threshold, int32_t flags, float* scores,
                            uint8_t* mask, void* stream, int32_t device);
+
+/* ---------------------------------------------------------------------------------
+ * Serving engine: many concurrent sensor streams on one device (the line-based
+ * detector of Sec. 6.1 for several imagers at once). Each admitted stream is a context
+ * with its statistics and factor resident on the device and its own CUDA stream; one
+ * native worker thread repeatedly pushes every stream's pending lines as one batch, so
+ * lines that arrive while a stream's previous batch is on the GPU are batched together
+ * and the work of different streams overlaps on the device.
+ * ------------------------------------------------------------------------------- */
+typedef struct hsad_engine hsad_engine;
+
+/* Start an engine on `device` whose streams share a device budget of budget_bytes
+ * (0 = unlimited; this sets the device-wide budget of hsad_set_device_budget). */
+int hsad_engine_create(int32_t device, int64_t budget_bytes, hsad_engine** out);
+
+/* Admit a stream with configuration *cfg (its device field is ignored). Returns
+ * HSAD_E_BUSY while the budget cannot hold it (retry after a stream closes; with
+ * HSAD_CREATE_WAIT in cfg->flags the call waits up to 10 s), HSAD_E_NOMEM if it can
+ * never fit, else HSAD_OK and the stream's id. */
+int hsad_engine_open(hsad_engine* e, const hsad_config* cfg, int32_t* stream_id);
+
+/* Queue n_lines host lines (BIP, the stream's in_dtype) for scoring; copies them and
+ * returns at once. *first_line_id receives the stream-local id of the first line. */
+int hsad_engine_submit(hsad_engine* e, int32_t stream_id, const void* lines, int64_t n_lines,
+                       uint64_t* first_line_id);
+
+/* Wait (timeout_ms; negative = no limit) until lines [first, first + n) of the stream
+ * are scored and copy their scores / mask to host memory (either may be NULL). Status
+ * as hsad_scores; HSAD_E_TIMEOUT when the wait expires. */
+int hsad_engine_results(hsad_engine* e, int32_t stream_id, uint64_t first_line_id, int64_t n_lines,
+                        float* scores, uint8_t* mask, int32_t timeout_ms);
+
+/* Close a stream (waits, bounded, for its work) and return its memory to the budget. */
+int hsad_engine_close(hsad_engine* e, int32_t stream_id);
+
+/* Lines pushed, batches pushed and the largest batch so far; returns the last push
+ * error (HSAD_OK if none). */
+int hsad_engine_counters(hsad_engine* e, int64_t* lines, int64_t* pushes, int64_t* max_batch);
+
+/* Stop the worker and close every stream. NULL-safe. */
+int hsad_engine_destroy(hsad_engine* e);
 
 /* Release the context. NULL-safe. Waits (up to 10 s) for in-flight work first. */
 int hsad_destroy(hsad_ctx* ctx);

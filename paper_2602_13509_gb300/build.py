@@ -74,5 +74,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+GEN_CSRC = os.path.join(os.path.dirname(HERE), "gen", "csrc")
+GEN_LIB = os.path.join(os.path.dirname(HERE), "gen", "libhsadgen.so")
+
+
+def build_gen(force: bool = False) -> str:
+    """Synthetic-input generator for large device-resident cubes (gen/csrc -> gen/libhsadgen.so)."""
+    srcs = sorted(glob.glob(os.path.join(GEN_CSRC, "*.cu")))
+    if not srcs:
+        return ""
+    if force or _stale(GEN_LIB, srcs):
+        tmp = GEN_LIB + ".tmp"
+        cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, *srcs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+        os.replace(tmp, GEN_LIB)
+    return GEN_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_gen(force="--force" in sys.argv))

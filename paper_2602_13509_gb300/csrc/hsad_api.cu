@@ -13,6 +13,8 @@
 // In CUBE mode (global RX per cube of cube_lines lines, Sec. 3.3) the cube's lines are
 // kept on the device; when the cube is complete: K1, K2 over the whole cube, K3 once,
 // K4+K5 once, K6 over every line, K7 maximum / normalisation / threshold.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -89,6 +91,9 @@ struct hsad_ctx {
   int32_t* status = nullptr;
   unsigned int* dmax_bits = nullptr;
   int32_t* bad_flag = nullptr;
+  int32_t* dev_err = nullptr;  // set by a kernel whose bounded wait expired
+  alignas(64) CUtensorMap gmap;  // TMA map over the 16-bit G planes (FP16/BF16 forms)
+  bool have_gmap = false;
   // result ring
   float* r_scores = nullptr;
   uint8_t* r_mask = nullptr;
@@ -106,6 +111,7 @@ struct hsad_ctx {
   int64_t n_stats = 0;      // pixels in the running statistics (stream modes)
   int64_t cube_fill = 0;    // lines in the open cube (CUBE mode)
   uint64_t cube_first = 0;  // id of the open cube's first line
+  int64_t last_cube_lines = 0;  // lines of the most recently scored cube
   std::deque<Record> records;
   std::vector<cudaEvent_t> event_pool;
 
@@ -220,7 +226,8 @@ void* dalloc(hsad_ctx* ctx, int64_t bytes, bool* ok) {
 
 int64_t plan_bytes(const hsad_ctx* c) {
   const int64_t B = c->B, Bp = c->Bp, L = c->Lmax;
-  const int64_t Lf = (c->mode == HSAD_CUBE) ? 1 : L;            // factors per batch
+  // factor slots per batch (EXCLUSIVE carries one more)
+  const int64_t Lf = (c->mode == HSAD_CUBE) ? 1 : (c->mode == HSAD_EXCLUSIVE ? L + 1 : L);
   const int64_t Ls = (c->mode == HSAD_CUBE) ? c->cfg.cube_lines : L;  // lines per batch
   int64_t b = 0;
   b += B * 4 + B * 4 + B * 8 + B * 8 + B * B * 8;                // c, dgain, S1, S2
@@ -289,6 +296,29 @@ void release(hsad_ctx* ctx) {
   delete ctx;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+bool encode_gmap(CUtensorMap* map, void* base, int64_t Bp, int64_t rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      return false;
+    }
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)Bp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Bp * 2};
+  const cuuint32_t box[2] = {64, 64};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -301,6 +331,25 @@ struct DeviceGuard {
 };
 
 }  // namespace
+
+// Internal (serving engine): 1 when lines [first, first+n) have been scored, 0 while
+// pending, negative status on error. Does not wait.
+int hsadi_lines_ready(hsad_ctx* ctx, uint64_t first, int64_t n) {
+  if (!ctx || n <= 0) return HSAD_E_INVALID;
+  if (ctx->failed) return HSAD_E_CUDA;
+  const uint64_t last = first + (uint64_t)n - 1;
+  if (last >= ctx->next_line) return 0;
+  DeviceGuard dg(ctx->device);
+  for (auto it = ctx->records.rbegin(); it != ctx->records.rend(); ++it) {
+    if (last >= it->first && last < it->first + it->n) {
+      const cudaError_t q = cudaEventQuery(it->ev);
+      if (q == cudaSuccess) return 1;
+      if (q == cudaErrorNotReady) return 0;
+      return fail(ctx, HSAD_E_CUDA, std::string("event: ") + cudaGetErrorString(q));
+    }
+  }
+  return 0;
+}
 
 // ------------------------------------------------------------------------------ ABI
 extern "C" {
@@ -421,7 +470,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     ok = false;
   }
   const int64_t B = ctx->B, Bp = ctx->Bp, L = ctx->Lmax;
-  const int64_t Lf = ctx->mode == HSAD_CUBE ? 1 : L;
+  const int64_t Lf = ctx->mode == HSAD_CUBE ? 1 : (ctx->mode == HSAD_EXCLUSIVE ? L + 1 : L);
   const int64_t Ls = ctx->mode == HSAD_CUBE ? cfg->cube_lines : L;
   ctx->c_int = (int32_t*)dalloc(ctx, B * 4, &ok);
   ctx->c_flt = (float*)dalloc(ctx, B * 4, &ok);
@@ -435,9 +484,10 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->wmat = dalloc(ctx, Lf * Bp * Bp * 4, &ok);
   ctx->y0 = (float*)dalloc(ctx, Lf * Bp * 4, &ok);
   ctx->inv_s2 = (float*)dalloc(ctx, Lf * 4, &ok);
-  ctx->status = (int32_t*)dalloc(ctx, Ls * 4, &ok);
+  ctx->status = (int32_t*)dalloc(ctx, std::max(Ls, Lf) * 4, &ok);
   ctx->dmax_bits = (unsigned int*)dalloc(ctx, 64, &ok);
   ctx->bad_flag = (int32_t*)((char*)ctx->dmax_bits + 32);
+  ctx->dev_err = (int32_t*)((char*)ctx->dmax_bits + 48);
   ctx->r_scores = (float*)dalloc(ctx, ctx->ring * ctx->W * 4, &ok);
   ctx->r_mask = (uint8_t*)dalloc(ctx, ctx->ring * ctx->W, &ok);
   ctx->r_status = (int32_t*)dalloc(ctx, ctx->ring * 4, &ok);
@@ -477,10 +527,20 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
       cudaMemsetAsync(ctx->state_s1, 0, B * 8, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->state_s2, 0, B * B * 8, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->r_status, 0xff, ctx->ring * 4, ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->dmax_bits, 0, 64, ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     release(ctx);
     return fail(nullptr, HSAD_E_CUDA, "device initialisation failed");
+  }
+  if (ctx->prec != P_FP32) {
+    // G planes [Lf][2][Bp][Bp] 16-bit as a 2-D tensor of Lf*2*Bp rows, 64 x 64 boxes
+    const int64_t rows = Lf * 2 * Bp;
+    if (!encode_gmap(&ctx->gmap, ctx->wmat, Bp, rows)) {
+      release(ctx);
+      return fail(nullptr, HSAD_E_CUDA, "cuTensorMapEncodeTiled failed for the whitening operand");
+    }
+    ctx->have_gmap = true;
   }
   *out = ctx;
   return HSAD_OK;
@@ -519,25 +579,113 @@ int add_record(hsad_ctx* ctx, uint64_t first, uint64_t n) {
   return HSAD_OK;
 }
 
+// K6: tensor cores (tcgen05, G by TMA) for the FP16 / BF16 forms, FFMA for FP32.
+int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o) {
+  cudaStream_t st = ctx->stream;
+  if (ctx->prec != P_FP32) {
+    KL("whiten_score", launch_whiten_tc(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec,
+                                        &ctx->gmap, ctx->y0, ctx->inv_s2, ctx->status, factor_stride, o,
+                                        ctx->dev_err, st, &ctx->lc));
+  } else {
+    KL("whiten_score", launch_whiten_score_simt(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt,
+                                                ctx->prec, ctx->wmat, ctx->y0, ctx->inv_s2, ctx->status,
+                                                factor_stride, o, st, &ctx->lc));
+  }
+  return HSAD_OK;
+}
+
+// K2: exact covariance sums of n_groups groups of pix pixels into out (lower triangle).
+// uint16 input runs on the tensor cores (integer split, exact); float input accumulates
+// FP32 x FP32 products in FP64 on the SIMT cores.
+int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* out, int64_t out_stride,
+         bool accumulate) {
+  cudaStream_t st = ctx->stream;
+  if (ctx->in_type == IN_U16) {
+    bool acc = accumulate;
+    if (!acc && pix > 4096) {  // exactness bound of one accumulation: add slices atomically
+      CK(cudaMemsetAsync(out, 0, (size_t)(n_groups * out_stride * 8), st));
+      acc = true;
+    }
+    KL("syrk", launch_syrk_tc((const uint16_t*)x, n_groups, pix, ctx->B, ctx->c_int, out, out_stride, acc ? 1 : 0,
+                              ctx->dev_err, st, &ctx->lc));
+  } else {
+    KL("syrk", launch_syrk_simt(x, n_groups, pix, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt, out, out_stride,
+                                accumulate ? 1 : 0, st, &ctx->lc));
+  }
+  return HSAD_OK;
+}
+
+// EXCLUSIVE batch of L lines, pipelined: factor slot 0 carries the factor of the
+// statistics before line `first` (computed at the end of the previous batch), so that
+// line is scored at once and its completion recorded before any statistics work; the
+// statistics through each line of the batch then give the factors of the next lines
+// (slots 1..L), and slot L is carried to slot 0 for the next batch.
+int stream_batch_excl(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
+  const int W = ctx->W, B = ctx->B, Bp = ctx->Bp;
+  const int64_t BB = (int64_t)B * B;
+  cudaStream_t st = ctx->stream;
+  if (ctx->n_stats == 0) {  // no statistics before this line: not ready
+    CK(cudaMemsetAsync(ctx->status, 0, 4, st));
+    CK(cudaMemsetAsync(ctx->status, LS_NOT_READY, 1, st));
+    KL("shift_init", launch_shift_init(x, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, st, &ctx->lc));
+  }
+  {
+    ScoreOut o0 = score_out(ctx, first, true);
+    int rc = whiten(ctx, x, 1, 1, o0);
+    if (rc == HSAD_OK) rc = add_record(ctx, first, 1);
+    if (rc != HSAD_OK) return rc;
+  }
+  CK(cudaMemsetAsync(ctx->status + 1, 0, (size_t)L * 4, st));
+  KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
+  {
+    int rc = syrk(ctx, x, L, W, ctx->sigma + BB, BB, false);
+    if (rc != HSAD_OK) return rc;
+  }
+  KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, 1,
+                                       ctx->min_pix, ctx->status + 1, st, &ctx->lc));
+  KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc));
+  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, ctx->dgain, L, B, ctx->prec,
+                             (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
+                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc));
+  if (L > 1) {
+    ScoreOut o1 = score_out(ctx, first + 1, true);
+    o1.factor_base = 1;
+    int rc = whiten(ctx, (const char*)x + ctx->line_bytes, L - 1, 1, o1);
+    if (rc == HSAD_OK) rc = add_record(ctx, first + 1, (uint64_t)(L - 1));
+    if (rc != HSAD_OK) return rc;
+  }
+  // carry the factor of all statistics so far to slot 0
+  const size_t wb = (size_t)Bp * Bp * 4;
+  CK(cudaMemcpyAsync(ctx->wmat, (char*)ctx->wmat + (size_t)L * wb, wb, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->y0, ctx->y0 + (size_t)L * Bp, (size_t)Bp * 4, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->inv_s2, ctx->inv_s2 + L, 4, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->status, ctx->status + L, 4, cudaMemcpyDeviceToDevice, st));
+  ctx->n_stats += (int64_t)L * W;
+  return HSAD_OK;
+}
+
 // One batch of L lines of a stream-mode context, all inside one statistics segment.
 int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
   const int W = ctx->W, B = ctx->B;
   cudaStream_t st = ctx->stream;
   const int incl = ctx->mode == HSAD_INCLUSIVE ? 1 : 0;
+  if (!incl) return stream_batch_excl(ctx, x, L, first);
   if (ctx->n_stats == 0) KL("shift_init", launch_shift_init(x, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, st, &ctx->lc));
   CK(cudaMemsetAsync(ctx->status, 0, (size_t)L * 4, st));
   KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
-  KL("syrk", launch_syrk_simt(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->sigma, (int64_t)B * B, 0,
-                      st, &ctx->lc));
+  {
+    int rc = syrk(ctx, x, L, W, ctx->sigma, (int64_t)B * B, false);
+    if (rc != HSAD_OK) return rc;
+  }
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, incl,
                         ctx->min_pix, ctx->status, st, &ctx->lc));
-  KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->m_line, ctx->state_s2, ctx->dgain, ctx->n_stats, W, L, B, incl,
-                       ctx->min_pix, st, &ctx->lc));
+  KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc));
   KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, L, B, ctx->prec, ctx->wmat, ctx->y0,
-                   ctx->inv_s2, ctx->status, st, &ctx->lc));
-  KL("whiten_score", launch_whiten_score_simt(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec, ctx->wmat,
-                              ctx->y0, ctx->inv_s2, ctx->status, 1, score_out(ctx, first, true), st,
-                              &ctx->lc));
+                   ctx->inv_s2, ctx->status, ctx->n_stats, W, incl, st, &ctx->lc));
+  {
+    int rc = whiten(ctx, x, L, 1, score_out(ctx, first, true));
+    if (rc != HSAD_OK) return rc;
+  }
   ctx->n_stats += (int64_t)L * W;
   return add_record(ctx, first, (uint64_t)L);
 }
@@ -554,20 +702,25 @@ int cube_score(hsad_ctx* ctx, const void* x, int64_t n) {
   CK(cudaMemsetAsync(ctx->status, 0, (size_t)n * 4, st));
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, 0, W, (int)n, B, 1, 0, ctx->status, st,
                         &ctx->lc));
-  KL("syrk", launch_syrk_simt(x, 1, N, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->state_s2, 0, 1, st,
-                      &ctx->lc));
+  {
+    int rc = syrk(ctx, x, 1, N, ctx->state_s2, 0, true);
+    if (rc != HSAD_OK) return rc;
+  }
   KL("finalize_cov", launch_finalize_cov(ctx->state_s1, ctx->state_s2, ctx->dgain, N, B, ctx->sigma, ctx->m_line,
                          ctx->min_pix, ctx->status, st, &ctx->lc));
   KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, 1, B, ctx->prec, ctx->wmat, ctx->y0,
-                   ctx->inv_s2, ctx->status, st, &ctx->lc));
+                   ctx->inv_s2, ctx->status, N, 0, 0, st, &ctx->lc));
   const bool rel = ctx->cfg.threshold_mode == HSAD_REL;
   const bool norm = (ctx->cfg.flags & HSAD_NORMALIZE_SCORES) != 0;
   ScoreOut o = score_out(ctx, ctx->cube_first, !(rel || norm));
-  KL("whiten_score", launch_whiten_score_simt(x, (int)n, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec, ctx->wmat,
-                              ctx->y0, ctx->inv_s2, ctx->status, 0, o, st, &ctx->lc));
+  {
+    int rc = whiten(ctx, x, (int)n, 0, o);
+    if (rc != HSAD_OK) return rc;
+  }
   if (rel || norm)
     KL("cube_normalize", launch_cube_normalize(o, n, W, rel ? 1 : 0, norm ? 1 : 0, ctx->dmax_bits, st, &ctx->lc));
   const uint64_t first = ctx->cube_first;
+  ctx->last_cube_lines = n;
   ctx->cube_first += (uint64_t)n;
   ctx->cube_fill = 0;
   return add_record(ctx, first, (uint64_t)n);
@@ -781,7 +934,13 @@ int hsad_scores(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, float* s
                        ctx->copy_stream));
     done += k;
   }
+  int32_t dev_err = 0;
+  CK(cudaMemcpyAsync(&dev_err, ctx->dev_err, 4, cudaMemcpyDeviceToHost, ctx->copy_stream));
   CK(cudaStreamSynchronize(ctx->copy_stream));
+  if (dev_err) {
+    ctx->failed = true;
+    return fail(ctx, HSAD_E_TIMEOUT, "a device-side bounded wait expired; the context is failed");
+  }
   bool nr = false, npd = false;
   for (int32_t s : st) {
     if (s == LS_NOT_PD) npd = true;
@@ -806,6 +965,37 @@ int hsad_reset(hsad_ctx* ctx) {
   ctx->n_stats = 0;
   ctx->cube_fill = 0;
   ctx->cube_first = 0;
+  ctx->last_cube_lines = 0;
+  return HSAD_OK;
+}
+
+int hsad_get_stats(hsad_ctx* ctx, int64_t* n_pixels, double* shift, double* s1, double* s2) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  DeviceGuard dg(ctx->device);
+  int rc = hsad_synchronize(ctx, 10000);
+  if (rc != HSAD_OK) return rc;
+  const int B = ctx->B;
+  if (n_pixels) {
+    if (ctx->mode == HSAD_CUBE) {
+      *n_pixels = ctx->last_cube_lines * ctx->W;
+    } else {
+      *n_pixels = ctx->n_stats;
+    }
+  }
+  if (shift) {
+    if (ctx->in_type == IN_U16) {
+      std::vector<int32_t> c(B);
+      CK(cudaMemcpy(c.data(), ctx->c_int, (size_t)B * 4, cudaMemcpyDeviceToHost));
+      for (int b = 0; b < B; ++b) shift[b] = (double)c[b];
+    } else {
+      std::vector<float> c(B);
+      CK(cudaMemcpy(c.data(), ctx->c_flt, (size_t)B * 4, cudaMemcpyDeviceToHost));
+      for (int b = 0; b < B; ++b) shift[b] = (double)c[b];
+    }
+  }
+  if (s1) CK(cudaMemcpy(s1, ctx->state_s1, (size_t)B * 8, cudaMemcpyDeviceToHost));
+  if (s2) CK(cudaMemcpy(s2, ctx->state_s2, (size_t)B * B * 8, cudaMemcpyDeviceToHost));
   return HSAD_OK;
 }
 

@@ -53,24 +53,31 @@ cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* sta
                                int W, int L, int B, int inclusive, int64_t min_pixels,
                                int32_t* status, cudaStream_t st, LaunchCounter* lc);
 
-// K3b: per-line covariance Sigma_t = D (S2_t - N_t m_t m_t^T) D / (N_t - 1) written in
-// place over the per-line SYRK results, and the updated state S2.
-cudaError_t launch_prefix_cov(double* buf, const double* m, double* state_s2, const double* dgain,
-                              int64_t n0, int W, int L, int B, int inclusive, int64_t min_pixels,
-                              cudaStream_t st, LaunchCounter* lc);
+// K3b: running raw sums S2_t (lower triangle) written in place over the per-line SYRK
+// results, and the updated state S2. The factor kernel turns them into Sigma_t.
+cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int inclusive, cudaStream_t st,
+                              LaunchCounter* lc);
 
-// K3c (cube): Sigma = D (S2 - N m m^T) D / (N - 1), m = S1 / N from the state; status[0]
-// becomes LS_OK or LS_NOT_READY (fewer than min_pixels pixels).
+// K2 (tcgen05, uint16 input): exact s2 = sum (x - c)(x - c)^T per group into the lower
+// triangle of out[g] (row stride B); groups above 4096 pixels need accumulate != 0
+// (atomic adds into a zeroed out). err is set if a bounded wait expires.
+cudaError_t launch_syrk_tc(const uint16_t* x, int64_t n_groups, int64_t pix_per_group, int B,
+                           const int32_t* c_int, double* out, int64_t out_stride, int accumulate, int32_t* err,
+                           cudaStream_t st, LaunchCounter* lc);
+
+// K3c (cube): raw sums S2 (lower triangle) copied from the state into sigma and
+// m = S1 / N; status[0] becomes LS_OK or LS_NOT_READY (fewer than min_pixels pixels).
 cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, const double* dgain,
                                 int64_t n, int B, double* sigma, double* m, int64_t min_pixels,
                                 int32_t* status, cudaStream_t st, LaunchCounter* lc);
 
-// K4+K5: FP64 Cholesky and triangular inverse of each ready line's Sigma_t (in place),
-// then G_t = s_t L^{-1} D cast to the working precision, y0 and 1/s_t^2.
-// scratch: [L][B][B] FP64.
+// K4+K5: from each ready line's raw sums (lower triangle of sigma[t]) and mean offset
+// m[t]: Sigma_t = D (S2_t - n_t m_t m_t^T) D / (n_t - 1) with n_t = n0 + (t + incl) W,
+// FP64 Cholesky and triangular inverse in place, then G_t = s_t L^{-1} D cast to the
+// working precision, y0 and 1/s_t^2. scratch: [L][B][B] FP64.
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
-                          int32_t* status, cudaStream_t st, LaunchCounter* lc);
+                          int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc);
 
 // K6 (SIMT): delta_p = inv_s2 * || G (x_p - c) - y0 ||^2 for every pixel of every line,
 // threshold, and scatter into the result ring. factor_stride = 0 makes every line
@@ -83,12 +90,20 @@ struct ScoreOut {
   int64_t ring;      // ring capacity in lines
   float tau;
   int write_mask;    // 1: mask = delta > tau here; 0: left to the cube normaliser
+  int factor_base = 0;  // factor slot of line 0 (slots advance with factor_stride)
 };
 cudaError_t launch_whiten_score_simt(const void* x, int L, int W, int B, int in_type,
                                      const int32_t* c_int, const float* c_flt, int prec,
                                      const void* wmat, const float* y0, const float* inv_s2,
                                      const int32_t* status, int factor_stride, ScoreOut out,
                                      cudaStream_t st, LaunchCounter* lc);
+
+// K6 (tcgen05, FP16 / BF16 forms): same contract as the SIMT form; gmap is the
+// CUtensorMap over the 16-bit G planes; err is set if a bounded wait expires.
+cudaError_t launch_whiten_tc(const void* x, int L, int W, int B, int in_type, const int32_t* c_int,
+                             const float* c_flt, int prec, const void* gmap, const float* y0,
+                             const float* inv_s2, const int32_t* status, int factor_stride, ScoreOut out,
+                             int32_t* err, cudaStream_t st, LaunchCounter* lc);
 
 // K7: cube maximum of delta over n_lines ring lines, then optional normalisation and
 // the REL / ABS mask.

@@ -76,10 +76,7 @@ __device__ double block_max(double v, double* red) {
 constexpr int NB = 16;      // Cholesky panel width = inverse block height
 constexpr int PS = NB + 1;  // padded panel row stride (doubles): rows fall in different banks
 
-__host__ __device__ inline int factor_smem_doubles(int B) {
-  const int a = B * PS, b = NB * (B + 1);
-  return a > b ? a : b;
-}
+__host__ __device__ inline int factor_smem_doubles(int B) { return B * PS; }
 
 // One CTA per line. Sigma (full B x B, lower triangle used) is factored in place in
 // global memory with a blocked right-looking Cholesky: the NB-column panel is staged in
@@ -96,7 +93,8 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
                                                        void* __restrict__ wmat,
                                                        float* __restrict__ y0_all,
                                                        float* __restrict__ inv_s2_all,
-                                                       int32_t* __restrict__ status) {
+                                                       int32_t* __restrict__ status, int64_t n0, int W,
+                                                       int incl) {
   const int t = blockIdx.x;
   if (status[t] != LS_OK) return;
   const int64_t BB = (int64_t)B * B;
@@ -107,6 +105,19 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
   extern __shared__ double smem[];
   __shared__ double red[FT / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // ---- covariance from the raw sums (lower triangle, in place) ----------------------
+  // Sigma_ij = d_i d_j (S2_ij - n m_i m_j) / (n - 1), n = pixels in this line's window.
+  {
+    const int64_t n = n0 + (int64_t)(t + incl) * W;
+    const double nn = (double)n, inv_nm1 = 1.0 / (double)(n - 1);
+    for (int i = warp; i < B; i += FT / 32) {
+      const double ai = dgain[i] * inv_nm1, nmi = nn * m[i];
+      double* row = A + (int64_t)i * B;
+      for (int j = lane; j <= i; j += 32) row[j] = ai * dgain[j] * fma(-nmi, m[j], row[j]);
+    }
+    __syncthreads();
+  }
 
   // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
   double* P = smem;  // panel: P[r * PS + j] = A[p + r][p + j]
@@ -124,7 +135,8 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
         return;
       }
       const double l = sqrt(piv);
-      for (int r = j + 1 + tid; r < rows; r += FT) P[r * PS + j] /= l;
+      const double rl = 1.0 / l;  // one division per pivot; the column is scaled by multiplies
+      for (int r = j + 1 + tid; r < rows; r += FT) P[r * PS + j] *= rl;
       __syncthreads();
       if (tid == 0) P[j * PS + j] = l;
       const int nc = kb - j - 1;
@@ -183,48 +195,65 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
     __syncthreads();
   }
 
-  // ---- blocked triangular inverse X = L^{-1} (lower; zeros stored above) -----------
-  double* Lb = smem;  // Lb[r * (B + 1) + k] = L[r0 + r][k]
-  const int LS = B + 1;
+  // ---- blocked triangular inverse, right-looking: X = L^{-1} in place of R = I ------
+  // For each block row i of NB rows: X_i = L_ii^{-1} R_i (forward substitution, one
+  // thread per column), then R_j -= L_ji X_i for every later row j (rank-NB update in
+  // 4 x 4 register tiles, the same balanced shape as the Cholesky trailing update).
+  // Entries above the diagonal start and stay zero.
+  double* R = Inv;
+  for (int64_t e = tid; e < BB; e += FT) R[e] = ((int)(e / B) == (int)(e % B)) ? 1.0 : 0.0;
+  __shared__ double rdiag[NB];  // 1 / L[r0 + r][r0 + r]
   for (int r0 = 0; r0 < B; r0 += NB) {
-    const int rb = min(NB, B - r0), ncols = r0 + rb;
-    for (int e = tid; e < rb * ncols; e += FT) {
-      const int r = e / ncols, k = e - r * ncols;
-      Lb[r * LS + k] = A[(int64_t)(r0 + r) * B + k];
+    const int rb = min(NB, B - r0), rows = B - r0, ncols = r0 + rb;
+    for (int e = tid; e < rows * rb; e += FT) {  // panel L[r0.., r0..r0+rb)
+      const int r = e / rb, j = e - r * rb;
+      P[r * PS + j] = A[(int64_t)(r0 + r) * B + r0 + j];
+    }
+    if (tid < rb) rdiag[tid] = 1.0 / A[(int64_t)(r0 + tid) * B + r0 + tid];
+    __syncthreads();
+    for (int c = tid; c < ncols; c += FT) {
+      double xr[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        xr[r] = 0.0;
+        if (r < rb) {
+          double v = R[(int64_t)(r0 + r) * B + c];
+#pragma unroll
+          for (int q = 0; q < r; ++q) v = fma(-P[r * PS + q], xr[q], v);
+          xr[r] = v * rdiag[r];
+          R[(int64_t)(r0 + r) * B + c] = xr[r];
+        }
+      }
     }
     __syncthreads();
-#pragma unroll 1
-    for (int q = 0; q < 2; ++q) {
-      const int c = q == 0 ? tid : 2 * FT - 1 - tid;  // paired columns balance the work
-      const bool active = c < ncols;
-      const int kstart = __reduce_min_sync(0xffffffffu, active ? c : 0x7fffffff);
-      if (active) {
-        double acc[NB];
+    const int mrem = rows - rb;
+    if (mrem > 0) {
+      const int mt = (mrem + 3) >> 2, nct = (ncols + 3) >> 2;
+      for (int idx = tid; idx < mt * nct; idx += FT) {
+        const int tr = idx / nct, tcx = idx - tr * nct;
+        const int j0 = rb + 4 * tr, c0 = 4 * tcx;  // j0 panel-relative row, c0 column
+        double acc[4][4];
 #pragma unroll
-        for (int r = 0; r < NB; ++r) acc[r] = 0.0;
-        // earlier block rows: X[k][c] = 0 for k < c, so a warp-uniform start is exact
-        for (int k = kstart; k < r0; ++k) {
-          const double xk = Inv[(int64_t)k * B + c];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int r = 0; r < NB; ++r)
-            if (r < rb) acc[r] = fma(Lb[r * LS + k], xk, acc[r]);
+          for (int b = 0; b < 4; ++b)
+            acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? R[(int64_t)(r0 + j0 + a) * B + c0 + b] : 0.0;
+        for (int q = 0; q < rb; ++q) {
+          double l[4], xq[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : 0.0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) xq[b] = (c0 + b < ncols) ? R[(int64_t)(r0 + q) * B + c0 + b] : 0.0;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(-l[a], xq[b], acc[a][b]);
         }
-        double xn[NB];
 #pragma unroll
-        for (int r = 0; r < NB; ++r) {
-          if (r < rb) {
-            double v = ((r0 + r) == c ? 1.0 : 0.0) - acc[r];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int q2 = 0; q2 < r; ++q2) v = fma(-Lb[r * LS + r0 + q2], xn[q2], v);
-            v /= Lb[r * LS + r0 + r];
-            xn[r] = v;
-            Inv[(int64_t)(r0 + r) * B + c] = v;
-          } else {
-            xn[r] = 0.0;
-          }
-        }
-      } else if (c < B) {
-        for (int r = 0; r < rb; ++r) Inv[(int64_t)(r0 + r) * B + c] = 0.0;
+          for (int b = 0; b < 4; ++b)
+            if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(r0 + j0 + a) * B + c0 + b] = acc[a][b];
       }
     }
     __syncthreads();
@@ -259,7 +288,7 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
 
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
-                          int32_t* status, cudaStream_t st, LaunchCounter* lc) {
+                          int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc) {
   if (L <= 0) return cudaSuccess;
   dim3 grid(L), block(FT);
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
@@ -268,17 +297,17 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const
     case P_FP32:
       e = cudaFuncSetAttribute(factor_kernel<P_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      factor_kernel<P_FP32><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
+      factor_kernel<P_FP32><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status, n0, W, incl);
       break;
     case P_FP16:
       e = cudaFuncSetAttribute(factor_kernel<P_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      factor_kernel<P_FP16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
+      factor_kernel<P_FP16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status, n0, W, incl);
       break;
     default:
       e = cudaFuncSetAttribute(factor_kernel<P_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      factor_kernel<P_BF16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status);
+      factor_kernel<P_BF16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status, n0, W, incl);
       break;
   }
   if (lc) lc->n += 1;

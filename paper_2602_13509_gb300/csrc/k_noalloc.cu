@@ -150,7 +150,8 @@ extern "C" int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t
     if (e == cudaSuccess) e = launch_syrk_simt(cube, 1, N, B, it, c_int, c_flt, s2, 0, 1, st, &lc);
     if (e == cudaSuccess)
       e = launch_finalize_cov(s1, s2, dgain, N, B, sigma, m_line, (int64_t)B + 1, status, st, &lc);
-    if (e == cudaSuccess) e = launch_factor(sigma, inv, m_line, dgain, 1, B, pr, wmat, y0, inv_s2, status, st, &lc);
+    if (e == cudaSuccess)
+      e = launch_factor(sigma, inv, m_line, dgain, 1, B, pr, wmat, y0, inv_s2, status, N, 0, 0, st, &lc);
     const bool rel = threshold_mode == HSAD_REL, norm = (flags & HSAD_NORMALIZE_SCORES) != 0;
     ScoreOut o;
     o.scores = scores;

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) whiten_score_kernel(
   __shared__ __align__(16) float Bs[2][WS_K][WS_N + 4];
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * WS_P;
-  const int f = factor_stride ? t : 0;
+  const int f = out.factor_base + (factor_stride ? t : 0);
   const int64_t slot = (out.slot0 + t) % out.ring;
   const int st = status[f];
   if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;

@@ -289,16 +289,17 @@ cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* sta
   HSAD_LAUNCH_CHECK(lc);
 }
 
-// K3b prefix_cov: thread per matrix entry walks the lines; in place over the per-line s2.
-__global__ void prefix_cov_kernel(double* __restrict__ buf, const double* __restrict__ m,
-                                  double* __restrict__ state_s2, const double* __restrict__ dgain,
-                                  int64_t n0, int W, int L, int B, int inclusive,
-                                  int64_t min_pixels) {
+// K3b prefix_cov: thread per lower-triangle entry walks the lines and replaces each
+// line's s2 by the running sum S2_t (EXCLUSIVE: lines before t; INCLUSIVE: through t).
+// One FP64 add per entry and line; the covariance itself is formed by the factor
+// kernel, which reads each entry once anyway.
+__global__ void prefix_cov_kernel(double* __restrict__ buf, double* __restrict__ state_s2, int L, int B,
+                                  int inclusive) {
   const int64_t BB = (int64_t)B * B;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= BB) return;
   const int i = (int)(e / B), j = (int)(e % B);
-  const double dd = dgain[i] * dgain[j];
+  if (j > i) return;
   double run = state_s2[e];
   constexpr int U = 8;  // lines whose loads are in flight together
   for (int t0 = 0; t0 < L; t0 += U) {
@@ -307,32 +308,24 @@ __global__ void prefix_cov_kernel(double* __restrict__ buf, const double* __rest
     for (int u = 0; u < U; ++u) v[u] = (t0 + u < L) ? buf[(int64_t)(t0 + u) * BB + e] : 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int t = t0 + u;
-      if (t >= L) break;
-      if (inclusive) run += v[u];
-      const int64_t n = n0 + (int64_t)(t + inclusive) * W;
-      double out = 0.0;
-      if (n >= min_pixels && n > 1) {
-        const double mi = m[(int64_t)t * B + i], mj = m[(int64_t)t * B + j];
-        out = dd * (run - (double)n * mi * mj) / (double)(n - 1);
-      }
-      buf[(int64_t)t * BB + e] = out;
-      if (!inclusive) run += v[u];
+      if (t0 + u >= L) break;
+      const double before = run;
+      run += v[u];
+      buf[(int64_t)(t0 + u) * BB + e] = inclusive ? run : before;
     }
   }
   state_s2[e] = run;
 }
 
-cudaError_t launch_prefix_cov(double* buf, const double* m, double* state_s2, const double* dgain,
-                              int64_t n0, int W, int L, int B, int inclusive, int64_t min_pixels,
-                              cudaStream_t st, LaunchCounter* lc) {
+cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int inclusive, cudaStream_t st,
+                              LaunchCounter* lc) {
   const int64_t BB = (int64_t)B * B;
-  prefix_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(buf, m, state_s2, dgain, n0, W,
-                                                                  L, B, inclusive, min_pixels);
+  prefix_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(buf, state_s2, L, B, inclusive);
   HSAD_LAUNCH_CHECK(lc);
 }
 
-// K3c finalize_cov (cube mode): statistics of the whole cube from the state.
+// K3c finalize_cov (cube mode): the cube's raw sums S2 (lower triangle, read from the
+// lower triangle of the state) and m = S1 / N; the factor kernel forms Sigma from them.
 __global__ void finalize_cov_kernel(const double* __restrict__ s1, const double* __restrict__ s2,
                                     const double* __restrict__ dgain, int64_t n, int B,
                                     double* __restrict__ sigma, double* __restrict__ m,
@@ -341,9 +334,9 @@ __global__ void finalize_cov_kernel(const double* __restrict__ s1, const double*
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= BB) return;
   const int i = (int)(e / B), j = (int)(e % B);
-  const double mi = s1[i] / (double)n, mj = s1[j] / (double)n;
-  sigma[e] = dgain[i] * dgain[j] * (s2[e] - (double)n * mi * mj) / (double)(n - 1);
-  if (j == 0) m[i] = mi;
+  (void)dgain;
+  if (j <= i) sigma[e] = s2[e];
+  if (j == 0) m[i] = s1[i] / (double)n;
   if (e == 0) status[0] = (n >= min_pixels && n > 1) ? LS_OK : LS_NOT_READY;
 }
 

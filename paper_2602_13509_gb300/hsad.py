@@ -63,6 +63,7 @@ def _load():
         "hsad_line_status": (C.c_int, [P, C.c_uint64, C.c_int64, P, C.c_int32]),
         "hsad_synchronize": (C.c_int, [P, C.c_int32]),
         "hsad_reset": (C.c_int, [P]),
+        "hsad_get_stats": (C.c_int, [P, C.POINTER(C.c_int64), P, P, P]),
         "hsad_stream": (P, [P]),
         "hsad_kernel_launches": (C.c_int64, [P]),
         "hsad_device_bytes": (C.c_int64, [P]),
@@ -75,6 +76,13 @@ def _load():
         "hsad_global_rx_noalloc": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                              C.POINTER(C.c_float), C.c_int32, C.c_float, C.c_int32, P, P, P,
                                              C.c_int32]),
+        "hsad_engine_create": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(P)]),
+        "hsad_engine_open": (C.c_int, [P, C.POINTER(hsad_config), C.POINTER(C.c_int32)]),
+        "hsad_engine_submit": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_uint64)]),
+        "hsad_engine_results": (C.c_int, [P, C.c_int32, C.c_uint64, C.c_int64, P, P, C.c_int32]),
+        "hsad_engine_close": (C.c_int, [P, C.c_int32]),
+        "hsad_engine_counters": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "hsad_engine_destroy": (C.c_int, [P]),
         "hsad_destroy": (C.c_int, [P]),
         "hsad_last_error": (C.c_char_p, [P]),
         "hsad_status_string": (C.c_char_p, [C.c_int]),
@@ -166,6 +174,17 @@ def hsad_reset(ctx) -> int:
     return _lib.hsad_reset(ctx)
 
 
+def hsad_get_stats(ctx, bands: int):
+    """Returns ``(status, n_pixels, shift [B], s1 [B], s2 [B, B])`` as numpy arrays."""
+    import numpy as np
+    n = C.c_int64(0)
+    c = np.zeros(bands, np.float64)
+    s1 = np.zeros(bands, np.float64)
+    s2 = np.zeros((bands, bands), np.float64)
+    rc = _lib.hsad_get_stats(ctx, C.byref(n), c.ctypes.data, s1.ctypes.data, s2.ctypes.data)
+    return rc, n.value, c, s1, s2
+
+
 def hsad_stream(ctx) -> int:
     return _lib.hsad_stream(ctx) or 0
 
@@ -213,6 +232,47 @@ def hsad_global_rx_noalloc(cube, n_lines, width, bands, in_dtype, precision, gai
     return _lib.hsad_global_rx_noalloc(_ptr(cube), int(n_lines), int(width), int(bands), int(in_dtype),
                                        int(precision), g, int(threshold_mode), float(threshold), int(flags),
                                        _ptr(scores), _ptr(mask), stream, int(device))
+
+
+def hsad_engine_create(device: int = 0, budget_bytes: int = 0):
+    """Returns ``(status, engine)``."""
+    out = C.c_void_p()
+    rc = _lib.hsad_engine_create(int(device), int(budget_bytes), C.byref(out))
+    return rc, (out.value if rc == HSAD_OK else None)
+
+
+def hsad_engine_open(engine, cfg: hsad_config):
+    """Returns ``(status, stream_id)``."""
+    sid = C.c_int32(-1)
+    rc = _lib.hsad_engine_open(engine, C.byref(cfg), C.byref(sid))
+    return rc, sid.value
+
+
+def hsad_engine_submit(engine, stream_id: int, lines, n_lines: int):
+    """Returns ``(status, first_line_id)``."""
+    first = C.c_uint64(0)
+    rc = _lib.hsad_engine_submit(engine, int(stream_id), _ptr(lines), int(n_lines), C.byref(first))
+    return rc, first.value
+
+
+def hsad_engine_results(engine, stream_id: int, first: int, n_lines: int, scores, mask, timeout_ms: int = -1):
+    return _lib.hsad_engine_results(engine, int(stream_id), int(first), int(n_lines), _ptr(scores), _ptr(mask),
+                                    int(timeout_ms))
+
+
+def hsad_engine_close(engine, stream_id: int) -> int:
+    return _lib.hsad_engine_close(engine, int(stream_id))
+
+
+def hsad_engine_counters(engine):
+    """Returns ``(last_error, lines, pushes, max_batch)``."""
+    a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    rc = _lib.hsad_engine_counters(engine, C.byref(a), C.byref(b), C.byref(c))
+    return rc, a.value, b.value, c.value
+
+
+def hsad_engine_destroy(engine) -> int:
+    return _lib.hsad_engine_destroy(engine)
 
 
 def hsad_destroy(ctx) -> int:

@@ -1,0 +1,85 @@
+"""Full-size workloads in the launch configuration bench.py times, checked on sampled lines.
+
+640 px x 270 bands x 4000 lines (whole stream in one batch) and 1024 px x 448 bands x
+8000 lines (batches of 2000), EXCLUSIVE statistics. The oracle scores a few sampled lines
+one by one against all the lines before them (its cost grows with the line index, so
+the samples sit early and in the middle of the stream). Tolerances as everywhere:
+relative error <= 1e-4 (FP32), <= 1e-2 (BF16 / FP16); masks bit-exact outside the margin.
+"""
+import numpy as np
+import pytest
+
+from oracle import rx as orx
+from tests._parity import MARGIN, TOL, mask_mismatch, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_13509_gb300 as hs
+    return hs
+
+
+def _run(hs, lines, sc, prec, batch):
+    import torch
+    T, W, B = lines.shape
+    x = torch.from_numpy(lines.view(np.int16)).cuda()
+    s = torch.empty((T, W), dtype=torch.float32, device="cuda")
+    m = torch.empty((T, W), dtype=torch.uint8, device="cuda")
+    det = hs.Detector(width=W, bands=B, stats_mode="exclusive", precision=prec, gain=sc.gain, offset=sc.offset,
+                      max_batch_lines=batch, result_lines=T)
+    rc, first = hs.hsad_push_lines(det.ctx, x, T, hs.HSAD_DEVICE)
+    assert rc == hs.HSAD_OK
+    rc = hs.hsad_scores(det.ctx, first, T, s, m, hs.HSAD_DEVICE, -1)
+    assert rc in (hs.HSAD_OK, hs.HSAD_E_NOT_READY)
+    st = np.empty(T, np.int32)
+    assert hs.hsad_line_status(det.ctx, first, T, st, 0) == hs.HSAD_OK
+    det.close()
+    return s.cpu().numpy(), m.cpu().numpy(), st
+
+
+@pytest.fixture(scope="module")
+def stream_640x270():
+    from gen import config_scene
+    sc, T = config_scene("stream_640x270")
+    return sc, sc.lines(0, T)
+
+
+@pytest.fixture(scope="module")
+def stream_1024x448():
+    from gen import config_scene
+    sc, T = config_scene("precision_1024x448")
+    return sc, sc.lines(0, T)
+
+
+def _check(s, m, st, lines, sc, prec, sample):
+    T, W, B = lines.shape
+    # warm-up: line t is ready once t * W >= B + 1 pixels precede it
+    first_ready = -(-(B + 1) // W)
+    assert (st[:first_ready] == orx.NOT_READY).all() and (st[first_ready:] == orx.OK).all()
+    assert np.isnan(s[:first_ready]).all() and np.isfinite(s[first_ready:]).all()
+    tau = B + 6 * np.sqrt(2 * B)
+    for t in sample:
+        ref, rst = orx.stream_rx_line(lines, t, "exclusive", gain=sc.gain, offset=sc.offset, n_lines=T)
+        assert rst == orx.OK
+        emax, _ = rel_err(s[t], ref)
+        assert emax <= TOL[prec], (t, emax)
+        assert mask_mismatch(m[t], ref, tau, MARGIN[prec]) == 0, t
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_stream_640x270_full(hs, stream_640x270, prec):
+    sc, lines = stream_640x270
+    s, m, st = _run(hs, lines, sc, prec, 4000)
+    _check(s, m, st, lines, sc, prec, sample=[1, 2, 500, 3999])
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "fp32"])
+def test_stream_1024x448_full(hs, stream_1024x448, prec):
+    sc, lines = stream_1024x448
+    s, m, st = _run(hs, lines, sc, prec, 2000)
+    _check(s, m, st, lines, sc, prec, sample=[1, 2001, 2400])
