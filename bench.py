@@ -119,6 +119,21 @@ def oracle_sample(lines, t_list, gain, offset):
     return px, time.perf_counter() - t0
 
 
+def max_over_ranks(ms, dist, device):
+    """Slowest rank's time (replicas run independent streams; this is the only collective)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(px_per_rank_step, world, ms):
+    """Whole-job pixel-spectra per second: every rank scores its own stream."""
+    return px_per_rank_step * world / (ms / 1e3)
+
+
 def run_serving(hs, device, precision, seconds, warm_s, pool_lines=96, seed_offset=0):
     """16 concurrent streams with Poisson line arrivals through the serving engine.
 
@@ -215,6 +230,91 @@ def run_serving(hs, device, precision, seconds, warm_s, pool_lines=96, seed_offs
     return out
 
 
+def run_stress(args, hs, local, world, rank, peaks):
+    """32 stored cubes of uneven size scored one by one in CUBE mode (global RX, Sec. 3.3).
+
+    Each cube is drawn on the GPU into one reused buffer (outside the timed region),
+    then pushed whole (scored in place) and its scores read into device memory; the
+    events bracket push + readback. BF16 and FP32 side by side. Each cube's in-sample
+    mean score is checked against the exact B (N-1) / N.
+    """
+    import numpy as np
+    import torch
+    from gen import PushbroomScene, stress_cubes
+    from gen.device import DeviceScene
+
+    specs = stress_cubes(32)
+    if args.stress_cubes:
+        specs = specs[:args.stress_cubes]
+    max_elems = max(s["lines"] * s["width"] * s["bands"] for s in specs)
+    max_px = max(s["lines"] * s["width"] for s in specs)
+    buf = torch.empty(max_elems, dtype=torch.int16, device=f"cuda:{local}")
+    sbuf = torch.empty(max_px, dtype=torch.float32, device=f"cuda:{local}")
+    mbuf = torch.empty(max_px, dtype=torch.uint8, device=f"cuda:{local}")
+    res = {}
+    for prec in ("bf16", "fp32"):
+        tot_px, tot_ms, worst, launches, kern = 0, 0.0, 0.0, 0, {}
+        for i, sp in enumerate(specs):
+            Lc, Wc, Bc = sp["lines"], sp["width"], sp["bands"]
+            sc = PushbroomScene(Wc, Bc, seed=sp["seed"] + 1000 * rank)
+            x = buf[:Lc * Wc * Bc].view(Lc, Wc, Bc)
+            DeviceScene(sc, device=f"cuda:{local}").generate(x, 0, seed=sp["seed"] + 1000 * rank)
+            det = hs.Detector(width=Wc, bands=Bc, stats_mode="cube", cube_lines=Lc, precision=prec, gain=sc.gain,
+                              offset=sc.offset, result_lines=Lc, device=local)
+            det.profile(i == 0)
+            stream = torch.cuda.ExternalStream(det.stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n0 = det.kernel_launches
+            e0.record(stream)
+            rc, first = hs.hsad_push_lines(det.ctx, x, Lc, hs.HSAD_DEVICE)
+            assert rc == hs.HSAD_OK, hs.hsad_last_error(det.ctx)
+            rc = hs.hsad_scores(det.ctx, first, Lc, sbuf, mbuf, hs.HSAD_DEVICE, -1)
+            e1.record(stream)
+            e1.synchronize()
+            launches += det.kernel_launches - n0
+            if i == 0:
+                kern = {k: round(ms, 3) for k, (n, ms) in det.profile_totals().items()}
+            det.close()
+            ms = e0.elapsed_time(e1)
+            N = Lc * Wc
+            mean = float(sbuf[:N].double().mean())
+            worst = max(worst, abs(mean - Bc * (N - 1) / N) / Bc)
+            tot_px += N
+            tot_ms += ms
+        res[prec] = {"value": tot_px * 1e3 / tot_ms, "seconds": tot_ms / 1e3, "cubes": len(specs),
+                     "pixels": tot_px, "gpu_launches": launches, "kernels_first_cube_ms": kern,
+                     "insample_mean_max_rel_dev": worst}
+    del buf
+    return res
+
+
+def main_stress(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle's global RX over 32 cubes of up to "
+                              "41M pixels x 448 bands is not a bounded host sample; see the stream workload"}))
+        return
+    import torch
+    import paper_2602_13509_gb300 as hs
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        res = run_stress(args, hs, local, world, rank, load_peaks())
+    b = res["bf16"]
+    out = {"metric": "pixel-spectra scored/s", "value": b["value"] * world, "unit": "pixel-spectra/s",
+           "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": b["seconds"] * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+           "data": "synthetic (drawn on the device)",
+           "config": {"workload": "stress_32_cubes", "cubes": b["cubes"], "stats": "cube (global RX)",
+                      "input": "uint16 12-bit DN", "l2": "cubes larger than L2"},
+           "fp32_path": res["fp32"], "bf16_path": b, "gpu_launches": b["gpu_launches"], "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def make_inputs(wl, rank):
     import numpy as np
     from gen import PushbroomScene, SEED_BASE
@@ -259,7 +359,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stream_640x270", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="stream_640x270", choices=sorted(WORKLOADS) + ["stress"])
+    ap.add_argument("--stress-cubes", type=int, default=0, help="score only the first k of the 32 cubes")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--batch", type=int, default=0, help="lines per internal batch (0 = workload default)")
     ap.add_argument("--lines", type=int, default=0, help="override the stream length (profiling captures)")
@@ -270,6 +371,8 @@ def main():
                     help="measured seconds of the 16-stream serving run (0 = skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "stress":
+        return main_stress(args)
     wl = dict(WORKLOADS[args.workload])
     if args.batch:
         wl["batch"] = args.batch
@@ -337,18 +440,14 @@ def main():
         e1.record(stream)
         e1.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / args.steps
-        if dist is not None:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, f"cuda:{local}")
         return ms, det.kernel_launches - n0
 
     px_step = T * W
     det = detector(args.precision)
     with ClockSampler(local) as clk:
         ms, launches = timed(det)
-    value = px_step * world / (ms / 1e3)
+    value = weak_value(px_step, world, ms)
 
     # per-kernel times, CUDA events on the library's stream (separate pass)
     prof_steps = 2

@@ -73,6 +73,7 @@ struct hsad_ctx {
   std::vector<void*> host_allocs;
   int64_t dev_bytes = 0;
   bool budget_charged = false;
+  int64_t charged = 0;  // bytes charged to the device budget at admission
 
   // device state
   int32_t* c_int = nullptr;
@@ -290,7 +291,7 @@ void release(hsad_ctx* ctx) {
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->budget_charged) {
     std::lock_guard<std::mutex> g(budget().mu);
-    budget().used[ctx->device] -= ctx->dev_bytes;
+    budget().used[ctx->device] -= ctx->charged;
   }
   if (prev >= 0) cudaSetDevice(prev);
   delete ctx;
@@ -446,6 +447,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
       if (lim == 0 || used + need <= lim) {
         budget().used[ctx->device] += need;
         ctx->budget_charged = true;
+        ctx->charged = need;
         break;
       }
       g.unlock();
@@ -492,7 +494,8 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->r_mask = (uint8_t*)dalloc(ctx, ctx->ring * ctx->W, &ok);
   ctx->r_status = (int32_t*)dalloc(ctx, ctx->ring * 4, &ok);
   if (ctx->mode == HSAD_CUBE) {
-    ctx->cube_buf = dalloc(ctx, (int64_t)cfg->cube_lines * ctx->line_bytes, &ok);
+    // the cube buffer is allocated on first use: a device push of one whole cube is
+    // scored in place and never needs it (its bytes are charged to the budget anyway)
   } else {
     for (int i = 0; i < 2; ++i) ctx->d_stage[i] = dalloc(ctx, L * ctx->line_bytes, &ok);
   }
@@ -510,10 +513,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     else ctx->host_allocs.push_back(h);
     ctx->h_small = (int32_t*)h;
   }
-  {
-    std::lock_guard<std::mutex> g(budget().mu);
-    budget().used[ctx->device] += ctx->dev_bytes - charged;  // settle planned vs actual
-  }
+  ctx->charged = charged;  // released as charged, whatever is allocated later
   if (!ok) {
     cudaGetLastError();
     release(ctx);
@@ -784,6 +784,11 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
         continue;
       }
       const int64_t take = std::min<int64_t>(n_lines - done, CL - ctx->cube_fill);
+      if (!ctx->cube_buf) {
+        bool ok = true;
+        ctx->cube_buf = dalloc(ctx, CL * ctx->line_bytes, &ok);
+        if (!ok) return fail(ctx, HSAD_E_NOMEM, "cube buffer allocation failed");
+      }
       char* dst = (char*)ctx->cube_buf + ctx->cube_fill * ctx->line_bytes;
       if (mem == HSAD_DEVICE) {
         CK(cudaMemcpyAsync(dst, src + done * ctx->line_bytes, (size_t)(take * ctx->line_bytes),
