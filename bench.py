@@ -193,16 +193,22 @@ def run_serving(hs, device, precision, seconds, warm_s, pool_lines=96, seed_offs
             rc = hs.hsad_engine_results(eng, sids[i], k, 1, s, m, 60000)
             t_done[i][k] = time.perf_counter() - start
 
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(1e-4)                         # GIL hand-over well below a line period
     threads = [threading.Thread(target=waiter, args=(i,), daemon=True) for i in range(len(specs))]
     for th in threads:
         th.start()
     for (t, i, k) in sched:
-        while time.perf_counter() < start + t:
-            pass
+        while True:                                     # sleep, do not spin: the waiters need the GIL
+            dt = start + t - time.perf_counter()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 0.0002))
         line = pools[i][k % pool_lines:k % pool_lines + 1]
         hs.hsad_engine_submit(eng, sids[i], line, 1)
     for th in threads:
         th.join()
+    sys.setswitchinterval(switch)
     err, lines_pushed, pushes, max_batch = hs.hsad_engine_counters(eng)
     hs.hsad_engine_destroy(eng)
 

@@ -211,6 +211,13 @@ int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int
                            int32_t threshold_mode, float threshold, int32_t flags, float* scores,
                            uint8_t* mask, void* stream, int32_t device);
 
+/* Self-test of the bounded device waits used by the tensor-core kernels (no
+ * counterpart in the paper): launches one kernel that waits on an mbarrier nothing
+ * arrives at, with a limit of limit_cycles SM clock cycles (1 .. 2e10). The wait gives
+ * up, *timed_out becomes 1 and the call returns HSAD_E_TIMEOUT; the device stays usable.
+ * HSAD_OK with *timed_out 0 would mean the wait completed, which cannot happen. */
+int hsad_selftest_bounded_wait(int32_t device, int64_t limit_cycles, int32_t* timed_out);
+
 /* ---------------------------------------------------------------------------------
  * Serving engine: many concurrent sensor streams on one device (the line-based
  * detector of Sec. 6.1 for several imagers at once). Each admitted stream is a context

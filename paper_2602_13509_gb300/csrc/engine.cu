@@ -26,6 +26,8 @@
 // internal helper of hsad_api.cu: 1 when every line of [first, first+n) has been scored,
 // 0 while pending, negative on error
 int hsadi_lines_ready(hsad_ctx* ctx, uint64_t first, int64_t n);
+// internal helper of hsad_api.cu: 1 when a host push would not wait for a staging buffer
+int hsadi_push_ready(hsad_ctx* ctx);
 
 namespace {
 
@@ -74,6 +76,12 @@ void worker_loop(hsad_engine* e) {
       if (!sp) continue;
       EStream& s = *sp;
       int64_t n = 0;
+      {
+        // a stream whose staging buffers are both in flight keeps its lines queued (they
+        // join its next, larger batch) instead of holding up every other stream
+        std::lock_guard<std::mutex> g(s.ctx_mu);
+        if (!s.ctx || !hsadi_push_ready(s.ctx)) continue;
+      }
       {
         std::lock_guard<std::mutex> g(s.q_mu);
         if (!s.open || s.q.empty()) continue;

@@ -352,6 +352,15 @@ int hsadi_lines_ready(hsad_ctx* ctx, uint64_t first, int64_t n) {
   return 0;
 }
 
+// 1 when a host push of up to Lmax lines would not wait for a staging buffer (the
+// buffer that push would fill has finished its previous copy), 0 otherwise.
+int hsadi_push_ready(hsad_ctx* ctx) {
+  if (!ctx || ctx->failed) return 1;  // the push itself reports the error
+  if (ctx->mode == HSAD_CUBE) return 1;
+  DeviceGuard dg(ctx->device);
+  return cudaEventQuery(ctx->stage_ev[ctx->stage_idx]) == cudaErrorNotReady ? 0 : 1;
+}
+
 // ------------------------------------------------------------------------------ ABI
 extern "C" {
 

@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "hsad_internal.h"
 
@@ -78,6 +79,34 @@ constexpr int PS = NB + 1;  // padded panel row stride (doubles): rows fall in d
 
 __host__ __device__ inline int factor_smem_doubles(int B) { return B * PS; }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// CL == 1: block barrier. CL > 1: cluster barrier with release / acquire ordering.
+template <int CL>
+__device__ __forceinline__ void csync() {
+  if (CL == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
+}
+// Global loads of data other CTAs of the cluster may have written: through L2.
+template <int CL>
+__device__ __forceinline__ double ldg_c(const double* p) {
+  return CL == 1 ? *p : __ldcg(p);
+}
+// A double in the shared memory of CTA `rank` of this cluster.
+__device__ __forceinline__ double ld_remote(const double* local, int rank) {
+  uint32_t laddr = (uint32_t)__cvta_generic_to_shared(local), raddr;
+  double v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(raddr) : "memory");
+  return v;
+}
+
 // One CTA per line. Sigma (full B x B, lower triangle used) is factored in place in
 // global memory with a blocked right-looking Cholesky: the NB-column panel is staged in
 // shared memory and factored there, and the trailing lower triangle is updated with
@@ -85,8 +114,13 @@ __host__ __device__ inline int factor_smem_doubles(int B) { return B * PS; }
 // is then built NB rows at a time: the contribution of earlier block rows is a
 // register-tiled product, and the within-block forward substitution runs per column,
 // each thread owning whole columns, so it needs no synchronisation.
-template <int PREC>
-__global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigma_all,
+// CL = 1: one CTA per line (throughput: many lines in flight). CL > 1: the CTAs of a
+// thread-block cluster share one line (latency: few lines). Each CTA then factors every
+// 16-column panel redundantly in its own shared memory, the updates and the final cast
+// are spread over all CL x FT threads, steps are separated by cluster barriers
+// (release / acquire), and data written by other CTAs is read through L2 (ld.global.cg).
+template <int PREC, int CL>
+__global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* __restrict__ sigma_all,
                                                        double* __restrict__ inv_all,
                                                        const double* __restrict__ m_all,
                                                        const double* __restrict__ dgain, int B,
@@ -95,8 +129,8 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
                                                        float* __restrict__ inv_s2_all,
                                                        int32_t* __restrict__ status, int64_t n0, int W,
                                                        int incl) {
-  const int t = blockIdx.x;
-  if (status[t] != LS_OK) return;
+  const int t = blockIdx.x / CL;
+  if (status[t] != LS_OK) return;  // same for every CTA of the cluster
   const int64_t BB = (int64_t)B * B;
   double* A = sigma_all + t * BB;
   double* Inv = inv_all + t * BB;
@@ -105,18 +139,21 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
   extern __shared__ double smem[];
   __shared__ double red[FT / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rank = CL > 1 ? (int)cluster_rank() : 0;
+  const int gtid = rank * FT + tid, gthreads = CL * FT;
+  const int gwarp = rank * (FT / 32) + warp, gwarps = CL * (FT / 32);
 
   // ---- covariance from the raw sums (lower triangle, in place) ----------------------
   // Sigma_ij = d_i d_j (S2_ij - n m_i m_j) / (n - 1), n = pixels in this line's window.
   {
     const int64_t n = n0 + (int64_t)(t + incl) * W;
     const double nn = (double)n, inv_nm1 = 1.0 / (double)(n - 1);
-    for (int i = warp; i < B; i += FT / 32) {
+    for (int i = gwarp; i < B; i += gwarps) {
       const double ai = dgain[i] * inv_nm1, nmi = nn * m[i];
       double* row = A + (int64_t)i * B;
       for (int j = lane; j <= i; j += 32) row[j] = ai * dgain[j] * fma(-nmi, m[j], row[j]);
     }
-    __syncthreads();
+    csync<CL>();
   }
 
   // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
@@ -125,7 +162,7 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
     const int kb = min(NB, B - p), rows = B - p;
     for (int e = tid; e < rows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
-      P[r * PS + j] = A[(int64_t)(p + r) * B + p + j];
+      P[r * PS + j] = ldg_c<CL>(A + (int64_t)(p + r) * B + p + j);
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
@@ -150,14 +187,14 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
     }
     for (int e = tid; e < rows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
-      if (r >= j) A[(int64_t)(p + r) * B + p + j] = P[r * PS + j];
+      if (r >= j && rank == 0) A[(int64_t)(p + r) * B + p + j] = P[r * PS + j];
     }
     // trailing update: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B
     const int mrem = rows - kb;
     if (mrem > 0) {
       const int mt = (mrem + 3) >> 2;
       const int ntiles = mt * (mt + 1) / 2;
-      for (int idx = tid; idx < ntiles; idx += FT) {
+      for (int idx = gtid; idx < ntiles; idx += gthreads) {
         int ti = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
         while (ti * (ti + 1) / 2 > idx) --ti;
         while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
@@ -169,7 +206,7 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int r = r0 + a, c = c0 + b;
-            acc[a][b] = (r < rows && c <= r) ? A[(int64_t)(p + r) * B + p + c] : 0.0;
+            acc[a][b] = (r < rows && c <= r) ? ldg_c<CL>(A + (int64_t)(p + r) * B + p + c) : 0.0;
           }
         for (int j = 0; j < kb; ++j) {
           double x[4], y[4];
@@ -192,7 +229,7 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
           }
       }
     }
-    __syncthreads();
+    csync<CL>();
   }
 
   // ---- blocked triangular inverse, right-looking: X = L^{-1} in place of R = I ------
@@ -201,23 +238,23 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
   // 4 x 4 register tiles, the same balanced shape as the Cholesky trailing update).
   // Entries above the diagonal start and stay zero.
   double* R = Inv;
-  for (int64_t e = tid; e < BB; e += FT) R[e] = ((int)(e / B) == (int)(e % B)) ? 1.0 : 0.0;
+  for (int64_t e = gtid; e < BB; e += gthreads) R[e] = ((int)(e / B) == (int)(e % B)) ? 1.0 : 0.0;
   __shared__ double rdiag[NB];  // 1 / L[r0 + r][r0 + r]
   for (int r0 = 0; r0 < B; r0 += NB) {
     const int rb = min(NB, B - r0), rows = B - r0, ncols = r0 + rb;
     for (int e = tid; e < rows * rb; e += FT) {  // panel L[r0.., r0..r0+rb)
       const int r = e / rb, j = e - r * rb;
-      P[r * PS + j] = A[(int64_t)(r0 + r) * B + r0 + j];
+      P[r * PS + j] = ldg_c<CL>(A + (int64_t)(r0 + r) * B + r0 + j);
     }
-    if (tid < rb) rdiag[tid] = 1.0 / A[(int64_t)(r0 + tid) * B + r0 + tid];
-    __syncthreads();
-    for (int c = tid; c < ncols; c += FT) {
+    if (tid < rb) rdiag[tid] = 1.0 / ldg_c<CL>(A + (int64_t)(r0 + tid) * B + r0 + tid);
+    csync<CL>();  // also publishes R (initial identity, or the previous update) cluster-wide
+    for (int c = gtid; c < ncols; c += gthreads) {
       double xr[NB];
 #pragma unroll
       for (int r = 0; r < NB; ++r) {
         xr[r] = 0.0;
         if (r < rb) {
-          double v = R[(int64_t)(r0 + r) * B + c];
+          double v = ldg_c<CL>(R + (int64_t)(r0 + r) * B + c);
 #pragma unroll
           for (int q = 0; q < r; ++q) v = fma(-P[r * PS + q], xr[q], v);
           xr[r] = v * rdiag[r];
@@ -225,11 +262,11 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
         }
       }
     }
-    __syncthreads();
+    csync<CL>();
     const int mrem = rows - rb;
     if (mrem > 0) {
       const int mt = (mrem + 3) >> 2, nct = (ncols + 3) >> 2;
-      for (int idx = tid; idx < mt * nct; idx += FT) {
+      for (int idx = gtid; idx < mt * nct; idx += gthreads) {
         const int tr = idx / nct, tcx = idx - tr * nct;
         const int j0 = rb + 4 * tr, c0 = 4 * tcx;  // j0 panel-relative row, c0 column
         double acc[4][4];
@@ -237,13 +274,13 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b)
-            acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? R[(int64_t)(r0 + j0 + a) * B + c0 + b] : 0.0;
+            acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(r0 + j0 + a) * B + c0 + b) : 0.0;
         for (int q = 0; q < rb; ++q) {
           double l[4], xq[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : 0.0;
 #pragma unroll
-          for (int b = 0; b < 4; ++b) xq[b] = (c0 + b < ncols) ? R[(int64_t)(r0 + q) * B + c0 + b] : 0.0;
+          for (int b = 0; b < 4; ++b) xq[b] = (c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(r0 + q) * B + c0 + b) : 0.0;
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -256,61 +293,128 @@ __global__ void __launch_bounds__(FT, 2) factor_kernel(double* __restrict__ sigm
             if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(r0 + j0 + a) * B + c0 + b] = acc[a][b];
       }
     }
-    __syncthreads();
+    csync<CL>();
   }
 
   // ---- G = Inv D, power-of-two scale, cast, y0 ------------------------------------
   double mx = 0.0;
-  for (int64_t e = tid; e < BB; e += FT) {
+  for (int64_t e = gtid; e < BB; e += gthreads) {
     const int k = (int)(e % B);
-    mx = fmax(mx, fabs(Inv[e] * dgain[k]));
+    mx = fmax(mx, fabs(ldg_c<CL>(Inv + e) * dgain[k]));
   }
   mx = block_max(mx, red);
+  if (CL > 1) {  // maximum over the cluster: read every CTA's partial from its shared memory
+    csync<CL>();
+    for (int r = 0; r < CL; ++r) mx = fmax(mx, ld_remote(&red[0], r));
+  }
   int ex = 0;
   frexp(mx, &ex);
   const double s = (mx > 0.0) ? ldexp(1.0, -ex) : 1.0;
   const int64_t plane = (int64_t)Bp * Bp;
   void* w = (char*)wmat + (size_t)t * plane * 4;  // 4 bytes per element pair in every format
   // one warp per output row n: write the row and accumulate y0[n] from the rounded values
-  for (int n = warp; n < Bp; n += FT / 32) {
+  for (int n = gwarp; n < Bp; n += gwarps) {
     double acc = 0.0;
     for (int k = lane; k < Bp; k += 32) {
       double v = 0.0;
-      if (n < B && k <= n) v = Inv[(int64_t)n * B + k] * dgain[k] * s;
+      if (n < B && k <= n) v = ldg_c<CL>(Inv + (int64_t)n * B + k) * dgain[k] * s;
       const double r = WOut<PREC>::store(w, plane, (int64_t)n * Bp + k, v);
       if (n < B && k <= n) acc += r * m[k];
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) y0_all[(int64_t)t * Bp + n] = (n < B) ? (float)acc : 0.0f;
   }
-  if (tid == 0) inv_s2_all[t] = (float)(1.0 / (s * s));
+  if (gtid == 0) inv_s2_all[t] = (float)(1.0 / (s * s));
+  if (CL > 1) csync<CL>();  // no CTA leaves while others may still read its shared memory
+}
+
+namespace {
+
+template <int PREC, int CL>
+cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, const double* dgain, int L, int B,
+                            void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
+                            cudaStream_t st) {
+  const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  if (CL > 8) {
+    e = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)L * CL);
+  cfg.blockDim = dim3(FT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (CL > 8) {  // a non-portable size: launch only where the device can place such a cluster
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, factor_kernel<PREC, CL>, &cfg);
+    if (e != cudaSuccess || nclusters <= 0) {
+      cudaGetLastError();
+      return cudaErrorInvalidConfiguration;
+    }
+  }
+  return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL>, sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status,
+                            n0, W, incl);
+}
+
+template <int PREC>
+cudaError_t launch_factor_p(int cl, double* sigma, double* scratch, const double* m, const double* dgain, int L,
+                            int B, void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
+                            int incl, cudaStream_t st) {
+  switch (cl) {
+    case 16: {
+      const cudaError_t e =
+          launch_factor_t<PREC, 16>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+      if (e != cudaErrorInvalidConfiguration) return e;
+      return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+    }
+    case 8: return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+    case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+    case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+    default: return launch_factor_t<PREC, 1>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+  }
+}
+
+}  // namespace
+
+// CTAs per factorisation. Few lines (latency) spread each factorisation over a cluster so
+// that about one CTA per SM is busy; many lines (throughput) give one CTA per line.
+// HSAD_FACTOR_CLUSTER = 1, 2, 4, 8 or 16 in the environment fixes the size (tuning).
+int factor_cluster_size(int L) {
+  static const int forced = [] {
+    const char* v = getenv("HSAD_FACTOR_CLUSTER");
+    const int c = v ? atoi(v) : 0;
+    return (c == 1 || c == 2 || c == 4 || c == 8 || c == 16) ? c : 0;
+  }();
+  if (forced) return forced;
+  if (L <= 19) return 8;
+  if (L <= 38) return 4;
+  if (L <= 76) return 2;
+  return 1;
 }
 
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
                           int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc) {
   if (L <= 0) return cudaSuccess;
-  dim3 grid(L), block(FT);
-  const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
-  cudaError_t e = cudaSuccess;
+  const int cl = factor_cluster_size(L);
+  cudaError_t e;
   switch (prec) {
-    case P_FP32:
-      e = cudaFuncSetAttribute(factor_kernel<P_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      factor_kernel<P_FP32><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status, n0, W, incl);
-      break;
-    case P_FP16:
-      e = cudaFuncSetAttribute(factor_kernel<P_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      factor_kernel<P_FP16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status, n0, W, incl);
-      break;
-    default:
-      e = cudaFuncSetAttribute(factor_kernel<P_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      factor_kernel<P_BF16><<<grid, block, smem, st>>>(sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status, n0, W, incl);
-      break;
+    case P_FP32: e = launch_factor_p<P_FP32>(cl, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
+    case P_FP16: e = launch_factor_p<P_FP16>(cl, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
+    default: e = launch_factor_p<P_BF16>(cl, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
   }
   if (lc) lc->n += 1;
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -83,6 +83,7 @@ def _load():
         "hsad_engine_close": (C.c_int, [P, C.c_int32]),
         "hsad_engine_counters": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "hsad_engine_destroy": (C.c_int, [P]),
+        "hsad_selftest_bounded_wait": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
         "hsad_destroy": (C.c_int, [P]),
         "hsad_last_error": (C.c_char_p, [P]),
         "hsad_status_string": (C.c_char_p, [C.c_int]),
@@ -273,6 +274,13 @@ def hsad_engine_counters(engine):
 
 def hsad_engine_destroy(engine) -> int:
     return _lib.hsad_engine_destroy(engine)
+
+
+def hsad_selftest_bounded_wait(device: int = 0, limit_cycles: int = 2_000_000):
+    """Returns ``(status, timed_out)``."""
+    flag = C.c_int32(-1)
+    rc = _lib.hsad_selftest_bounded_wait(int(device), int(limit_cycles), C.byref(flag))
+    return rc, flag.value
 
 
 def hsad_destroy(ctx) -> int:
