@@ -20,6 +20,10 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "hsad_internal.h"
 
 namespace hsad {
@@ -140,8 +144,11 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* _
   __shared__ double red[FT / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rank = CL > 1 ? (int)cluster_rank() : 0;
-  const int gtid = rank * FT + tid, gthreads = CL * FT;
-  const int gwarp = rank * (FT / 32) + warp, gwarps = CL * (FT / 32);
+  // cluster-wide warp and thread indices: warps are dealt round-robin over the CTAs and
+  // a work list is cut into warp-sized pieces, so that any prefix of it (a shrinking
+  // trailing matrix) runs as full warps spread over every CTA of the cluster
+  const int gwarp = rank + CL * warp, gwarps = CL * (FT / 32);
+  const int gtid = gwarp * 32 + lane, gthreads = CL * FT;
 
   // ---- covariance from the raw sums (lower triangle, in place) ----------------------
   // Sigma_ij = d_i d_j (S2_ij - n m_i m_j) / (n - 1), n = pixels in this line's window.
@@ -158,9 +165,15 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* _
 
   // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
   double* P = smem;  // panel: P[r * PS + j] = A[p + r][p + j]
+  __shared__ double rdg[NB];  // 1 / L[p + j][p + j] of the current panel
   for (int p = 0; p < B; p += NB) {
     const int kb = min(NB, B - p), rows = B - p;
-    for (int e = tid; e < rows * kb; e += FT) {
+    // One CTA factors the whole panel in shared memory. In a cluster every CTA factors
+    // only the kb x kb diagonal block (the same values everywhere, so a non-positive
+    // pivot exits every CTA alike) and the rows below it are solved once, spread over
+    // the cluster, then gathered by every CTA.
+    const int frows = CL == 1 ? rows : kb;
+    for (int e = tid; e < frows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
       P[r * PS + j] = ldg_c<CL>(A + (int64_t)(p + r) * B + p + j);
     }
@@ -173,19 +186,51 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* _
       }
       const double l = sqrt(piv);
       const double rl = 1.0 / l;  // one division per pivot; the column is scaled by multiplies
-      for (int r = j + 1 + tid; r < rows; r += FT) P[r * PS + j] *= rl;
+      for (int r = j + 1 + tid; r < frows; r += FT) P[r * PS + j] *= rl;
       __syncthreads();
-      if (tid == 0) P[j * PS + j] = l;
+      if (tid == 0) {
+        P[j * PS + j] = l;
+        rdg[j] = rl;
+      }
       const int nc = kb - j - 1;
       if (nc > 0) {
-        for (int e = tid; e < (rows - j - 1) * nc; e += FT) {
+        for (int e = tid; e < (frows - j - 1) * nc; e += FT) {
           const int r = j + 1 + e / nc, k = j + 1 + e % nc;
           if (k <= r) P[r * PS + k] = fma(-P[r * PS + j], P[k * PS + j], P[r * PS + k]);
         }
       }
       __syncthreads();
     }
-    for (int e = tid; e < rows * kb; e += FT) {
+    if (CL > 1) {
+      // L21 = A21 L11^{-T}: forward substitution along each row, in the same order of
+      // operations as the single-CTA column sweep above (bitwise the same factor)
+      for (int r = kb + gtid; r < rows; r += gthreads) {
+        double v[NB];
+        const double* arow = A + (int64_t)(p + r) * B + p;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v[j] = j < kb ? ldg_c<CL>(arow + j) : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (j < kb) {
+            double a = v[j];
+#pragma unroll
+            for (int q = 0; q < j; ++q) a = fma(-v[q], P[j * PS + q], a);
+            v[j] = a * rdg[j];
+          }
+        }
+        double* wrow = A + (int64_t)(p + r) * B + p;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+          if (j < kb) wrow[j] = v[j];
+      }
+      csync<CL>();
+      for (int e = tid; e < (rows - kb) * kb; e += FT) {
+        const int r = kb + e / kb, j = e - (r - kb) * kb;
+        P[r * PS + j] = ldg_c<CL>(A + (int64_t)(p + r) * B + p + j);
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < frows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
       if (r >= j && rank == 0) A[(int64_t)(p + r) * B + p + j] = P[r * PS + j];
     }
@@ -330,6 +375,43 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* _
 
 namespace {
 
+// How many clusters of CL factor CTAs the device can run at once (queried once per
+// device, working precision, cluster size and shared-memory size; 0 if none fits).
+template <int PREC, int CL>
+int factor_cluster_capacity(size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_pair(dev, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  bool ok = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) == cudaSuccess;
+  if (ok && CL > 8)
+    ok = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+         cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(FT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, factor_kernel<PREC, CL>, &cfg) != cudaSuccess) n = 0;
+  }
+  cudaGetLastError();
+  cache[key] = n;
+  return n;
+}
+
 template <int PREC, int CL>
 cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, const double* dgain, int L, int B,
                             void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
@@ -354,14 +436,8 @@ cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, con
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (CL > 8) {  // a non-portable size: launch only where the device can place such a cluster
-    int nclusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&nclusters, factor_kernel<PREC, CL>, &cfg);
-    if (e != cudaSuccess || nclusters <= 0) {
-      cudaGetLastError();
-      return cudaErrorInvalidConfiguration;
-    }
-  }
+  // a non-portable size: launch only where the device can place such a cluster
+  if (CL > 8 && factor_cluster_capacity<PREC, CL>(smem) <= 0) return cudaErrorInvalidConfiguration;
   return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL>, sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status,
                             n0, W, incl);
 }
@@ -384,34 +460,38 @@ cudaError_t launch_factor_p(int cl, double* sigma, double* scratch, const double
   }
 }
 
-}  // namespace
-
-// CTAs per factorisation. Few lines (latency) spread each factorisation over a cluster so
-// that about one CTA per SM is busy; many lines (throughput) give one CTA per line.
+// CTAs per factorisation. A cluster shortens one factorisation (the trailing updates and
+// the inverse are shared; each CTA still factors every 16-column panel), so few lines
+// (latency) take the largest cluster of which the device can run one per line at once,
+// and many lines (throughput) one CTA each.
 // HSAD_FACTOR_CLUSTER = 1, 2, 4, 8 or 16 in the environment fixes the size (tuning).
-int factor_cluster_size(int L) {
+template <int PREC>
+int factor_cluster_size(int L, size_t smem) {
   static const int forced = [] {
     const char* v = getenv("HSAD_FACTOR_CLUSTER");
     const int c = v ? atoi(v) : 0;
     return (c == 1 || c == 2 || c == 4 || c == 8 || c == 16) ? c : 0;
   }();
   if (forced) return forced;
-  if (L <= 19) return 8;
-  if (L <= 38) return 4;
-  if (L <= 76) return 2;
+  if (L <= factor_cluster_capacity<PREC, 16>(smem)) return 16;
+  if (L <= factor_cluster_capacity<PREC, 8>(smem)) return 8;
+  if (L <= factor_cluster_capacity<PREC, 4>(smem)) return 4;
+  if (L <= factor_cluster_capacity<PREC, 2>(smem)) return 2;
   return 1;
 }
+
+}  // namespace
 
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
                           int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc) {
   if (L <= 0) return cudaSuccess;
-  const int cl = factor_cluster_size(L);
+  const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   cudaError_t e;
   switch (prec) {
-    case P_FP32: e = launch_factor_p<P_FP32>(cl, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
-    case P_FP16: e = launch_factor_p<P_FP16>(cl, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
-    default: e = launch_factor_p<P_BF16>(cl, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
+    case P_FP32: e = launch_factor_p<P_FP32>(factor_cluster_size<P_FP32>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
+    case P_FP16: e = launch_factor_p<P_FP16>(factor_cluster_size<P_FP16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
+    default: e = launch_factor_p<P_BF16>(factor_cluster_size<P_BF16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
   }
   if (lc) lc->n += 1;
   if (e != cudaSuccess) return e;

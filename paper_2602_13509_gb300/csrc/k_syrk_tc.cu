@@ -38,10 +38,6 @@ constexpr int SK_MAX_PIX = 4096;                // exactness bound of one accumu
 
 __host__ __device__ inline uint32_t sk_raw_bytes(int B) { return ((uint32_t)SK_KC * B * 2 + 127) / 128 * 128; }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
-  return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
-}
 }  // namespace
 
 __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* __restrict__ x,
@@ -142,21 +138,28 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
       if (!ok) atomicExch(err, 1);
     }
   } else {
-    // ---------------- converters: thread = band row of both blocks, half of the pixels ----
-    const int i = tid & (SK_M - 1), half = tid >> 7;
-    const int bi = i0 + i, bj = j0 + i;
-    const bool vi = bi < B, vj = (!diag) && (i < N) && (bj < B);
-    const int ci = vi ? c_int[bi] : 0, cj = vj ? c_int[bj] : 0;
+    // ---------------- converters ----------------
+    // Thread = one band row and 8 consecutive pixels at a time: 8 two-byte loads from the
+    // raw chunk (a warp reads 32 consecutive bands of one pixel), then one 16-byte store
+    // of H and one of R (8 consecutive K elements of one swizzled row; the 8 rows of an
+    // atom land in 8 different bank groups). Off the diagonal the first 128 threads
+    // convert the i block (A operands), the others the j block (B operands); on the
+    // diagonal both halves convert the i block, half of the pixels each.
+    const int row = tid & (SK_M - 1), half = tid >> 7;
+    const bool jside = !diag && half == 1;
+    const int band = (jside ? j0 : i0) + row;
+    const bool valid = band < B && (!jside || row < N);
+    // x' = DN - c as an exact float: the bits of 1.5 * 2^23 + x' (|x'| < 2^22) minus 1.5 * 2^23
+    const int magic_c = 0x4B400000 - (valid ? c_int[band] : 0);
+    const int g_begin = diag ? half * (SK_KC / 16) : 0, g_end = diag ? g_begin + SK_KC / 16 : SK_KC / 8;
     for (int c = 0; c < nchunks; ++c) {
       const int s = c & 1;
       if (!tc::mbar_wait(empty + 8 * s, (uint32_t)(((c >> 1) & 1) ^ 1), limit)) {
         ok = false;
         atomicExch(err, 1);
       }
-      uint8_t* AH = sm + s * SK_STAGE;
-      uint8_t* AR = AH + SK_TILE;
-      uint8_t* BH = AH + 2 * SK_TILE;
-      uint8_t* BR = AH + 3 * SK_TILE;
+      uint8_t* OH = sm + s * SK_STAGE + (jside ? 2 * SK_TILE : 0);
+      uint8_t* OR = OH + SK_TILE;
       const int64_t pc = p_begin + (int64_t)c * SK_KC;
       const int r = bulk ? c % raw_bufs : 0;
       if (bulk && !tc::mbar_wait(rfull + 8 * r, (uint32_t)((c / raw_bufs) & 1), limit)) {
@@ -167,24 +170,28 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
       const uint16_t* src = bulk ? (const uint16_t*)(raw + r * rawb) : xg + pc * B;
       const int npx = (int)min((int64_t)SK_KC, p_end - pc);
       if (ok) {
-#pragma unroll 4
-        for (int kk = half * (SK_KC / 2); kk < (half + 1) * (SK_KC / 2); kk += 2) {
-          const bool in0 = kk < npx, in1 = kk + 1 < npx;
-          const uint32_t off = tc::sw128_offset(i, kk);
-          {
-            const float v0 = (vi && in0) ? (float)((int)src[kk * B + bi] - ci) : 0.f;
-            const float v1 = (vi && in1) ? (float)((int)src[(kk + 1) * B + bi] - ci) : 0.f;
-            const float h0 = 64.f * rintf(v0 * (1.f / 64.f)), h1 = 64.f * rintf(v1 * (1.f / 64.f));
-            *(uint32_t*)(AH + off) = pack_bf16(h0 * (1.f / 64.f), h1 * (1.f / 64.f));
-            *(uint32_t*)(AR + off) = pack_bf16(v0 - h0, v1 - h1);
+        for (int gi = g_begin; gi < g_end; ++gi) {
+          uint32_t hw[4], rw[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float hv[2], rv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int k = gi * 8 + 2 * q + u;
+              const int dn = (valid && k < npx) ? (int)src[k * B + band] : 0;
+              const float xv = (valid && k < npx) ? __int_as_float(magic_c + dn) - 12582912.0f : 0.f;
+              // h = rint(x'/64) (round to nearest even, exact: |x'/64| <= 64), r = x' - 64 h
+              const float hf = __fmaf_rn(xv, 1.f / 64.f, 12582912.0f) - 12582912.0f;
+              hv[u] = hf;
+              rv[u] = __fmaf_rn(hf, -64.f, xv);
+            }
+            // both are small integers, exact in BF16: the BF16 bits are the float's top half
+            hw[q] = __byte_perm(__float_as_uint(hv[0]), __float_as_uint(hv[1]), 0x7632);
+            rw[q] = __byte_perm(__float_as_uint(rv[0]), __float_as_uint(rv[1]), 0x7632);
           }
-          if (!diag) {
-            const float v0 = (vj && in0) ? (float)((int)src[kk * B + bj] - cj) : 0.f;
-            const float v1 = (vj && in1) ? (float)((int)src[(kk + 1) * B + bj] - cj) : 0.f;
-            const float h0 = 64.f * rintf(v0 * (1.f / 64.f)), h1 = 64.f * rintf(v1 * (1.f / 64.f));
-            *(uint32_t*)(BH + off) = pack_bf16(h0 * (1.f / 64.f), h1 * (1.f / 64.f));
-            *(uint32_t*)(BR + off) = pack_bf16(v0 - h0, v1 - h1);
-          }
+          const uint32_t off = tc::sw128_offset(row, gi * 8);
+          *(uint4*)(OH + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *(uint4*)(OR + off) = make_uint4(rw[0], rw[1], rw[2], rw[3]);
         }
       }
       tc::fence_proxy_async();
@@ -198,7 +205,8 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
     if (!dok) atomicExch(err, 1);
     const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
     double* o = out + g * out_stride;
-    const bool write = dok && ok && vi;
+    const int bi = i0 + row;  // warps 0-3: row = TMEM lane = band of the i block
+    const bool write = dok && ok && bi < B;
     // TMEM has 128 lanes, one quarter per warp of 0..3: only those warps read it
     for (int c0 = 0; warp < 4 && c0 < N; c0 += 32) {
       float hh[32], xr[32], rr[32];

@@ -148,6 +148,23 @@ def test_pushes_of_one_line_match_one_batch(hs):
     np.testing.assert_allclose(np.nan_to_num(s), np.nan_to_num(a[1]), rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("B", [16, 130])
+def test_cluster_and_single_cta_factors_agree_bitwise(hs, B):
+    """One 160-line push factors each line in one CTA; pushes of one line spread each
+    factorisation over a thread-block cluster. The covariance sums are exact and both
+    factor forms perform the same FP64 operations in the same order per element, so the
+    scores must be identical, not merely close."""
+    sc, lines = _scene_lines(160, 40, B, seed=12)
+    a = _run(hs, lines, stats_mode="exclusive", precision="fp32")
+    det = hs.Detector(width=40, bands=B, stats_mode="exclusive", precision="fp32")
+    for t in range(160):
+        det.push(lines[t:t + 1])
+    rc, s, m, st = det.scores(0, 160)
+    det.close()
+    np.testing.assert_array_equal(s, a[1])
+    np.testing.assert_array_equal(m, a[2])
+
+
 def test_not_positive_definite_is_reported(hs):
     sc, lines = _scene_lines(12, 40, 8, seed=2)
     lines = lines.copy()
