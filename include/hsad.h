@@ -65,7 +65,11 @@ enum { HSAD_HOST = 0, HSAD_DEVICE = 1 };
 /* flags */
 enum {
   HSAD_CREATE_WAIT = 1,      /* hsad_create blocks (bounded) until the device budget admits the context */
-  HSAD_NORMALIZE_SCORES = 2  /* CUBE mode: report delta / cube max instead of delta (Sec. 3.3) */
+  HSAD_NORMALIZE_SCORES = 2, /* CUBE mode: report delta / cube max instead of delta (Sec. 3.3) */
+  HSAD_CUDA_GRAPHS = 4       /* EXCLUSIVE mode, host pushes: the statistics, factor and scoring
+                                launches of a batch are captured once per batch size and replayed
+                                as a CUDA graph (same kernels, same results; fewer host calls).
+                                No counterpart in the paper. Ignored while profiling is on. */
 };
 
 typedef struct {
@@ -83,7 +87,7 @@ typedef struct {
   int64_t warmup_pixels;       /* a line is scored only once its statistics hold at least
                                   max(B + 1, warmup_pixels) pixels */
   int64_t device_budget_bytes; /* 0 = no cap for this context */
-  int32_t flags;               /* HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES */
+  int32_t flags;               /* HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES | HSAD_CUDA_GRAPHS */
   int32_t device;              /* CUDA device ordinal */
   int32_t max_batch_lines;     /* lines processed per internal batch (0 = default 256) */
   int32_t result_lines;        /* lines of scores kept for hsad_scores (0 = default) */

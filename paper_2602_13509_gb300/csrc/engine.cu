@@ -6,8 +6,10 @@
 // factor, its own CUDA stream, so the work of different streams overlaps on the device);
 // callers submit lines at any time; one worker thread repeatedly takes every stream's
 // pending lines and pushes them as one batch (lines that arrived while the stream's
-// previous batch was on the GPU form the next batch). Admission is by the device-wide
-// byte budget: a stream is opened only when its device memory fits.
+// previous batch was on the GPU form the next batch). Each stream replays a captured CUDA
+// graph per batch size for the launches after its batch's first line (HSAD_CUDA_GRAPHS).
+// Admission is by the device-wide byte budget: a stream is opened only when its device
+// memory fits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -152,6 +154,7 @@ int hsad_engine_open(hsad_engine* e, const hsad_config* cfg, int32_t* stream_id)
   if (!e || !cfg || !stream_id) return HSAD_E_INVALID;
   hsad_config c = *cfg;
   c.device = e->device;
+  c.flags |= HSAD_CUDA_GRAPHS;  // repeated small batches: replay captured launch sequences
   hsad_ctx* ctx = nullptr;
   const int rc = hsad_create(&c, &ctx);
   if (rc != HSAD_OK) return rc;

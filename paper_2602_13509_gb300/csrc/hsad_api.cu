@@ -93,6 +93,7 @@ struct hsad_ctx {
   unsigned int* dmax_bits = nullptr;
   int32_t* bad_flag = nullptr;
   int32_t* dev_err = nullptr;  // set by a kernel whose bounded wait expired
+  int64_t* bdesc = nullptr;    // per-batch values read by replayed CUDA graphs
   alignas(64) CUtensorMap gmap;  // TMA map over the 16-bit G planes (FP16/BF16 forms)
   bool have_gmap = false;
   // result ring
@@ -115,6 +116,14 @@ struct hsad_ctx {
   int64_t last_cube_lines = 0;  // lines of the most recently scored cube
   std::deque<Record> records;
   std::vector<cudaEvent_t> event_pool;
+
+  // CUDA graphs of the EXCLUSIVE batch tail, one per (lines in the batch, staging buffer)
+  bool use_graphs = false;
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;  // kernels in the graph (added to the launch counter per replay)
+  };
+  std::map<std::pair<int, int>, GraphEntry> graphs;
 
   // profiling: pending (name, begin, end) event triples and per-name totals
   bool prof_on = false;
@@ -258,7 +267,7 @@ int validate(const hsad_config* cfg, std::string* why) {
   if (cfg->device_budget_bytes < 0) return bad("device_budget_bytes must be >= 0");
   if (cfg->max_batch_lines < 0 || cfg->max_batch_lines > 65535) return bad("max_batch_lines must be in [0, 65535]");
   if (cfg->result_lines < 0) return bad("result_lines must be >= 0");
-  if (cfg->flags & ~(HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES)) return bad("unknown flags");
+  if (cfg->flags & ~(HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES | HSAD_CUDA_GRAPHS)) return bad("unknown flags");
   if ((cfg->flags & HSAD_NORMALIZE_SCORES) && cfg->stats_mode != HSAD_CUBE) return bad("HSAD_NORMALIZE_SCORES needs CUBE mode");
   if (cfg->gain)
     for (int b = 0; b < cfg->bands; ++b)
@@ -285,6 +294,8 @@ void release(hsad_ctx* ctx) {
   }
   for (int i = 0; i < 2; ++i)
     if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
+  for (auto& g : ctx->graphs)
+    if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
   for (void* p : ctx->dev_allocs) cudaFree(p);
   for (void* p : ctx->host_allocs) cudaFreeHost(p);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -313,7 +324,7 @@ bool encode_gmap(CUtensorMap* map, void* base, int64_t Bp, int64_t rows) {
   }
   const cuuint64_t dims[2] = {(cuuint64_t)Bp, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)Bp * 2};
-  const cuuint32_t box[2] = {64, 64};
+  const cuuint32_t box[2] = {64, 128};  // 64 k (128 B, the swizzle span) x two 64-row n blocks
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -424,6 +435,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->Bp = pad64(cfg->bands);
   ctx->in_type = cfg->in_dtype == HSAD_U16 ? IN_U16 : IN_F32;
   ctx->prec = cfg->precision == HSAD_FP32 ? P_FP32 : (cfg->precision == HSAD_BF16 ? P_BF16 : P_FP16);
+  ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE;
   ctx->mode = cfg->stats_mode;
   ctx->elem = ctx->in_type == IN_U16 ? 2 : 4;
   ctx->line_elems = (int64_t)ctx->W * ctx->B;
@@ -497,6 +509,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->inv_s2 = (float*)dalloc(ctx, Lf * 4, &ok);
   ctx->status = (int32_t*)dalloc(ctx, std::max(Ls, Lf) * 4, &ok);
   ctx->dmax_bits = (unsigned int*)dalloc(ctx, 64, &ok);
+  ctx->bdesc = (int64_t*)dalloc(ctx, 16, &ok);
   ctx->bad_flag = (int32_t*)((char*)ctx->dmax_bits + 32);
   ctx->dev_err = (int32_t*)((char*)ctx->dmax_bits + 48);
   ctx->r_scores = (float*)dalloc(ctx, ctx->ring * ctx->W * 4, &ok);
@@ -551,6 +564,8 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     }
     ctx->have_gmap = true;
   }
+  factor_prepare(ctx->B, ctx->prec);  // cluster capacities: off the first line's latency path
+  cudaGetLastError();
   *out = ctx;
   return HSAD_OK;
 }
@@ -629,9 +644,78 @@ int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* ou
 // line is scored at once and its completion recorded before any statistics work; the
 // statistics through each line of the batch then give the factors of the next lines
 // (slots 1..L), and slot L is carried to slot 0 for the next batch.
-int stream_batch_excl(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
+// Everything of an EXCLUSIVE batch after its first line is scored: the batch's statistics,
+// the factors of slots 1..L, the scores of lines 1..L-1 and the carry of slot L to slot 0.
+// With dev = true the per-batch values (pixels before the batch, ring slot of line 1) are
+// read from ctx->bdesc at run time, so that the launches can be captured once and replayed.
+int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   const int W = ctx->W, B = ctx->B, Bp = ctx->Bp;
   const int64_t BB = (int64_t)B * B;
+  cudaStream_t st = ctx->stream;
+  const int64_t* n0_dev = dev ? ctx->bdesc : nullptr;
+  CK(cudaMemsetAsync(ctx->status + 1, 0, (size_t)L * 4, st));
+  KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
+  {
+    int rc = syrk(ctx, x, L, W, ctx->sigma + BB, BB, false);
+    if (rc != HSAD_OK) return rc;
+  }
+  KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, 1,
+                                       ctx->min_pix, ctx->status + 1, st, &ctx->lc, n0_dev));
+  KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc));
+  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, ctx->dgain, L, B, ctx->prec,
+                             (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
+                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev));
+  if (L > 1) {
+    ScoreOut o1 = score_out(ctx, first + 1, true);
+    o1.factor_base = 1;
+    if (dev) o1.slot0_dev = ctx->bdesc + 1;
+    int rc = whiten(ctx, (const char*)x + ctx->line_bytes, L - 1, 1, o1);
+    if (rc != HSAD_OK) return rc;
+  }
+  // carry the factor of all statistics so far to slot 0
+  const size_t wb = (size_t)Bp * Bp * 4;
+  CK(cudaMemcpyAsync(ctx->wmat, (char*)ctx->wmat + (size_t)L * wb, wb, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->y0, ctx->y0 + (size_t)L * Bp, (size_t)Bp * 4, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->inv_s2, ctx->inv_s2 + L, 4, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->status, ctx->status + L, 4, cudaMemcpyDeviceToDevice, st));
+  return HSAD_OK;
+}
+
+// The replayable graph of excl_tail for (L, staging buffer s), captured on first use.
+// Returns nullptr if capture or instantiation fails (the caller then launches directly).
+hsad_ctx::GraphEntry* excl_graph(hsad_ctx* ctx, const void* x, int L, int s, uint64_t first) {
+  auto key = std::make_pair(L, s);
+  auto it = ctx->graphs.find(key);
+  if (it != ctx->graphs.end()) return it->second.exec ? &it->second : nullptr;
+  hsad_ctx::GraphEntry ge;
+  cudaGraph_t graph = nullptr;
+  const int64_t lc0 = ctx->lc.n;
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const int rc = excl_tail(ctx, x, L, first, true);
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc == HSAD_OK && e == cudaSuccess && graph) {
+      if (cudaGraphInstantiate(&ge.exec, graph, 0) != cudaSuccess) ge.exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  ge.launches = ctx->lc.n - lc0;
+  ctx->lc.n = lc0;  // captured, not launched
+  cudaGetLastError();
+  ctx->failed = false;  // a failed capture launched nothing; the batch runs directly
+  ctx->err.clear();
+  auto& slot = ctx->graphs[key];
+  slot = ge;
+  return slot.exec ? &slot : nullptr;
+}
+
+// One EXCLUSIVE batch (Sec. 6.1 line-based form) of L lines starting at line `first`.
+// Line t is scored against the statistics of lines [r, t). Pipelining: slot 0 holds the
+// factor of all statistics before the batch, so the batch's first line is scored before
+// anything else and its scores become readable at once; the batch's own statistics then
+// give the factors of slots 1..L (slot k: lines before line k of the batch), lines 1..L-1
+// are scored with slots 1..L-1, and slot L is carried to slot 0 for the next batch.
+int stream_batch_excl(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
+  const int W = ctx->W, B = ctx->B;
   cudaStream_t st = ctx->stream;
   if (ctx->n_stats == 0) {  // no statistics before this line: not ready
     CK(cudaMemsetAsync(ctx->status, 0, 4, st));
@@ -644,31 +728,22 @@ int stream_batch_excl(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
     if (rc == HSAD_OK) rc = add_record(ctx, first, 1);
     if (rc != HSAD_OK) return rc;
   }
-  CK(cudaMemsetAsync(ctx->status + 1, 0, (size_t)L * 4, st));
-  KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
-  {
-    int rc = syrk(ctx, x, L, W, ctx->sigma + BB, BB, false);
+  const int s = x == ctx->d_stage[0] ? 0 : (x == ctx->d_stage[1] ? 1 : -1);
+  hsad_ctx::GraphEntry* ge = nullptr;
+  if (ctx->use_graphs && !ctx->prof_on && ctx->n_stats > 0 && s >= 0) ge = excl_graph(ctx, x, L, s, first);
+  if (ge) {
+    KL("set_batch_desc", launch_set_batch_desc(ctx->bdesc, ctx->n_stats,
+                                               (int64_t)((first + 1) % (uint64_t)ctx->ring), st, &ctx->lc));
+    CK(cudaGraphLaunch(ge->exec, st));
+    ctx->lc.n += ge->launches;
+  } else {
+    int rc = excl_tail(ctx, x, L, first, false);
     if (rc != HSAD_OK) return rc;
   }
-  KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, 1,
-                                       ctx->min_pix, ctx->status + 1, st, &ctx->lc));
-  KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc));
-  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, ctx->dgain, L, B, ctx->prec,
-                             (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
-                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc));
   if (L > 1) {
-    ScoreOut o1 = score_out(ctx, first + 1, true);
-    o1.factor_base = 1;
-    int rc = whiten(ctx, (const char*)x + ctx->line_bytes, L - 1, 1, o1);
-    if (rc == HSAD_OK) rc = add_record(ctx, first + 1, (uint64_t)(L - 1));
+    int rc = add_record(ctx, first + 1, (uint64_t)(L - 1));
     if (rc != HSAD_OK) return rc;
   }
-  // carry the factor of all statistics so far to slot 0
-  const size_t wb = (size_t)Bp * Bp * 4;
-  CK(cudaMemcpyAsync(ctx->wmat, (char*)ctx->wmat + (size_t)L * wb, wb, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ctx->y0, ctx->y0 + (size_t)L * Bp, (size_t)Bp * 4, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ctx->inv_s2, ctx->inv_s2 + L, 4, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ctx->status, ctx->status + L, 4, cudaMemcpyDeviceToDevice, st));
   ctx->n_stats += (int64_t)L * W;
   return HSAD_OK;
 }

@@ -51,7 +51,12 @@ cudaError_t launch_syrk_simt(const void* x, int64_t n_groups, int64_t pix_per_gr
 // readiness, and the updated state S1.
 cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
                                int W, int L, int B, int inclusive, int64_t min_pixels,
-                               int32_t* status, cudaStream_t st, LaunchCounter* lc);
+                               int32_t* status, cudaStream_t st, LaunchCounter* lc,
+                               const int64_t* n0_dev = nullptr);
+// Writes the per-batch values a replayed CUDA graph reads: desc[0] = pixels in the
+// statistics before the batch, desc[1] = ring slot of the batch's second line.
+cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1, cudaStream_t st,
+                                  LaunchCounter* lc);
 
 // K3b: running raw sums S2_t (lower triangle) written in place over the per-line SYRK
 // results, and the updated state S2. The factor kernel turns them into Sigma_t.
@@ -75,9 +80,14 @@ cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, 
 // m[t]: Sigma_t = D (S2_t - n_t m_t m_t^T) D / (n_t - 1) with n_t = n0 + (t + incl) W,
 // FP64 Cholesky and triangular inverse in place, then G_t = s_t L^{-1} D cast to the
 // working precision, y0 and 1/s_t^2. scratch: [L][B][B] FP64.
+// Query and cache, once per device, B and precision, how many clusters of each size the
+// factor kernel can run at once (host calls that must not land on a line's latency path).
+void factor_prepare(int B, int prec);
+// n0_dev: if set, n0 is read there at run time (replayed CUDA graphs).
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
-                          int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc);
+                          int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
+                          const int64_t* n0_dev = nullptr);
 
 // K6 (SIMT): delta_p = inv_s2 * || G (x_p - c) - y0 ||^2 for every pixel of every line,
 // threshold, and scatter into the result ring. factor_stride = 0 makes every line
@@ -91,7 +101,11 @@ struct ScoreOut {
   float tau;
   int write_mask;    // 1: mask = delta > tau here; 0: left to the cube normaliser
   int factor_base = 0;  // factor slot of line 0 (slots advance with factor_stride)
+  const int64_t* slot0_dev = nullptr;  // if set, slot0 is read here (replayed CUDA graphs)
 };
+#ifdef __CUDACC__
+__device__ __forceinline__ int64_t slot0_of(const ScoreOut& o) { return o.slot0_dev ? *o.slot0_dev : o.slot0; }
+#endif
 cudaError_t launch_whiten_score_simt(const void* x, int L, int W, int B, int in_type,
                                      const int32_t* c_int, const float* c_flt, int prec,
                                      const void* wmat, const float* y0, const float* inv_s2,

@@ -29,7 +29,7 @@
 namespace hsad {
 
 namespace {
-constexpr int FT = 256;  // threads per factorisation CTA
+constexpr int FT_CLUSTER = 256;  // threads per factorisation CTA in a cluster
 
 template <int PREC>
 struct WOut;
@@ -62,6 +62,7 @@ struct WOut<P_BF16> {
   }
 };
 
+template <int FT>
 __device__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -123,16 +124,16 @@ __device__ __forceinline__ double ld_remote(const double* local, int rank) {
 // 16-column panel redundantly in its own shared memory, the updates and the final cast
 // are spread over all CL x FT threads, steps are separated by cluster barriers
 // (release / acquire), and data written by other CTAs is read through L2 (ld.global.cg).
-template <int PREC, int CL>
-__global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* __restrict__ sigma_all,
+template <int PREC, int CL, int FT>
+__global__ void __launch_bounds__(FT, (CL == 1 ? 512 / FT : 1)) factor_kernel(double* __restrict__ sigma_all,
                                                        double* __restrict__ inv_all,
                                                        const double* __restrict__ m_all,
                                                        const double* __restrict__ dgain, int B,
                                                        void* __restrict__ wmat,
                                                        float* __restrict__ y0_all,
                                                        float* __restrict__ inv_s2_all,
-                                                       int32_t* __restrict__ status, int64_t n0, int W,
-                                                       int incl) {
+                                                       int32_t* __restrict__ status, int64_t n0_arg, int W,
+                                                       int incl, const int64_t* __restrict__ n0_dev) {
   const int t = blockIdx.x / CL;
   if (status[t] != LS_OK) return;  // same for every CTA of the cluster
   const int64_t BB = (int64_t)B * B;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* _
   // ---- covariance from the raw sums (lower triangle, in place) ----------------------
   // Sigma_ij = d_i d_j (S2_ij - n m_i m_j) / (n - 1), n = pixels in this line's window.
   {
-    const int64_t n = n0 + (int64_t)(t + incl) * W;
+    const int64_t n = (n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W;
     const double nn = (double)n, inv_nm1 = 1.0 / (double)(n - 1);
     for (int i = gwarp; i < B; i += gwarps) {
       const double ai = dgain[i] * inv_nm1, nmi = nn * m[i];
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 2 : 1)) factor_kernel(double* _
     const int k = (int)(e % B);
     mx = fmax(mx, fabs(ldg_c<CL>(Inv + e) * dgain[k]));
   }
-  mx = block_max(mx, red);
+  mx = block_max<FT>(mx, red);
   if (CL > 1) {  // maximum over the cluster: read every CTA's partial from its shared memory
     csync<CL>();
     for (int r = 0; r < CL; ++r) mx = fmax(mx, ld_remote(&red[0], r));
@@ -377,7 +378,7 @@ namespace {
 
 // How many clusters of CL factor CTAs the device can run at once (queried once per
 // device, working precision, cluster size and shared-memory size; 0 if none fits).
-template <int PREC, int CL>
+template <int PREC, int CL, int FT = FT_CLUSTER>
 int factor_cluster_capacity(size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> cache;
@@ -388,10 +389,10 @@ int factor_cluster_capacity(size_t smem) {
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   int n = 0;
-  bool ok = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  bool ok = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) == cudaSuccess;
   if (ok && CL > 8)
-    ok = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+    ok = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
          cudaSuccess;
   if (ok) {
     cudaLaunchConfig_t cfg = {};
@@ -405,23 +406,23 @@ int factor_cluster_capacity(size_t smem) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&n, factor_kernel<PREC, CL>, &cfg) != cudaSuccess) n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, factor_kernel<PREC, CL, FT>, &cfg) != cudaSuccess) n = 0;
   }
   cudaGetLastError();
   cache[key] = n;
   return n;
 }
 
-template <int PREC, int CL>
+template <int PREC, int CL, int FT = FT_CLUSTER>
 cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, const double* dgain, int L, int B,
                             void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
-                            cudaStream_t st) {
+                            cudaStream_t st, const int64_t* n0_dev) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   if (CL > 8) {
-    e = cudaFuncSetAttribute(factor_kernel<PREC, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
@@ -437,26 +438,43 @@ cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, con
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // a non-portable size: launch only where the device can place such a cluster
-  if (CL > 8 && factor_cluster_capacity<PREC, CL>(smem) <= 0) return cudaErrorInvalidConfiguration;
-  return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL>, sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status,
-                            n0, W, incl);
+  if (CL > 8 && factor_cluster_capacity<PREC, CL, FT>(smem) <= 0) return cudaErrorInvalidConfiguration;
+  return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL, FT>, sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status,
+                            n0, W, incl, n0_dev);
+}
+
+// Threads of a one-CTA-per-line factorisation: 128 (4 CTAs per SM, so that one CTA's
+// barrier-bound panel step overlaps other CTAs' updates; measured 62.2 ms against
+// 66.6 ms for 256 threads on 4000 lines of B = 270) or 256 (2 CTAs per SM).
+// HSAD_FACTOR_THREADS = 128 or 256 in the environment fixes it (tuning).
+int factor_single_threads() {
+  static const int n = [] {
+    const char* v = getenv("HSAD_FACTOR_THREADS");
+    const int c = v ? atoi(v) : 0;
+    return (c == 128 || c == 256) ? c : 128;
+  }();
+  return n;
 }
 
 template <int PREC>
 cudaError_t launch_factor_p(int cl, double* sigma, double* scratch, const double* m, const double* dgain, int L,
                             int B, void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
-                            int incl, cudaStream_t st) {
+                            int incl, cudaStream_t st, const int64_t* n0_dev) {
   switch (cl) {
     case 16: {
       const cudaError_t e =
-          launch_factor_t<PREC, 16>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+          launch_factor_t<PREC, 16>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
       if (e != cudaErrorInvalidConfiguration) return e;
-      return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+      return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
     }
-    case 8: return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
-    case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
-    case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
-    default: return launch_factor_t<PREC, 1>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st);
+    case 8: return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
+    case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
+    case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
+    default:
+      if (factor_single_threads() == 128)
+        return launch_factor_t<PREC, 1, 128>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl,
+                                             st, n0_dev);
+      return launch_factor_t<PREC, 1, 256>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
   }
 }
 
@@ -482,16 +500,32 @@ int factor_cluster_size(int L, size_t smem) {
 
 }  // namespace
 
+void factor_prepare(int B, int prec) {
+  const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
+#define HSAD_FP(P)                             \
+  factor_cluster_capacity<P, 16>(smem);        \
+  factor_cluster_capacity<P, 8>(smem);         \
+  factor_cluster_capacity<P, 4>(smem);         \
+  factor_cluster_capacity<P, 2>(smem)
+  switch (prec) {
+    case P_FP32: HSAD_FP(P_FP32); break;
+    case P_FP16: HSAD_FP(P_FP16); break;
+    default: HSAD_FP(P_BF16); break;
+  }
+#undef HSAD_FP
+}
+
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
-                          int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc) {
+                          int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
+                          const int64_t* n0_dev) {
   if (L <= 0) return cudaSuccess;
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   cudaError_t e;
   switch (prec) {
-    case P_FP32: e = launch_factor_p<P_FP32>(factor_cluster_size<P_FP32>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
-    case P_FP16: e = launch_factor_p<P_FP16>(factor_cluster_size<P_FP16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
-    default: e = launch_factor_p<P_BF16>(factor_cluster_size<P_BF16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st); break;
+    case P_FP32: e = launch_factor_p<P_FP32>(factor_cluster_size<P_FP32>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
+    case P_FP16: e = launch_factor_p<P_FP16>(factor_cluster_size<P_FP16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
+    default: e = launch_factor_p<P_BF16>(factor_cluster_size<P_BF16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
   }
   if (lc) lc->n += 1;
   if (e != cudaSuccess) return e;

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) whiten_score_kernel(
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * WS_P;
   const int f = out.factor_base + (factor_stride ? t : 0);
-  const int64_t slot = (out.slot0 + t) % out.ring;
+  const int64_t slot = (slot0_of(out) + t) % out.ring;
   const int st = status[f];
   if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;
   if (st != LS_OK) {
@@ -228,7 +228,7 @@ __global__ void cube_max_kernel(ScoreOut out, int64_t n_lines, int W, unsigned i
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t line = i / W, p = i % W;
-    const float v = out.scores[((out.slot0 + line) % out.ring) * W + p];
+    const float v = out.scores[((slot0_of(out) + line) % out.ring) * W + p];
     if (v > mx) mx = v;  // NaN compares false
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -242,7 +242,7 @@ __global__ void cube_norm_kernel(ScoreOut out, int64_t n_lines, int W, int rel, 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t line = i / W, p = i % W;
-    const int64_t at = ((out.slot0 + line) % out.ring) * W + p;
+    const int64_t at = ((slot0_of(out) + line) % out.ring) * W + p;
     const float v = out.scores[at];
     const float r = v / dmax;
     out.mask[at] = (rel ? (r > out.tau) : (v > out.tau)) ? 1 : 0;

@@ -250,8 +250,10 @@ cudaError_t launch_syrk_simt(const void* x, int64_t n_groups, int64_t pix_per_gr
 // One warp per band scans 32 lines at a time with shuffles (u16 sums are exact
 // integers, so the scan order does not change them).
 __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* __restrict__ m_out,
-                                   double* __restrict__ state_s1, int64_t n0, int W, int L, int B,
-                                   int inclusive, int64_t min_pixels, int32_t* __restrict__ status) {
+                                   double* __restrict__ state_s1, int64_t n0_arg, int W, int L, int B,
+                                   int inclusive, int64_t min_pixels, int32_t* __restrict__ status,
+                                   const int64_t* __restrict__ n0_dev) {
+  const int64_t n0 = n0_dev ? *n0_dev : n0_arg;
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (b < B) {
@@ -283,9 +285,20 @@ __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* _
 
 cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
                                int W, int L, int B, int inclusive, int64_t min_pixels,
-                               int32_t* status, cudaStream_t st, LaunchCounter* lc) {
+                               int32_t* status, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev) {
   prefix_mean_kernel<<<(B + 7) / 8, 256, 0, st>>>(s1_line, m_out, state_s1, n0, W, L, B, inclusive,
-                                                  min_pixels, status);
+                                                  min_pixels, status, n0_dev);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+__global__ void set_batch_desc_kernel(int64_t* desc, int64_t n_stats, int64_t slot1) {
+  desc[0] = n_stats;
+  desc[1] = slot1;
+}
+
+cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1, cudaStream_t st,
+                                  LaunchCounter* lc) {
+  set_batch_desc_kernel<<<1, 1, 0, st>>>(desc, n_stats, slot1);
   HSAD_LAUNCH_CHECK(lc);
 }
 

@@ -6,15 +6,18 @@
 // One CTA scores one tile of 128 pixels of one line:
 //   warp 4 (one lane)  copy engine: the tile's raw values (128 pixels x B bands are
 //                      contiguous in the BIP layout) in one bulk copy when aligned and it
-//                      fits, then 64 x 64 blocks (n, k) of the hi and lo planes of G by
-//                      TMA into a ring of 2 or 4 stages with the 128-byte swizzle; only
-//                      blocks with n-block >= k-block (G is lower triangular).
+//                      fits, then 128 x 64 blocks (n, k) (two 64-row n blocks) of the hi
+//                      and lo planes of G by TMA into a ring of 2 to 4 stages with the
+//                      128-byte swizzle; only blocks with n-block >= k-block (G is lower
+//                      triangular).
 //   warps 0-3          convert the pixels' value - c of one 64-band block into the A
 //                      operand (FP16: one plane; BF16: H = 64 rint(x'/64) and R = x' - H,
 //                      both exact for integer input) in the same swizzled K-major layout,
-//                      double buffered; afterwards the same 128 threads are the epilogue,
-//                      one pixel (TMEM lane) each.
-//   warp 5 (one lane)  issues tcgen05.mma (M = 128, N = 64, K = 16) into a 128 x Bp FP32
+//                      double buffered: a thread takes 8 consecutive bands of one pixel
+//                      and writes them with one 16-byte store per plane (8 threads fill a
+//                      128-byte row, conflict free); afterwards the same 128 threads are
+//                      the epilogue, one pixel (TMEM lane) each.
+//   warp 5 (one lane)  issues tcgen05.mma (M = 128, N = 128 or 64, K = 16) into a 128 x Bp FP32
 //                      accumulator in TMEM: FP16 terms x'.G_hi + x'.G_lo, BF16 terms
 //                      H.G_hi + H.G_lo + R.G_hi; commits free the smem stages.
 // Every wait is bounded; a timeout sets *err and the CTA drains and exits.
@@ -30,9 +33,9 @@
 namespace hsad {
 
 namespace {
-constexpr int WT_M = 128, WT_KB = 64, WT_NB = 64, WT_MAX_STAGES = 4, WT_THREADS = 192;
+constexpr int WT_M = 128, WT_KB = 64, WT_NB = 64, WT_NPAIR = 128, WT_MAX_STAGES = 4, WT_THREADS = 192;
 constexpr uint32_t A_TILE = WT_M * WT_KB * 2;     // 16 KB
-constexpr uint32_t B_TILE = WT_NB * WT_KB * 2;    // 8 KB per plane
+constexpr uint32_t B_TILE = WT_NPAIR * WT_KB * 2; // 16 KB per plane: two 64-row blocks of n
 constexpr uint32_t SMEM_A = 2 * 2 * A_TILE;       // 2 buffers x 2 operands
 constexpr uint32_t SMEM_BAR = 128;
 constexpr uint32_t SMEM_MAX = 227 * 1024;
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * WT_M;
   const int f = out.factor_base + (factor_stride ? t : 0);
-  const int64_t slot = (out.slot0 + t) % out.ring;
+  const int64_t slot = (slot0_of(out) + t) % out.ring;
   const int st = status[f];
   if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;
   if (st != LS_OK) {
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
       }
       int it = 0;
       for (int kb = 0; kb < nkb && ok; ++kb)
-        for (int nb = kb; nb < nkb && ok; ++nb, ++it) {
+        for (int nb = kb; nb < nkb && ok; nb += 2, ++it) {
           const int s = it % stages;
           const uint32_t use = (uint32_t)(it / stages);
           if (!tc::mbar_wait(b_empty + 8 * s, (use & 1) ^ 1, limit)) { ok = false; break; }
@@ -153,7 +156,8 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
   } else if (warp == 5) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_f16(PREC == P_BF16 ? 1 : 0, WT_M, WT_NB);
+      const uint32_t idesc2 = tc::idesc_f16(PREC == P_BF16 ? 1 : 0, WT_M, WT_NPAIR);
+      const uint32_t idesc1 = tc::idesc_f16(PREC == P_BF16 ? 1 : 0, WT_M, WT_NB);
       int it = 0;
       bool issued_any = false;
       for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -162,7 +166,8 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
         tc::fence_after_sync();
         const uint32_t a0 = tc::smem_u32(sA + (ab * 2 + 0) * A_TILE);
         const uint32_t a1 = tc::smem_u32(sA + (ab * 2 + 1) * A_TILE);
-        for (int nb = kb; nb < nkb; ++nb, ++it) {
+        for (int nb = kb; nb < nkb; nb += 2, ++it) {
+          const uint32_t idesc = nb + 1 < nkb ? idesc2 : idesc1;
           const int s = it % stages;
           if (!tc::mbar_wait(b_full + 8 * s, (uint32_t)((it / stages) & 1), limit)) { ok = false; break; }
           tc::fence_after_sync();
@@ -192,41 +197,106 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
     }
   } else {
     // ---------------- converters (warps 0-3) ----------------
-    const int kk = tid & 63, g = tid >> 6;
     if (raw_tile && !tc::mbar_wait(raw_full, 0, limit)) {
       ok = false;
       atomicExch(err, 1);
     }
     // raw values of pixel r, band k: shared memory when staged, else global
     const In* src = raw_tile ? (const In*)sRaw : xl + (int64_t)p0 * B;
+    // unit = (pixel row, 8 consecutive bands); thread tid takes units tid + 128 i, so its
+    // band group kg = tid % 8 is the same in every unit
+    const int kg = tid & 7;
+    const bool vec = (sizeof(In) == 2) && (B % 8 == 0) && (((uintptr_t)src & 15) == 0);
     for (int kb = 0; kb < nkb; ++kb) {
       const int ab = kb & 1;
       if (!tc::mbar_wait(a_empty + 8 * ab, (uint32_t)(((kb >> 1) & 1) ^ 1), limit)) {
         ok = false;
         atomicExch(err, 1);
       }
-      const int k = kb * WT_KB + kk;
       uint8_t* A0 = sA + (ab * 2 + 0) * A_TILE;
       uint8_t* A1 = sA + (ab * 2 + 1) * A_TILE;
+      const int k0 = kb * WT_KB + kg * 8;
       if (ok) {
-#pragma unroll 8
-        for (int r = g; r < WT_M; r += 2) {
-          float v = 0.f;
-          if (r < npx && k < B) v = centred_tc<In>(src[(int64_t)r * B + k], c_int, c_flt, k);
-          const uint32_t off = tc::sw128_offset(r, kk);
-          if (PREC == P_FP16) {
-            *(__half*)(A0 + off) = __float2half_rn(v);
-          } else {
-            float h, rr;
-            if (sizeof(In) == 2) {
-              h = 64.f * rintf(v * (1.f / 64.f));
-              rr = v - h;
-            } else {
-              h = __bfloat162float(__float2bfloat16_rn(v));
-              rr = v - h;
+        if (sizeof(In) == 2) {
+          // x' = DN - c as an exact float: the bits of 1.5 * 2^23 + x' minus 1.5 * 2^23
+          int mc[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) mc[j] = 0x4B400000 - (k0 + j < B ? c_int[k0 + j] : 0);
+          // 16-byte rows: issue this thread's 8 unit loads together (8 in flight per thread)
+          uint4 qv[8];
+          if (vec) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int r = (tid + WT_M * i) >> 3;
+              qv[i] = (r < npx && k0 + 8 <= B) ? *(const uint4*)((const uint16_t*)src + (int64_t)r * B + k0)
+                                               : make_uint4(0, 0, 0, 0);
             }
-            *(__nv_bfloat16*)(A0 + off) = __float2bfloat16_rn(h);
-            *(__nv_bfloat16*)(A1 + off) = __float2bfloat16_rn(rr);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int u = tid + WT_M * i;
+            const int r = u >> 3;
+            const bool rv = r < npx;
+            int dn[8];
+            if (vec && k0 + 8 <= B) {
+              const uint32_t w[4] = {qv[i].x, qv[i].y, qv[i].z, qv[i].w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                dn[2 * j] = (int)(w[j] & 0xffffu);
+                dn[2 * j + 1] = (int)(w[j] >> 16);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                dn[j] = (rv && k0 + j < B) ? (int)((const uint16_t*)src)[(int64_t)r * B + k0 + j] : 0;
+            }
+            uint32_t p0w[4], p1w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float v[2];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int jj = 2 * j + e;
+                v[e] = (rv && k0 + jj < B) ? __int_as_float(mc[jj] + dn[jj]) - 12582912.0f : 0.f;
+              }
+              if (PREC == P_FP16) {
+                const __half2 h2 = __floats2half2_rn(v[0], v[1]);
+                p0w[j] = *(const uint32_t*)&h2;
+              } else {
+                // H = 64 rint(x'/64) (round to nearest even), R = x' - H: small integers times
+                // powers of two, exact in BF16, whose bits are the float's top half
+                float h[2], rr[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                  h[e] = (__fmaf_rn(v[e], 1.f / 64.f, 12582912.0f) - 12582912.0f) * 64.f;
+                  rr[e] = v[e] - h[e];
+                }
+                p0w[j] = __byte_perm(__float_as_uint(h[0]), __float_as_uint(h[1]), 0x7632);
+                p1w[j] = __byte_perm(__float_as_uint(rr[0]), __float_as_uint(rr[1]), 0x7632);
+              }
+            }
+            const uint32_t off = tc::sw128_offset(r, kg * 8);
+            *(uint4*)(A0 + off) = make_uint4(p0w[0], p0w[1], p0w[2], p0w[3]);
+            if (PREC != P_FP16) *(uint4*)(A1 + off) = make_uint4(p1w[0], p1w[1], p1w[2], p1w[3]);
+          }
+        } else {
+          // float input: one value at a time (BF16: H = bf16(v), R = bf16(v - H))
+          for (int u = tid; u < WT_M * 8; u += WT_M) {
+            const int r = u >> 3;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int k = k0 + j;
+              float v = 0.f;
+              if (r < npx && k < B) v = centred_tc<In>(src[(int64_t)r * B + k], c_int, c_flt, k);
+              const uint32_t off = tc::sw128_offset(r, kg * 8 + j);
+              if (PREC == P_FP16) {
+                *(__half*)(A0 + off) = __float2half_rn(v);
+              } else {
+                const float h = __bfloat162float(__float2bfloat16_rn(v));
+                *(__nv_bfloat16*)(A0 + off) = __float2bfloat16_rn(h);
+                *(__nv_bfloat16*)(A1 + off) = __float2bfloat16_rn(v - h);
+              }
+            }
           }
         }
       }
@@ -282,11 +352,14 @@ cudaError_t launch_whiten_tc(const void* x, int L, int W, int B, int in_type, co
   const bool aligned = ((uintptr_t)x % 16 == 0) && (((int64_t)W * B * esz) % 16 == 0) &&
                        (((int64_t)(W % WT_M) * B * esz) % 16 == 0);
   const uint32_t rawb = (uint32_t)(((int64_t)WT_M * B * esz + 127) / 128 * 128);
+  // the deepest G ring that leaves room for the raw tile; else read the pixels from global
   int stages = WT_MAX_STAGES, raw_tile = 0;
-  if (aligned) {
-    if (wt_fixed_smem(4, pad64(B)) + rawb <= SMEM_MAX) raw_tile = 1;
-    else if (wt_fixed_smem(2, pad64(B)) + rawb <= SMEM_MAX) { raw_tile = 1; stages = 2; }
-  }
+  if (aligned)
+    for (int sg = WT_MAX_STAGES; sg >= 2 && !raw_tile; --sg)
+      if (wt_fixed_smem(sg, pad64(B)) + rawb <= SMEM_MAX) {
+        raw_tile = 1;
+        stages = sg;
+      }
   const uint32_t smem = wt_fixed_smem(stages, pad64(B)) + (raw_tile ? rawb : 0);
   cudaError_t e = cudaSuccess;
 #define HSAD_WT(IN, P)                                                                                  \

@@ -24,7 +24,7 @@ HSAD_FP32, HSAD_BF16, HSAD_FP16 = 0, 1, 2
 HSAD_EXCLUSIVE, HSAD_INCLUSIVE, HSAD_CUBE = 0, 1, 2
 HSAD_ABS, HSAD_REL = 0, 1
 HSAD_HOST, HSAD_DEVICE = 0, 1
-HSAD_CREATE_WAIT, HSAD_NORMALIZE_SCORES = 1, 2
+HSAD_CREATE_WAIT, HSAD_NORMALIZE_SCORES, HSAD_CUDA_GRAPHS = 1, 2, 4
 # per-line status
 LS_OK, LS_NOT_READY, LS_NOT_PD, LS_INVALID_DATA = 0, 1, 2, 3
 

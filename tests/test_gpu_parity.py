@@ -165,6 +165,30 @@ def test_cluster_and_single_cta_factors_agree_bitwise(hs, B):
     np.testing.assert_array_equal(m, a[2])
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_cuda_graph_replay_matches_direct_launches(hs, prec):
+    """HSAD_CUDA_GRAPHS replays a captured launch sequence per batch size; the kernels and
+    their arguments are those of the direct path, so the scores must be identical."""
+    sc, lines = _scene_lines(90, 72, 40, seed=13)
+    out = []
+    for flags in (0, hs.HSAD_CUDA_GRAPHS):
+        det = hs.Detector(width=72, bands=40, stats_mode="exclusive", precision=prec, flags=flags)
+        t = 0
+        for n in [1, 1, 2, 1, 3, 3, 1, 2] * 10:   # repeated batch sizes: captured once, replayed
+            if t + n > 90:
+                break
+            det.push(lines[t:t + n])
+            t += n
+        rc, s, m, st = det.scores(0, t)
+        launches = det.kernel_launches
+        det.close()
+        out.append((s, m, st, launches))
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    np.testing.assert_array_equal(out[1][1], out[0][1])
+    np.testing.assert_array_equal(out[1][2], out[0][2])
+    assert out[1][3] >= out[0][3]  # every replayed kernel is counted (plus one descriptor write per batch)
+
+
 def test_not_positive_definite_is_reported(hs):
     sc, lines = _scene_lines(12, 40, 8, seed=2)
     lines = lines.copy()
