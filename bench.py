@@ -252,6 +252,9 @@ def run_stress(args, hs, local, world, rank, peaks):
     specs = stress_cubes(32)
     if args.stress_cubes:
         specs = specs[:args.stress_cubes]
+    if args.cube:  # one cube of a given shape (small cases for profiling)
+        Lc, Wc, Bc = (int(v) for v in args.cube.split(","))
+        specs = [dict(lines=Lc, width=Wc, bands=Bc, seed=specs[0]["seed"])]
     max_elems = max(s["lines"] * s["width"] * s["bands"] for s in specs)
     max_px = max(s["lines"] * s["width"] for s in specs)
     buf = torch.empty(max_elems, dtype=torch.int16, device=f"cuda:{local}")
@@ -314,7 +317,8 @@ def main_stress(args):
            "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": b["seconds"] * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
            "data": "synthetic (drawn on the device)",
-           "config": {"workload": "stress_32_cubes", "cubes": b["cubes"], "stats": "cube (global RX)",
+           "config": {"workload": f"cube_{args.cube.replace(',', 'x')}" if args.cube else "stress_32_cubes",
+                      "cubes": b["cubes"], "stats": "cube (global RX)",
                       "input": "uint16 12-bit DN", "l2": "cubes larger than L2"},
            "fp32_path": res["fp32"], "bf16_path": b, "gpu_launches": b["gpu_launches"], "clocks": clk.summary()}
     if rank == 0:
@@ -367,6 +371,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stream_640x270", choices=sorted(WORKLOADS) + ["stress"])
     ap.add_argument("--stress-cubes", type=int, default=0, help="score only the first k of the 32 cubes")
+    ap.add_argument("--cube", default="", help="stress workload: one cube 'lines,width,bands' instead")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--batch", type=int, default=0, help="lines per internal batch (0 = workload default)")
     ap.add_argument("--lines", type=int, default=0, help="override the stream length (profiling captures)")

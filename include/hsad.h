@@ -106,8 +106,10 @@ int hsad_config_init(hsad_config* cfg);
 int hsad_create(const hsad_config* cfg, hsad_ctx** out);
 
 /* Append n_lines lines (BIP, in_dtype) to the stream and enqueue their work.
- * mem = HSAD_HOST: the data are copied into library staging before return, so the
- *   buffer may be reused at once.
+ * mem = HSAD_HOST: the data are copied before return, so the buffer may be reused at
+ *   once. Page-locked (pinned) host memory is copied straight to device staging by DMA
+ *   (the call returns when those copies have landed, not when the batch is scored);
+ *   pageable memory goes through library pinned staging first.
  * mem = HSAD_DEVICE: the lines are read in place, stream-ordered: the buffer must
  *   stay unchanged until hsad_scores has returned for these lines (or
  *   hsad_synchronize). In CUBE mode device lines are copied into the cube buffer
@@ -214,6 +216,20 @@ int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int
                            int32_t in_dtype, int32_t precision, const float* gain,
                            int32_t threshold_mode, float threshold, int32_t flags, float* scores,
                            uint8_t* mask, void* stream, int32_t device);
+
+/* Factor-kernel autotuner (no counterpart in the paper). Times every launch shape of the
+ * FP64 factorisation (one 128- or 256-thread CTA per line, or a 2/4/8/16-CTA cluster per
+ * line) on synthetic positive definite problems of `bands` bands, for batches of 1, 2, 4,
+ * ..., max_lines lines (1 .. 4096), and makes contexts on `device` with that band count
+ * and precision use the fastest shape per batch size from then on. Results do not depend
+ * on the shape (bitwise). The measurement is kept per process: a second call with no
+ * larger max_lines returns at once. report (nullable): rows of 4 floats (largest batch
+ * size of the bucket, CTAs per line, threads per CTA, milliseconds), up to *n_rows rows;
+ * *n_rows (nullable on input only if report is NULL) receives the number of buckets.
+ * Allocates (and frees) scratch device memory for max_lines problems. Returns HSAD_OK,
+ * HSAD_E_INVALID, or HSAD_E_CUDA. */
+int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32_t max_lines, float* report,
+                         int32_t* n_rows);
 
 /* Self-test of the bounded device waits used by the tensor-core kernels (no
  * counterpart in the paper): launches one kernel that waits on an mbarrier nothing

@@ -8,12 +8,14 @@
 // pending lines and pushes them as one batch (lines that arrived while the stream's
 // previous batch was on the GPU form the next batch). Each stream replays a captured CUDA
 // graph per batch size for the launches after its batch's first line (HSAD_CUDA_GRAPHS).
-// Admission is by the device-wide byte budget: a stream is opened only when its device
-// memory fits.
+// Opening a stream with a new band count first runs the factor autotuner for it
+// (hsad_autotune_factor). Admission is by the device-wide byte budget: a stream is opened
+// only when its device memory fits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -155,6 +157,9 @@ int hsad_engine_open(hsad_engine* e, const hsad_config* cfg, int32_t* stream_id)
   hsad_config c = *cfg;
   c.device = e->device;
   c.flags |= HSAD_CUDA_GRAPHS;  // repeated small batches: replay captured launch sequences
+  // measured factor launch shapes for this band count (kept per process; fast when known)
+  const int32_t tune_lines = cfg->max_batch_lines > 0 ? std::min<int32_t>(cfg->max_batch_lines, 64) : 64;
+  hsad_autotune_factor(e->device, cfg->bands, cfg->precision, tune_lines, nullptr, nullptr);
   hsad_ctx* ctx = nullptr;
   const int rc = hsad_create(&c, &ctx);
   if (rc != HSAD_OK) return rc;

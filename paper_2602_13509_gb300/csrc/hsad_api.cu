@@ -104,6 +104,10 @@ struct hsad_ctx {
   void* h_stage[2] = {nullptr, nullptr};
   void* d_stage[2] = {nullptr, nullptr};
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  // pinned caller buffers are copied straight to d_stage on h2d_stream: copy_ev marks the
+  // copy done, free_ev the end of the last batch that read d_stage[i]
+  cudaStream_t h2d_stream = nullptr;
+  cudaEvent_t copy_ev[2] = {nullptr, nullptr}, free_ev[2] = {nullptr, nullptr};
   int stage_idx = 0;
   void* cube_buf = nullptr;
   int32_t* h_small = nullptr;  // pinned scratch for small host->device values
@@ -292,14 +296,19 @@ void release(hsad_ctx* ctx) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
   }
-  for (int i = 0; i < 2; ++i)
+  if (ctx->h2d_stream) cudaStreamSynchronize(ctx->h2d_stream);
+  for (int i = 0; i < 2; ++i) {
     if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
+    if (ctx->copy_ev[i]) cudaEventDestroy(ctx->copy_ev[i]);
+    if (ctx->free_ev[i]) cudaEventDestroy(ctx->free_ev[i]);
+  }
   for (auto& g : ctx->graphs)
     if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
   for (void* p : ctx->dev_allocs) cudaFree(p);
   for (void* p : ctx->host_allocs) cudaFreeHost(p);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->h2d_stream) cudaStreamDestroy(ctx->h2d_stream);
   if (ctx->budget_charged) {
     std::lock_guard<std::mutex> g(budget().mu);
     budget().used[ctx->device] -= ctx->charged;
@@ -374,6 +383,26 @@ int hsadi_push_ready(hsad_ctx* ctx) {
 
 // ------------------------------------------------------------------------------ ABI
 extern "C" {
+
+int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32_t max_lines, float* report,
+                         int32_t* n_rows) {
+  if (bands < 1 || bands > 512 || max_lines < 1 || max_lines > 4096) return HSAD_E_INVALID;
+  if (precision < HSAD_FP32 || precision > HSAD_FP16) return HSAD_E_INVALID;
+  if (report && !n_rows) return HSAD_E_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return ndev <= 0 ? HSAD_E_CUDA : HSAD_E_INVALID;
+  }
+  DeviceGuard dg(device);
+  const int prec = precision == HSAD_FP32 ? P_FP32 : (precision == HSAD_BF16 ? P_BF16 : P_FP16);
+  factor_prepare(bands, prec);
+  const int cap = report ? *n_rows : 0;
+  const int n = factor_autotune(bands, prec, max_lines, report, cap);
+  if (n < 0) return HSAD_E_CUDA;
+  if (n_rows) *n_rows = n;
+  return HSAD_OK;
+}
 
 const char* hsad_status_string(int s) {
   switch (s) {
@@ -489,7 +518,8 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
 
   bool ok = true;
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->h2d_stream, cudaStreamNonBlocking) != cudaSuccess) {
     ok = false;
   }
   const int64_t B = ctx->B, Bp = ctx->Bp, L = ctx->Lmax;
@@ -527,7 +557,10 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     if (cudaHostAlloc(&h, (size_t)hb, cudaHostAllocDefault) != cudaSuccess) ok = false;
     else ctx->host_allocs.push_back(h);
     ctx->h_stage[i] = h;
-    if (cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming) != cudaSuccess) ok = false;
+    if (cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->copy_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->free_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      ok = false;
   }
   if (ok) {
     void* h = nullptr;
@@ -639,11 +672,6 @@ int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* ou
   return HSAD_OK;
 }
 
-// EXCLUSIVE batch of L lines, pipelined: factor slot 0 carries the factor of the
-// statistics before line `first` (computed at the end of the previous batch), so that
-// line is scored at once and its completion recorded before any statistics work; the
-// statistics through each line of the batch then give the factors of the next lines
-// (slots 1..L), and slot L is carried to slot 0 for the next batch.
 // Everything of an EXCLUSIVE batch after its first line is scored: the batch's statistics,
 // the factors of slots 1..L, the scores of lines 1..L-1 and the carry of slot L to slot 0.
 // With dev = true the per-batch values (pixels before the batch, ring slot of line 1) are
@@ -810,6 +838,15 @@ int cube_score(hsad_ctx* ctx, const void* x, int64_t n) {
   return add_record(ctx, first, (uint64_t)n);
 }
 
+bool is_pinned_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 bool is_device_ptr(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -905,6 +942,8 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
 
   // stream modes: batches of <= Lmax lines, never across a statistics reset
   const int64_t CLr = ctx->cfg.cube_lines;
+  const bool pinned = mem == HSAD_HOST && is_pinned_host_ptr(lines);
+  cudaEvent_t last_copy = nullptr;
   while (done < n_lines) {
     int64_t take = std::min<int64_t>(n_lines - done, ctx->Lmax);
     if (CLr > 0) {
@@ -912,10 +951,23 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
       take = std::min<int64_t>(take, CLr - into);
     }
     const void* x;
+    int s = -1;
     if (mem == HSAD_DEVICE) {
       x = src + done * ctx->line_bytes;
+    } else if (pinned) {
+      // DMA straight from the caller's pinned buffer, on its own stream, once the batch that
+      // last read d_stage[s] is done; the kernels wait for the copy
+      s = ctx->stage_idx;
+      CK(cudaStreamWaitEvent(ctx->h2d_stream, ctx->free_ev[s], 0));
+      CK(cudaMemcpyAsync(ctx->d_stage[s], src + done * ctx->line_bytes, (size_t)(take * ctx->line_bytes),
+                         cudaMemcpyHostToDevice, ctx->h2d_stream));
+      CK(cudaEventRecord(ctx->copy_ev[s], ctx->h2d_stream));
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->copy_ev[s], 0));
+      last_copy = ctx->copy_ev[s];
+      ctx->stage_idx ^= 1;
+      x = ctx->d_stage[s];
     } else {
-      const int s = ctx->stage_idx;
+      s = ctx->stage_idx;
       int rc = wait_event(ctx, ctx->stage_ev[s], 10000);
       if (rc != HSAD_OK) return rc == HSAD_E_NOT_READY ? fail(ctx, HSAD_E_TIMEOUT, "staging busy") : rc;
       memcpy(ctx->h_stage[s], src + done * ctx->line_bytes, (size_t)(take * ctx->line_bytes));
@@ -929,12 +981,18 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
     ctx->next_line += (uint64_t)take;
     int rc = stream_batch(ctx, x, (int)take, first);
     if (rc != HSAD_OK) return rc;
+    if (s >= 0) CK(cudaEventRecord(ctx->free_ev[s], ctx->stream));
     done += take;
     if (CLr > 0 && ctx->next_line % (uint64_t)CLr == 0) {  // statistics reset
       CK(cudaMemsetAsync(ctx->state_s1, 0, (size_t)ctx->B * 8, ctx->stream));
       CK(cudaMemsetAsync(ctx->state_s2, 0, (size_t)ctx->B * ctx->B * 8, ctx->stream));
       ctx->n_stats = 0;
     }
+  }
+  // the caller may reuse its buffer once the copies from it have landed
+  if (last_copy) {
+    const int rc = wait_event(ctx, last_copy, 60000);
+    if (rc != HSAD_OK) return rc;
   }
   return HSAD_OK;
 }

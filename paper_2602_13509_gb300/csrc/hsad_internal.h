@@ -80,6 +80,16 @@ cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, 
 // m[t]: Sigma_t = D (S2_t - n_t m_t m_t^T) D / (n_t - 1) with n_t = n0 + (t + incl) W,
 // FP64 Cholesky and triangular inverse in place, then G_t = s_t L^{-1} D cast to the
 // working precision, y0 and 1/s_t^2. scratch: [L][B][B] FP64.
+// The factor kernel with a given launch shape: cl CTAs per line (1, 2, 4, 8, 16) and, for
+// cl = 1, ft threads per CTA (128 or 256).
+cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m, const double* dgain,
+                                int L, int B, int prec, void* wmat, float* y0, float* inv_s2, int32_t* status,
+                                int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
+                                const int64_t* n0_dev);
+// Measure the launch shapes for batch-size buckets 1, 2, 4, ..., max_lines and keep the
+// fastest per bucket for launch_factor (current device). report: rows of (bucket, cl, ft,
+// ms), up to cap rows. Returns the number of buckets or a negative value on failure.
+int factor_autotune(int B, int prec, int max_lines, float* report, int cap);
 // Query and cache, once per device, B and precision, how many clusters of each size the
 // factor kernel can run at once (host calls that must not land on a line's latency path).
 void factor_prepare(int B, int prec);

@@ -20,9 +20,12 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
+#include <vector>
 
 #include "hsad_internal.h"
 
@@ -31,34 +34,50 @@ namespace hsad {
 namespace {
 constexpr int FT_CLUSTER = 256;  // threads per factorisation CTA in a cluster
 
+// Store one element of the whitening operand and return the value actually stored (the
+// sum of the stored planes, exact in FP32), converted once from FP64 to FP32: the hi / lo
+// split of the FP32 value keeps 16 (BF16) or 22 (FP16) of its 24 bits.
 template <int PREC>
 struct WOut;
 template <>
 struct WOut<P_FP32> {
-  __device__ static double store(void* w, int64_t plane, int64_t idx, double v) {
+  __device__ static float store(void* w, int64_t, int64_t idx, double v) {
     const float f = (float)v;
     ((float*)w)[idx] = f;
-    return (double)f;
+    return f;
   }
+  __device__ static void zero(void* w, int64_t, int64_t idx) { ((float*)w)[idx] = 0.f; }
 };
 template <>
 struct WOut<P_FP16> {
-  __device__ static double store(void* w, int64_t plane, int64_t idx, double v) {
-    const __half hi = __double2half(v);
-    const __half lo = __double2half(v - (double)__half2float(hi));
+  __device__ static float store(void* w, int64_t plane, int64_t idx, double v) {
+    const float f = (float)v;
+    const __half hi = __float2half_rn(f);
+    const float hf = __half2float(hi);
+    const __half lo = __float2half_rn(f - hf);
     ((__half*)w)[idx] = hi;
     ((__half*)w)[plane + idx] = lo;
-    return (double)__half2float(hi) + (double)__half2float(lo);
+    return hf + __half2float(lo);
+  }
+  __device__ static void zero(void* w, int64_t plane, int64_t idx) {
+    ((uint16_t*)w)[idx] = 0;
+    ((uint16_t*)w)[plane + idx] = 0;
   }
 };
 template <>
 struct WOut<P_BF16> {
-  __device__ static double store(void* w, int64_t plane, int64_t idx, double v) {
-    const __nv_bfloat16 hi = __double2bfloat16(v);
-    const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+  __device__ static float store(void* w, int64_t plane, int64_t idx, double v) {
+    const float f = (float)v;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const float hf = __bfloat162float(hi);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(f - hf);
     ((__nv_bfloat16*)w)[idx] = hi;
     ((__nv_bfloat16*)w)[plane + idx] = lo;
-    return (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
+    return hf + __bfloat162float(lo);
+  }
+  __device__ static void zero(void* w, int64_t plane, int64_t idx) {
+    ((uint16_t*)w)[idx] = 0;
+    ((uint16_t*)w)[plane + idx] = 0;
   }
 };
 
@@ -124,8 +143,10 @@ __device__ __forceinline__ double ld_remote(const double* local, int rank) {
 // 16-column panel redundantly in its own shared memory, the updates and the final cast
 // are spread over all CL x FT threads, steps are separated by cluster barriers
 // (release / acquire), and data written by other CTAs is read through L2 (ld.global.cg).
-template <int PREC, int CL, int FT>
-__global__ void __launch_bounds__(FT, (CL == 1 ? 512 / FT : 1)) factor_kernel(double* __restrict__ sigma_all,
+// MB: CTAs per SM the register allocation is sized for (a one-CTA-per-line launch of 128
+// threads fits 4 at <= 128 registers or 5 at <= 96; 256 threads fit 2).
+template <int PREC, int CL, int FT, int MB = (CL == 1 ? 512 / FT : 1)>
+__global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sigma_all,
                                                        double* __restrict__ inv_all,
                                                        const double* __restrict__ m_all,
                                                        const double* __restrict__ dgain, int B,
@@ -344,10 +365,8 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 512 / FT : 1)) factor_kernel(do
 
   // ---- G = Inv D, power-of-two scale, cast, y0 ------------------------------------
   double mx = 0.0;
-  for (int64_t e = gtid; e < BB; e += gthreads) {
-    const int k = (int)(e % B);
-    mx = fmax(mx, fabs(ldg_c<CL>(Inv + e) * dgain[k]));
-  }
+  for (int n = gwarp; n < B; n += gwarps)  // X is lower triangular
+    for (int k = lane; k <= n; k += 32) mx = fmax(mx, fabs(ldg_c<CL>(Inv + (int64_t)n * B + k) * dgain[k]));
   mx = block_max<FT>(mx, red);
   if (CL > 1) {  // maximum over the cluster: read every CTA's partial from its shared memory
     csync<CL>();
@@ -358,14 +377,20 @@ __global__ void __launch_bounds__(FT, (CL == 1 ? 512 / FT : 1)) factor_kernel(do
   const double s = (mx > 0.0) ? ldexp(1.0, -ex) : 1.0;
   const int64_t plane = (int64_t)Bp * Bp;
   void* w = (char*)wmat + (size_t)t * plane * 4;  // 4 bytes per element pair in every format
+  double* ds = P;  // the panel buffer is free: d_k s per band (s is a power of two: exact)
+  for (int k = tid; k < B; k += FT) ds[k] = dgain[k] * s;
+  __syncthreads();
   // one warp per output row n: write the row and accumulate y0[n] from the rounded values
   for (int n = gwarp; n < Bp; n += gwarps) {
     double acc = 0.0;
     for (int k = lane; k < Bp; k += 32) {
-      double v = 0.0;
-      if (n < B && k <= n) v = ldg_c<CL>(Inv + (int64_t)n * B + k) * dgain[k] * s;
-      const double r = WOut<PREC>::store(w, plane, (int64_t)n * Bp + k, v);
-      if (n < B && k <= n) acc += r * m[k];
+      const int64_t idx = (int64_t)n * Bp + k;
+      if (n < B && k <= n) {
+        const float r = WOut<PREC>::store(w, plane, idx, ldg_c<CL>(Inv + (int64_t)n * B + k) * ds[k]);
+        acc = fma((double)r, m[k], acc);
+      } else {
+        WOut<PREC>::zero(w, plane, idx);
+      }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) y0_all[(int64_t)t * Bp + n] = (n < B) ? (float)acc : 0.0f;
@@ -378,7 +403,7 @@ namespace {
 
 // How many clusters of CL factor CTAs the device can run at once (queried once per
 // device, working precision, cluster size and shared-memory size; 0 if none fits).
-template <int PREC, int CL, int FT = FT_CLUSTER>
+template <int PREC, int CL, int FT = FT_CLUSTER, int MB = (CL == 1 ? 512 / FT : 1)>
 int factor_cluster_capacity(size_t smem) {
   static std::mutex mu;
   static std::map<std::pair<int, size_t>, int> cache;
@@ -389,10 +414,10 @@ int factor_cluster_capacity(size_t smem) {
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   int n = 0;
-  bool ok = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  bool ok = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) == cudaSuccess;
   if (ok && CL > 8)
-    ok = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+    ok = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT, MB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
          cudaSuccess;
   if (ok) {
     cudaLaunchConfig_t cfg = {};
@@ -406,23 +431,23 @@ int factor_cluster_capacity(size_t smem) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&n, factor_kernel<PREC, CL, FT>, &cfg) != cudaSuccess) n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, factor_kernel<PREC, CL, FT, MB>, &cfg) != cudaSuccess) n = 0;
   }
   cudaGetLastError();
   cache[key] = n;
   return n;
 }
 
-template <int PREC, int CL, int FT = FT_CLUSTER>
+template <int PREC, int CL, int FT = FT_CLUSTER, int MB = (CL == 1 ? 512 / FT : 1)>
 cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, const double* dgain, int L, int B,
                             void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
                             cudaStream_t st, const int64_t* n0_dev) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   if (CL > 8) {
-    e = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT, MB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
@@ -438,26 +463,27 @@ cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, con
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // a non-portable size: launch only where the device can place such a cluster
-  if (CL > 8 && factor_cluster_capacity<PREC, CL, FT>(smem) <= 0) return cudaErrorInvalidConfiguration;
-  return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL, FT>, sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status,
+  if (CL > 8 && factor_cluster_capacity<PREC, CL, FT, MB>(smem) <= 0) return cudaErrorInvalidConfiguration;
+  return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL, FT, MB>, sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status,
                             n0, W, incl, n0_dev);
 }
 
 // Threads of a one-CTA-per-line factorisation: 128 (4 CTAs per SM, so that one CTA's
 // barrier-bound panel step overlaps other CTAs' updates; measured 62.2 ms against
 // 66.6 ms for 256 threads on 4000 lines of B = 270) or 256 (2 CTAs per SM).
-// HSAD_FACTOR_THREADS = 128 or 256 in the environment fixes it (tuning).
+// HSAD_FACTOR_THREADS = 128 or 256 in the environment fixes it; 96 selects 128 threads
+// with registers for 5 CTAs per SM (tuning).
 int factor_single_threads() {
   static const int n = [] {
     const char* v = getenv("HSAD_FACTOR_THREADS");
     const int c = v ? atoi(v) : 0;
-    return (c == 128 || c == 256) ? c : 128;
+    return (c == 96 || c == 128 || c == 256) ? c : 128;
   }();
   return n;
 }
 
 template <int PREC>
-cudaError_t launch_factor_p(int cl, double* sigma, double* scratch, const double* m, const double* dgain, int L,
+cudaError_t launch_factor_p(int cl, int ft, double* sigma, double* scratch, const double* m, const double* dgain, int L,
                             int B, void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
                             int incl, cudaStream_t st, const int64_t* n0_dev) {
   switch (cl) {
@@ -471,7 +497,10 @@ cudaError_t launch_factor_p(int cl, double* sigma, double* scratch, const double
     case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
     case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
     default:
-      if (factor_single_threads() == 128)
+      if (ft == 96)  // 128 threads sized for 5 CTAs per SM
+        return launch_factor_t<PREC, 1, 128, 5>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W,
+                                                incl, st, n0_dev);
+      if (ft == 128)
         return launch_factor_t<PREC, 1, 128>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl,
                                              st, n0_dev);
       return launch_factor_t<PREC, 1, 256>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev);
@@ -500,6 +529,35 @@ int factor_cluster_size(int L, size_t smem) {
 
 }  // namespace
 
+// Measured launch shapes (hsad_autotune_factor): per (device, precision, B) a list of
+// (largest batch size of the bucket, cluster size, threads of a one-CTA factorisation).
+struct TunedShape {
+  int max_lines, cl, ft;
+  float ms;
+};
+std::mutex& tune_mu() {
+  static std::mutex m;
+  return m;
+}
+std::map<std::tuple<int, int, int>, std::vector<TunedShape>>& tune_table() {
+  static std::map<std::tuple<int, int, int>, std::vector<TunedShape>> t;
+  return t;
+}
+bool tuned_shape(int B, int prec, int L, int* cl, int* ft) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(tune_mu());
+  auto it = tune_table().find(std::make_tuple(dev, prec, B));
+  if (it == tune_table().end() || it->second.empty()) return false;
+  for (const auto& t : it->second)
+    if (L <= t.max_lines) {
+      *cl = t.cl;
+      *ft = t.ft;
+      return true;
+    }
+  return false;  // larger than every measured batch: the occupancy rule
+}
+
 void factor_prepare(int B, int prec) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
 #define HSAD_FP(P)                             \
@@ -521,15 +579,145 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const
                           const int64_t* n0_dev) {
   if (L <= 0) return cudaSuccess;
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
+  int cl = 0, ft = 0;
+  if (getenv("HSAD_FACTOR_CLUSTER") || getenv("HSAD_FACTOR_THREADS") || !tuned_shape(B, prec, L, &cl, &ft)) {
+    cl = prec == P_FP32 ? factor_cluster_size<P_FP32>(L, smem)
+                        : (prec == P_FP16 ? factor_cluster_size<P_FP16>(L, smem) : factor_cluster_size<P_BF16>(L, smem));
+    ft = factor_single_threads();
+  }
+  return launch_factor_shape(cl, ft, sigma, scratch, m, dgain, L, B, prec, wmat, y0, inv_s2, status, n0, W, incl,
+                             st, lc, n0_dev);
+}
+
+cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m, const double* dgain,
+                                int L, int B, int prec, void* wmat, float* y0, float* inv_s2, int32_t* status,
+                                int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
+                                const int64_t* n0_dev) {
+  if (L <= 0) return cudaSuccess;
   cudaError_t e;
   switch (prec) {
-    case P_FP32: e = launch_factor_p<P_FP32>(factor_cluster_size<P_FP32>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
-    case P_FP16: e = launch_factor_p<P_FP16>(factor_cluster_size<P_FP16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
-    default: e = launch_factor_p<P_BF16>(factor_cluster_size<P_BF16>(L, smem), sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
+    case P_FP32: e = launch_factor_p<P_FP32>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
+    case P_FP16: e = launch_factor_p<P_FP16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
+    default: e = launch_factor_p<P_BF16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
   }
   if (lc) lc->n += 1;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+namespace {
+__global__ void tune_identity_kernel(double* sigma, int L, int B, double c) {
+  const int64_t BB = (int64_t)B * B;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)L * BB;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e % BB;
+    sigma[e] = (k / B == k % B) ? c : 0.0;
+  }
+}
+}  // namespace
+
+// Time every launch shape of the factor kernel on L synthetic SPD problems (raw sums
+// c * I, zero mean: every shape does the same arithmetic on any data) for each batch-size
+// bucket and keep the fastest. Returns the number of buckets, or a negative status.
+int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> g(tune_mu());
+    auto it = tune_table().find(std::make_tuple(dev, prec, B));
+    if (it != tune_table().end() && !it->second.empty() && it->second.back().max_lines >= max_lines) {
+      const auto& v = it->second;
+      for (int i = 0; i < (int)v.size() && i < cap && report; ++i) {
+        report[4 * i] = (float)v[i].max_lines;
+        report[4 * i + 1] = (float)v[i].cl;
+        report[4 * i + 2] = (float)v[i].ft;
+        report[4 * i + 3] = v[i].ms;
+      }
+      return (int)v.size();
+    }
+  }
+  std::vector<int> buckets;
+  for (int b = 1; b < max_lines; b *= 2) buckets.push_back(b);
+  buckets.push_back(max_lines);
+  const int Lt = max_lines, Bp = pad64(B);
+  const int64_t BB = (int64_t)B * B;
+  double *sigma = nullptr, *inv = nullptr, *m = nullptr, *dgain = nullptr;
+  float *y0 = nullptr, *inv_s2 = nullptr;
+  int32_t* status = nullptr;
+  void* wmat = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaMalloc(&sigma, (size_t)Lt * BB * 8) == cudaSuccess && cudaMalloc(&inv, (size_t)Lt * BB * 8) == cudaSuccess &&
+            cudaMalloc(&m, (size_t)Lt * B * 8) == cudaSuccess && cudaMalloc(&dgain, (size_t)B * 8) == cudaSuccess &&
+            cudaMalloc(&y0, (size_t)Lt * Bp * 4) == cudaSuccess && cudaMalloc(&inv_s2, (size_t)Lt * 4) == cudaSuccess &&
+            cudaMalloc(&status, (size_t)Lt * 4) == cudaSuccess &&
+            cudaMalloc(&wmat, (size_t)Lt * Bp * Bp * 4) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  std::vector<TunedShape> result;
+  if (ok) {
+    std::vector<double> ones(B, 1.0);
+    ok = cudaMemcpyAsync(dgain, ones.data(), (size_t)B * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+         cudaMemsetAsync(m, 0, (size_t)Lt * B * 8, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
+  for (size_t bi = 0; ok && bi < buckets.size(); ++bi) {
+    const int L = buckets[bi];
+    std::vector<std::pair<int, int>> cands = {{1, 128}, {1, 256}};
+    const int cls[4] = {2, 4, 8, 16};
+    for (int c : cls) {
+      int capc = 0;
+      switch (prec) {
+        case P_FP32: capc = c == 2 ? factor_cluster_capacity<P_FP32, 2>(smem) : c == 4 ? factor_cluster_capacity<P_FP32, 4>(smem) : c == 8 ? factor_cluster_capacity<P_FP32, 8>(smem) : factor_cluster_capacity<P_FP32, 16>(smem); break;
+        case P_FP16: capc = c == 2 ? factor_cluster_capacity<P_FP16, 2>(smem) : c == 4 ? factor_cluster_capacity<P_FP16, 4>(smem) : c == 8 ? factor_cluster_capacity<P_FP16, 8>(smem) : factor_cluster_capacity<P_FP16, 16>(smem); break;
+        default: capc = c == 2 ? factor_cluster_capacity<P_BF16, 2>(smem) : c == 4 ? factor_cluster_capacity<P_BF16, 4>(smem) : c == 8 ? factor_cluster_capacity<P_BF16, 8>(smem) : factor_cluster_capacity<P_BF16, 16>(smem); break;
+      }
+      if (capc > 0 && L <= 2 * capc) cands.push_back({c, FT_CLUSTER});  // larger batches only queue
+    }
+    TunedShape best{L, 1, 128, 1e30f};
+    for (const auto& cf : cands) {
+      float tot = 0.f;
+      for (int rep = 0; ok && rep < 4; ++rep) {  // one untimed run, then three timed
+        tune_identity_kernel<<<256, 256, 0, st>>>(sigma, L, B, 1.0e6);
+        ok = cudaMemsetAsync(status, 0, (size_t)L * 4, st) == cudaSuccess;
+        cudaEventRecord(e0, st);
+        if (launch_factor_shape(cf.first, cf.second, sigma, inv, m, dgain, L, B, prec, wmat, y0, inv_s2, status,
+                                1000, 1, 0, st, nullptr, nullptr) != cudaSuccess)
+          ok = false;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;
+      }
+      if (ok && tot / 3.f < best.ms) best = TunedShape{L, cf.first, cf.second, tot / 3.f};
+    }
+    if (ok) result.push_back(best);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(sigma);
+  cudaFree(inv);
+  cudaFree(m);
+  cudaFree(dgain);
+  cudaFree(y0);
+  cudaFree(inv_s2);
+  cudaFree(status);
+  cudaFree(wmat);
+  cudaGetLastError();
+  if (!ok) return -1;
+  {
+    std::lock_guard<std::mutex> g(tune_mu());
+    tune_table()[std::make_tuple(dev, prec, B)] = result;
+  }
+  for (int i = 0; i < (int)result.size() && i < cap && report; ++i) {
+    report[4 * i] = (float)result[i].max_lines;
+    report[4 * i + 1] = (float)result[i].cl;
+    report[4 * i + 2] = (float)result[i].ft;
+    report[4 * i + 3] = result[i].ms;
+  }
+  return (int)result.size();
 }
 
 }  // namespace hsad

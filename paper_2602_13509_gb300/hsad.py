@@ -84,6 +84,8 @@ def _load():
         "hsad_engine_counters": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "hsad_engine_destroy": (C.c_int, [P]),
         "hsad_selftest_bounded_wait": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
+        "hsad_autotune_factor": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                                           C.POINTER(C.c_int32)]),
         "hsad_destroy": (C.c_int, [P]),
         "hsad_last_error": (C.c_char_p, [P]),
         "hsad_status_string": (C.c_char_p, [C.c_int]),
@@ -274,6 +276,16 @@ def hsad_engine_counters(engine):
 
 def hsad_engine_destroy(engine) -> int:
     return _lib.hsad_engine_destroy(engine)
+
+
+def hsad_autotune_factor(device: int, bands: int, precision: str, max_lines: int):
+    """Returns ``(status, rows)``, rows = [(bucket, ctas_per_line, threads, ms), ...]."""
+    cap = 16
+    buf = (C.c_float * (4 * cap))()
+    n = C.c_int32(cap)
+    rc = _lib.hsad_autotune_factor(int(device), int(bands), _NAMES[precision], int(max_lines), buf, C.byref(n))
+    rows = [tuple(buf[4 * i:4 * i + 4]) for i in range(min(n.value, cap))] if rc == HSAD_OK else []
+    return rc, rows
 
 
 def hsad_selftest_bounded_wait(device: int = 0, limit_cycles: int = 2_000_000):

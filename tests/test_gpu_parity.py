@@ -189,6 +189,64 @@ def test_cuda_graph_replay_matches_direct_launches(hs, prec):
     assert out[1][3] >= out[0][3]  # every replayed kernel is counted (plus one descriptor write per batch)
 
 
+def test_autotuned_factor_shapes_give_identical_scores(hs):
+    """The autotuner only picks launch shapes; every shape computes the same factor."""
+    sc, lines = _scene_lines(40, 48, 24, seed=14)
+
+    def run():
+        det = hs.Detector(width=48, bands=24, stats_mode="exclusive", precision="bf16")
+        for t in range(0, 40, 2):
+            det.push(lines[t:t + 2])
+        rc, s, m, st = det.scores(0, 40)
+        det.close()
+        return s, m
+
+    before = run()
+    rc, rows = hs.hsad_autotune_factor(0, 24, "bf16", 8)
+    assert rc == hs.HSAD_OK and [int(r[0]) for r in rows] == [1, 2, 4, 8]
+    for bucket, cl, ft, ms in rows:
+        assert int(cl) in (1, 2, 4, 8, 16) and int(ft) in (128, 256) and ms > 0
+    after = run()
+    np.testing.assert_array_equal(after[0], before[0])
+    np.testing.assert_array_equal(after[1], before[1])
+    assert hs.hsad_autotune_factor(0, 24, "bf16", 5000)[0] == hs.HSAD_E_INVALID
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_pinned_pageable_and_device_pushes_agree(hs, graphs):
+    """Pinned host lines go to the device by DMA on a copy stream, pageable ones through
+    library staging, device lines in place: the scores must be identical, and a pinned
+    buffer may be overwritten as soon as its push returns."""
+    import torch
+    sc, lines = _scene_lines(36, 40, 20, seed=15)
+    flags = hs.HSAD_CUDA_GRAPHS if graphs else 0
+    chunks = [(0, 1), (1, 7), (8, 1), (9, 1), (10, 7), (17, 7), (24, 12)]
+
+    def run(kind):
+        det = hs.Detector(width=40, bands=20, stats_mode="exclusive", precision="bf16", flags=flags)
+        buf = torch.empty((12, 40, 20), dtype=torch.int16).pin_memory()
+        dev = torch.from_numpy(lines.view(np.int16)).cuda()
+        for a, n in chunks:
+            if kind == "pageable":
+                rc, _ = hs.hsad_push_lines(det.ctx, np.ascontiguousarray(lines[a:a + n]), n, hs.HSAD_HOST)
+            elif kind == "pinned":
+                buf[:n].copy_(torch.from_numpy(lines[a:a + n].view(np.int16)))
+                rc, _ = hs.hsad_push_lines(det.ctx, buf[:n], n, hs.HSAD_HOST)
+                buf.fill_(-1)  # reused at once: the push has already copied it
+            else:
+                rc, _ = hs.hsad_push_lines(det.ctx, dev[a:a + n], n, hs.HSAD_DEVICE)
+            assert rc == hs.HSAD_OK
+        rc, s, m, st = det.scores(0, 36)
+        det.close()
+        return s, m
+
+    ref = run("pageable")
+    for kind in ("pinned", "device"):
+        s, m = run(kind)
+        np.testing.assert_array_equal(s, ref[0])
+        np.testing.assert_array_equal(m, ref[1])
+
+
 def test_not_positive_definite_is_reported(hs):
     sc, lines = _scene_lines(12, 40, 8, seed=2)
     lines = lines.copy()
