@@ -48,6 +48,12 @@ def load_peaks():
                 sm_max_mhz=2070.0)
 
 
+# DRAM bytes per line of the factor kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of a 512-line launch, profiles/factor_512x640x270.md), scaled to a
+# launch by its lines; keyed by band count, and to be refreshed whenever the kernel changes.
+FACTOR_DRAM_BYTES_PER_LINE = {270: (2.009082e9 + 2.316017e9) / 512}
+
+
 # FP64 and FP32 SIMT peaks derived from unit counts x clock (no measured figure exists):
 # 152 SMs x 2070 MHz x (4 FP64 flops / clk / SM, i.e. the 1.25 TF/s nominal) and
 # x (128 FP32 lanes x 2 flops / clk / SM).
@@ -538,7 +544,10 @@ def main():
             ach = work / (avg_ms / 1e3) / 1e12
             pk = fp64_peak_tflops(mhz)
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": None, "kernel": "factor (FP64 Cholesky + triangular inverse)",
+                    "traffic": (FACTOR_DRAM_BYTES_PER_LINE[B] * lines_per_launch
+                                if B in FACTOR_DRAM_BYTES_PER_LINE else None),
+                    "traffic_source": "ncu dram bytes per line of a 512-line capture x lines per launch",
+                    "kernel": "factor (FP64 Cholesky + triangular inverse)",
                     "work_per_launch": f"{lines_per_launch:.0f} lines x 2B^3/3 FP64 flop",
                     "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk (nominal 1.25 TF/s; "
                                    "a DFMA probe measured 1.20 TF/s)"}

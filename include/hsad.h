@@ -218,13 +218,14 @@ int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int
                            uint8_t* mask, void* stream, int32_t device);
 
 /* Factor-kernel autotuner (no counterpart in the paper). Times every launch shape of the
- * FP64 factorisation (one 128- or 256-thread CTA per line, or a 2/4/8/16-CTA cluster per
- * line) on synthetic positive definite problems of `bands` bands, for batches of 1, 2, 4,
+ * FP64 factorisation (one 128-thread CTA per line with registers for 4 or 5 CTAs per SM,
+ * one 256-thread CTA per line, or a 2/4/8/16-CTA cluster per line) on synthetic positive definite problems of `bands` bands, for batches of 1, 2, 4,
  * ..., max_lines lines (1 .. 4096), and makes contexts on `device` with that band count
  * and precision use the fastest shape per batch size from then on. Results do not depend
  * on the shape (bitwise). The measurement is kept per process: a second call with no
  * larger max_lines returns at once. report (nullable): rows of 4 floats (largest batch
- * size of the bucket, CTAs per line, threads per CTA, milliseconds), up to *n_rows rows;
+ * size of the bucket, CTAs per line, threads per CTA (96 = 128 threads sized for 5 CTAs
+ * per SM), milliseconds), up to *n_rows rows;
  * *n_rows (nullable on input only if report is NULL) receives the number of buckets.
  * Allocates (and frees) scratch device memory for max_lines problems. Returns HSAD_OK,
  * HSAD_E_INVALID, or HSAD_E_CUDA. */

@@ -182,6 +182,8 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       double* row = A + (int64_t)i * B;
       for (int j = lane; j <= i; j += 32) row[j] = ai * dgain[j] * fma(-nmi, m[j], row[j]);
     }
+    // the inverse is built in place of R = I (entries above the diagonal stay zero)
+    for (int64_t e = gtid; e < BB; e += gthreads) Inv[e] = ((int)(e / B) == (int)(e % B)) ? 1.0 : 0.0;
     csync<CL>();
   }
 
@@ -296,71 +298,62 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
           }
       }
     }
-    csync<CL>();
-  }
-
-  // ---- blocked triangular inverse, right-looking: X = L^{-1} in place of R = I ------
-  // For each block row i of NB rows: X_i = L_ii^{-1} R_i (forward substitution, one
-  // thread per column), then R_j -= L_ji X_i for every later row j (rank-NB update in
-  // 4 x 4 register tiles, the same balanced shape as the Cholesky trailing update).
-  // Entries above the diagonal start and stay zero.
-  double* R = Inv;
-  for (int64_t e = gtid; e < BB; e += gthreads) R[e] = ((int)(e / B) == (int)(e % B)) ? 1.0 : 0.0;
-  __shared__ double rdiag[NB];  // 1 / L[r0 + r][r0 + r]
-  for (int r0 = 0; r0 < B; r0 += NB) {
-    const int rb = min(NB, B - r0), rows = B - r0, ncols = r0 + rb;
-    for (int e = tid; e < rows * rb; e += FT) {  // panel L[r0.., r0..r0+rb)
-      const int r = e / rb, j = e - r * rb;
-      P[r * PS + j] = ldg_c<CL>(A + (int64_t)(r0 + r) * B + r0 + j);
-    }
-    if (tid < rb) rdiag[tid] = 1.0 / ldg_c<CL>(A + (int64_t)(r0 + tid) * B + r0 + tid);
-    csync<CL>();  // also publishes R (initial identity, or the previous update) cluster-wide
-    for (int c = gtid; c < ncols; c += gthreads) {
-      double xr[NB];
+    // ---- triangular inverse, block row p, fused into the Cholesky step ----------------
+    // X = L^{-1} is built right-looking in place of R = I: once panel p is factored, block
+    // row p of X is X_p = L_pp^{-1} R_p (forward substitution, one thread per column, in
+    // this phase next to the trailing update), and every later block row takes the rank-kb
+    // update R_j -= L_jp X_p (next phase, 4 x 4 register tiles). R_p has received the
+    // updates of every earlier block row, and the operations per element run in the same
+    // order as in a separate inverse sweep after the whole factorisation.
+    double* R = Inv;
+    {
+      const int ncols = p + kb;
+      for (int c = gtid; c < ncols; c += gthreads) {
+        double xr[NB];
 #pragma unroll
-      for (int r = 0; r < NB; ++r) {
-        xr[r] = 0.0;
-        if (r < rb) {
-          double v = ldg_c<CL>(R + (int64_t)(r0 + r) * B + c);
+        for (int r = 0; r < NB; ++r) {
+          xr[r] = 0.0;
+          if (r < kb) {
+            double v = ldg_c<CL>(R + (int64_t)(p + r) * B + c);
 #pragma unroll
-          for (int q = 0; q < r; ++q) v = fma(-P[r * PS + q], xr[q], v);
-          xr[r] = v * rdiag[r];
-          R[(int64_t)(r0 + r) * B + c] = xr[r];
+            for (int q = 0; q < r; ++q) v = fma(-P[r * PS + q], xr[q], v);
+            xr[r] = v * rdg[r];
+            R[(int64_t)(p + r) * B + c] = xr[r];
+          }
         }
       }
-    }
-    csync<CL>();
-    const int mrem = rows - rb;
-    if (mrem > 0) {
-      const int mt = (mrem + 3) >> 2, nct = (ncols + 3) >> 2;
-      for (int idx = gtid; idx < mt * nct; idx += gthreads) {
-        const int tr = idx / nct, tcx = idx - tr * nct;
-        const int j0 = rb + 4 * tr, c0 = 4 * tcx;  // j0 panel-relative row, c0 column
-        double acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(r0 + j0 + a) * B + c0 + b) : 0.0;
-        for (int q = 0; q < rb; ++q) {
-          double l[4], xq[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : 0.0;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) xq[b] = (c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(r0 + q) * B + c0 + b) : 0.0;
+      csync<CL>();  // the trailing update of A and X_p are complete cluster-wide
+      if (mrem > 0) {
+        const int mt = (mrem + 3) >> 2, nct = (ncols + 3) >> 2;
+        for (int idx = gtid; idx < mt * nct; idx += gthreads) {
+          const int tr = idx / nct, tcx = idx - tr * nct;
+          const int j0 = kb + 4 * tr, c0 = 4 * tcx;  // j0 panel-relative row, c0 column
+          double acc[4][4];
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(-l[a], xq[b], acc[a][b]);
+            for (int b = 0; b < 4; ++b)
+              acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + j0 + a) * B + c0 + b) : 0.0;
+          for (int q = 0; q < kb; ++q) {
+            double l[4], xq[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : 0.0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) xq[b] = (c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + q) * B + c0 + b) : 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 4; ++b) acc[a][b] = fma(-l[a], xq[b], acc[a][b]);
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(p + j0 + a) * B + c0 + b] = acc[a][b];
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(r0 + j0 + a) * B + c0 + b] = acc[a][b];
       }
+      csync<CL>();  // panel p done: next panel (and its shared-memory buffer) may start
     }
-    csync<CL>();
   }
 
   // ---- G = Inv D, power-of-two scale, cast, y0 ------------------------------------
@@ -468,16 +461,16 @@ cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, con
                             n0, W, incl, n0_dev);
 }
 
-// Threads of a one-CTA-per-line factorisation: 128 (4 CTAs per SM, so that one CTA's
-// barrier-bound panel step overlaps other CTAs' updates; measured 62.2 ms against
-// 66.6 ms for 256 threads on 4000 lines of B = 270) or 256 (2 CTAs per SM).
-// HSAD_FACTOR_THREADS = 128 or 256 in the environment fixes it; 96 selects 128 threads
-// with registers for 5 CTAs per SM (tuning).
+// Threads of a one-CTA-per-line factorisation: 128 threads with registers for 5 CTAs per
+// SM (code 96; so that one CTA's barrier-bound panel step overlaps other CTAs' updates),
+// 128 threads for 4 CTAs per SM (code 128), or 256 threads, 2 per SM. Measured on 4000
+// lines of B = 270: 57.1, 57.6 and 66.6 ms. HSAD_FACTOR_THREADS = 96, 128 or 256 in the
+// environment fixes it (tuning).
 int factor_single_threads() {
   static const int n = [] {
     const char* v = getenv("HSAD_FACTOR_THREADS");
     const int c = v ? atoi(v) : 0;
-    return (c == 96 || c == 128 || c == 256) ? c : 128;
+    return (c == 96 || c == 128 || c == 256) ? c : 96;
   }();
   return n;
 }
@@ -663,7 +656,7 @@ int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   for (size_t bi = 0; ok && bi < buckets.size(); ++bi) {
     const int L = buckets[bi];
-    std::vector<std::pair<int, int>> cands = {{1, 128}, {1, 256}};
+    std::vector<std::pair<int, int>> cands = {{1, 96}, {1, 128}, {1, 256}};
     const int cls[4] = {2, 4, 8, 16};
     for (int c : cls) {
       int capc = 0;

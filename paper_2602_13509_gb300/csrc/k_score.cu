@@ -78,9 +78,10 @@ __global__ void __launch_bounds__(256) whiten_score_kernel(
     const float* __restrict__ c_flt, const void* __restrict__ wmat, const float* __restrict__ y0_all,
     const float* __restrict__ inv_s2_all, const int32_t* __restrict__ status, int factor_stride,
     ScoreOut out) {
-  // rows padded by 4 floats: the staging stores walk k fastest
-  __shared__ __align__(16) float As[2][WS_K][WS_P + 4];
-  __shared__ __align__(16) float Bs[2][WS_K][WS_N + 4];
+  // two stages (double buffering) x two operand terms; rows padded by 4 floats: the
+  // staging stores walk k fastest
+  __shared__ __align__(16) float As[2][2][WS_K][WS_P + 4];
+  __shared__ __align__(16) float Bs[2][2][WS_K][WS_N + 4];
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * WS_P;
   const int f = out.factor_base + (factor_stride ? t : 0);
@@ -101,80 +102,113 @@ __global__ void __launch_bounds__(256) whiten_score_kernel(
   const In* xl = x + (int64_t)t * W * B;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 
-  float dsum[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int n0 = 0; n0 < B; n0 += WS_N) {
-    float acc[4][4];
+  // One step = (output block n0, k slice k0); G is lower triangular, so block n0 stops at
+  // k = n0 + 64. The next step's operands are loaded into registers while the current
+  // step computes from shared memory, then stored into the other stage.
+  float ra0[4], ra1[4], rb0[4], rb1[4];
+  auto load_step = [&](int n0s, int k0s) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int s = 0; s < 4; ++s) acc[r][s] = 0.f;
-    const int kmax = min(B, n0 + WS_N);
-    for (int k0 = 0; k0 < kmax; k0 += WS_K) {
-      // stage: element e -> (row e/16, k e%16) for both operands
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = threadIdx.x + q * 256;
-        const int rr = e >> 4, kk = e & 15;
-        const int k = k0 + kk;
-        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-        const int p = p0 + rr;
-        if (p < W && k < B) {
-          const float xc = centred<In>(xl[(int64_t)p * B + k], c_int, c_flt, k);
-          split_x<In, PREC>(xc, a0, a1);
-        }
-        const int n = n0 + rr;
-        if (n < B && k < Bp) load_w<PREC>(w, plane, (int64_t)n * Bp + k, b0, b1);
-        As[0][kk][rr] = a0;
-        As[1][kk][rr] = a1;
-        Bs[0][kk][rr] = b0;
-        Bs[1][kk][rr] = b1;
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * 256;
+      const int rr = e >> 4, kk = e & 15;
+      const int k = k0s + kk;
+      float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+      const int p = p0 + rr;
+      if (p < W && k < B) {
+        const float xc = centred<In>(xl[(int64_t)p * B + k], c_int, c_flt, k);
+        split_x<In, PREC>(xc, a0, a1);
       }
-      __syncthreads();
+      const int n = n0s + rr;
+      if (n < B && k < Bp) load_w<PREC>(w, plane, (int64_t)n * Bp + k, b0, b1);
+      ra0[q] = a0;
+      ra1[q] = a1;
+      rb0[q] = b0;
+      rb1[q] = b1;
+    }
+  };
+  auto store_step = [&](int buf) {
 #pragma unroll
-      for (int kk = 0; kk < WS_K; ++kk) {
-        float a0[4], b0[4];
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * 256;
+      const int rr = e >> 4, kk = e & 15;
+      As[buf][0][kk][rr] = ra0[q];
+      As[buf][1][kk][rr] = ra1[q];
+      Bs[buf][0][kk][rr] = rb0[q];
+      Bs[buf][1][kk][rr] = rb1[q];
+    }
+  };
+
+  float dsum[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[4][4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          a0[r] = As[0][kk][ty * 4 + r];
-          b0[r] = Bs[0][kk][tx * 4 + r];
-        }
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) acc[r][s2] = 0.f;
+  int n0 = 0, k0 = 0, cur = 0;
+  load_step(n0, k0);
+  store_step(0);
+  __syncthreads();
+  while (n0 < B) {
+    int nn = n0, nk = k0 + WS_K;
+    const bool last_k = nk >= min(B, n0 + WS_N);
+    if (last_k) {
+      nn = n0 + WS_N;
+      nk = 0;
+    }
+    const bool more = nn < B;
+    if (more) load_step(nn, nk);
+#pragma unroll
+    for (int kk = 0; kk < WS_K; ++kk) {
+      float a0[4], b0[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        a0[r] = As[cur][0][kk][ty * 4 + r];
+        b0[r] = Bs[cur][0][kk][tx * 4 + r];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) acc[r][s2] = fmaf(a0[r], b0[s2], acc[r][s2]);
+      if (PREC != P_FP32) {
+        float b1[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b1[r] = Bs[cur][1][kk][tx * 4 + r];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int s = 0; s < 4; ++s) acc[r][s] = fmaf(a0[r], b0[s], acc[r][s]);
-        if (PREC != P_FP32) {
-          float b1[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) b1[r] = Bs[1][kk][tx * 4 + r];
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int s = 0; s < 4; ++s) acc[r][s] = fmaf(a0[r], b1[s], acc[r][s]);
-        }
-        if (PREC == P_BF16) {
-          float a1[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) a1[r] = As[1][kk][ty * 4 + r];
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int s = 0; s < 4; ++s) acc[r][s] = fmaf(a1[r], b0[s], acc[r][s]);
-        }
+          for (int s2 = 0; s2 < 4; ++s2) acc[r][s2] = fmaf(a0[r], b1[s2], acc[r][s2]);
       }
-      __syncthreads();
-    }
+      if (PREC == P_BF16) {
+        float a1[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int n = n0 + tx * 4 + s;
-      if (n < B) {
-        const float yn = y0[n];
+        for (int r = 0; r < 4; ++r) a1[r] = As[cur][1][kk][ty * 4 + r];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float v = acc[r][s] - yn;
-          dsum[r] = fmaf(v, v, dsum[r]);
-        }
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int s2 = 0; s2 < 4; ++s2) acc[r][s2] = fmaf(a1[r], b0[s2], acc[r][s2]);
       }
     }
+    if (last_k) {  // block n0 complete: fold its outputs into the row norms
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2) {
+        const int n = n0 + tx * 4 + s2;
+        if (n < B) {
+          const float yn = y0[n];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float v = acc[r][s2] - yn;
+            dsum[r] = fmaf(v, v, dsum[r]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r][s2] = 0.f;
+      }
+    }
+    if (more) store_step(cur ^ 1);
+    __syncthreads();
+    cur ^= 1;
+    n0 = nn;
+    k0 = nk;
   }
   // row norm: reduce over the 16 lanes sharing ty (lanes tx = 0..15 are contiguous)
 #pragma unroll

@@ -205,7 +205,7 @@ def test_autotuned_factor_shapes_give_identical_scores(hs):
     rc, rows = hs.hsad_autotune_factor(0, 24, "bf16", 8)
     assert rc == hs.HSAD_OK and [int(r[0]) for r in rows] == [1, 2, 4, 8]
     for bucket, cl, ft, ms in rows:
-        assert int(cl) in (1, 2, 4, 8, 16) and int(ft) in (128, 256) and ms > 0
+        assert int(cl) in (1, 2, 4, 8, 16) and int(ft) in (96, 128, 256) and ms > 0
     after = run()
     np.testing.assert_array_equal(after[0], before[0])
     np.testing.assert_array_equal(after[1], before[1])
