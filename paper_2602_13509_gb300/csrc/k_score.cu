@@ -229,12 +229,156 @@ __global__ void __launch_bounds__(256) whiten_score_kernel(
   }
 }
 
+// FP32 form, larger register tiles: one CTA = 128 pixels x 64 outputs n, a thread 8 pixels
+// x 4 outputs (32 FFMA per three shared-memory vector loads), k slices of 16 bands staged
+// through two shared-memory buffers with the next slice prefetched into registers.
+constexpr int WF_P = 128, WF_N = 64, WF_K = 16;
+
+template <typename In>
+__global__ void __launch_bounds__(256) whiten_fp32_kernel(
+    const In* __restrict__ x, int W, int B, const int32_t* __restrict__ c_int, const float* __restrict__ c_flt,
+    const float* __restrict__ wmat, const float* __restrict__ y0_all, const float* __restrict__ inv_s2_all,
+    const int32_t* __restrict__ status, int factor_stride, ScoreOut out) {
+  __shared__ __align__(16) float As[2][WF_K][WF_P + 4];
+  __shared__ __align__(16) float Bs[2][WF_K][WF_N + 4];
+  const int t = blockIdx.y;
+  const int p0 = blockIdx.x * WF_P;
+  const int f = out.factor_base + (factor_stride ? t : 0);
+  const int64_t slot = (slot0_of(out) + t) % out.ring;
+  const int st = status[f];
+  if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;
+  if (st != LS_OK) {
+    for (int p = p0 + threadIdx.x; p < p0 + WF_P && p < W; p += blockDim.x) {
+      out.scores[slot * W + p] = __int_as_float(0x7fc00000);
+      out.mask[slot * W + p] = 0;
+    }
+    return;
+  }
+  const int Bp = pad64(B);
+  const float* g = wmat + (size_t)f * Bp * Bp;
+  const float* y0 = y0_all + (int64_t)f * Bp;
+  const In* xl = x + (int64_t)t * W * B;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 4 outputs tx*4.., 8 pixels ty*8..
+
+  float ra[8], rb[4];
+  auto load_step = [&](int n0s, int k0s) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {  // pixels: 16 threads read 16 consecutive bands of one pixel
+      const int e = threadIdx.x + q * 256;
+      const int pr = e >> 4, kk = e & 15, k = k0s + kk, p = p0 + pr;
+      ra[q] = (p < W && k < B) ? centred<In>(xl[(int64_t)p * B + k], c_int, c_flt, k) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * 256;
+      const int nr = e >> 4, kk = e & 15, k = k0s + kk, n = n0s + nr;
+      rb[q] = (n < B && k < Bp) ? g[(int64_t)n * Bp + k] : 0.f;
+    }
+  };
+  auto store_step = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = threadIdx.x + q * 256;
+      As[buf][e & 15][e >> 4] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * 256;
+      Bs[buf][e & 15][e >> 4] = rb[q];
+    }
+  };
+
+  float dsum[8];
+  float acc[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    dsum[r] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+  }
+  int n0 = 0, k0 = 0, cur = 0;
+  load_step(n0, k0);
+  store_step(0);
+  __syncthreads();
+  while (n0 < B) {  // G is lower triangular: block n0 stops at k = n0 + 64
+    int nn = n0, nk = k0 + WF_K;
+    const bool last_k = nk >= min(B, n0 + WF_N);
+    if (last_k) {
+      nn = n0 + WF_N;
+      nk = 0;
+    }
+    const bool more = nn < B;
+    if (more) load_step(nn, nk);
+#pragma unroll
+    for (int kk = 0; kk < WF_K; ++kk) {
+      const float4 a0 = *(const float4*)&As[cur][kk][ty * 8];
+      const float4 a1 = *(const float4*)&As[cur][kk][ty * 8 + 4];
+      const float4 b = *(const float4*)&Bs[cur][kk][tx * 4];
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+    }
+    if (last_k) {  // block n0 complete: fold its outputs into the row norms
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int n = n0 + tx * 4 + c;
+        if (n < B) {
+          const float yn = y0[n];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const float v = acc[r][c] - yn;
+            dsum[r] = fmaf(v, v, dsum[r]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[r][c] = 0.f;
+      }
+    }
+    if (more) store_step(cur ^ 1);
+    __syncthreads();
+    cur ^= 1;
+    n0 = nn;
+    k0 = nk;
+  }
+  // row norm: reduce over the 16 lanes sharing ty (lanes tx = 0..15 are contiguous)
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) dsum[r] += __shfl_xor_sync(0xffffffffu, dsum[r], o);
+  if (tx == 0) {
+    const float is2 = inv_s2_all[f];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int p = p0 + ty * 8 + r;
+      if (p < W) {
+        const float d = dsum[r] * is2;
+        out.scores[slot * W + p] = d;
+        if (out.write_mask) out.mask[slot * W + p] = d > out.tau ? 1 : 0;
+      }
+    }
+  }
+}
+
 cudaError_t launch_whiten_score_simt(const void* x, int L, int W, int B, int in_type,
                                      const int32_t* c_int, const float* c_flt, int prec,
                                      const void* wmat, const float* y0, const float* inv_s2,
                                      const int32_t* status, int factor_stride, ScoreOut out,
                                      cudaStream_t st, LaunchCounter* lc) {
   if (L <= 0) return cudaSuccess;
+  if (prec == P_FP32) {
+    dim3 g2((W + WF_P - 1) / WF_P, L), b2(256);
+    if (in_type == IN_U16)
+      whiten_fp32_kernel<uint16_t><<<g2, b2, 0, st>>>((const uint16_t*)x, W, B, c_int, c_flt, (const float*)wmat, y0,
+                                                      inv_s2, status, factor_stride, out);
+    else
+      whiten_fp32_kernel<float><<<g2, b2, 0, st>>>((const float*)x, W, B, c_int, c_flt, (const float*)wmat, y0,
+                                                   inv_s2, status, factor_stride, out);
+    if (lc) lc->n += 1;
+    return cudaGetLastError();
+  }
   dim3 grid((W + WS_P - 1) / WS_P, L), block(256);
 #define HSAD_WS(IN, P)                                                                          \
   whiten_score_kernel<IN, P><<<grid, block, 0, st>>>((const IN*)x, W, B, c_int, c_flt, wmat, y0, \
