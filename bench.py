@@ -125,6 +125,34 @@ def oracle_sample(lines, t_list, gain, offset):
     return px, time.perf_counter() - t0
 
 
+def gpu_local_cpus(index):
+    """CPUs next to GPU `index` (its sysfs local_cpulist) that this process may use."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(index)
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (p.pci_domain_id, p.pci_bus_id,
+                                                                        p.pci_device_id)
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return sorted(cpus & os.sched_getaffinity(0))
+    except Exception:
+        return []
+
+
+def bind_near_gpu(index):
+    """Run on the GPU's local CPUs, so that host buffers (first touched by this process)
+    sit on the GPU's NUMA node and host<->device copies take the direct link."""
+    cpus = gpu_local_cpus(index)
+    if cpus and set(cpus) != os.sched_getaffinity(0):
+        os.sched_setaffinity(0, cpus)
+        how = "bound to the GPU's local CPUs"
+    else:
+        how = "all GPU-local" if cpus else "GPU locality unknown"
+    return "%d CPUs (%s)" % (len(os.sched_getaffinity(0)), how)
+
+
 def max_over_ranks(ms, dist, device):
     """Slowest rank's time (replicas run independent streams; this is the only collective)."""
     if dist is None:
@@ -408,6 +436,7 @@ def main():
     import paper_2602_13509_gb300 as hs
 
     torch.cuda.set_device(local)
+    host_cpus = bind_near_gpu(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -575,7 +604,8 @@ def main():
         "config": {"workload": args.workload, "width": W, "bands": B, "lines": T, "stats": "exclusive",
                    "input": "uint16 12-bit DN", "batch_lines": wl["batch"],
                    "parallelism": f"replicas x{world} (independent streams)" if world > 1 else "single stream",
-                   "l2": "inputs larger than L2 (%.2f GB per step)" % (x_dev.numel() * 2 / 1e9)},
+                   "l2": "inputs larger than L2 (%.2f GB per step)" % (x_dev.numel() * 2 / 1e9),
+                   "host": host_cpus},
         "latency": lat, "e2e": e2e, "gpu_launches": launches, "fp32_path": fp32_arm,
         "roofline": roof, "kernels": per_kernel, "cpu_baseline": cpu, "clocks": clk.summary(),
         "serving": serving,
