@@ -246,7 +246,7 @@ def run_serving(hs, device, precision, seconds, warm_s, pool_lines=96, seed_offs
     err, lines_pushed, pushes, max_batch = hs.hsad_engine_counters(eng)
     hs.hsad_engine_destroy(eng)
 
-    lat_all, px = [], 0
+    lat_all, px, over = [], 0, []
     by_b, ok_streams = {}, 0
     for i, sp in enumerate(specs):
         sel = t_sched[i] >= warm_s
@@ -256,6 +256,9 @@ def run_serving(hs, device, precision, seconds, warm_s, pool_lines=96, seed_offs
         by_b.setdefault(sp["bands"], []).append(lat)
         if lat.size and np.percentile(lat, 99) < 1e3 / sp["rate"]:
             ok_streams += 1
+        elif lat.size:
+            over.append({"stream": i, "width": sp["width"], "bands": sp["bands"],
+                         "p99_ms": round(float(np.percentile(lat, 99)), 3), "period_ms": round(1e3 / sp["rate"], 3)})
     allv = np.concatenate(lat_all)
     out = {
         "streams": len(specs), "precision": precision, "seconds": seconds, "lines": int(allv.size),
@@ -264,7 +267,8 @@ def run_serving(hs, device, precision, seconds, warm_s, pool_lines=96, seed_offs
         "p99_ms_by_bands": {str(b): float(np.percentile(np.concatenate(v), 99)) for b, v in sorted(by_b.items())},
         "line_period_ms": [round(1e3 / max(sp["rate"] for sp in specs), 2),
                            round(1e3 / min(sp["rate"] for sp in specs), 2)],
-        "streams_p99_below_period": ok_streams, "pushes": pushes, "max_batch": max_batch,
+        "streams_p99_below_period": ok_streams, "streams_over_period": over, "pushes": pushes,
+        "max_batch": max_batch,
         "engine_error": hs.hsad_status_string(err),
     }
     return out

@@ -131,6 +131,84 @@ __device__ __forceinline__ double ld_remote(const double* local, int rank) {
   return v;
 }
 
+// Trailing update of panel p: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B,
+// in TS x TS register tiles over the lower triangle (same operations per element for any
+// TS). The panel P (rows p.., kb columns) is in shared memory.
+template <int CL, int TS>
+__device__ __forceinline__ void trailing_update(double* A, const double* P, int B, int p, int kb, int rows, int gtid,
+                                                int gthreads) {
+  const int mt = (rows - kb + TS - 1) / TS;
+  const int ntiles = mt * (mt + 1) / 2;
+  for (int idx = gtid; idx < ntiles; idx += gthreads) {
+    int ti = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+    while (ti * (ti + 1) / 2 > idx) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
+    const int tk = idx - ti * (ti + 1) / 2;
+    const int r0 = kb + TS * ti, c0 = kb + TS * tk;  // panel-relative
+    double acc[TS][TS];
+#pragma unroll
+    for (int a = 0; a < TS; ++a)
+#pragma unroll
+      for (int b = 0; b < TS; ++b) {
+        const int r = r0 + a, c = c0 + b;
+        acc[a][b] = (r < rows && c <= r) ? ldg_c<CL>(A + (int64_t)(p + r) * B + p + c) : 0.0;
+      }
+    for (int j = 0; j < kb; ++j) {
+      double x[TS], y[TS];
+#pragma unroll
+      for (int a = 0; a < TS; ++a) {
+        x[a] = (r0 + a < rows) ? P[(r0 + a) * PS + j] : 0.0;
+        y[a] = (c0 + a < rows) ? P[(c0 + a) * PS + j] : 0.0;
+      }
+#pragma unroll
+      for (int a = 0; a < TS; ++a)
+#pragma unroll
+        for (int b = 0; b < TS; ++b) acc[a][b] = fma(-x[a], y[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TS; ++a)
+#pragma unroll
+      for (int b = 0; b < TS; ++b) {
+        const int r = r0 + a, c = c0 + b;
+        if (r < rows && c <= r) A[(int64_t)(p + r) * B + p + c] = acc[a][b];
+      }
+  }
+}
+
+// Inverse update of block row p: R_j -= L_jp X_p for the rows below the block (panel-
+// relative kb..rows) and the columns c < ncols, in TS x TS register tiles.
+template <int CL, int TS>
+__device__ __forceinline__ void inverse_update(double* R, const double* P, int B, int p, int kb, int rows, int ncols,
+                                               int gtid, int gthreads) {
+  const int mt = (rows - kb + TS - 1) / TS, nct = (ncols + TS - 1) / TS;
+  for (int idx = gtid; idx < mt * nct; idx += gthreads) {
+    const int tr = idx / nct, tcx = idx - tr * nct;
+    const int j0 = kb + TS * tr, c0 = TS * tcx;  // j0 panel-relative row, c0 column
+    double acc[TS][TS];
+#pragma unroll
+    for (int a = 0; a < TS; ++a)
+#pragma unroll
+      for (int b = 0; b < TS; ++b)
+        acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + j0 + a) * B + c0 + b) : 0.0;
+    for (int q = 0; q < kb; ++q) {
+      double l[TS], xq[TS];
+#pragma unroll
+      for (int a = 0; a < TS; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : 0.0;
+#pragma unroll
+      for (int b = 0; b < TS; ++b) xq[b] = (c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + q) * B + c0 + b) : 0.0;
+#pragma unroll
+      for (int a = 0; a < TS; ++a)
+#pragma unroll
+        for (int b = 0; b < TS; ++b) acc[a][b] = fma(-l[a], xq[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TS; ++a)
+#pragma unroll
+      for (int b = 0; b < TS; ++b)
+        if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(p + j0 + a) * B + c0 + b] = acc[a][b];
+  }
+}
+
 // One CTA per line. Sigma (full B x B, lower triangle used) is factored in place in
 // global memory with a blocked right-looking Cholesky: the NB-column panel is staged in
 // shared memory and factored there, and the trailing lower triangle is updated with
@@ -190,6 +268,9 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
   double* P = smem;  // panel: P[r * PS + j] = A[p + r][p + j]
   __shared__ double rdg[NB];  // 1 / L[p + j][p + j] of the current panel
+  __shared__ int notpd;       // a non-positive pivot in the diagonal block (cluster form)
+  if (tid == 0) notpd = 0;
+  __syncthreads();
   for (int p = 0; p < B; p += NB) {
     const int kb = min(NB, B - p), rows = B - p;
     // One CTA factors the whole panel in shared memory. In a cluster every CTA factors
@@ -202,28 +283,61 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       P[r * PS + j] = ldg_c<CL>(A + (int64_t)(p + r) * B + p + j);
     }
     __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-      const double piv = P[j * PS + j];
-      if (!(piv > 0.0) || !isfinite(piv)) {  // same value in every thread: uniform exit
-        if (tid == 0) status[t] = LS_NOT_PD;
-        return;
-      }
-      const double l = sqrt(piv);
-      const double rl = 1.0 / l;  // one division per pivot; the column is scaled by multiplies
-      for (int r = j + 1 + tid; r < frows; r += FT) P[r * PS + j] *= rl;
-      __syncthreads();
-      if (tid == 0) {
-        P[j * PS + j] = l;
-        rdg[j] = rl;
-      }
-      const int nc = kb - j - 1;
-      if (nc > 0) {
-        for (int e = tid; e < (frows - j - 1) * nc; e += FT) {
-          const int r = j + 1 + e / nc, k = j + 1 + e % nc;
-          if (k <= r) P[r * PS + k] = fma(-P[r * PS + j], P[k * PS + j], P[r * PS + k]);
+    if (CL > 1) {
+      // the kb x kb diagonal block alone: one warp, warp-level syncs only (the same
+      // operations per element as the CTA-wide sweep below)
+      if (warp == 0) {
+        for (int j = 0; j < kb; ++j) {
+          const double piv = P[j * PS + j];
+          if (!(piv > 0.0) || !isfinite(piv)) {  // same value in every lane
+            if (lane == 0) notpd = 1;
+            break;
+          }
+          const double l = sqrt(piv);
+          const double rl = 1.0 / l;
+          for (int r = j + 1 + lane; r < kb; r += 32) P[r * PS + j] *= rl;
+          __syncwarp();
+          if (lane == 0) {
+            P[j * PS + j] = l;
+            rdg[j] = rl;
+          }
+          const int nc = kb - j - 1;
+          for (int e = lane; e < nc * nc; e += 32) {
+            const int r = j + 1 + e / nc, k = j + 1 + e % nc;
+            if (k <= r) P[r * PS + k] = fma(-P[r * PS + j], P[k * PS + j], P[r * PS + k]);
+          }
+          __syncwarp();
         }
       }
       __syncthreads();
+      if (notpd) {  // the same in every CTA of the cluster: uniform exit
+        if (tid == 0) status[t] = LS_NOT_PD;
+        return;
+      }
+    } else {
+      for (int j = 0; j < kb; ++j) {
+        const double piv = P[j * PS + j];
+        if (!(piv > 0.0) || !isfinite(piv)) {  // same value in every thread: uniform exit
+          if (tid == 0) status[t] = LS_NOT_PD;
+          return;
+        }
+        const double l = sqrt(piv);
+        const double rl = 1.0 / l;  // one division per pivot; the column is scaled by multiplies
+        for (int r = j + 1 + tid; r < frows; r += FT) P[r * PS + j] *= rl;
+        __syncthreads();
+        if (tid == 0) {
+          P[j * PS + j] = l;
+          rdg[j] = rl;
+        }
+        const int nc = kb - j - 1;
+        if (nc > 0) {
+          for (int e = tid; e < (frows - j - 1) * nc; e += FT) {
+            const int r = j + 1 + e / nc, k = j + 1 + e % nc;
+            if (k <= r) P[r * PS + k] = fma(-P[r * PS + j], P[k * PS + j], P[r * PS + k]);
+          }
+        }
+        __syncthreads();
+      }
     }
     if (CL > 1) {
       // L21 = A21 L11^{-T}: forward substitution along each row, in the same order of
@@ -258,51 +372,22 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       const int r = e / kb, j = e - r * kb;
       if (r >= j && rank == 0) A[(int64_t)(p + r) * B + p + j] = P[r * PS + j];
     }
-    // trailing update: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B
+    // trailing update: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B. A cluster
+    // switches to 2 x 2 tiles once the 4 x 4 tiles of a phase no longer cover all of its
+    // threads (late panels), so that every SM sub-partition of the cluster has work.
     const int mrem = rows - kb;
     if (mrem > 0) {
-      const int mt = (mrem + 3) >> 2;
-      const int ntiles = mt * (mt + 1) / 2;
-      for (int idx = gtid; idx < ntiles; idx += gthreads) {
-        int ti = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
-        while (ti * (ti + 1) / 2 > idx) --ti;
-        while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
-        const int tk = idx - ti * (ti + 1) / 2;
-        const int r0 = kb + 4 * ti, c0 = kb + 4 * tk;  // panel-relative
-        double acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int r = r0 + a, c = c0 + b;
-            acc[a][b] = (r < rows && c <= r) ? ldg_c<CL>(A + (int64_t)(p + r) * B + p + c) : 0.0;
-          }
-        for (int j = 0; j < kb; ++j) {
-          double x[4], y[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            x[a] = (r0 + a < rows) ? P[(r0 + a) * PS + j] : 0.0;
-            y[a] = (c0 + a < rows) ? P[(c0 + a) * PS + j] : 0.0;
-          }
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(-x[a], y[b], acc[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int r = r0 + a, c = c0 + b;
-            if (r < rows && c <= r) A[(int64_t)(p + r) * B + p + c] = acc[a][b];
-          }
-      }
+      const int mt4 = (mrem + 3) >> 2;
+      if (CL > 1 && mt4 * (mt4 + 1) / 2 < gthreads)
+        trailing_update<CL, 2>(A, P, B, p, kb, rows, gtid, gthreads);
+      else
+        trailing_update<CL, 4>(A, P, B, p, kb, rows, gtid, gthreads);
     }
     // ---- triangular inverse, block row p, fused into the Cholesky step ----------------
     // X = L^{-1} is built right-looking in place of R = I: once panel p is factored, block
     // row p of X is X_p = L_pp^{-1} R_p (forward substitution, one thread per column, in
     // this phase next to the trailing update), and every later block row takes the rank-kb
-    // update R_j -= L_jp X_p (next phase, 4 x 4 register tiles). R_p has received the
+    // update R_j -= L_jp X_p (next phase, register tiles). R_p has received the
     // updates of every earlier block row, and the operations per element run in the same
     // order as in a separate inverse sweep after the whole factorisation.
     double* R = Inv;
@@ -324,33 +409,10 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       }
       csync<CL>();  // the trailing update of A and X_p are complete cluster-wide
       if (mrem > 0) {
-        const int mt = (mrem + 3) >> 2, nct = (ncols + 3) >> 2;
-        for (int idx = gtid; idx < mt * nct; idx += gthreads) {
-          const int tr = idx / nct, tcx = idx - tr * nct;
-          const int j0 = kb + 4 * tr, c0 = 4 * tcx;  // j0 panel-relative row, c0 column
-          double acc[4][4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-              acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + j0 + a) * B + c0 + b) : 0.0;
-          for (int q = 0; q < kb; ++q) {
-            double l[4], xq[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : 0.0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) xq[b] = (c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + q) * B + c0 + b) : 0.0;
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) acc[a][b] = fma(-l[a], xq[b], acc[a][b]);
-          }
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-              if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(p + j0 + a) * B + c0 + b] = acc[a][b];
-        }
+        if (CL > 1 && ((mrem + 3) >> 2) * ((ncols + 3) >> 2) < gthreads)
+          inverse_update<CL, 2>(R, P, B, p, kb, rows, ncols, gtid, gthreads);
+        else
+          inverse_update<CL, 4>(R, P, B, p, kb, rows, ncols, gtid, gthreads);
       }
       csync<CL>();  // panel p done: next panel (and its shared-memory buffer) may start
     }
