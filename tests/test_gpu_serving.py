@@ -95,3 +95,41 @@ def test_admission_by_device_budget(hs):
     hs.hsad_engine_destroy(eng)
     hs.hsad_set_device_budget(0, 0)
     assert hs.hsad_device_budget_used(0) == base
+
+
+def test_stream_closed_mid_flight_leaves_the_others_intact(hs):
+    """Closing a stream while its lines are queued and on the GPU waits (bounded) for its
+    work, frees its budget and returns OK; the other stream's results are unaffected, and
+    destroying a plain context with work in flight also returns OK."""
+    from gen import PushbroomScene
+    gc_base = hs.hsad_device_budget_used(0)
+    scs = [PushbroomScene(128, 96, seed=600), PushbroomScene(96, 40, seed=601)]
+    lines = [sc.lines(0, 60) for sc in scs]
+    rc, eng = hs.hsad_engine_create(0, 0)
+    assert rc == hs.HSAD_OK
+    sids = []
+    for sc, ln in zip(scs, lines):
+        cfg = hs.make_config(ln.shape[1], ln.shape[2], precision="bf16", gain=sc.gain, offset=sc.offset,
+                             max_batch_lines=8)
+        rc, sid = hs.hsad_engine_open(eng, cfg)
+        assert rc == hs.HSAD_OK
+        sids.append(sid)
+    for t in range(0, 60, 3):  # both streams busy
+        for k in range(2):
+            assert hs.hsad_engine_submit(eng, sids[k], np.ascontiguousarray(lines[k][t:t + 3]), 3)[0] == hs.HSAD_OK
+    assert hs.hsad_engine_close(eng, sids[0]) == hs.HSAD_OK          # mid-flight
+    assert hs.hsad_engine_submit(eng, sids[0], np.ascontiguousarray(lines[0][:1]), 1)[0] == hs.HSAD_E_INVALID
+    s = np.empty((60, 96), np.float32)
+    m = np.empty((60, 96), np.uint8)
+    rc = hs.hsad_engine_results(eng, sids[1], 0, 60, s, m, 20000)
+    assert rc in (hs.HSAD_OK, hs.HSAD_E_NOT_READY), hs.hsad_status_string(rc)
+    s0, m0 = _alone(hs, lines[1], scs[1], "bf16")
+    np.testing.assert_array_equal(np.nan_to_num(s), np.nan_to_num(s0))
+    np.testing.assert_array_equal(m, m0)
+    assert hs.hsad_engine_destroy(eng) == hs.HSAD_OK
+    # a plain context destroyed with pushed, unread work in flight
+    det = hs.Detector(width=128, bands=96, precision="bf16", gain=scs[0].gain, offset=scs[0].offset)
+    det.push(lines[0])
+    assert hs.hsad_destroy(det.ctx) == hs.HSAD_OK
+    det.ctx = None
+    assert hs.hsad_device_budget_used(0) == gc_base
