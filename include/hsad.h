@@ -156,6 +156,18 @@ int hsad_reset(hsad_ctx* ctx);
  * exact integer. Synchronises the context's stream (bounded, 10 s). */
 int hsad_get_stats(hsad_ctx* ctx, int64_t* n_pixels, double* shift, double* s1, double* s2);
 
+/* Import running statistics exported by hsad_get_stats (checkpoint / resume of a stream;
+ * the paper keeps no detector state). Stream modes only, on a context with no line pushed
+ * since creation or hsad_reset. n_pixels >= 0; shift[B] (uint16 input: integers in
+ * [0, 65535]), s1[B], s2[B*B] (lower triangle read) are host arrays. Lines pushed next are
+ * scored against the imported statistics exactly as if they had followed the exported
+ * lines in one stream (for uint16 input the sums are exact, so the scores are bitwise the
+ * same); EXCLUSIVE mode also rebuilds the carried factor here (enqueued on the context's
+ * stream). Line ids and the reset schedule (cube_lines) count from 0 in the new context.
+ * Returns HSAD_E_INVALID for CUBE mode, a context already in use, NULL arrays or a bad
+ * shift. */
+int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const double* s1, const double* s2);
+
 /* Block until all work enqueued on the context has finished (bounded by timeout_ms,
  * negative = no limit). */
 int hsad_synchronize(hsad_ctx* ctx, int32_t timeout_ms);

@@ -1146,6 +1146,54 @@ int hsad_get_stats(hsad_ctx* ctx, int64_t* n_pixels, double* shift, double* s1, 
   return HSAD_OK;
 }
 
+int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const double* s1, const double* s2) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  if (ctx->mode == HSAD_CUBE) return fail(ctx, HSAD_E_INVALID, "statistics import is for stream modes");
+  if (!shift || !s1 || !s2 || n_pixels < 0) return fail(ctx, HSAD_E_INVALID, "NULL array or negative n_pixels");
+  if (ctx->next_line != 0 || ctx->n_stats != 0)
+    return fail(ctx, HSAD_E_INVALID, "import needs a context with no line pushed since creation or reset");
+  const int B = ctx->B;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t st = ctx->stream;
+  if (ctx->in_type == IN_U16) {
+    std::vector<int32_t> c(B);
+    for (int b = 0; b < B; ++b) {
+      if (!(shift[b] >= 0.0 && shift[b] <= 65535.0) || shift[b] != std::floor(shift[b]))
+        return fail(ctx, HSAD_E_INVALID, "uint16 shift must hold integers in [0, 65535]");
+      c[b] = (int32_t)shift[b];
+    }
+    CK(cudaMemcpyAsync(ctx->c_int, c.data(), (size_t)B * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::vector<float> c(B);
+    for (int b = 0; b < B; ++b) {
+      if (!std::isfinite(shift[b])) return fail(ctx, HSAD_E_INVALID, "shift must be finite");
+      c[b] = (float)shift[b];
+    }
+    CK(cudaMemcpyAsync(ctx->c_flt, c.data(), (size_t)B * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  CK(cudaMemcpyAsync(ctx->state_s1, s1, (size_t)B * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->state_s2, s2, (size_t)B * B * 8, cudaMemcpyHostToDevice, st));
+  if (ctx->mode == HSAD_EXCLUSIVE && n_pixels > 0) {
+    // slot 0: the factor of the imported statistics, as the last batch would have left it
+    std::vector<double> m(B);
+    for (int b = 0; b < B; ++b) m[b] = s1[b] / (double)n_pixels;
+    const int32_t st0 = n_pixels >= ctx->min_pix ? LS_OK : LS_NOT_READY;
+    CK(cudaMemcpyAsync(ctx->sigma, s2, (size_t)B * B * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->m_line, m.data(), (size_t)B * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->status, &st0, 4, cudaMemcpyHostToDevice, st));
+    KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, 1, B, ctx->prec, ctx->wmat, ctx->y0,
+                               ctx->inv_s2, ctx->status, n_pixels, 0, 0, st, &ctx->lc));
+    CK(cudaStreamSynchronize(st));  // the host vectors above are copied before they go out of scope
+  } else {
+    CK(cudaStreamSynchronize(st));
+  }
+  ctx->n_stats = n_pixels;
+  return HSAD_OK;
+}
+
 int hsad_synchronize(hsad_ctx* ctx, int32_t timeout_ms) {
   if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
   if (ctx->failed) return HSAD_E_CUDA;

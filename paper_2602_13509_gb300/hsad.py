@@ -84,6 +84,7 @@ def _load():
         "hsad_engine_counters": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "hsad_engine_destroy": (C.c_int, [P]),
         "hsad_selftest_bounded_wait": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
+        "hsad_set_stats": (C.c_int, [P, C.c_int64, P, P, P]),
         "hsad_autotune_factor": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float),
                                            C.POINTER(C.c_int32)]),
         "hsad_destroy": (C.c_int, [P]),
@@ -276,6 +277,13 @@ def hsad_engine_counters(engine):
 
 def hsad_engine_destroy(engine) -> int:
     return _lib.hsad_engine_destroy(engine)
+
+
+def hsad_set_stats(ctx, n_pixels: int, shift, s1, s2) -> int:
+    """Import statistics exported by hsad_get_stats (float64 numpy arrays)."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (shift, s1, s2)]
+    return _lib.hsad_set_stats(ctx, int(n_pixels), *(a.ctypes.data for a in arrs))
 
 
 def hsad_autotune_factor(device: int, bands: int, precision: str, max_lines: int):

@@ -247,6 +247,41 @@ def test_pinned_pageable_and_device_pushes_agree(hs, graphs):
         np.testing.assert_array_equal(m, ref[1])
 
 
+@pytest.mark.parametrize("mode", ["exclusive", "inclusive"])
+def test_statistics_export_import_resumes_bitwise(hs, mode):
+    """Checkpoint / resume: a stream exported after 12 lines and imported into a fresh
+    context scores the remaining lines exactly as the uninterrupted stream does."""
+    sc, lines = _scene_lines(30, 48, 20, seed=16)
+    kw = dict(width=48, bands=20, stats_mode=mode, precision="bf16", gain=sc.gain, offset=sc.offset)
+    a = hs.Detector(**kw)
+    a.push(lines)
+    rc, sa, ma, sta = a.scores(0, 30)
+    a.close()
+    b = hs.Detector(**kw)
+    b.push(lines[:12])
+    rc, n, shift, s1, s2 = hs.hsad_get_stats(b.ctx, 20)
+    b.close()
+    assert rc == hs.HSAD_OK and n == 12 * 48
+    c = hs.Detector(**kw)
+    assert hs.hsad_set_stats(c.ctx, n, shift, s1, s2) == hs.HSAD_OK
+    for t in range(12, 30, 6):
+        c.push(lines[t:t + 6])
+    rc, sc_, mc, stc = c.scores(0, 18)
+    assert hs.hsad_set_stats(c.ctx, n, shift, s1, s2) == hs.HSAD_E_INVALID  # context in use
+    c.close()
+    np.testing.assert_array_equal(sc_, sa[12:])
+    np.testing.assert_array_equal(mc, ma[12:])
+    np.testing.assert_array_equal(stc, sta[12:])
+    cube = hs.Detector(width=48, bands=20, stats_mode="cube", cube_lines=8)
+    assert hs.hsad_set_stats(cube.ctx, n, shift, s1, s2) == hs.HSAD_E_INVALID
+    bad = np.array(shift, dtype=np.float64)
+    bad[0] += 0.5
+    d = hs.Detector(**kw)
+    assert hs.hsad_set_stats(d.ctx, n, bad, s1, s2) == hs.HSAD_E_INVALID
+    cube.close()
+    d.close()
+
+
 def test_not_positive_definite_is_reported(hs):
     sc, lines = _scene_lines(12, 40, 8, seed=2)
     lines = lines.copy()
