@@ -944,8 +944,17 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
   const int64_t CLr = ctx->cfg.cube_lines;
   const bool pinned = mem == HSAD_HOST && is_pinned_host_ptr(lines);
   cudaEvent_t last_copy = nullptr;
+  // A large pinned push runs as batches of two factor waves (the lines one launch of the
+  // factor kernel holds resident, twice), so that the copy of each batch overlaps the
+  // previous batch's kernels while the factor launches stay whole waves; the statistics
+  // are exact, so batch boundaries do not change any score.
+  int64_t pinned_batch = ctx->Lmax;
+  if (pinned) {
+    const int64_t wave = factor_wave_lines(ctx->B, ctx->prec);
+    if (wave > 0 && n_lines >= 3 * wave) pinned_batch = std::min<int64_t>(ctx->Lmax, 2 * wave);
+  }
   while (done < n_lines) {
-    int64_t take = std::min<int64_t>(n_lines - done, ctx->Lmax);
+    int64_t take = std::min<int64_t>(n_lines - done, pinned ? pinned_batch : ctx->Lmax);
     if (CLr > 0) {
       const int64_t into = (int64_t)(ctx->next_line % (uint64_t)CLr);
       take = std::min<int64_t>(take, CLr - into);

@@ -90,6 +90,9 @@ cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, 
 // fastest per bucket for launch_factor (current device). report: rows of (bucket, cl, ft,
 // ms), up to cap rows. Returns the number of buckets or a negative value on failure.
 int factor_autotune(int B, int prec, int max_lines, float* report, int cap);
+// Lines one launch of the one-CTA-per-line factor holds resident on the current device
+// (SMs x CTAs per SM for its default shape), 0 if unknown.
+int factor_wave_lines(int B, int prec);
 // Query and cache, once per device, B and precision, how many clusters of each size the
 // factor kernel can run at once (host calls that must not land on a line's latency path).
 void factor_prepare(int B, int prec);

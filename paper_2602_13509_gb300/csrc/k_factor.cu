@@ -613,6 +613,42 @@ bool tuned_shape(int B, int prec, int L, int* cl, int* ft) {
   return false;  // larger than every measured batch: the occupancy rule
 }
 
+namespace {
+// Resident one-CTA-per-line factor CTAs on the whole device (SMs x CTAs per SM), cached.
+template <int PREC, int FT, int MB>
+int wave_slots_t(size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_pair(dev, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0, sms = 0;
+  if (cudaFuncSetAttribute(factor_kernel<PREC, 1, FT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<PREC, 1, FT, MB>, FT, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    per_sm = 0;
+  cudaGetLastError();
+  return cache[key] = per_sm * sms;
+}
+template <int PREC>
+int wave_slots_p(int ft, size_t smem) {
+  if (ft == 96) return wave_slots_t<PREC, 128, 5>(smem);
+  if (ft == 128) return wave_slots_t<PREC, 128, 4>(smem);
+  return wave_slots_t<PREC, 256, 2>(smem);
+}
+}  // namespace
+
+int factor_wave_lines(int B, int prec) {
+  const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
+  const int ft = factor_single_threads();
+  return prec == P_FP32 ? wave_slots_p<P_FP32>(ft, smem)
+                        : (prec == P_FP16 ? wave_slots_p<P_FP16>(ft, smem) : wave_slots_p<P_BF16>(ft, smem));
+}
+
 void factor_prepare(int B, int prec) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
 #define HSAD_FP(P)                             \
@@ -626,6 +662,7 @@ void factor_prepare(int B, int prec) {
     default: HSAD_FP(P_BF16); break;
   }
 #undef HSAD_FP
+  factor_wave_lines(B, prec);
 }
 
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,

@@ -282,6 +282,31 @@ def test_statistics_export_import_resumes_bitwise(hs, mode):
     d.close()
 
 
+def test_large_pinned_push_runs_as_wave_batches_bitwise(hs):
+    """A pinned host push of several factor waves runs as batches of two waves whose
+    copies overlap the previous batch's kernels; the scores equal those of the same lines
+    pushed from device memory in one batch."""
+    import torch
+    T, W, B = 2600, 32, 16
+    sc, lines = _scene_lines(T, W, B, seed=17)
+    out = []
+    for kind in ("pinned", "device"):
+        det = hs.Detector(width=W, bands=B, stats_mode="exclusive", precision="bf16", max_batch_lines=4096,
+                          result_lines=T)
+        if kind == "pinned":
+            x = torch.from_numpy(lines.view(np.int16)).pin_memory()
+            rc, first = hs.hsad_push_lines(det.ctx, x, T, hs.HSAD_HOST)
+        else:
+            x = torch.from_numpy(lines.view(np.int16)).cuda()
+            rc, first = hs.hsad_push_lines(det.ctx, x, T, hs.HSAD_DEVICE)
+        assert rc == hs.HSAD_OK
+        rc, s, m, st = det.scores(first, T)
+        out.append((s, m, det.kernel_launches))
+        det.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
 def test_not_positive_definite_is_reported(hs):
     sc, lines = _scene_lines(12, 40, 8, seed=2)
     lines = lines.copy()
