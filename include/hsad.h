@@ -231,16 +231,17 @@ int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int
 
 /* Factor-kernel autotuner (no counterpart in the paper). Times every launch shape of the
  * FP64 factorisation (one 128-thread CTA per line with registers for 4 or 5 CTAs per SM,
- * one 256-thread CTA per line, or a 2/4/8/16-CTA cluster per line) on synthetic positive definite problems of `bands` bands, for batches of 1, 2, 4,
- * ..., max_lines lines (1 .. 4096), and makes contexts on `device` with that band count
- * and precision use the fastest shape per batch size from then on. Results do not depend
- * on the shape (bitwise). The measurement is kept per process: a second call with no
- * larger max_lines returns at once. report (nullable): rows of 4 floats (largest batch
- * size of the bucket, CTAs per line, threads per CTA (96 = 128 threads sized for 5 CTAs
- * per SM), milliseconds), up to *n_rows rows;
- * *n_rows (nullable on input only if report is NULL) receives the number of buckets.
- * Allocates (and frees) scratch device memory for max_lines problems. Returns HSAD_OK,
- * HSAD_E_INVALID, or HSAD_E_CUDA. */
+ * one 256-thread CTA per line, or a 2/4/8/16-CTA cluster per line) on synthetic
+ * positive definite problems of `bands` bands, for batches of 1, 2, 4, ..., max_lines
+ * lines (1 .. 4096), and makes contexts on `device` with that band count and precision
+ * use the fastest shape per batch size from then on (larger batches keep the built-in
+ * rule). Results do not depend on the shape (bitwise). The measurement is kept per
+ * process: a second call with no larger max_lines returns at once. report (nullable):
+ * rows of 4 floats (largest batch size of the bucket, CTAs per line, threads per CTA
+ * (96 = 128 threads sized for 5 CTAs per SM), milliseconds), up to *n_rows rows; *n_rows
+ * (nullable only if report is NULL) receives the number of buckets. Allocates (and
+ * frees) scratch device memory for max_lines problems. Returns HSAD_OK, HSAD_E_INVALID,
+ * or HSAD_E_CUDA. */
 int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32_t max_lines, float* report,
                          int32_t* n_rows);
 
@@ -265,7 +266,9 @@ typedef struct hsad_engine hsad_engine;
  * (0 = unlimited; this sets the device-wide budget of hsad_set_device_budget). */
 int hsad_engine_create(int32_t device, int64_t budget_bytes, hsad_engine** out);
 
-/* Admit a stream with configuration *cfg (its device field is ignored). Returns
+/* Admit a stream with configuration *cfg (its device field is ignored; HSAD_CUDA_GRAPHS
+ * is added to its flags). A band count the engine has not served before is first
+ * autotuned (hsad_autotune_factor, batches up to min(max_batch_lines, 64)). Returns
  * HSAD_E_BUSY while the budget cannot hold it (retry after a stream closes; with
  * HSAD_CREATE_WAIT in cfg->flags the call waits up to 10 s), HSAD_E_NOMEM if it can
  * never fit, else HSAD_OK and the stream's id. */
