@@ -50,8 +50,19 @@ def load_peaks():
 
 # DRAM bytes per line of the factor kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of a 512-line launch, profiles/factor_512x640x270.md), scaled to a
-# launch by its lines; keyed by band count, and to be refreshed whenever the kernel changes.
-FACTOR_DRAM_BYTES_PER_LINE = {270: (2.009082e9 + 2.316017e9) / 512}
+# launch by its lines; keyed by (band count, whitening form), and to be refreshed whenever
+# the kernel changes (a form without a capture of the current kernel reports null).
+FACTOR_DRAM_BYTES_PER_LINE = {}
+
+
+def factor_flops_per_line(B, form):
+    """Algorithmic FP64 flops of one line's factorisation: the Cholesky factor (B^3 / 3)
+    plus the full triangular inverse (B^3 / 3) for the explicit-inverse form, or plus only
+    the inverses of the 64 x 64 diagonal blocks (b^3 / 3 each) for the triangular solve."""
+    if form == 0:
+        return 2.0 * B ** 3 / 3.0
+    blocks = [min(64, B - b) for b in range(0, B, 64)]
+    return B ** 3 / 3.0 + sum(b ** 3 / 3.0 for b in blocks)
 
 
 # FP64 and FP32 SIMT peaks derived from unit counts x clock (no measured figure exists):
@@ -495,6 +506,7 @@ def main():
 
     px_step = T * W
     det = detector(args.precision)
+    form = det.whitening_form
     with ClockSampler(local) as clk:
         ms, launches = timed(det)
     value = weak_value(px_step, world, ms)
@@ -573,15 +585,18 @@ def main():
         launches_per_step = n / prof_steps
         if dom == "factor":
             lines_per_launch = T / launches_per_step
-            work = lines_per_launch * 2.0 * B ** 3 / 3.0
+            work = lines_per_launch * factor_flops_per_line(B, form)
             ach = work / (avg_ms / 1e3) / 1e12
             pk = fp64_peak_tflops(mhz)
+            key = (B, form)
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": (FACTOR_DRAM_BYTES_PER_LINE[B] * lines_per_launch
-                                if B in FACTOR_DRAM_BYTES_PER_LINE else None),
+                    "traffic": (FACTOR_DRAM_BYTES_PER_LINE[key] * lines_per_launch
+                                if key in FACTOR_DRAM_BYTES_PER_LINE else None),
                     "traffic_source": "ncu dram bytes per line of a 512-line capture x lines per launch",
-                    "kernel": "factor (FP64 Cholesky + triangular inverse)",
-                    "work_per_launch": f"{lines_per_launch:.0f} lines x 2B^3/3 FP64 flop",
+                    "kernel": ("factor (FP64 Cholesky + inverses of the 64 x 64 diagonal blocks)" if form
+                               else "factor (FP64 Cholesky + triangular inverse)"),
+                    "work_per_launch": (f"{lines_per_launch:.0f} lines x (B^3/3 + sum of 64-block b^3/3) FP64 flop"
+                                        if form else f"{lines_per_launch:.0f} lines x 2B^3/3 FP64 flop"),
                     "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk (nominal 1.25 TF/s; "
                                    "a DFMA probe measured 1.20 TF/s)"}
         else:
@@ -607,6 +622,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "width": W, "bands": B, "lines": T, "stats": "exclusive",
                    "input": "uint16 12-bit DN", "batch_lines": wl["batch"],
+                   "whitening": "triangular solve" if form else "explicit inverse",
                    "parallelism": f"replicas x{world} (independent streams)" if world > 1 else "single stream",
                    "l2": "inputs larger than L2 (%.2f GB per step)" % (x_dev.numel() * 2 / 1e9),
                    "host": host_cpus},

@@ -49,9 +49,16 @@ typedef enum {
 /* input element type */
 enum { HSAD_U16 = 0, HSAD_F32 = 1 };
 /* working precision of the whitening contraction (the covariance sums are exact
- * for HSAD_U16 input in every mode; the Cholesky factorisation and triangular
- * inverse are always FP64) */
+ * for HSAD_U16 input in every mode; the Cholesky factorisation and the triangular
+ * inverses are always FP64) */
 enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
+/* whitening form of a context (Eq. 1, Sec. 3.3), see hsad_whitening_form:
+ * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1} D, the full triangular
+ *                              inverse (FP32, FP16; BF16 with float input or B > 448);
+ * HSAD_FORM_TRIANGULAR_SOLVE   L y = x' - m solved blockwise on the tensor cores from L and
+ *                              the inverses of its 64 x 64 diagonal blocks only (BF16 with
+ *                              uint16 input and B <= 448): half the FP64 factor work. */
+enum { HSAD_FORM_INVERSE = 0, HSAD_FORM_TRIANGULAR_SOLVE = 1 };
 /* statistics window (which pixels form mu and Sigma for a scored line t) */
 enum {
   HSAD_EXCLUSIVE = 0, /* lines [r, t): line t scored against earlier lines only */
@@ -191,6 +198,9 @@ int hsad_profile_read(hsad_ctx* ctx, int32_t index, char* name, int32_t name_len
 
 /* Clear the per-kernel totals. */
 int hsad_profile_reset(hsad_ctx* ctx);
+
+/* The context's whitening form (HSAD_FORM_*), or HSAD_E_INVALID for a null context. */
+int hsad_whitening_form(const hsad_ctx* ctx);
 
 /* Bytes of device memory the context holds. */
 int64_t hsad_device_bytes(const hsad_ctx* ctx);

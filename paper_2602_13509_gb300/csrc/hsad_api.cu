@@ -318,7 +318,7 @@ void release(hsad_ctx* ctx) {
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
-bool encode_gmap(CUtensorMap* map, void* base, int64_t Bp, int64_t rows) {
+bool encode_gmap(CUtensorMap* map, void* base, int64_t Bp, int64_t rows, int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -333,7 +333,8 @@ bool encode_gmap(CUtensorMap* map, void* base, int64_t Bp, int64_t rows) {
   }
   const cuuint64_t dims[2] = {(cuuint64_t)Bp, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)Bp * 2};
-  const cuuint32_t box[2] = {64, 128};  // 64 k (128 B, the swizzle span) x two 64-row n blocks
+  // 64 k (128 B, the swizzle span) x one (triangular solve) or two 64-row n blocks
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -395,7 +396,10 @@ int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32
     return ndev <= 0 ? HSAD_E_CUDA : HSAD_E_INVALID;
   }
   DeviceGuard dg(device);
-  const int prec = precision == HSAD_FP32 ? P_FP32 : (precision == HSAD_BF16 ? P_BF16 : P_FP16);
+  // BF16: the form of a uint16-input context (the streaming case)
+  const int prec = precision == HSAD_FP32 ? P_FP32
+                   : precision == HSAD_BF16 ? bf16_form(bands, IN_U16)
+                                            : P_FP16;
   factor_prepare(bands, prec);
   const int cap = report ? *n_rows : 0;
   const int n = factor_autotune(bands, prec, max_lines, report, cap);
@@ -463,7 +467,9 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->B = cfg->bands;
   ctx->Bp = pad64(cfg->bands);
   ctx->in_type = cfg->in_dtype == HSAD_U16 ? IN_U16 : IN_F32;
-  ctx->prec = cfg->precision == HSAD_FP32 ? P_FP32 : (cfg->precision == HSAD_BF16 ? P_BF16 : P_FP16);
+  ctx->prec = cfg->precision == HSAD_FP32 ? P_FP32
+              : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type)
+                                            : P_FP16;
   ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE;
   ctx->mode = cfg->stats_mode;
   ctx->elem = ctx->in_type == IN_U16 ? 2 : 4;
@@ -591,7 +597,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   if (ctx->prec != P_FP32) {
     // G planes [Lf][2][Bp][Bp] 16-bit as a 2-D tensor of Lf*2*Bp rows, 64 x 64 boxes
     const int64_t rows = Lf * 2 * Bp;
-    if (!encode_gmap(&ctx->gmap, ctx->wmat, Bp, rows)) {
+    if (!encode_gmap(&ctx->gmap, ctx->wmat, Bp, rows, ctx->prec == P_BF16T ? 64 : 128)) {
       release(ctx);
       return fail(nullptr, HSAD_E_CUDA, "cuTensorMapEncodeTiled failed for the whitening operand");
     }
@@ -639,7 +645,10 @@ int add_record(hsad_ctx* ctx, uint64_t first, uint64_t n) {
 // K6: tensor cores (tcgen05, G by TMA) for the FP16 / BF16 forms, FFMA for FP32.
 int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o) {
   cudaStream_t st = ctx->stream;
-  if (ctx->prec != P_FP32) {
+  if (ctx->prec == P_BF16T) {
+    KL("whiten_score", launch_whiten_trsm((const uint16_t*)x, L, ctx->W, ctx->B, ctx->c_int, &ctx->gmap, ctx->y0,
+                                          ctx->inv_s2, ctx->status, factor_stride, o, ctx->dev_err, st, &ctx->lc));
+  } else if (ctx->prec != P_FP32) {
     KL("whiten_score", launch_whiten_tc(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec,
                                         &ctx->gmap, ctx->y0, ctx->inv_s2, ctx->status, factor_stride, o,
                                         ctx->dev_err, st, &ctx->lc));
@@ -1267,6 +1276,11 @@ void* hsad_stream(hsad_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 int64_t hsad_kernel_launches(const hsad_ctx* ctx) { return ctx ? ctx->lc.n : 0; }
 
 int64_t hsad_device_bytes(const hsad_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+int hsad_whitening_form(const hsad_ctx* ctx) {
+  if (!ctx) return HSAD_E_INVALID;
+  return ctx->prec == P_BF16T ? HSAD_FORM_TRIANGULAR_SOLVE : HSAD_FORM_INVERSE;
+}
 
 int hsad_destroy(hsad_ctx* ctx) {
   if (!ctx) return HSAD_OK;

@@ -21,7 +21,10 @@ namespace hsad {
 
 enum LineStatus : int32_t { LS_OK = 0, LS_NOT_READY = 1, LS_NOT_PD = 2, LS_INVALID_DATA = 3 };
 enum InType : int32_t { IN_U16 = 0, IN_F32 = 1 };
-enum Prec : int32_t { P_FP32 = 0, P_BF16 = 1, P_FP16 = 2 };
+enum Prec : int32_t { P_FP32 = 0, P_BF16 = 1, P_FP16 = 2,
+                      // factor output for the BF16 triangular-solve whitening: L's off-diagonal
+                      // 64 x 64 blocks and the inverses of its diagonal blocks, BF16 hi / lo
+                      P_BF16T = 3 };
 
 __host__ __device__ inline int pad64(int b) { return (b + 63) / 64 * 64; }
 
@@ -131,6 +134,20 @@ cudaError_t launch_whiten_tc(const void* x, int L, int W, int B, int in_type, co
                              const float* c_flt, int prec, const void* gmap, const float* y0,
                              const float* inv_s2, const int32_t* status, int factor_stride, ScoreOut out,
                              int32_t* err, cudaStream_t st, LaunchCounter* lc);
+
+// K6, triangular-solve form (P_BF16T factors, uint16 input): delta = ||L^{-1} (x' - m)||^2 by
+// blocked forward substitution on the tensor cores; hmap is the CUtensorMap over the BF16
+// hi / lo planes of H with 64 x 64 boxes, m the FP32 means (the y0 rows of the factor).
+cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, const int32_t* c_int, const void* hmap,
+                               const float* m, const float* inv_s2, const int32_t* status, int factor_stride,
+                               ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc);
+// Ring depth the triangular-solve whitening runs with for B bands; 0 if it does not fit.
+int whiten_trsm_stages(int B);
+// Working form of a BF16 context: P_BF16T (triangular solve) for uint16 input where the
+// solve fits on chip, else P_BF16 (explicit inverse).
+inline int bf16_form(int B, int in_type) {
+  return in_type == IN_U16 && whiten_trsm_stages(B) > 0 ? P_BF16T : P_BF16;
+}
 
 // K7: cube maximum of delta over n_lines ring lines, then optional normalisation and
 // the REL / ABS mask.

@@ -65,6 +65,8 @@ struct WOut<P_FP16> {
   }
 };
 template <>
+struct WOut<P_BF16T>;
+template <>
 struct WOut<P_BF16> {
   __device__ static float store(void* w, int64_t plane, int64_t idx, double v) {
     const float f = (float)v;
@@ -80,6 +82,8 @@ struct WOut<P_BF16> {
     ((uint16_t*)w)[plane + idx] = 0;
   }
 };
+template <>
+struct WOut<P_BF16T> : WOut<P_BF16> {};
 
 template <int FT>
 __device__ double block_max(double v, double* red) {
@@ -178,12 +182,12 @@ __device__ __forceinline__ void trailing_update(double* A, const double* P, int 
 // Inverse update of block row p: R_j -= L_jp X_p for the rows below the block (panel-
 // relative kb..rows) and the columns c < ncols, in TS x TS register tiles.
 template <int CL, int TS>
-__device__ __forceinline__ void inverse_update(double* R, const double* P, int B, int p, int kb, int rows, int ncols,
-                                               int gtid, int gthreads) {
-  const int mt = (rows - kb + TS - 1) / TS, nct = (ncols + TS - 1) / TS;
+__device__ __forceinline__ void inverse_update(double* R, const double* P, int B, int p, int kb, int rows, int cbase,
+                                               int ncols, int gtid, int gthreads) {
+  const int mt = (rows - kb + TS - 1) / TS, nct = (ncols - cbase + TS - 1) / TS;
   for (int idx = gtid; idx < mt * nct; idx += gthreads) {
     const int tr = idx / nct, tcx = idx - tr * nct;
-    const int j0 = kb + TS * tr, c0 = TS * tcx;  // j0 panel-relative row, c0 column
+    const int j0 = kb + TS * tr, c0 = cbase + TS * tcx;  // j0 panel-relative row, c0 column
     double acc[TS][TS];
 #pragma unroll
     for (int a = 0; a < TS; ++a)
@@ -252,13 +256,16 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
 
   // ---- covariance from the raw sums (lower triangle, in place) ----------------------
   // Sigma_ij = d_i d_j (S2_ij - n m_i m_j) / (n - 1), n = pixels in this line's window.
+  // (triangular-solve form: the DN-frame covariance S_ij = (S2_ij - n m_i m_j) / (n - 1);
+  // the gains cancel from Eq. 1, delta = (x' - m)^T S^{-1} (x' - m))
+  constexpr bool TRSM = PREC == P_BF16T;
   {
     const int64_t n = (n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W;
     const double nn = (double)n, inv_nm1 = 1.0 / (double)(n - 1);
     for (int i = gwarp; i < B; i += gwarps) {
-      const double ai = dgain[i] * inv_nm1, nmi = nn * m[i];
+      const double ai = (TRSM ? 1.0 : dgain[i]) * inv_nm1, nmi = nn * m[i];
       double* row = A + (int64_t)i * B;
-      for (int j = lane; j <= i; j += 32) row[j] = ai * dgain[j] * fma(-nmi, m[j], row[j]);
+      for (int j = lane; j <= i; j += 32) row[j] = ai * (TRSM ? 1.0 : dgain[j]) * fma(-nmi, m[j], row[j]);
     }
     // the inverse is built in place of R = I (entries above the diagonal stay zero)
     for (int64_t e = gtid; e < BB; e += gthreads) Inv[e] = ((int)(e / B) == (int)(e % B)) ? 1.0 : 0.0;
@@ -392,8 +399,12 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     // order as in a separate inverse sweep after the whole factorisation.
     double* R = Inv;
     {
+      // triangular-solve form: only the inverses of the 64 x 64 diagonal blocks of L
+      const int cbase = TRSM ? p / 64 * 64 : 0;
+      const int irows = TRSM ? min(B, cbase + 64) - p : rows;  // panel-relative row limit
+      const int imrem = irows - kb;
       const int ncols = p + kb;
-      for (int c = gtid; c < ncols; c += gthreads) {
+      for (int c = cbase + gtid; c < ncols; c += gthreads) {
         double xr[NB];
 #pragma unroll
         for (int r = 0; r < NB; ++r) {
@@ -408,16 +419,37 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
         }
       }
       csync<CL>();  // the trailing update of A and X_p are complete cluster-wide
-      if (mrem > 0) {
-        if (CL > 1 && ((mrem + 3) >> 2) * ((ncols + 3) >> 2) < gthreads)
-          inverse_update<CL, 2>(R, P, B, p, kb, rows, ncols, gtid, gthreads);
+      if (imrem > 0) {
+        if (CL > 1 && ((imrem + 3) >> 2) * ((ncols - cbase + 3) >> 2) < gthreads)
+          inverse_update<CL, 2>(R, P, B, p, kb, irows, cbase, ncols, gtid, gthreads);
         else
-          inverse_update<CL, 4>(R, P, B, p, kb, rows, ncols, gtid, gthreads);
+          inverse_update<CL, 4>(R, P, B, p, kb, irows, cbase, ncols, gtid, gthreads);
       }
       csync<CL>();  // panel p done: next panel (and its shared-memory buffer) may start
     }
   }
 
+  if (TRSM) {
+    // ---- triangular-solve operand H, BF16 hi / lo: H_ij = L_ij below the diagonal 64 x 64
+    // blocks, H_ii = L_ii^{-1}; y0 = m (the whitening forms x' - m in FP32); no scale -----
+    const int64_t plane = (int64_t)Bp * Bp;
+    void* w = (char*)wmat + (size_t)t * plane * 4;
+    for (int n = gwarp; n < Bp; n += gwarps) {
+      for (int k = lane; k < Bp; k += 32) {
+        const int64_t idx = (int64_t)n * Bp + k;
+        if (n < B && k <= n) {
+          const double* src = ((n >> 6) == (k >> 6)) ? Inv : A;
+          WOut<PREC>::store(w, plane, idx, ldg_c<CL>(src + (int64_t)n * B + k));
+        } else {
+          WOut<PREC>::zero(w, plane, idx);
+        }
+      }
+      if (lane == 0) y0_all[(int64_t)t * Bp + n] = (n < B) ? (float)m[n] : 0.0f;
+    }
+    if (gtid == 0) inv_s2_all[t] = 1.0f;
+    if (CL > 1) csync<CL>();  // no CTA leaves while others may still read its shared memory
+    return;
+  }
   // ---- G = Inv D, power-of-two scale, cast, y0 ------------------------------------
   double mx = 0.0;
   for (int n = gwarp; n < B; n += gwarps)  // X is lower triangular
@@ -645,8 +677,10 @@ int wave_slots_p(int ft, size_t smem) {
 int factor_wave_lines(int B, int prec) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   const int ft = factor_single_threads();
-  return prec == P_FP32 ? wave_slots_p<P_FP32>(ft, smem)
-                        : (prec == P_FP16 ? wave_slots_p<P_FP16>(ft, smem) : wave_slots_p<P_BF16>(ft, smem));
+  return prec == P_FP32    ? wave_slots_p<P_FP32>(ft, smem)
+         : prec == P_FP16  ? wave_slots_p<P_FP16>(ft, smem)
+         : prec == P_BF16T ? wave_slots_p<P_BF16T>(ft, smem)
+                           : wave_slots_p<P_BF16>(ft, smem);
 }
 
 void factor_prepare(int B, int prec) {
@@ -659,6 +693,7 @@ void factor_prepare(int B, int prec) {
   switch (prec) {
     case P_FP32: HSAD_FP(P_FP32); break;
     case P_FP16: HSAD_FP(P_FP16); break;
+    case P_BF16T: HSAD_FP(P_BF16T); break;
     default: HSAD_FP(P_BF16); break;
   }
 #undef HSAD_FP
@@ -673,8 +708,10 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   int cl = 0, ft = 0;
   if (getenv("HSAD_FACTOR_CLUSTER") || getenv("HSAD_FACTOR_THREADS") || !tuned_shape(B, prec, L, &cl, &ft)) {
-    cl = prec == P_FP32 ? factor_cluster_size<P_FP32>(L, smem)
-                        : (prec == P_FP16 ? factor_cluster_size<P_FP16>(L, smem) : factor_cluster_size<P_BF16>(L, smem));
+    cl = prec == P_FP32    ? factor_cluster_size<P_FP32>(L, smem)
+         : prec == P_FP16  ? factor_cluster_size<P_FP16>(L, smem)
+         : prec == P_BF16T ? factor_cluster_size<P_BF16T>(L, smem)
+                           : factor_cluster_size<P_BF16>(L, smem);
     ft = factor_single_threads();
   }
   return launch_factor_shape(cl, ft, sigma, scratch, m, dgain, L, B, prec, wmat, y0, inv_s2, status, n0, W, incl,
@@ -690,6 +727,7 @@ cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, 
   switch (prec) {
     case P_FP32: e = launch_factor_p<P_FP32>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
     case P_FP16: e = launch_factor_p<P_FP16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
+    case P_BF16T: e = launch_factor_p<P_BF16T>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
     default: e = launch_factor_p<P_BF16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
   }
   if (lc) lc->n += 1;
@@ -762,6 +800,7 @@ int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
       switch (prec) {
         case P_FP32: capc = c == 2 ? factor_cluster_capacity<P_FP32, 2>(smem) : c == 4 ? factor_cluster_capacity<P_FP32, 4>(smem) : c == 8 ? factor_cluster_capacity<P_FP32, 8>(smem) : factor_cluster_capacity<P_FP32, 16>(smem); break;
         case P_FP16: capc = c == 2 ? factor_cluster_capacity<P_FP16, 2>(smem) : c == 4 ? factor_cluster_capacity<P_FP16, 4>(smem) : c == 8 ? factor_cluster_capacity<P_FP16, 8>(smem) : factor_cluster_capacity<P_FP16, 16>(smem); break;
+        case P_BF16T: capc = c == 2 ? factor_cluster_capacity<P_BF16T, 2>(smem) : c == 4 ? factor_cluster_capacity<P_BF16T, 4>(smem) : c == 8 ? factor_cluster_capacity<P_BF16T, 8>(smem) : factor_cluster_capacity<P_BF16T, 16>(smem); break;
         default: capc = c == 2 ? factor_cluster_capacity<P_BF16, 2>(smem) : c == 4 ? factor_cluster_capacity<P_BF16, 4>(smem) : c == 8 ? factor_cluster_capacity<P_BF16, 8>(smem) : factor_cluster_capacity<P_BF16, 16>(smem); break;
       }
       if (capc > 0 && L <= 2 * capc) cands.push_back({c, FT_CLUSTER});  // larger batches only queue

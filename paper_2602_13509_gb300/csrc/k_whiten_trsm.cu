@@ -1,0 +1,347 @@
+// K6, triangular-solve form (BF16 working precision, uint16 input): the whitened vector
+// y = L^{-1} (x' - m) by blocked forward substitution on the tensor cores, and the score
+// delta = ||y||^2 (Eq. 1, Sec. 3.3) read out of tensor memory.
+//
+// With S = L L^T the DN-frame covariance, delta = (x' - m)^T S^{-1} (x' - m) = ||y||^2 with
+// L y = x' - m. The bands are cut into 64-band blocks; for block k
+//   z_k = (x'_k - m_k) - sum_{j<k} L_kj y_j,   y_k = L_kk^{-1} z_k.
+// The factor kernel leaves H (BF16 hi / lo planes) with H_jk = L_jk below the diagonal
+// blocks and H_kk = L_kk^{-1} on them, so that every step is one contraction with H.
+// Right-looking: once y_k is known, the contributions L_jk y_k of every later block j are
+// accumulated in that block's tensor-memory columns, block k + 1 first, so that the
+// converters can form z_{k+1} while the remaining updates run.
+//
+// One CTA scores 128 pixels of one line; tensor memory holds a 128 x Bp FP32 matrix whose
+// 64-column block k holds first the accumulated sum for z_k and then y_k.
+//   warps 0-3          one pixel (TMEM lane) each: z_k = v_k - acc_k in FP32, split into
+//                      BF16 hi + lo and written as the A operand; y_k read back, its square
+//                      summed into the score, split and written as the A operand of the
+//                      updates. v = x' - m in FP32 from the raw tile, which is first moved
+//                      into shared memory in the 128-byte swizzled layout (64 bands per
+//                      128-byte row: a thread reads its own pixel's bands without bank
+//                      conflicts).
+//   warp 4 (one lane)  TMA: the 64 x 64 blocks (j, k), j >= k, of the hi and lo planes of
+//                      H in the order the MMAs use them, through a ring of 2 to 4 stages.
+//   warp 5 (one lane)  tcgen05.mma (M = 128, N = 64, K = 16), three products per block:
+//                      a_hi h_hi + a_hi h_lo + a_lo h_hi, FP32 accumulation in TMEM.
+// Every wait is bounded; a timeout sets *err and the CTA drains its copies and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hsad_internal.h"
+#include "tc_util.cuh"
+
+namespace hsad {
+
+namespace {
+constexpr int TS_M = 128, TS_KB = 64, TS_THREADS = 192, TS_MAX_STAGES = 4;
+constexpr uint32_t TS_BLK = TS_M * TS_KB * 2;  // one 128 x 64 16-bit operand block: 16 KB
+constexpr uint32_t TS_HALF = 64 * TS_KB * 2;   // one 64 x 64 16-bit block of H: 8 KB
+constexpr uint32_t TS_STAGE = 2 * TS_HALF;     // hi + lo planes of one block of H
+constexpr uint32_t TS_BAR = 256;
+constexpr uint32_t TS_SMEM_MAX = 227 * 1024;
+
+__host__ __device__ inline uint32_t ts_cols(int Bp) {
+  uint32_t c = 32;
+  while (c < (uint32_t)Bp) c <<= 1;
+  return c;
+}
+// shared memory after 1024-byte alignment: raw tile (Bp/64 blocks), Z (hi, lo), Y (hi, lo),
+// ring, m (float) and c (int) per band, barriers
+__host__ __device__ inline uint32_t ts_smem(int Bp, int stages) {
+  return 1024 + (uint32_t)(Bp / 64) * TS_BLK + 4 * TS_BLK + (uint32_t)stages * TS_STAGE + (uint32_t)Bp * 8 +
+         TS_BAR;
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *(const uint32_t*)&v; }
+
+// hi = bf16(z), lo = bf16(z - hi) for a pair of values; returns the two packed words
+__device__ __forceinline__ void split2(float z0, float z1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
+  const float h0 = __low2float(h), h1 = __high2float(h);
+  hi = bf16x2_bits(h);
+  lo = bf16x2_bits(__floats2bfloat162_rn(z0 - h0, z1 - h1));
+}
+}  // namespace
+
+__global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
+    const uint16_t* __restrict__ x, int W, int B, const int32_t* __restrict__ c_int,
+    const __grid_constant__ CUtensorMap hmap, const float* __restrict__ m_all,
+    const float* __restrict__ inv_s2_all, const int32_t* __restrict__ status, int factor_stride, ScoreOut out,
+    int32_t* __restrict__ err, long long limit, int stages, int bulk) {
+  const int t = blockIdx.y;
+  const int p0 = blockIdx.x * TS_M;
+  const int f = out.factor_base + (factor_stride ? t : 0);
+  const int64_t slot = (slot0_of(out) + t) % out.ring;
+  const int st = status[f];
+  if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;
+  if (st != LS_OK) {
+    for (int p = p0 + threadIdx.x; p < p0 + TS_M && p < W; p += blockDim.x) {
+      out.scores[slot * W + p] = __int_as_float(0x7fc00000);
+      out.mask[slot * W + p] = 0;
+    }
+    return;
+  }
+  const int Bp = pad64(B), nkb = Bp / TS_KB;
+  const int npx = min(TS_M, W - p0);
+  const uint32_t tcols = ts_cols(Bp);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sX = sm;                          // [nkb][128 x 64] raw values, swizzled
+  uint8_t* sZ = sX + nkb * TS_BLK;           // z_k: hi block, lo block
+  uint8_t* sY = sZ + 2 * TS_BLK;             // y_k: hi block, lo block
+  uint8_t* sR = sY + 2 * TS_BLK;             // ring: [stage][hi 64 x 64][lo 64 x 64]
+  float* mS = (float*)(sR + stages * TS_STAGE);
+  int32_t* cS = (int32_t*)(mS + Bp);
+  uint64_t* bars = (uint64_t*)(cS + Bp);
+  uint32_t* tslot = (uint32_t*)(bars + 2 * TS_MAX_STAGES + 8);
+  const uint32_t b_full = tc::smem_u32(bars), b_empty = b_full + 8 * TS_MAX_STAGES;
+  const uint32_t z_full = b_empty + 8 * TS_MAX_STAGES, y_full = z_full + 8, ya_full = y_full + 8;
+  const uint32_t acc_full = ya_full + 8, done = acc_full + 8, raw_full = done + 8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint16_t* xt = x + ((int64_t)t * W + p0) * B;  // the tile's 128 x B values are contiguous
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) {
+      tc::mbar_init(b_full + 8 * s, 1);
+      tc::mbar_init(b_empty + 8 * s, 1);
+    }
+    tc::mbar_init(z_full, TS_M);
+    tc::mbar_init(y_full, 1);
+    tc::mbar_init(ya_full, TS_M);
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(done, 1);
+    tc::mbar_init(raw_full, 1);
+    tc::mbar_init_fence();
+  }
+  const float* mf = m_all + (int64_t)f * Bp;
+  for (int n = tid; n < Bp; n += TS_THREADS) {
+    mS[n] = n < B ? mf[n] : 0.f;
+    cS[n] = n < B ? c_int[n] : 0;
+  }
+  if (warp == 5) tc::tmem_alloc(tc::smem_u32(tslot), tcols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  bool ok = true;
+
+  // ---- raw tile -> sX (128-byte swizzle, 64 bands per row and block) ----------------
+  // The tile is bulk-copied into the still unused Z / Y / ring area when it fits, else
+  // read from global memory; rows of one warp are contiguous in either source.
+  const uint16_t* src = xt;
+  if (bulk) {
+    const uint32_t bytes = (uint32_t)npx * B * 2;
+    if (tid == 0) {
+      tc::mbar_arrive_expect_tx(raw_full, bytes);
+      tc::bulk_load(tc::smem_u32(sZ), xt, bytes, raw_full);
+    }
+    if (!tc::mbar_wait(raw_full, 0, limit)) {
+      ok = false;
+      atomicExch(err, 1);
+    }
+    src = (const uint16_t*)sZ;
+  }
+  if ((B & 1) == 0 && ((uintptr_t)src & 3) == 0) {
+    const int hw = B >> 1;
+    for (int r = warp; r < npx; r += TS_THREADS / 32) {
+      const uint32_t* row = (const uint32_t*)(src + (int64_t)r * B);
+      for (int w = lane; w < hw; w += 32) {
+        const int k = 2 * w;
+        *(uint32_t*)(sX + (k >> 6) * TS_BLK + tc::sw128_offset(r, k & 63)) = bulk ? row[w] : __ldg(row + w);
+      }
+    }
+  } else {
+    for (int r = warp; r < npx; r += TS_THREADS / 32)
+      for (int k = lane; k < B; k += 32) {
+        const uint16_t v = bulk ? src[(int64_t)r * B + k] : __ldg(src + (int64_t)r * B + k);
+        *(uint16_t*)(sX + (k >> 6) * TS_BLK + tc::sw128_offset(r, k & 63)) = v;
+      }
+  }
+  tc::fence_proxy_async();  // the staging area is overwritten by TMA / read by the MMAs next
+  __syncthreads();
+
+  if (warp == 4) {
+    // ---------------- TMA: blocks (j, k) of H, j = k .. nkb - 1, k = 0 .. nkb - 1 ----------
+    if (lane == 0) {
+      int it = 0;
+      for (int k = 0; k < nkb && ok; ++k)
+        for (int j = k; j < nkb && ok; ++j, ++it) {
+          const int s = it % stages;
+          const uint32_t use = (uint32_t)(it / stages);
+          if (!tc::mbar_wait(b_empty + 8 * s, (use & 1) ^ 1, limit)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(b_full + 8 * s, TS_STAGE);
+          const uint32_t dst = tc::smem_u32(sR + s * TS_STAGE);
+          const int row = (f * 2) * Bp + j * TS_KB;
+          tc::tma_load_2d(dst, &hmap, k * TS_KB, row, b_full + 8 * s);
+          tc::tma_load_2d(dst + TS_HALF, &hmap, k * TS_KB, row + Bp, b_full + 8 * s);
+        }
+      // drain: every copy issued here has landed before the CTA may exit
+      const int issued = it;
+      for (int s = 0; s < stages && s < issued; ++s) {
+        const int last = issued - 1 - ((issued - 1 - s) % stages);
+        if (!tc::mbar_wait(b_full + 8 * s, (uint32_t)(last / stages) & 1, limit)) ok = false;
+      }
+      if (!ok) atomicExch(err, 1);
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16(1, TS_M, 64);
+      const uint32_t zhi = tc::smem_u32(sZ), zlo = zhi + TS_BLK, yhi = tc::smem_u32(sY), ylo = yhi + TS_BLK;
+      int it = 0;
+      bool issued_any = false;
+      for (int k = 0; k < nkb && ok; ++k) {
+        if (!tc::mbar_wait(z_full, (uint32_t)(k & 1), limit)) { ok = false; break; }
+        tc::fence_after_sync();
+        for (int j = k; j < nkb; ++j, ++it) {
+          if (j == k + 1) {  // y_k is in shared memory
+            if (!tc::mbar_wait(ya_full, (uint32_t)(k & 1), limit)) { ok = false; break; }
+            tc::fence_after_sync();
+          }
+          const int s = it % stages;
+          if (!tc::mbar_wait(b_full + 8 * s, (uint32_t)((it / stages) & 1), limit)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t hhi = tc::smem_u32(sR + s * TS_STAGE), hlo = hhi + TS_HALF;
+          const uint32_t d = tbase + (uint32_t)(j * TS_KB);
+          const uint32_t ahi = j == k ? zhi : yhi, alo = j == k ? zlo : ylo;
+#pragma unroll
+          for (int term = 0; term < 3; ++term) {
+            const uint32_t aop = term == 2 ? alo : ahi;
+            const uint32_t bop = term == 1 ? hlo : hhi;
+#pragma unroll
+            for (int ks = 0; ks < TS_KB / 16; ++ks) {
+              // y_k overwrites block k; the updates of block j start at k = 0
+              const bool first = term == 0 && ks == 0 && (j == k || k == 0);
+              tc::mma_f16(d, tc::desc_sw128(aop + ks * 32), tc::desc_sw128(bop + ks * 32), idesc, first ? 0u : 1u);
+            }
+          }
+          issued_any = true;
+          tc::mma_commit(b_empty + 8 * s);
+          if (j == k) tc::mma_commit(y_full);
+          if (j == k + 1) tc::mma_commit(acc_full);
+        }
+      }
+      if (issued_any) tc::mma_commit(done);
+      else tc::mbar_arrive(done);
+      if (!ok) atomicExch(err, 1);
+      if (!tc::mbar_wait(done, 0, limit)) atomicExch(err, 1);  // MMAs finished before TMEM is freed
+    }
+  } else {
+    // ---------------- warps 0-3: one pixel each ----------------
+    const int r = tid;
+    const bool rv = r < npx;
+    const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
+    float dsum = 0.f;
+    for (int k = 0; k < nkb; ++k) {
+      float a[64];
+      if (k > 0) {
+        if (ok && !tc::mbar_wait(acc_full, (uint32_t)((k - 1) & 1), limit)) ok = false;
+        __syncwarp();
+        tc::fence_after_sync();
+        tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB), a);
+        tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB + 32), a + 32);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) a[i] = 0.f;
+      }
+      // z_k = (x' - m) - acc, x' = DN - c exact in FP32
+      const uint8_t* xb = sX + k * TS_BLK;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint4 raw = *(const uint4*)(xb + tc::sw128_offset(r, 8 * q));
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float z[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int n = k * TS_KB + 8 * q + 2 * j + e;
+            const int dn = (int)((w4[j] >> (16 * e)) & 0xffffu);
+            z[e] = (rv && n < B) ? ((float)(dn - cS[n]) - mS[n]) - a[8 * q + 2 * j + e] : 0.f;
+          }
+          split2(z[0], z[1], hi[j], lo[j]);
+        }
+        const uint32_t off = tc::sw128_offset(r, 8 * q);
+        *(uint4*)(sZ + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *(uint4*)(sZ + TS_BLK + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      tc::mbar_arrive(z_full);
+      // y_k: score, and the A operand of the updates of the later blocks
+      if (ok && !tc::mbar_wait(y_full, (uint32_t)(k & 1), limit)) ok = false;
+      __syncwarp();
+      tc::fence_after_sync();
+      tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB), a);
+      tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB + 32), a + 32);
+#pragma unroll
+      for (int i = 0; i < 64; ++i) dsum = fmaf(a[i], a[i], dsum);
+      if (k + 1 < nkb) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) split2(a[8 * q + 2 * j], a[8 * q + 2 * j + 1], hi[j], lo[j]);
+          const uint32_t off = tc::sw128_offset(r, 8 * q);
+          *(uint4*)(sY + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *(uint4*)(sY + TS_BLK + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        tc::mbar_arrive(ya_full);
+      }
+    }
+    if (!ok) atomicExch(err, 1);
+    const int p = p0 + r;
+    if (p < W) {
+      const float dlt = ok ? dsum * inv_s2_all[f] : __int_as_float(0x7fc00000);
+      out.scores[slot * W + p] = dlt;
+      if (out.write_mask) out.mask[slot * W + p] = dlt > out.tau ? 1 : 0;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 5) {
+    __syncwarp();
+    tc::tmem_dealloc(tbase, tcols);
+  }
+}
+
+int whiten_trsm_stages(int B) {
+  for (int s = TS_MAX_STAGES; s >= 2; --s)
+    if (ts_smem(pad64(B), s) <= TS_SMEM_MAX) return s;
+  return 0;
+}
+
+cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, const int32_t* c_int, const void* hmap,
+                               const float* m, const float* inv_s2, const int32_t* status, int factor_stride,
+                               ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc) {
+  if (L <= 0) return cudaSuccess;
+  const int Bp = pad64(B);
+  const int stages = whiten_trsm_stages(B);
+  if (stages == 0) return cudaErrorInvalidValue;
+  const uint32_t smem = ts_smem(Bp, stages);
+  // bulk copy of a tile into the Z / Y / ring area: 16-byte aligned start and size for
+  // every tile (line base, 128-pixel steps, the last partial tile) and room for it
+  const uint32_t area = 4 * TS_BLK + (uint32_t)stages * TS_STAGE;
+  const int bulk = ((uintptr_t)x % 16 == 0) && (((int64_t)W * B * 2) % 16 == 0) &&
+                   (((int64_t)(W % TS_M) * B * 2) % 16 == 0) && ((int64_t)TS_M * B * 2 <= (int64_t)area);
+  const long long limit = 4000000000LL;  // ~2 s of clock cycles
+  cudaError_t e = cudaFuncSetAttribute(whiten_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((W + TS_M - 1) / TS_M, L), block(TS_THREADS);
+  whiten_trsm_kernel<<<grid, block, smem, st>>>(x, W, B, c_int, *(const CUtensorMap*)hmap, m, inv_s2, status,
+                                                factor_stride, out, err, limit, stages, bulk);
+  if (lc) lc->n += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace hsad

@@ -21,6 +21,7 @@ HSAD_E_NOT_PD, HSAD_E_TIMEOUT, HSAD_E_CUDA, HSAD_E_BUSY, HSAD_E_INVALID_DATA = -
 # enums
 HSAD_U16, HSAD_F32 = 0, 1
 HSAD_FP32, HSAD_BF16, HSAD_FP16 = 0, 1, 2
+HSAD_FORM_INVERSE, HSAD_FORM_TRIANGULAR_SOLVE = 0, 1
 HSAD_EXCLUSIVE, HSAD_INCLUSIVE, HSAD_CUBE = 0, 1, 2
 HSAD_ABS, HSAD_REL = 0, 1
 HSAD_HOST, HSAD_DEVICE = 0, 1
@@ -67,6 +68,7 @@ def _load():
         "hsad_stream": (P, [P]),
         "hsad_kernel_launches": (C.c_int64, [P]),
         "hsad_device_bytes": (C.c_int64, [P]),
+        "hsad_whitening_form": (C.c_int, [P]),
         "hsad_set_device_budget": (C.c_int, [C.c_int, C.c_int64]),
         "hsad_device_budget_used": (C.c_int64, [C.c_int]),
         "hsad_profile_enable": (C.c_int, [P, C.c_int32]),
@@ -199,6 +201,10 @@ def hsad_kernel_launches(ctx) -> int:
 
 def hsad_device_bytes(ctx) -> int:
     return int(_lib.hsad_device_bytes(ctx))
+
+
+def hsad_whitening_form(ctx) -> int:
+    return int(_lib.hsad_whitening_form(ctx))
 
 
 def hsad_set_device_budget(device: int, nbytes: int) -> int:
@@ -421,6 +427,10 @@ class Detector:
     @property
     def device_bytes(self) -> int:
         return hsad_device_bytes(self.ctx)
+
+    @property
+    def whitening_form(self) -> int:
+        return hsad_whitening_form(self.ctx)
 
     def close(self):
         if self.ctx is not None:

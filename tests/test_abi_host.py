@@ -74,6 +74,7 @@ def test_null_handling(hs):
     assert lib.hsad_config_init(None) == hs.HSAD_E_INVALID
     assert isinstance(hs.hsad_last_error(None), str)
     assert hs.hsad_stream(None) == 0 and hs.hsad_kernel_launches(None) == 0
+    assert hs.hsad_whitening_form(None) == hs.HSAD_E_INVALID
 
 
 def test_status_strings(hs):

@@ -111,6 +111,31 @@ def test_stream_ragged_shapes(hs, W, B):
     assert emax <= TOL["fp32"], emax
 
 
+@pytest.mark.parametrize("W,B", [(1, 1), (7, 3), (129, 64), (65, 65), (33, 127), (300, 130), (130, 270),
+                                 (640, 270), (130, 448), (40, 500)])
+def test_stream_bf16_ragged_shapes(hs, W, B):
+    """BF16 streams of uint16 lines whiten by the blocked triangular solve: one and several
+    64-band blocks with ragged tails, odd B (2-byte staging), tiles staged by bulk copy
+    (B = 270) and from global memory (B = 448); B = 500 takes the explicit-inverse form."""
+    sc, lines = _scene_lines(max(6, (B + 1) // W + 4), W, B, seed=W * 1000 + B + 1)
+    rc, s, m, st, _ = _run(hs, lines, stats_mode="exclusive", precision="bf16", gain=sc.gain, offset=sc.offset)
+    ref, rst = orx.stream_rx(lines, oracle.EXCLUSIVE, gain=sc.gain, offset=sc.offset)
+    np.testing.assert_array_equal(st, rst)
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL["bf16"], emax
+    tau = B + 6 * np.sqrt(2 * B)
+    assert mask_mismatch(m, ref, tau, MARGIN["bf16"]) == 0
+
+
+@pytest.mark.parametrize("prec,dtype,B,form", [("bf16", "u16", 270, 1), ("bf16", "u16", 448, 1),
+                                                ("bf16", "u16", 449, 0), ("bf16", "f32", 270, 0),
+                                                ("fp16", "u16", 270, 0), ("fp32", "u16", 270, 0)])
+def test_whitening_form_per_context(hs, prec, dtype, B, form):
+    det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype)
+    assert det.whitening_form == form
+    det.close()
+
+
 def test_stream_resets_and_warmup(hs):
     sc, lines = _scene_lines(50, 40, 20, seed=11)
     kw = dict(stats_mode="exclusive", cube_lines=16, warmup_pixels=100, gain=sc.gain, offset=sc.offset,
