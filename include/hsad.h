@@ -54,10 +54,11 @@ enum { HSAD_U16 = 0, HSAD_F32 = 1 };
 enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
 /* whitening form of a context (Eq. 1, Sec. 3.3), see hsad_whitening_form:
  * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1} D, the full triangular
- *                              inverse (FP32, FP16; BF16 with float input or B > 448);
- * HSAD_FORM_TRIANGULAR_SOLVE   L y = x' - m solved blockwise on the tensor cores from L and
- *                              the inverses of its 64 x 64 diagonal blocks only (BF16 with
- *                              uint16 input and B <= 448): half the FP64 factor work. */
+ *                              inverse (FP16; BF16 with float input or B > 448);
+ * HSAD_FORM_TRIANGULAR_SOLVE   L y = x' - m solved blockwise from L and the inverses of its
+ *                              64 x 64 diagonal blocks only, half the FP64 factor work: on the
+ *                              tensor cores for BF16 (uint16 input, B <= 448), on the SIMT
+ *                              cores for FP32. */
 enum { HSAD_FORM_INVERSE = 0, HSAD_FORM_TRIANGULAR_SOLVE = 1 };
 /* statistics window (which pixels form mu and Sigma for a scored line t) */
 enum {
@@ -74,9 +75,10 @@ enum {
   HSAD_CREATE_WAIT = 1,      /* hsad_create blocks (bounded) until the device budget admits the context */
   HSAD_NORMALIZE_SCORES = 2, /* CUBE mode: report delta / cube max instead of delta (Sec. 3.3) */
   HSAD_CUDA_GRAPHS = 4       /* EXCLUSIVE mode, host pushes: the statistics, factor and scoring
-                                launches of a batch are captured once per batch size and replayed
-                                as a CUDA graph (same kernels, same results; fewer host calls).
-                                No counterpart in the paper. Ignored while profiling is on. */
+                                launches of a batch of up to 8 lines are captured once per batch
+                                size and replayed as a CUDA graph (same kernels, same results;
+                                fewer host calls); larger batches launch directly. No counterpart
+                                in the paper. Ignored while profiling is on. */
 };
 
 typedef struct {

@@ -397,7 +397,7 @@ int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32
   }
   DeviceGuard dg(device);
   // BF16: the form of a uint16-input context (the streaming case)
-  const int prec = precision == HSAD_FP32 ? P_FP32
+  const int prec = precision == HSAD_FP32 ? fp32_form()
                    : precision == HSAD_BF16 ? bf16_form(bands, IN_U16)
                                             : P_FP16;
   factor_prepare(bands, prec);
@@ -467,7 +467,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->B = cfg->bands;
   ctx->Bp = pad64(cfg->bands);
   ctx->in_type = cfg->in_dtype == HSAD_U16 ? IN_U16 : IN_F32;
-  ctx->prec = cfg->precision == HSAD_FP32 ? P_FP32
+  ctx->prec = cfg->precision == HSAD_FP32 ? fp32_form()
               : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type)
                                             : P_FP16;
   ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE;
@@ -594,7 +594,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     release(ctx);
     return fail(nullptr, HSAD_E_CUDA, "device initialisation failed");
   }
-  if (ctx->prec != P_FP32) {
+  if (ctx->prec == P_BF16 || ctx->prec == P_FP16 || ctx->prec == P_BF16T) {
     // G planes [Lf][2][Bp][Bp] 16-bit as a 2-D tensor of Lf*2*Bp rows, 64 x 64 boxes
     const int64_t rows = Lf * 2 * Bp;
     if (!encode_gmap(&ctx->gmap, ctx->wmat, Bp, rows, ctx->prec == P_BF16T ? 64 : 128)) {
@@ -648,6 +648,10 @@ int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o) {
   if (ctx->prec == P_BF16T) {
     KL("whiten_score", launch_whiten_trsm((const uint16_t*)x, L, ctx->W, ctx->B, ctx->c_int, &ctx->gmap, ctx->y0,
                                           ctx->inv_s2, ctx->status, factor_stride, o, ctx->dev_err, st, &ctx->lc));
+  } else if (ctx->prec == P_FP32T) {
+    KL("whiten_score", launch_whiten_trsm_simt(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt,
+                                               (const float*)ctx->wmat, ctx->y0, ctx->inv_s2, ctx->status,
+                                               factor_stride, o, st, &ctx->lc));
   } else if (ctx->prec != P_FP32) {
     KL("whiten_score", launch_whiten_tc(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec,
                                         &ctx->gmap, ctx->y0, ctx->inv_s2, ctx->status, factor_stride, o,
@@ -718,6 +722,8 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   return HSAD_OK;
 }
 
+constexpr int kGraphMaxLines = 8;
+
 // The replayable graph of excl_tail for (L, staging buffer s), captured on first use.
 // Returns nullptr if capture or instantiation fails (the caller then launches directly).
 hsad_ctx::GraphEntry* excl_graph(hsad_ctx* ctx, const void* x, int L, int s, uint64_t first) {
@@ -767,7 +773,10 @@ int stream_batch_excl(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
   }
   const int s = x == ctx->d_stage[0] ? 0 : (x == ctx->d_stage[1] ? 1 : -1);
   hsad_ctx::GraphEntry* ge = nullptr;
-  if (ctx->use_graphs && !ctx->prof_on && ctx->n_stats > 0 && s >= 0) ge = excl_graph(ctx, x, L, s, first);
+  // graphs for small batches only: their launch overhead is what a graph saves, and a
+  // backlog (large batches of many sizes) must not turn into a capture per new size
+  if (ctx->use_graphs && !ctx->prof_on && ctx->n_stats > 0 && s >= 0 && L <= kGraphMaxLines)
+    ge = excl_graph(ctx, x, L, s, first);
   if (ge) {
     KL("set_batch_desc", launch_set_batch_desc(ctx->bdesc, ctx->n_stats,
                                                (int64_t)((first + 1) % (uint64_t)ctx->ring), st, &ctx->lc));
@@ -1279,7 +1288,7 @@ int64_t hsad_device_bytes(const hsad_ctx* ctx) { return ctx ? ctx->dev_bytes : 0
 
 int hsad_whitening_form(const hsad_ctx* ctx) {
   if (!ctx) return HSAD_E_INVALID;
-  return ctx->prec == P_BF16T ? HSAD_FORM_TRIANGULAR_SOLVE : HSAD_FORM_INVERSE;
+  return is_trsm(ctx->prec) ? HSAD_FORM_TRIANGULAR_SOLVE : HSAD_FORM_INVERSE;
 }
 
 int hsad_destroy(hsad_ctx* ctx) {

@@ -22,9 +22,11 @@ namespace hsad {
 enum LineStatus : int32_t { LS_OK = 0, LS_NOT_READY = 1, LS_NOT_PD = 2, LS_INVALID_DATA = 3 };
 enum InType : int32_t { IN_U16 = 0, IN_F32 = 1 };
 enum Prec : int32_t { P_FP32 = 0, P_BF16 = 1, P_FP16 = 2,
-                      // factor output for the BF16 triangular-solve whitening: L's off-diagonal
-                      // 64 x 64 blocks and the inverses of its diagonal blocks, BF16 hi / lo
-                      P_BF16T = 3 };
+                      // factor output for the triangular-solve whitening: L's off-diagonal
+                      // 64 x 64 blocks and the inverses of its diagonal blocks, as BF16 hi / lo
+                      // planes (tensor cores) or FP32 (SIMT)
+                      P_BF16T = 3, P_FP32T = 4 };
+__host__ __device__ constexpr bool is_trsm(int prec) { return prec == P_BF16T || prec == P_FP32T; }
 
 __host__ __device__ inline int pad64(int b) { return (b + 63) / 64 * 64; }
 
@@ -141,13 +143,21 @@ cudaError_t launch_whiten_tc(const void* x, int L, int W, int B, int in_type, co
 cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, const int32_t* c_int, const void* hmap,
                                const float* m, const float* inv_s2, const int32_t* status, int factor_stride,
                                ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc);
+// K6, triangular-solve form on the SIMT cores (P_FP32T factors): the same blocked forward
+// substitution in FP32 with H in FP32, 64 pixels per CTA.
+cudaError_t launch_whiten_trsm_simt(const void* x, int L, int W, int B, int in_type, const int32_t* c_int,
+                                    const float* c_flt, const float* H, const float* m, const float* inv_s2,
+                                    const int32_t* status, int factor_stride, ScoreOut out, cudaStream_t st,
+                                    LaunchCounter* lc);
 // Ring depth the triangular-solve whitening runs with for B bands; 0 if it does not fit.
 int whiten_trsm_stages(int B);
 // Working form of a BF16 context: P_BF16T (triangular solve) for uint16 input where the
 // solve fits on chip, else P_BF16 (explicit inverse).
-inline int bf16_form(int B, int in_type) {
-  return in_type == IN_U16 && whiten_trsm_stages(B) > 0 ? P_BF16T : P_BF16;
-}
+// HSAD_BF16_FORM=inverse in the environment keeps the explicit-inverse form (comparisons).
+int bf16_form(int B, int in_type);
+// Working form of an FP32 context: P_FP32T (triangular solve on the SIMT cores) unless
+// HSAD_FP32_FORM=inverse in the environment keeps P_FP32 (explicit inverse).
+int fp32_form();
 
 // K7: cube maximum of delta over n_lines ring lines, then optional normalisation and
 // the REL / ABS mask.

@@ -84,6 +84,8 @@ struct WOut<P_BF16> {
 };
 template <>
 struct WOut<P_BF16T> : WOut<P_BF16> {};
+template <>
+struct WOut<P_FP32T> : WOut<P_FP32> {};
 
 template <int FT>
 __device__ double block_max(double v, double* red) {
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   // Sigma_ij = d_i d_j (S2_ij - n m_i m_j) / (n - 1), n = pixels in this line's window.
   // (triangular-solve form: the DN-frame covariance S_ij = (S2_ij - n m_i m_j) / (n - 1);
   // the gains cancel from Eq. 1, delta = (x' - m)^T S^{-1} (x' - m))
-  constexpr bool TRSM = PREC == P_BF16T;
+  constexpr bool TRSM = is_trsm(PREC);
   {
     const int64_t n = (n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W;
     const double nn = (double)n, inv_nm1 = 1.0 / (double)(n - 1);
@@ -430,8 +432,8 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   }
 
   if (TRSM) {
-    // ---- triangular-solve operand H, BF16 hi / lo: H_ij = L_ij below the diagonal 64 x 64
-    // blocks, H_ii = L_ii^{-1}; y0 = m (the whitening forms x' - m in FP32); no scale -----
+    // ---- triangular-solve operand H (BF16 hi / lo or FP32): H_ij = L_ij below the diagonal
+    // 64 x 64 blocks, H_ii = L_ii^{-1}; y0 = m (the whitening forms x' - m in FP32); no scale
     const int64_t plane = (int64_t)Bp * Bp;
     void* w = (char*)wmat + (size_t)t * plane * 4;
     for (int n = gwarp; n < Bp; n += gwarps) {
@@ -680,6 +682,7 @@ int factor_wave_lines(int B, int prec) {
   return prec == P_FP32    ? wave_slots_p<P_FP32>(ft, smem)
          : prec == P_FP16  ? wave_slots_p<P_FP16>(ft, smem)
          : prec == P_BF16T ? wave_slots_p<P_BF16T>(ft, smem)
+         : prec == P_FP32T ? wave_slots_p<P_FP32T>(ft, smem)
                            : wave_slots_p<P_BF16>(ft, smem);
 }
 
@@ -694,6 +697,7 @@ void factor_prepare(int B, int prec) {
     case P_FP32: HSAD_FP(P_FP32); break;
     case P_FP16: HSAD_FP(P_FP16); break;
     case P_BF16T: HSAD_FP(P_BF16T); break;
+    case P_FP32T: HSAD_FP(P_FP32T); break;
     default: HSAD_FP(P_BF16); break;
   }
 #undef HSAD_FP
@@ -711,6 +715,7 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const
     cl = prec == P_FP32    ? factor_cluster_size<P_FP32>(L, smem)
          : prec == P_FP16  ? factor_cluster_size<P_FP16>(L, smem)
          : prec == P_BF16T ? factor_cluster_size<P_BF16T>(L, smem)
+         : prec == P_FP32T ? factor_cluster_size<P_FP32T>(L, smem)
                            : factor_cluster_size<P_BF16>(L, smem);
     ft = factor_single_threads();
   }
@@ -728,6 +733,7 @@ cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, 
     case P_FP32: e = launch_factor_p<P_FP32>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
     case P_FP16: e = launch_factor_p<P_FP16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
     case P_BF16T: e = launch_factor_p<P_BF16T>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
+    case P_FP32T: e = launch_factor_p<P_FP32T>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
     default: e = launch_factor_p<P_BF16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev); break;
   }
   if (lc) lc->n += 1;
@@ -801,6 +807,7 @@ int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
         case P_FP32: capc = c == 2 ? factor_cluster_capacity<P_FP32, 2>(smem) : c == 4 ? factor_cluster_capacity<P_FP32, 4>(smem) : c == 8 ? factor_cluster_capacity<P_FP32, 8>(smem) : factor_cluster_capacity<P_FP32, 16>(smem); break;
         case P_FP16: capc = c == 2 ? factor_cluster_capacity<P_FP16, 2>(smem) : c == 4 ? factor_cluster_capacity<P_FP16, 4>(smem) : c == 8 ? factor_cluster_capacity<P_FP16, 8>(smem) : factor_cluster_capacity<P_FP16, 16>(smem); break;
         case P_BF16T: capc = c == 2 ? factor_cluster_capacity<P_BF16T, 2>(smem) : c == 4 ? factor_cluster_capacity<P_BF16T, 4>(smem) : c == 8 ? factor_cluster_capacity<P_BF16T, 8>(smem) : factor_cluster_capacity<P_BF16T, 16>(smem); break;
+        case P_FP32T: capc = c == 2 ? factor_cluster_capacity<P_FP32T, 2>(smem) : c == 4 ? factor_cluster_capacity<P_FP32T, 4>(smem) : c == 8 ? factor_cluster_capacity<P_FP32T, 8>(smem) : factor_cluster_capacity<P_FP32T, 16>(smem); break;
         default: capc = c == 2 ? factor_cluster_capacity<P_BF16, 2>(smem) : c == 4 ? factor_cluster_capacity<P_BF16, 4>(smem) : c == 8 ? factor_cluster_capacity<P_BF16, 8>(smem) : factor_cluster_capacity<P_BF16, 16>(smem); break;
       }
       if (capc > 0 && L <= 2 * capc) cands.push_back({c, FT_CLUSTER});  // larger batches only queue

@@ -29,6 +29,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "hsad_internal.h"
 #include "tc_util.cuh"
@@ -313,6 +315,17 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     __syncwarp();
     tc::tmem_dealloc(tbase, tcols);
   }
+}
+
+int bf16_form(int B, int in_type) {
+  const char* v = getenv("HSAD_BF16_FORM");
+  if (v && strcmp(v, "inverse") == 0) return P_BF16;
+  return in_type == IN_U16 && whiten_trsm_stages(B) > 0 ? P_BF16T : P_BF16;
+}
+
+int fp32_form() {
+  const char* v = getenv("HSAD_FP32_FORM");
+  return v && strcmp(v, "inverse") == 0 ? P_FP32 : P_FP32T;
 }
 
 int whiten_trsm_stages(int B) {

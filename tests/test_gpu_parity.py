@@ -101,7 +101,7 @@ def test_stream_modes_small(hs, mode, prec):
 
 
 @pytest.mark.parametrize("W,B", [(1, 1), (7, 1), (3, 2), (9, 3), (65, 64), (33, 127), (64, 128),
-                                 (17, 129), (130, 200)])
+                                 (17, 129), (130, 200), (130, 448), (40, 512)])
 def test_stream_ragged_shapes(hs, W, B):
     sc, lines = _scene_lines(max(6, (B + 1) // W + 4), W, B, seed=W * 1000 + B)
     rc, s, m, st, _ = _run(hs, lines, stats_mode="exclusive", gain=sc.gain, offset=sc.offset)
@@ -129,7 +129,8 @@ def test_stream_bf16_ragged_shapes(hs, W, B):
 
 @pytest.mark.parametrize("prec,dtype,B,form", [("bf16", "u16", 270, 1), ("bf16", "u16", 448, 1),
                                                 ("bf16", "u16", 449, 0), ("bf16", "f32", 270, 0),
-                                                ("fp16", "u16", 270, 0), ("fp32", "u16", 270, 0)])
+                                                ("fp16", "u16", 270, 0), ("fp32", "u16", 270, 1),
+                                                ("fp32", "f32", 270, 1), ("fp32", "u16", 512, 1)])
 def test_whitening_form_per_context(hs, prec, dtype, B, form):
     det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype)
     assert det.whitening_form == form
@@ -199,7 +200,8 @@ def test_cuda_graph_replay_matches_direct_launches(hs, prec):
     for flags in (0, hs.HSAD_CUDA_GRAPHS):
         det = hs.Detector(width=72, bands=40, stats_mode="exclusive", precision=prec, flags=flags)
         t = 0
-        for n in [1, 1, 2, 1, 3, 3, 1, 2] * 10:   # repeated batch sizes: captured once, replayed
+        # repeated batch sizes: captured once, replayed; batches above 8 lines launch directly
+        for n in [1, 1, 2, 1, 3, 3, 1, 2, 12] * 10:
             if t + n > 90:
                 break
             det.push(lines[t:t + n])
