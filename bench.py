@@ -49,10 +49,11 @@ def load_peaks():
 
 
 # DRAM bytes per line of the factor kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of a 512-line launch, profiles/factor_512x640x270.md), scaled to a
-# launch by its lines; keyed by (band count, whitening form), and to be refreshed whenever
-# the kernel changes (a form without a capture of the current kernel reports null).
-FACTOR_DRAM_BYTES_PER_LINE = {}
+# dram__bytes_write.sum of a 512-line launch, profiles/factor_trsm_512x640x270.md), scaled
+# to a launch by its lines; keyed by (band count, whitening form: 1 = triangular solve), and
+# to be refreshed whenever the kernel changes (a form without a capture of the current
+# kernel reports null).
+FACTOR_DRAM_BYTES_PER_LINE = {(270, 1): (0.931178e9 + 1.376609e9) / 512}
 
 
 def factor_flops_per_line(B, form):

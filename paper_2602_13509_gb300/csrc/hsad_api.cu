@@ -396,9 +396,9 @@ int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32
     return ndev <= 0 ? HSAD_E_CUDA : HSAD_E_INVALID;
   }
   DeviceGuard dg(device);
-  // BF16: the form of a uint16-input context (the streaming case)
-  const int prec = precision == HSAD_FP32 ? fp32_form()
-                   : precision == HSAD_BF16 ? bf16_form(bands, IN_U16)
+  // the form of a streamed uint16-input context (the case with a factorisation per line)
+  const int prec = precision == HSAD_FP32 ? fp32_form(false)
+                   : precision == HSAD_BF16 ? bf16_form(bands, IN_U16, false)
                                             : P_FP16;
   factor_prepare(bands, prec);
   const int cap = report ? *n_rows : 0;
@@ -467,8 +467,9 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->B = cfg->bands;
   ctx->Bp = pad64(cfg->bands);
   ctx->in_type = cfg->in_dtype == HSAD_U16 ? IN_U16 : IN_F32;
-  ctx->prec = cfg->precision == HSAD_FP32 ? fp32_form()
-              : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type)
+  const bool cube = cfg->stats_mode == HSAD_CUBE;
+  ctx->prec = cfg->precision == HSAD_FP32 ? fp32_form(cube)
+              : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type, cube)
                                             : P_FP16;
   ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE;
   ctx->mode = cfg->stats_mode;

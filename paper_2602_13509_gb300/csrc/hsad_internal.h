@@ -151,13 +151,16 @@ cudaError_t launch_whiten_trsm_simt(const void* x, int L, int W, int B, int in_t
                                     LaunchCounter* lc);
 // Ring depth the triangular-solve whitening runs with for B bands; 0 if it does not fit.
 int whiten_trsm_stages(int B);
-// Working form of a BF16 context: P_BF16T (triangular solve) for uint16 input where the
-// solve fits on chip, else P_BF16 (explicit inverse).
-// HSAD_BF16_FORM=inverse in the environment keeps the explicit-inverse form (comparisons).
-int bf16_form(int B, int in_type);
-// Working form of an FP32 context: P_FP32T (triangular solve on the SIMT cores) unless
-// HSAD_FP32_FORM=inverse in the environment keeps P_FP32 (explicit inverse).
-int fp32_form();
+// Working form of a context. The triangular solve halves the FP64 factor work but its
+// whitening is a chain of dependent block steps: it pays where a factorisation per line
+// dominates (streamed statistics), not in CUBE mode (one factorisation per cube, the
+// whitening dominates), which keeps the explicit inverse.
+// BF16: P_BF16T for uint16 input where the solve fits on chip, else P_BF16.
+// FP32: P_FP32T (triangular solve on the SIMT cores), else P_FP32.
+// HSAD_BF16_FORM=inverse / HSAD_FP32_FORM=inverse in the environment keep the explicit
+// inverse everywhere (comparisons).
+int bf16_form(int B, int in_type, bool cube);
+int fp32_form(bool cube);
 
 // K7: cube maximum of delta over n_lines ring lines, then optional normalisation and
 // the REL / ABS mask.

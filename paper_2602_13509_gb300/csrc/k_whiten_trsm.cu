@@ -317,15 +317,15 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   }
 }
 
-int bf16_form(int B, int in_type) {
+int bf16_form(int B, int in_type, bool cube) {
   const char* v = getenv("HSAD_BF16_FORM");
-  if (v && strcmp(v, "inverse") == 0) return P_BF16;
+  if (cube || (v && strcmp(v, "inverse") == 0)) return P_BF16;
   return in_type == IN_U16 && whiten_trsm_stages(B) > 0 ? P_BF16T : P_BF16;
 }
 
-int fp32_form() {
+int fp32_form(bool cube) {
   const char* v = getenv("HSAD_FP32_FORM");
-  return v && strcmp(v, "inverse") == 0 ? P_FP32 : P_FP32T;
+  return cube || (v && strcmp(v, "inverse") == 0) ? P_FP32 : P_FP32T;
 }
 
 int whiten_trsm_stages(int B) {

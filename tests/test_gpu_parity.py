@@ -127,12 +127,19 @@ def test_stream_bf16_ragged_shapes(hs, W, B):
     assert mask_mismatch(m, ref, tau, MARGIN["bf16"]) == 0
 
 
-@pytest.mark.parametrize("prec,dtype,B,form", [("bf16", "u16", 270, 1), ("bf16", "u16", 448, 1),
-                                                ("bf16", "u16", 449, 0), ("bf16", "f32", 270, 0),
-                                                ("fp16", "u16", 270, 0), ("fp32", "u16", 270, 1),
-                                                ("fp32", "f32", 270, 1), ("fp32", "u16", 512, 1)])
-def test_whitening_form_per_context(hs, prec, dtype, B, form):
-    det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype)
+@pytest.mark.parametrize("prec,dtype,B,mode,form", [("bf16", "u16", 270, "exclusive", 1),
+                                                     ("bf16", "u16", 448, "inclusive", 1),
+                                                     ("bf16", "u16", 449, "exclusive", 0),
+                                                     ("bf16", "f32", 270, "exclusive", 0),
+                                                     ("bf16", "u16", 270, "cube", 0),
+                                                     ("fp16", "u16", 270, "exclusive", 0),
+                                                     ("fp32", "u16", 270, "exclusive", 1),
+                                                     ("fp32", "f32", 270, "inclusive", 1),
+                                                     ("fp32", "u16", 512, "exclusive", 1),
+                                                     ("fp32", "f32", 270, "cube", 0)])
+def test_whitening_form_per_context(hs, prec, dtype, B, mode, form):
+    kw = dict(cube_lines=16) if mode == "cube" else {}
+    det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype, stats_mode=mode, **kw)
     assert det.whitening_form == form
     det.close()
 
