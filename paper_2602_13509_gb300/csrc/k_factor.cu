@@ -217,14 +217,16 @@ __device__ __forceinline__ void inverse_update(double* R, const double* P, int B
 
 // One CTA per line. Sigma (full B x B, lower triangle used) is factored in place in
 // global memory with a blocked right-looking Cholesky: the NB-column panel is staged in
-// shared memory and factored there, and the trailing lower triangle is updated with
-// 4 x 4 register tiles (NB DFMA per element loaded and stored). The inverse X = L^{-1}
-// is then built NB rows at a time: the contribution of earlier block rows is a
-// register-tiled product, and the within-block forward substitution runs per column,
-// each thread owning whole columns, so it needs no synchronisation.
+// shared memory and factored there (its diagonal block by one warp, the rows below by
+// one thread each), and the trailing lower triangle is updated with 4 x 4 register tiles
+// (NB DFMA per element loaded and stored). The inverse X = L^{-1} (all of it, or only its
+// 64 x 64 diagonal blocks in the triangular-solve form) is built NB rows at a time, fused
+// into the same loop: the contribution of earlier block rows is a register-tiled product,
+// and the within-block forward substitution runs per column, each thread owning whole
+// columns, so it needs no synchronisation.
 // CL = 1: one CTA per line (throughput: many lines in flight). CL > 1: the CTAs of a
 // thread-block cluster share one line (latency: few lines). Each CTA then factors every
-// 16-column panel redundantly in its own shared memory, the updates and the final cast
+// diagonal block redundantly in its own shared memory, the updates and the final cast
 // are spread over all CL x FT threads, steps are separated by cluster barriers
 // (release / acquire), and data written by other CTAs is read through L2 (ld.global.cg).
 // MB: CTAs per SM the register allocation is sized for (a one-CTA-per-line launch of 128
@@ -277,24 +279,24 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
   double* P = smem;  // panel: P[r * PS + j] = A[p + r][p + j]
   __shared__ double rdg[NB];  // 1 / L[p + j][p + j] of the current panel
-  __shared__ int notpd;       // a non-positive pivot in the diagonal block (cluster form)
+  __shared__ int notpd;       // a non-positive pivot in the diagonal block
   if (tid == 0) notpd = 0;
   __syncthreads();
   for (int p = 0; p < B; p += NB) {
     const int kb = min(NB, B - p), rows = B - p;
-    // One CTA factors the whole panel in shared memory. In a cluster every CTA factors
-    // only the kb x kb diagonal block (the same values everywhere, so a non-positive
-    // pivot exits every CTA alike) and the rows below it are solved once, spread over
-    // the cluster, then gathered by every CTA.
+    // One warp factors the kb x kb diagonal block of the panel (in a cluster every CTA
+    // does, with the same values everywhere, so a non-positive pivot exits every CTA
+    // alike); the rows below it are then solved one per thread: by the CTA in shared
+    // memory, or once across the cluster and gathered by every CTA.
     const int frows = CL == 1 ? rows : kb;
     for (int e = tid; e < frows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
       P[r * PS + j] = ldg_c<CL>(A + (int64_t)(p + r) * B + p + j);
     }
     __syncthreads();
-    if (CL > 1) {
-      // the kb x kb diagonal block alone: one warp, warp-level syncs only (the same
-      // operations per element as the CTA-wide sweep below)
+    {
+      // the kb x kb diagonal block: one warp, column by column, warp-level syncs only
+      // (pivot, reciprocal, column scaled by it, rank-1 update of the block's remainder)
       if (warp == 0) {
         for (int j = 0; j < kb; ++j) {
           const double piv = P[j * PS + j];
@@ -323,34 +325,33 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
         if (tid == 0) status[t] = LS_NOT_PD;
         return;
       }
-    } else {
-      for (int j = 0; j < kb; ++j) {
-        const double piv = P[j * PS + j];
-        if (!(piv > 0.0) || !isfinite(piv)) {  // same value in every thread: uniform exit
-          if (tid == 0) status[t] = LS_NOT_PD;
-          return;
-        }
-        const double l = sqrt(piv);
-        const double rl = 1.0 / l;  // one division per pivot; the column is scaled by multiplies
-        for (int r = j + 1 + tid; r < frows; r += FT) P[r * PS + j] *= rl;
-        __syncthreads();
-        if (tid == 0) {
-          P[j * PS + j] = l;
-          rdg[j] = rl;
-        }
-        const int nc = kb - j - 1;
-        if (nc > 0) {
-          for (int e = tid; e < (frows - j - 1) * nc; e += FT) {
-            const int r = j + 1 + e / nc, k = j + 1 + e % nc;
-            if (k <= r) P[r * PS + k] = fma(-P[r * PS + j], P[k * PS + j], P[r * PS + k]);
+    }
+    if (CL == 1) {
+      // L21 = A21 L11^{-T} in shared memory, one thread per row: forward substitution in
+      // the order of a column-by-column sweep (each element takes its updates in column
+      // order, then the pivot's reciprocal)
+      for (int r = kb + tid; r < rows; r += FT) {
+        double v[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v[j] = j < kb ? P[r * PS + j] : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (j < kb) {
+            double a = v[j];
+#pragma unroll
+            for (int q = 0; q < j; ++q) a = fma(-v[q], P[j * PS + q], a);
+            v[j] = a * rdg[j];
           }
         }
-        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+          if (j < kb) P[r * PS + j] = v[j];
       }
+      __syncthreads();
     }
     if (CL > 1) {
-      // L21 = A21 L11^{-T}: forward substitution along each row, in the same order of
-      // operations as the single-CTA column sweep above (bitwise the same factor)
+      // L21 = A21 L11^{-T}: the same forward substitution as the one-CTA form (bitwise
+      // the same factor), rows spread over the cluster
       for (int r = kb + gtid; r < rows; r += gthreads) {
         double v[NB];
         const double* arow = A + (int64_t)(p + r) * B + p;
