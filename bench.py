@@ -53,7 +53,7 @@ def load_peaks():
 # to a launch by its lines; keyed by (band count, whitening form: 1 = triangular solve), and
 # to be refreshed whenever the kernel changes (a form without a capture of the current
 # kernel reports null).
-FACTOR_DRAM_BYTES_PER_LINE = {}
+FACTOR_DRAM_BYTES_PER_LINE = {(270, 1): (0.945713e9 + 1.386916e9) / 512}
 
 
 def factor_flops_per_line(B, form):
