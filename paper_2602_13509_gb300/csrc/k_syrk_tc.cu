@@ -7,7 +7,7 @@
 //     S2 = 4096 H^T H + 64 (H^T R + R^T H) + R^T R,
 // three sums that stay exact in FP32 accumulators (TMEM) for up to 4096 pixels
 // (|h h| <= 4096, |h r + r h| <= 4096, |r r| <= 1024 per pixel, all below 2^24 in sum).
-// They are combined in FP64 in the epilogue, so S2 is exact.
+// They are combined exactly (int64) in the epilogue and stored as FP64, so S2 is exact.
 //
 // One CTA: one 128 x N block (bands i in [i0, i0+128), j in [j0, j0+N), j-block >= i-block)
 // of one group of pixels (one line, or a slice of a cube). One warp streams each 64-pixel
@@ -219,7 +219,11 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
         for (int jj = 0; jj < 32; ++jj) {
           const int gj = j0 + c0 + jj;
           if (c0 + jj < N && gj < B && gj >= bi) {
-            const double v = 4096.0 * (double)hh[jj] + 64.0 * (double)xr[jj] + (double)rr[jj];
+            // the three sums are exact integers below 2^24: combine them in int64 (integer
+            // ALU) and convert once; the FP64 pipe is far slower than the integer one
+            const long long iv = ((long long)__float2int_rn(hh[jj]) << 12) +
+                                 ((long long)__float2int_rn(xr[jj]) << 6) + (long long)__float2int_rn(rr[jj]);
+            const double v = (double)iv;
             double* dst = o + (int64_t)gj * B + bi;
             if (accumulate) atomicAdd(dst, v);
             else *dst = v;
