@@ -55,12 +55,12 @@ enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
 /* whitening form of a context (Eq. 1, Sec. 3.3), see hsad_whitening_form:
  * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1} D, the full triangular
  *                              inverse: CUBE mode (one factorisation per cube, where the
- *                              whitening dominates), FP16, BF16 with float input or B > 448;
+ *                              whitening dominates), FP16, BF16 with float input;
  * HSAD_FORM_TRIANGULAR_SOLVE   streamed statistics (EXCLUSIVE, INCLUSIVE: a factorisation
  *                              per line): L y = x' - m solved blockwise from L and the
  *                              inverses of its 64 x 64 diagonal blocks only, half the FP64
- *                              factor work; on the tensor cores for BF16 (uint16 input,
- *                              B <= 448), on the SIMT cores for FP32. */
+ *                              factor work; on the tensor cores for BF16 (uint16 input), on
+ *                              the SIMT cores for FP32. */
 enum { HSAD_FORM_INVERSE = 0, HSAD_FORM_TRIANGULAR_SOLVE = 1 };
 /* statistics window (which pixels form mu and Sigma for a scored line t) */
 enum {

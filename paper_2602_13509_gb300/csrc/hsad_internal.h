@@ -155,7 +155,7 @@ int whiten_trsm_stages(int B);
 // whitening is a chain of dependent block steps: it pays where a factorisation per line
 // dominates (streamed statistics), not in CUBE mode (one factorisation per cube, the
 // whitening dominates), which keeps the explicit inverse.
-// BF16: P_BF16T for uint16 input where the solve fits on chip, else P_BF16.
+// BF16: P_BF16T for uint16 input, else P_BF16.
 // FP32: P_FP32T (triangular solve on the SIMT cores), else P_FP32.
 // HSAD_BF16_FORM=inverse / HSAD_FP32_FORM=inverse in the environment keep the explicit
 // inverse everywhere (comparisons).

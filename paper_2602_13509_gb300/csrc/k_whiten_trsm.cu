@@ -16,12 +16,12 @@
 //   warps 0-3          one pixel (TMEM lane) each: z_k = v_k - acc_k in FP32, split into
 //                      BF16 hi + lo and written as the A operand; y_k read back, its square
 //                      summed into the score, split and written as the A operand of the
-//                      updates. v = x' - m in FP32 from the raw tile, which is first moved
-//                      into shared memory in the 128-byte swizzled layout (64 bands per
-//                      128-byte row: a thread reads its own pixel's bands without bank
-//                      conflicts).
+//                      updates. v = x' - m in FP32; the pixel's raw values of block k + 1
+//                      are loaded into registers while block k is solved.
 //   warp 4 (one lane)  TMA: the 64 x 64 blocks (j, k), j >= k, of the hi and lo planes of
-//                      H in the order the MMAs use them, through a ring of 2 to 4 stages.
+//                      H in the order the MMAs use them, through a ring of up to 10 stages
+//                      (the whole solve streams ~(Bp/64)^2/2 blocks of 16 KB per CTA from
+//                      L2, so the ring depth sets how much of that latency is hidden).
 //   warp 5 (one lane)  tcgen05.mma (M = 128, N = 64, K = 16), three products per block:
 //                      a_hi h_hi + a_hi h_lo + a_lo h_hi, FP32 accumulation in TMEM.
 // Every wait is bounded; a timeout sets *err and the CTA drains its copies and exits.
@@ -32,13 +32,15 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "hsad_internal.h"
 #include "tc_util.cuh"
 
 namespace hsad {
 
 namespace {
-constexpr int TS_M = 128, TS_KB = 64, TS_THREADS = 192, TS_MAX_STAGES = 4;
+constexpr int TS_M = 128, TS_KB = 64, TS_THREADS = 192, TS_MAX_STAGES = 10;
 constexpr uint32_t TS_BLK = TS_M * TS_KB * 2;  // one 128 x 64 16-bit operand block: 16 KB
 constexpr uint32_t TS_HALF = 64 * TS_KB * 2;   // one 64 x 64 16-bit block of H: 8 KB
 constexpr uint32_t TS_STAGE = 2 * TS_HALF;     // hi + lo planes of one block of H
@@ -50,11 +52,10 @@ __host__ __device__ inline uint32_t ts_cols(int Bp) {
   while (c < (uint32_t)Bp) c <<= 1;
   return c;
 }
-// shared memory after 1024-byte alignment: raw tile (Bp/64 blocks), Z (hi, lo), Y (hi, lo),
-// ring, m (float) and c (int) per band, barriers
+// shared memory after 1024-byte alignment: Z (hi, lo), Y (hi, lo), ring, m (float) and
+// c (int) per band, barriers
 __host__ __device__ inline uint32_t ts_smem(int Bp, int stages) {
-  return 1024 + (uint32_t)(Bp / 64) * TS_BLK + 4 * TS_BLK + (uint32_t)stages * TS_STAGE + (uint32_t)Bp * 8 +
-         TS_BAR;
+  return 1024 + 4 * TS_BLK + (uint32_t)stages * TS_STAGE + (uint32_t)Bp * 8 + TS_BAR;
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *(const uint32_t*)&v; }
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     const uint16_t* __restrict__ x, int W, int B, const int32_t* __restrict__ c_int,
     const __grid_constant__ CUtensorMap hmap, const float* __restrict__ m_all,
     const float* __restrict__ inv_s2_all, const int32_t* __restrict__ status, int factor_stride, ScoreOut out,
-    int32_t* __restrict__ err, long long limit, int stages, int bulk) {
+    int32_t* __restrict__ err, long long limit, int stages) {
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * TS_M;
   const int f = out.factor_base + (factor_stride ? t : 0);
@@ -91,8 +92,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   const uint32_t tcols = ts_cols(Bp);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sX = sm;                          // [nkb][128 x 64] raw values, swizzled
-  uint8_t* sZ = sX + nkb * TS_BLK;           // z_k: hi block, lo block
+  uint8_t* sZ = sm;                          // z_k: hi block, lo block
   uint8_t* sY = sZ + 2 * TS_BLK;             // y_k: hi block, lo block
   uint8_t* sR = sY + 2 * TS_BLK;             // ring: [stage][hi 64 x 64][lo 64 x 64]
   float* mS = (float*)(sR + stages * TS_STAGE);
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   uint32_t* tslot = (uint32_t*)(bars + 2 * TS_MAX_STAGES + 8);
   const uint32_t b_full = tc::smem_u32(bars), b_empty = b_full + 8 * TS_MAX_STAGES;
   const uint32_t z_full = b_empty + 8 * TS_MAX_STAGES, y_full = z_full + 8, ya_full = y_full + 8;
-  const uint32_t acc_full = ya_full + 8, done = acc_full + 8, raw_full = done + 8;
+  const uint32_t acc_full = ya_full + 8, done = acc_full + 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint16_t* xt = x + ((int64_t)t * W + p0) * B;  // the tile's 128 x B values are contiguous
 
@@ -115,7 +115,6 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     tc::mbar_init(ya_full, TS_M);
     tc::mbar_init(acc_full, 1);
     tc::mbar_init(done, 1);
-    tc::mbar_init(raw_full, 1);
     tc::mbar_init_fence();
   }
   const float* mf = m_all + (int64_t)f * Bp;
@@ -129,41 +128,6 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   bool ok = true;
-
-  // ---- raw tile -> sX (128-byte swizzle, 64 bands per row and block) ----------------
-  // The tile is bulk-copied into the still unused Z / Y / ring area when it fits, else
-  // read from global memory; rows of one warp are contiguous in either source.
-  const uint16_t* src = xt;
-  if (bulk) {
-    const uint32_t bytes = (uint32_t)npx * B * 2;
-    if (tid == 0) {
-      tc::mbar_arrive_expect_tx(raw_full, bytes);
-      tc::bulk_load(tc::smem_u32(sZ), xt, bytes, raw_full);
-    }
-    if (!tc::mbar_wait(raw_full, 0, limit)) {
-      ok = false;
-      atomicExch(err, 1);
-    }
-    src = (const uint16_t*)sZ;
-  }
-  if ((B & 1) == 0 && ((uintptr_t)src & 3) == 0) {
-    const int hw = B >> 1;
-    for (int r = warp; r < npx; r += TS_THREADS / 32) {
-      const uint32_t* row = (const uint32_t*)(src + (int64_t)r * B);
-      for (int w = lane; w < hw; w += 32) {
-        const int k = 2 * w;
-        *(uint32_t*)(sX + (k >> 6) * TS_BLK + tc::sw128_offset(r, k & 63)) = bulk ? row[w] : __ldg(row + w);
-      }
-    }
-  } else {
-    for (int r = warp; r < npx; r += TS_THREADS / 32)
-      for (int k = lane; k < B; k += 32) {
-        const uint16_t v = bulk ? src[(int64_t)r * B + k] : __ldg(src + (int64_t)r * B + k);
-        *(uint16_t*)(sX + (k >> 6) * TS_BLK + tc::sw128_offset(r, k & 63)) = v;
-      }
-  }
-  tc::fence_proxy_async();  // the staging area is overwritten by TMA / read by the MMAs next
-  __syncthreads();
 
   if (warp == 4) {
     // ---------------- TMA: blocks (j, k) of H, j = k .. nkb - 1, k = 0 .. nkb - 1 ----------
@@ -239,6 +203,27 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     const int r = tid;
     const bool rv = r < npx;
     const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
+    // this pixel's raw values of bands [64 k, 64 k + 64) as 32 packed pairs (zero past B and
+    // for pixels past the tile); 4-byte loads when every row starts 4-byte aligned
+    const uint16_t* px = xt + (int64_t)r * B;
+    const bool pairs = (B & 1) == 0 && ((uintptr_t)x & 3) == 0;
+    uint32_t rw[32];
+    auto load_raw = [&](int k) {
+      const int nb = rv ? min(TS_KB, B - k * TS_KB) : 0;
+      const uint16_t* pk = px + k * TS_KB;
+      if (pairs) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) rw[i] = 2 * i < nb ? __ldg((const uint32_t*)pk + i) : 0u;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const uint32_t lo = 2 * i < nb ? __ldg(pk + 2 * i) : 0u;
+          const uint32_t hi = 2 * i + 1 < nb ? __ldg(pk + 2 * i + 1) : 0u;
+          rw[i] = lo | (hi << 16);
+        }
+      }
+    };
+    load_raw(0);
     float dsum = 0.f;
     for (int k = 0; k < nkb; ++k) {
       float a[64];
@@ -253,11 +238,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
         for (int i = 0; i < 64; ++i) a[i] = 0.f;
       }
       // z_k = (x' - m) - acc, x' = DN - c exact in FP32
-      const uint8_t* xb = sX + k * TS_BLK;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const uint4 raw = *(const uint4*)(xb + tc::sw128_offset(r, 8 * q));
-        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+        const uint32_t w4[4] = {rw[4 * q], rw[4 * q + 1], rw[4 * q + 2], rw[4 * q + 3]};
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -277,6 +260,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
       tc::fence_proxy_async();
       tc::fence_before_sync();
       tc::mbar_arrive(z_full);
+      if (k + 1 < nkb) load_raw(k + 1);  // in flight while y_k is computed
       // y_k: score, and the A operand of the updates of the later blocks
       if (ok && !tc::mbar_wait(y_full, (uint32_t)(k & 1), limit)) ok = false;
       __syncwarp();
@@ -329,7 +313,9 @@ int fp32_form(bool cube) {
 }
 
 int whiten_trsm_stages(int B) {
-  for (int s = TS_MAX_STAGES; s >= 2; --s)
+  // no deeper than the blocks one CTA streams (small B: less shared memory, more CTAs per SM)
+  const int nkb = pad64(B) / TS_KB, blocks = nkb * (nkb + 1) / 2;
+  for (int s = std::min(TS_MAX_STAGES, blocks); s >= 1; --s)
     if (ts_smem(pad64(B), s) <= TS_SMEM_MAX) return s;
   return 0;
 }
@@ -342,17 +328,12 @@ cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, const int
   const int stages = whiten_trsm_stages(B);
   if (stages == 0) return cudaErrorInvalidValue;
   const uint32_t smem = ts_smem(Bp, stages);
-  // bulk copy of a tile into the Z / Y / ring area: 16-byte aligned start and size for
-  // every tile (line base, 128-pixel steps, the last partial tile) and room for it
-  const uint32_t area = 4 * TS_BLK + (uint32_t)stages * TS_STAGE;
-  const int bulk = ((uintptr_t)x % 16 == 0) && (((int64_t)W * B * 2) % 16 == 0) &&
-                   (((int64_t)(W % TS_M) * B * 2) % 16 == 0) && ((int64_t)TS_M * B * 2 <= (int64_t)area);
   const long long limit = 4000000000LL;  // ~2 s of clock cycles
   cudaError_t e = cudaFuncSetAttribute(whiten_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((W + TS_M - 1) / TS_M, L), block(TS_THREADS);
   whiten_trsm_kernel<<<grid, block, smem, st>>>(x, W, B, c_int, *(const CUtensorMap*)hmap, m, inv_s2, status,
-                                                factor_stride, out, err, limit, stages, bulk);
+                                                factor_stride, out, err, limit, stages);
   if (lc) lc->n += 1;
   return cudaGetLastError();
 }

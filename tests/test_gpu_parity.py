@@ -112,11 +112,11 @@ def test_stream_ragged_shapes(hs, W, B):
 
 
 @pytest.mark.parametrize("W,B", [(1, 1), (7, 3), (129, 64), (65, 65), (33, 127), (300, 130), (130, 270),
-                                 (640, 270), (130, 448), (40, 500)])
+                                 (640, 270), (130, 448), (40, 500), (21, 512)])
 def test_stream_bf16_ragged_shapes(hs, W, B):
     """BF16 streams of uint16 lines whiten by the blocked triangular solve: one and several
-    64-band blocks with ragged tails, odd B (2-byte staging), tiles staged by bulk copy
-    (B = 270) and from global memory (B = 448); B = 500 takes the explicit-inverse form."""
+    64-band blocks with ragged tails, odd B (2-byte raw loads), ring depths from 1 to 9
+    stages, B up to the 512-band maximum."""
     sc, lines = _scene_lines(max(6, (B + 1) // W + 4), W, B, seed=W * 1000 + B + 1)
     rc, s, m, st, _ = _run(hs, lines, stats_mode="exclusive", precision="bf16", gain=sc.gain, offset=sc.offset)
     ref, rst = orx.stream_rx(lines, oracle.EXCLUSIVE, gain=sc.gain, offset=sc.offset)
@@ -129,7 +129,7 @@ def test_stream_bf16_ragged_shapes(hs, W, B):
 
 @pytest.mark.parametrize("prec,dtype,B,mode,form", [("bf16", "u16", 270, "exclusive", 1),
                                                      ("bf16", "u16", 448, "inclusive", 1),
-                                                     ("bf16", "u16", 449, "exclusive", 0),
+                                                     ("bf16", "u16", 512, "exclusive", 1),
                                                      ("bf16", "f32", 270, "exclusive", 0),
                                                      ("bf16", "u16", 270, "cube", 0),
                                                      ("fp16", "u16", 270, "exclusive", 0),
