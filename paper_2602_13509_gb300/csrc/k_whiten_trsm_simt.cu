@@ -23,6 +23,33 @@ namespace {
 constexpr int TF_P = 64, TF_N = 64, TF_K = 16, TF_THREADS = 256;
 constexpr int TF_YS = TF_P + 4;  // band-row stride of the pixel buffer (floats)
 
+// acc[r][c] += y[p_r][c0 + kk] * H[n_c][c0 + kk] over one 16-column slice, for the first NC
+// of the thread's four bands (the block's bands past B need no work: NC < 4 only in the
+// last block)
+template <int NC>
+__device__ __forceinline__ void slice_fma(float (&acc)[4][4], const float* ysrow, const float* hs, int ty, int tx) {
+#pragma unroll
+  for (int kk = 0; kk < TF_K; ++kk) {
+    const float4 a = *(const float4*)&ysrow[kk * TF_YS + ty * 4];
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    float bv[4];
+    if (NC == 4) {
+      const float4 b = *(const float4*)&hs[kk * (TF_N + 4) + tx * 4];
+      bv[0] = b.x;
+      bv[1] = b.y;
+      bv[2] = b.z;
+      bv[3] = b.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) bv[c] = hs[kk * (TF_N + 4) + tx * 4 + c];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+  }
+}
+
 template <typename In>
 __device__ __forceinline__ float centred_t(In v, const int32_t* ci, const float* cf, int b);
 template <>
@@ -125,16 +152,15 @@ __global__ void __launch_bounds__(TF_THREADS) whiten_trsm_simt_kernel(
       }
       __syncthreads();
     }
-#pragma unroll
-    for (int kk = 0; kk < TF_K; ++kk) {
-      const float4 a = *(const float4*)&ys[(c0 + kk) * TF_YS + ty * 4];
-      const float4 b = *(const float4*)&Hs[cur][kk][tx * 4];
-      const float av[4] = {a.x, a.y, a.z, a.w};
-      const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+    // columns past B are zero in H; band groups past B need no output
+    if (c0 < B) {
+      const int nc = min(4, (B - n0 + 15) >> 4);
+      const float* ysrow = &ys[c0 * TF_YS];
+      const float* hs = &Hs[cur][0][0];
+      if (nc == 4) slice_fma<4>(acc, ysrow, hs, ty, tx);
+      else if (nc == 3) slice_fma<3>(acc, ysrow, hs, ty, tx);
+      else if (nc == 2) slice_fma<2>(acc, ysrow, hs, ty, tx);
+      else slice_fma<1>(acc, ysrow, hs, ty, tx);
     }
     if (last) {
       // y_k = L_kk^{-1} z_k: replaces z_k once every thread has read it
