@@ -963,17 +963,23 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
   const int64_t CLr = ctx->cfg.cube_lines;
   const bool pinned = mem == HSAD_HOST && is_pinned_host_ptr(lines);
   cudaEvent_t last_copy = nullptr;
-  // A large pinned push runs as batches of two factor waves (the lines one launch of the
-  // factor kernel holds resident, twice), so that the copy of each batch overlaps the
-  // previous batch's kernels while the factor launches stay whole waves; the statistics
-  // are exact, so batch boundaries do not change any score.
-  int64_t pinned_batch = ctx->Lmax;
+  // A large pinned push is cut so that copies overlap kernels: a first batch of one factor
+  // wave (the lines one launch of the factor kernel holds resident: its copy is the only
+  // one nothing hides), then batches of as many whole waves as fit in a staging buffer,
+  // each copied while the previous batch runs. The statistics are exact, so batch
+  // boundaries do not change any score.
+  int64_t first_batch = ctx->Lmax, pinned_batch = ctx->Lmax;
   if (pinned) {
     const int64_t wave = factor_wave_lines(ctx->B, ctx->prec);
-    if (wave > 0 && n_lines >= 3 * wave) pinned_batch = std::min<int64_t>(ctx->Lmax, 2 * wave);
+    if (wave > 0 && n_lines >= 2 * wave && ctx->Lmax >= 2 * wave) {
+      first_batch = wave;
+      pinned_batch = ctx->Lmax / wave * wave;
+    }
   }
   while (done < n_lines) {
-    int64_t take = std::min<int64_t>(n_lines - done, pinned ? pinned_batch : ctx->Lmax);
+    int64_t take = std::min<int64_t>(n_lines - done, !pinned ? ctx->Lmax : done == 0 ? first_batch : pinned_batch);
+    // a remainder that fits the staging buffer joins this batch instead of running alone
+    if (pinned && done > 0 && n_lines - done - take > 0 && n_lines - done <= ctx->Lmax) take = n_lines - done;
     if (CLr > 0) {
       const int64_t into = (int64_t)(ctx->next_line % (uint64_t)CLr);
       take = std::min<int64_t>(take, CLr - into);

@@ -317,9 +317,9 @@ def test_statistics_export_import_resumes_bitwise(hs, mode):
 
 
 def test_large_pinned_push_runs_as_wave_batches_bitwise(hs):
-    """A pinned host push of several factor waves runs as batches of two waves whose
-    copies overlap the previous batch's kernels; the scores equal those of the same lines
-    pushed from device memory in one batch."""
+    """A pinned host push of several factor waves runs as a one-wave batch and then whole
+    waves, each batch's copy overlapping the previous batch's kernels; the scores equal
+    those of the same lines pushed from device memory in one batch."""
     import torch
     T, W, B = 2600, 32, 16
     sc, lines = _scene_lines(T, W, B, seed=17)
