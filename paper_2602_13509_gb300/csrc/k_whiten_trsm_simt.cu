@@ -154,12 +154,12 @@ __global__ void __launch_bounds__(TF_THREADS) whiten_trsm_simt_kernel(
     }
     // columns past B are zero in H; band groups past B need no output
     if (c0 < B) {
-      const int nc = min(4, (B - n0 + 15) >> 4);
+      const int groups = min(4, (B - n0 + 15) >> 4);  // band groups of this block below B
       const float* ysrow = &ys[c0 * TF_YS];
       const float* hs = &Hs[cur][0][0];
-      if (nc == 4) slice_fma<4>(acc, ysrow, hs, ty, tx);
-      else if (nc == 3) slice_fma<3>(acc, ysrow, hs, ty, tx);
-      else if (nc == 2) slice_fma<2>(acc, ysrow, hs, ty, tx);
+      if (groups == 4) slice_fma<4>(acc, ysrow, hs, ty, tx);
+      else if (groups == 3) slice_fma<3>(acc, ysrow, hs, ty, tx);
+      else if (groups == 2) slice_fma<2>(acc, ysrow, hs, ty, tx);
       else slice_fma<1>(acc, ysrow, hs, ty, tx);
     }
     if (last) {
