@@ -52,8 +52,8 @@ __host__ __device__ inline uint32_t ts_cols(int Bp) {
   while (c < (uint32_t)Bp) c <<= 1;
   return c;
 }
-// shared memory after 1024-byte alignment: Z (hi, lo), Y (hi, lo), ring, m (float) and
-// c (int) per band, barriers
+// shared memory after 1024-byte alignment: Z (hi, lo), Y (hi, lo), ring, {c, m} per band,
+// barriers
 __host__ __device__ inline uint32_t ts_smem(int Bp, int stages) {
   return 1024 + 4 * TS_BLK + (uint32_t)stages * TS_STAGE + (uint32_t)Bp * 8 + TS_BAR;
 }
@@ -95,9 +95,10 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   uint8_t* sZ = sm;                          // z_k: hi block, lo block
   uint8_t* sY = sZ + 2 * TS_BLK;             // y_k: hi block, lo block
   uint8_t* sR = sY + 2 * TS_BLK;             // ring: [stage][hi 64 x 64][lo 64 x 64]
-  float* mS = (float*)(sR + stages * TS_STAGE);
-  int32_t* cS = (int32_t*)(mS + Bp);
-  uint64_t* bars = (uint64_t*)(cS + Bp);
+  // per band n: {bits of 1.5 * 2^23 - c_n, m_n} (zero past B), read as one 16-byte load per
+  // two bands
+  int2* cmS = (int2*)(sR + stages * TS_STAGE);
+  uint64_t* bars = (uint64_t*)(cmS + Bp);
   uint32_t* tslot = (uint32_t*)(bars + 2 * TS_MAX_STAGES + 8);
   const uint32_t b_full = tc::smem_u32(bars), b_empty = b_full + 8 * TS_MAX_STAGES;
   const uint32_t z_full = b_empty + 8 * TS_MAX_STAGES, y_full = z_full + 8, ya_full = y_full + 8;
@@ -118,10 +119,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     tc::mbar_init_fence();
   }
   const float* mf = m_all + (int64_t)f * Bp;
-  for (int n = tid; n < Bp; n += TS_THREADS) {
-    mS[n] = n < B ? mf[n] : 0.f;
-    cS[n] = n < B ? c_int[n] : 0;
-  }
+  for (int n = tid; n < Bp; n += TS_THREADS)
+    cmS[n] = make_int2(0x4B400000 - (n < B ? c_int[n] : 0), __float_as_int(n < B ? mf[n] : 0.f));
   if (warp == 5) tc::tmem_alloc(tc::smem_u32(tslot), tcols);
   tc::fence_before_sync();
   __syncthreads();
@@ -237,21 +236,22 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
 #pragma unroll
         for (int i = 0; i < 64; ++i) a[i] = 0.f;
       }
-      // z_k = (x' - m) - acc, x' = DN - c exact in FP32
+      // z_k = (x' - m) - acc, x' = DN - c exact in FP32: the bits of 1.5 * 2^23 + x' minus
+      // 1.5 * 2^23 (integer add + float subtract, no conversion instruction). Bands past B
+      // give 0 (raw 0, c = m = 0, acc 0); pixels past the tile give values never stored.
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t w4[4] = {rw[4 * q], rw[4 * q + 1], rw[4 * q + 2], rw[4 * q + 3]};
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          float z[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int n = k * TS_KB + 8 * q + 2 * j + e;
-            const int dn = (int)((w4[j] >> (16 * e)) & 0xffffu);
-            z[e] = (rv && n < B) ? ((float)(dn - cS[n]) - mS[n]) - a[8 * q + 2 * j + e] : 0.f;
-          }
-          split2(z[0], z[1], hi[j], lo[j]);
+          const int n = k * TS_KB + 8 * q + 2 * j;
+          const int4 cm = *(const int4*)&cmS[n];  // bands n, n + 1
+          const float x0 = __int_as_float(cm.x + (int)(w4[j] & 0xffffu)) - 12582912.0f;
+          const float x1 = __int_as_float(cm.z + (int)(w4[j] >> 16)) - 12582912.0f;
+          const float z0 = (x0 - __int_as_float(cm.y)) - a[8 * q + 2 * j];
+          const float z1 = (x1 - __int_as_float(cm.w)) - a[8 * q + 2 * j + 1];
+          split2(z0, z1, hi[j], lo[j]);
         }
         const uint32_t off = tc::sw128_offset(r, 8 * q);
         *(uint4*)(sZ + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
