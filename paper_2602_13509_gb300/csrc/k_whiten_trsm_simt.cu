@@ -54,7 +54,8 @@ template <typename In>
 __device__ __forceinline__ float centred_t(In v, const int32_t* ci, const float* cf, int b);
 template <>
 __device__ __forceinline__ float centred_t<uint16_t>(uint16_t v, const int32_t* ci, const float*, int b) {
-  return (float)((int)v - ci[b]);
+  // DN - c exactly: the bits of 1.5 * 2^23 + (DN - c) minus 1.5 * 2^23 (no conversion instruction)
+  return __int_as_float(0x4B400000 + (int)v - ci[b]) - 12582912.0f;
 }
 template <>
 __device__ __forceinline__ float centred_t<float>(float v, const int32_t*, const float* cf, int b) {
