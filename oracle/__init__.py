@@ -17,7 +17,9 @@ from .rx import (  # noqa: F401
     NotPositiveDefinite,
     calibrate,
     cholesky_lower,
+    encode_tx,
     forward_substitution,
+    frontend,
     global_rx,
     rx_scores,
     sample_covariance,

@@ -24,6 +24,16 @@ What it computes, and where the paper says so:
   statistics hold fewer than max(B+1, warmup_pixels) pixels is not ready
   (NaN score).
 
+* Transmit encoding, Sec. 3.5 ("Data Transmission"): each score is sent as an
+  IEEE-754 half-precision value of its square root, normalised to the cube's
+  maximum; the scores themselves are computed in single precision. Reading: code =
+  binary16(sqrt(delta / delta_max)) with the division and the square root in FP32
+  and round-to-nearest-even to binary16, delta_max the largest finite score of the
+  block being sent; NaN scores stay NaN.
+* Front end, Sec. 3.2 ("Data Acquisition"): the out-of-specification bands are
+  discarded and four consecutive bands are summed into one. Reading: keep raw bands
+  [first, first + bin * B) and sum groups of ``bin`` consecutive bands (integers, exact).
+
 Pins (tests/test_oracle_*.py): exact rational brute force on tiny inputs, the
 in-sample identity mean(delta) = B (N-1)/N, invariance under invertible affine
 band maps, closed forms for B = 1 and B = 2, delta(mu) = 0, the Hotelling T^2
@@ -210,3 +220,35 @@ def stream_rx(lines: np.ndarray, mode: str = EXCLUSIVE, cube_lines: int = 0, war
         delta[t], status[t] = stream_rx_line(lines, t, mode, cube_lines, warmup_pixels,
                                              gain, offset, n_lines=T)
     return delta, status
+
+
+def encode_tx(scores):
+    """Transmit encoding of a block of scores (Sec. 3.5): ``(codes uint16, delta_max)``.
+
+    code = binary16(sqrt(delta / delta_max)) with the division and square root in FP32
+    (the paper computes scores in single precision) and round-to-nearest-even to
+    binary16; delta_max = the largest finite score (0 if none: every finite score then
+    encodes as 0); NaN stays NaN, +Inf encodes as +Inf.
+    Pinned by hand-computed binary16 patterns, a nearest-rounding check that decodes the
+    codes bit by bit, and monotonicity (tests/test_oracle_pins.py).
+    """
+    s = np.asarray(scores, dtype=np.float32)
+    finite = np.isfinite(s)
+    dmax = np.float32(s[finite].max()) if finite.any() else np.float32(0.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        if dmax > 0:
+            r = np.sqrt(s / dmax)  # float32 / float32 and float32 sqrt: IEEE, correctly rounded
+        else:
+            r = np.where(np.isnan(s), np.float32(np.nan), np.where(np.isinf(s), s, np.float32(0.0)))
+    return r.astype(np.float32).astype(np.float16).view(np.uint16), float(dmax)
+
+
+def frontend(raw, first: int, bin_: int, bands: int) -> np.ndarray:
+    """Band discard and binning of raw lines [..., B_raw] (Sec. 3.2): the sum of raw bands
+    first + bin * b .. first + bin * b + bin - 1 for b = 0 .. bands - 1, as integers.
+    Pinned by a hand example and by the band-sum invariant (tests/test_oracle_pins.py)."""
+    raw = np.asarray(raw)
+    if first < 0 or bin_ < 1 or bands < 1 or first + bin_ * bands > raw.shape[-1]:
+        raise ValueError("band range outside the raw line")
+    kept = raw[..., first:first + bin_ * bands].astype(np.int64)
+    return kept.reshape(raw.shape[:-1] + (bands, bin_)).sum(axis=-1)

@@ -71,3 +71,40 @@ def test_pins_reject_mutant(monkeypatch, target, mutant):
     monkeypatch.setattr(orx, target, mutant)
     monkeypatch.setattr(oracle, target, mutant)
     assert _checks_fail(), f"mutant {mutant.__name__} of {target} was not caught"
+
+
+def _encode_no_sqrt(scores):                  # drops the square root
+    s = np.asarray(scores, dtype=np.float32)
+    dmax = np.float32(s[np.isfinite(s)].max())
+    return (s / dmax).astype(np.float16).view(np.uint16), float(dmax)
+
+
+def _encode_by_sum(scores):                   # normalises by the sum instead of the maximum
+    s = np.asarray(scores, dtype=np.float32)
+    tot = np.float32(s[np.isfinite(s)].sum())
+    return np.sqrt(s / tot).astype(np.float16).view(np.uint16), float(tot)
+
+
+def _frontend_shifted(raw, first, bin_, bands):  # bins start one band late
+    raw = np.asarray(raw)[..., first + 1:first + 1 + bin_ * bands].astype(np.int64)
+    return raw.reshape(raw.shape[:-1] + (bands, bin_)).sum(axis=-1)
+
+
+@pytest.mark.parametrize("target,mutant", [("encode_tx", _encode_no_sqrt), ("encode_tx", _encode_by_sum),
+                                           ("frontend", _frontend_shifted)])
+def test_encoding_and_front_end_pins_reject_mutant(monkeypatch, target, mutant):
+    import tests.test_oracle_pins as pins
+    checks = [pins.test_transmit_encoding_hand_values, pins.test_frontend_band_discard_and_binning]
+
+    def fails():
+        for c in checks:
+            try:
+                c()
+            except AssertionError:
+                return True
+        return False
+
+    assert not fails(), "pins must accept the unmodified oracle"
+    monkeypatch.setattr(orx, target, mutant)
+    monkeypatch.setattr(oracle, target, mutant)
+    assert fails(), f"mutant {mutant.__name__} of {target} was not caught"

@@ -301,3 +301,58 @@ def test_pushbroom_anomalies_rank_above_background():
     assert mm.sum() > 0
     assert _auc(dd[mm], dd[~mm]) > 0.99
     assert np.median(dd[mm]) > np.percentile(dd[~mm], 99)
+
+
+# ------------------------------------------------------------------ transmit encoding (Sec. 3.5)
+def _binary16_value(c):
+    """Value of a binary16 bit pattern, decoded field by field (sign, exponent, mantissa)."""
+    c = int(c)
+    sign = -1.0 if c >> 15 else 1.0
+    e, m = (c >> 10) & 31, c & 1023
+    if e == 0:
+        return sign * m / 1024.0 * 2.0 ** -14
+    if e == 31:
+        return sign * (math.inf if m == 0 else math.nan)
+    return sign * (1.0 + m / 1024.0) * 2.0 ** (e - 15)
+
+
+def test_transmit_encoding_hand_values():
+    # binary16: 1.0 = 0x3C00, 0.5 = 0x3800, 1/3 -> exponent -2, mantissa 341 -> 0x3555
+    codes, dmax = oracle.encode_tx([0.0, 1.0, 4.0])
+    assert dmax == 4.0 and list(codes) == [0x0000, 0x3800, 0x3C00]
+    codes, _ = oracle.encode_tx([9.0, 1.0])
+    assert list(codes) == [0x3C00, 0x3555]
+    codes, dmax = oracle.encode_tx([float("nan"), 2.0, float("inf")])
+    assert dmax == 2.0 and codes[0] == 0x7E00 and codes[1] == 0x3C00 and codes[2] == 0x7C00
+    codes, dmax = oracle.encode_tx([0.0, 0.0, float("nan")])  # no positive maximum: zeros stay zero
+    assert dmax == 0.0 and list(codes[:2]) == [0, 0] and codes[2] == 0x7E00
+
+
+def test_transmit_encoding_rounds_to_nearest_and_is_monotone():
+    rng = np.random.default_rng(5)
+    s = np.concatenate([rng.gamma(0.7, 30.0, 4000), [0.0, 1e-30, 7e3]]).astype(np.float32)
+    codes, dmax = oracle.encode_tx(s)
+    r64 = np.sqrt(s.astype(np.float64) / dmax)
+    for c, r in zip(codes[:600], r64[:600]):
+        v = _binary16_value(c)
+        # the nearest binary16 value to the (FP32) ratio: no neighbour is closer by more than
+        # the FP32 rounding of the ratio itself
+        tol = 2.0 ** -23 * max(r, 2.0 ** -14)
+        assert abs(v - r) <= abs(_binary16_value(c + 1) - r) + tol
+        if c > 0:
+            assert abs(v - r) <= abs(_binary16_value(c - 1) - r) + tol
+    order = np.argsort(s, kind="stable")
+    assert (np.diff(codes[order].astype(np.int64)) >= 0).all()
+    assert codes[np.argmax(s)] == 0x3C00
+
+
+# ------------------------------------------------------------------ front end (Sec. 3.2)
+def test_frontend_band_discard_and_binning():
+    raw = np.arange(2 * 3 * 12, dtype=np.uint16).reshape(2, 3, 12)
+    out = oracle.frontend(raw, first=1, bin_=4, bands=2)
+    # pixel (0, 0): raw bands 0..11 hold 0..11; kept 1..8, binned (1+2+3+4, 5+6+7+8)
+    assert out.shape == (2, 3, 2) and list(out[0, 0]) == [10, 26]
+    assert (out.sum(axis=-1) == raw[..., 1:9].astype(np.int64).sum(axis=-1)).all()
+    assert (oracle.frontend(raw, 0, 1, 12) == raw).all()
+    with pytest.raises(ValueError):
+        oracle.frontend(raw, 5, 4, 2)
