@@ -564,6 +564,23 @@ def main():
     if rank == 0 and args.serving_seconds > 0:
         serving = {p: run_serving(hs, local, p, args.serving_seconds, 1.0) for p in ("bf16", "fp32")}
 
+    # transmit encoding (Sec. 3.5) of the step's last full ring of scores, through the
+    # public API into device memory (a full call: launches, copy stream sync included)
+    tx = None
+    if rank == 0:
+        n_tx, first_tx = T, 0  # every step resets the stream: its lines are 0 .. T-1
+        codes = torch.empty((n_tx, W), dtype=torch.int16, device=f"cuda:{local}")
+        for _ in range(3):
+            hs.hsad_scores_tx(det.ctx, first_tx, n_tx, codes, hs.HSAD_DEVICE, -1)
+        t0 = time.perf_counter()
+        reps = 20
+        for _ in range(reps):
+            rc_tx, _ = hs.hsad_scores_tx(det.ctx, first_tx, n_tx, codes, hs.HSAD_DEVICE, -1)
+        tx_ms = (time.perf_counter() - t0) * 1e3 / reps
+        tx = {"lines": n_tx, "ms_per_call": tx_ms, "status": hs.hsad_status_string(rc_tx),
+              "bytes_per_pixel": 6, "what": "hsad_scores_tx: block maximum + binary16(sqrt(delta/max)) codes, "
+                                            "device output, host-timed API call"}
+
     # end to end through the public API from pinned host memory
     e2e_ms, _ = timed(det, host=True)
     e2e = {"value": px_step * world / (e2e_ms / 1e3), "unit": "pixel-spectra/s",
@@ -629,7 +646,7 @@ def main():
                    "host": host_cpus},
         "latency": lat, "e2e": e2e, "gpu_launches": launches, "fp32_path": fp32_arm,
         "roofline": roof, "kernels": per_kernel, "cpu_baseline": cpu, "clocks": clk.summary(),
-        "serving": serving,
+        "serving": serving, "tx_encode": tx,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

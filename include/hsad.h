@@ -102,6 +102,15 @@ typedef struct {
   int32_t device;              /* CUDA device ordinal */
   int32_t max_batch_lines;     /* lines processed per internal batch (0 = default 256) */
   int32_t result_lines;        /* lines of scores kept for hsad_scores (0 = default) */
+  /* Front end (Sec. 3.2: out-of-specification bands discarded, band_bin consecutive bands
+   * summed into one). raw_bands = 0 (default): off, pushed lines have `bands` bands.
+   * raw_bands > 0 (HSAD_U16 input of 12-bit DN only): pushed lines have raw_bands bands;
+   * band b of the detector is the sum of raw bands band_first + band_bin * b .. + band_bin - 1,
+   * band_bin in [1, 4], band_first + band_bin * bands <= raw_bands. The sums stay exact (the
+   * covariance sums are accumulated in slices small enough for the wider values). */
+  int32_t raw_bands;
+  int32_t band_first;
+  int32_t band_bin;
 } hsad_config;
 
 /* Fill *cfg with defaults: U16, FP32, EXCLUSIVE, cube_lines 0, ABS threshold
@@ -125,6 +134,8 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out);
  *   stay unchanged until hsad_scores has returned for these lines (or
  *   hsad_synchronize). In CUBE mode device lines are copied into the cube buffer
  *   unless the push holds exactly one whole cube starting at its first line.
+ * With the front end (raw_bands > 0) the lines have raw_bands bands; they are binned
+ * on the device (Sec. 3.2) before anything else reads them.
  * *first_line_id (optional) receives the id of the first pushed line; ids count
  * lines from 0 in push order. n_lines = 0 is a no-op. Returns HSAD_E_INVALID for
  * NULL data, a negative count, a pointer in the wrong memory space, or a push
@@ -152,6 +163,34 @@ int hsad_scores(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, float* s
  * Same waiting rules as hsad_scores. */
 int hsad_line_status(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines,
                      int32_t* status, int32_t timeout_ms);
+
+/* Transmit encoding (Sec. 3.5, data transmission) of lines [first_line_id, first_line_id +
+ * n_lines): code = IEEE binary16 of sqrt(delta / delta_max), delta_max the largest finite
+ * score of the block (the cube maximum of the paper when the block is one cube), the
+ * division and square root in FP32 (correctly rounded) and the conversion rounded to nearest
+ * even. NaN scores (lines in warm-up) give the NaN code 0x7E00; if no score of the block is
+ * positive every finite score gives 0. codes: n_lines x width uint16, row-major, in host
+ * (mem = HSAD_HOST) or device memory; *max_score (nullable) receives delta_max. Waits and
+ * returns like hsad_scores (HSAD_E_NOT_READY after writing the codes if some lines are in
+ * warm-up). Runs on the context's copy stream; allocates nothing. */
+int hsad_scores_tx(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, uint16_t* codes, float* max_score,
+                   int32_t mem, int32_t timeout_ms);
+
+/* The front end alone (Sec. 3.2) on device buffers of `device`: out[p][b] = sum of
+ * raw[p][band_first + band_bin * b + i] for i < band_bin, b < bands, p < n_pixels; raw is
+ * [n_pixels][raw_bands] uint16, out [n_pixels][bands] uint16 (sums wrap above 65535: use
+ * 12-bit DN and band_bin <= 16). stream: a cudaStream_t of that device or NULL; the call
+ * synchronises it. Returns HSAD_OK, HSAD_E_INVALID or HSAD_E_CUDA. */
+int hsad_frontend(const uint16_t* raw, int64_t n_pixels, int32_t raw_bands, int32_t band_first, int32_t band_bin,
+                  int32_t bands, uint16_t* out, int32_t device, void* stream);
+
+/* The same transmit encoding of n scores already in device memory of `device` into n
+ * device codes, delta_max over those n scores (returned in *max_score, nullable).
+ * stream: a cudaStream_t of that device, or NULL for its default stream; the call
+ * synchronises it. Keeps one 4-byte device scratch per device for the process. Returns
+ * HSAD_OK, HSAD_E_INVALID (n < 0, NULL pointers, bad device), HSAD_E_NOMEM or HSAD_E_CUDA. */
+int hsad_encode_scores(const float* scores, int64_t n, uint16_t* codes, float* max_score, int32_t device,
+                       void* stream);
 
 /* Restart the stream: the running statistics, the open cube and the result ring are
  * cleared and line ids start again at 0. Work already enqueued completes first

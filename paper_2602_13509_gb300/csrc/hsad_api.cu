@@ -99,10 +99,20 @@ struct hsad_ctx {
   // result ring
   float* r_scores = nullptr;
   uint8_t* r_mask = nullptr;
+  uint16_t* r_codes = nullptr;      // transmit codes of a requested block, for host copies
+  unsigned int* tx_max = nullptr;   // bits of the block maximum of the transmit encoding
   int32_t* r_status = nullptr;
   // input staging (host pushes) and cube buffer
   void* h_stage[2] = {nullptr, nullptr};
   void* d_stage[2] = {nullptr, nullptr};
+  // front end (raw_bands > 0): raw lines are copied to d_raw (host pushes) and binned into
+  // d_bin[i], alternately, before the pipeline reads them
+  bool fe = false;
+  int64_t raw_line_bytes = 0;
+  void* d_raw = nullptr;
+  void* d_bin[2] = {nullptr, nullptr};
+  int fe_idx = 0;
+  int64_t syrk_max_pix = 4096;  // pixels one exact SYRK accumulation may hold
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   // pinned caller buffers are copied straight to d_stage on h2d_stream: copy_ev marks the
   // copy done, free_ev the end of the last batch that read d_stage[i]
@@ -249,8 +259,10 @@ int64_t plan_bytes(const hsad_ctx* c) {
   b += Lf * B * B * 8 * 2;                                       // sigma, inv
   b += Lf * Bp * Bp * 4 + Lf * Bp * 4 + Lf * 4 + Ls * 4;        // wmat, y0, inv_s2, status
   b += c->ring * c->W * 5 + c->ring * 4 + 64;                    // result ring
+  b += c->ring * c->W * 2 + 64;                                  // transmit codes scratch
   if (c->mode == HSAD_CUBE) b += (int64_t)c->cfg.cube_lines * c->line_bytes;
   else b += 2 * L * c->line_bytes;                               // device staging
+  if (c->fe) b += L * c->raw_line_bytes + 2 * L * c->line_bytes;  // front end: raw copy, binned lines
   return b;
 }
 
@@ -280,6 +292,14 @@ int validate(const hsad_config* cfg, std::string* why) {
     for (int b = 0; b < cfg->bands; ++b)
       if (!std::isfinite(cfg->offset[b])) return bad("offset must be finite");
   if ((int64_t)cfg->width * cfg->bands > (int64_t)1 << 31) return bad("line too large");
+  if (cfg->raw_bands < 0) return bad("raw_bands must be >= 0");
+  if (cfg->raw_bands > 0) {
+    if (cfg->in_dtype != HSAD_U16) return bad("the front end (raw_bands > 0) needs HSAD_U16 input");
+    if (cfg->band_bin < 1 || cfg->band_bin > 4) return bad("band_bin must be in [1, 4]");
+    if (cfg->band_first < 0 || (int64_t)cfg->band_first + (int64_t)cfg->band_bin * cfg->bands > cfg->raw_bands)
+      return bad("band_first + band_bin * bands must be <= raw_bands");
+    if ((int64_t)cfg->width * cfg->raw_bands > (int64_t)1 << 31) return bad("raw line too large");
+  }
   return HSAD_OK;
 }
 
@@ -476,6 +496,11 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->elem = ctx->in_type == IN_U16 ? 2 : 4;
   ctx->line_elems = (int64_t)ctx->W * ctx->B;
   ctx->line_bytes = ctx->line_elems * ctx->elem;
+  ctx->fe = cfg->raw_bands > 0;
+  ctx->raw_line_bytes = ctx->fe ? (int64_t)ctx->W * cfg->raw_bands * 2 : ctx->line_bytes;
+  // sums of bin 12-bit DN: |x'| < 2^(12 + ceil(log2 bin)); an exact accumulation holds
+  // 2^24 / (|x'| / 64)^2 pixels: 4096 (bin 1), 1024 (bin 2), 256 (bin 3, 4)
+  if (ctx->fe) ctx->syrk_max_pix = cfg->band_bin == 1 ? 4096 : (cfg->band_bin == 2 ? 1024 : 256);
   ctx->min_pix = std::max<int64_t>((int64_t)ctx->B + 1, cfg->warmup_pixels);
   ctx->tau = cfg->threshold > 0.f
                  ? cfg->threshold
@@ -551,12 +576,18 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->dev_err = (int32_t*)((char*)ctx->dmax_bits + 48);
   ctx->r_scores = (float*)dalloc(ctx, ctx->ring * ctx->W * 4, &ok);
   ctx->r_mask = (uint8_t*)dalloc(ctx, ctx->ring * ctx->W, &ok);
+  ctx->r_codes = (uint16_t*)dalloc(ctx, ctx->ring * ctx->W * 2, &ok);
+  ctx->tx_max = (unsigned int*)dalloc(ctx, 64, &ok);
   ctx->r_status = (int32_t*)dalloc(ctx, ctx->ring * 4, &ok);
   if (ctx->mode == HSAD_CUBE) {
     // the cube buffer is allocated on first use: a device push of one whole cube is
     // scored in place and never needs it (its bytes are charged to the budget anyway)
   } else {
     for (int i = 0; i < 2; ++i) ctx->d_stage[i] = dalloc(ctx, L * ctx->line_bytes, &ok);
+  }
+  if (ctx->fe) {
+    ctx->d_raw = dalloc(ctx, L * ctx->raw_line_bytes, &ok);
+    for (int i = 0; i < 2; ++i) ctx->d_bin[i] = dalloc(ctx, L * ctx->line_bytes, &ok);
   }
   for (int i = 0; i < 2 && ok; ++i) {
     void* h = nullptr;
@@ -673,12 +704,12 @@ int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* ou
   cudaStream_t st = ctx->stream;
   if (ctx->in_type == IN_U16) {
     bool acc = accumulate;
-    if (!acc && pix > 4096) {  // exactness bound of one accumulation: add slices atomically
+    if (!acc && pix > ctx->syrk_max_pix) {  // exactness bound of one accumulation: add slices atomically
       CK(cudaMemsetAsync(out, 0, (size_t)(n_groups * out_stride * 8), st));
       acc = true;
     }
     KL("syrk", launch_syrk_tc((const uint16_t*)x, n_groups, pix, ctx->B, ctx->c_int, out, out_stride, acc ? 1 : 0,
-                              ctx->dev_err, st, &ctx->lc));
+                              ctx->dev_err, st, &ctx->lc, ctx->syrk_max_pix));
   } else {
     KL("syrk", launch_syrk_simt(x, n_groups, pix, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt, out, out_stride,
                                 accumulate ? 1 : 0, st, &ctx->lc));
@@ -879,6 +910,8 @@ bool is_device_ptr(const void* p, int device) {
 
 extern "C" {
 
+static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem);
+
 int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem, uint64_t* first_line_id) {
   if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
   if (ctx->failed) return HSAD_E_CUDA;
@@ -893,6 +926,38 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
     return fail(ctx, HSAD_E_INVALID, "lines is not device memory of this context's device");
   if (mem == HSAD_HOST && is_device_ptr(lines, ctx->device))
     return fail(ctx, HSAD_E_INVALID, "lines is device memory but mem = HSAD_HOST");
+  if (!ctx->fe) return push_impl(ctx, lines, n_lines, mem);
+  // front end: raw lines to the device (host pushes), binned on the context's stream, then
+  // pushed as device lines; chunks of at most Lmax lines alternate between two buffers
+  const char* raw = (const char*)lines;
+  for (int64_t done = 0; done < n_lines;) {
+    const int64_t k = std::min<int64_t>(n_lines - done, ctx->Lmax);
+    const void* src = raw + done * ctx->raw_line_bytes;
+    if (mem == HSAD_HOST) {
+      CK(cudaMemcpyAsync(ctx->d_raw, src, (size_t)(k * ctx->raw_line_bytes), cudaMemcpyHostToDevice, ctx->stream));
+      src = ctx->d_raw;
+    }
+    void* bin = ctx->d_bin[ctx->fe_idx];
+    ctx->fe_idx ^= 1;
+    KL("frontend", launch_frontend((const uint16_t*)src, k * ctx->W, ctx->cfg.raw_bands, ctx->cfg.band_first,
+                                   ctx->cfg.band_bin, ctx->B, (uint16_t*)bin, ctx->stream, &ctx->lc));
+    const int rc = push_impl(ctx, bin, k, HSAD_DEVICE);
+    if (rc != HSAD_OK) return rc;
+    done += k;
+  }
+  // the caller may reuse a host buffer once the copies from it have landed
+  if (mem == HSAD_HOST) {
+    cudaEvent_t ev = get_event(ctx);
+    if (!ev) return fail(ctx, HSAD_E_CUDA, "event creation failed");
+    CK(cudaEventRecord(ev, ctx->stream));
+    const int rc = wait_event(ctx, ev, 60000);
+    ctx->event_pool.push_back(ev);
+    if (rc != HSAD_OK) return rc;
+  }
+  return HSAD_OK;
+}
+
+static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem) {
 
   // float input: reject non-finite values before anything is enqueued
   if (ctx->in_type == IN_F32) {
@@ -1130,6 +1195,47 @@ int hsad_scores(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, float* s
   if (npd) return fail(ctx, HSAD_E_NOT_PD, "covariance not positive definite for some requested lines");
   if (nr) return HSAD_E_NOT_READY;
   return HSAD_OK;
+}
+
+int hsad_scores_tx(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, uint16_t* codes, float* max_score,
+                   int32_t mem, int32_t timeout_ms) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  if (n_lines < 0) return fail(ctx, HSAD_E_INVALID, "n_lines < 0");
+  if (mem != HSAD_HOST && mem != HSAD_DEVICE) return fail(ctx, HSAD_E_INVALID, "mem must be HSAD_HOST or HSAD_DEVICE");
+  if (n_lines > ctx->ring) return fail(ctx, HSAD_E_INVALID, "request larger than the result ring");
+  if (n_lines == 0) return HSAD_OK;
+  if (!codes) return fail(ctx, HSAD_E_INVALID, "codes is NULL");
+  DeviceGuard dg(ctx->device);
+  // the block's scores are final once their batches' events have completed
+  int rc = find_ready(ctx, first_line_id, n_lines, timeout_ms);
+  if (rc != HSAD_OK) return rc;  // not scored yet (e.g. an open cube), timed out, or invalid  // pushed but unscored (an open cube): nothing to encode yet
+  cudaStream_t st = ctx->copy_stream;
+  uint16_t* out = mem == HSAD_DEVICE ? codes : ctx->r_codes;
+  // the ring segments of the block (at most two: the ring wraps)
+  int64_t seg_slot[2], seg_n[2], nseg = 0, done = 0;
+  while (done < n_lines) {
+    const int64_t slot = (int64_t)((first_line_id + (uint64_t)done) % (uint64_t)ctx->ring);
+    const int64_t k = std::min<int64_t>(n_lines - done, ctx->ring - slot);
+    seg_slot[nseg] = slot;
+    seg_n[nseg++] = k;
+    done += k;
+  }
+  const int64_t W = ctx->W;
+  CK(cudaMemsetAsync(ctx->tx_max, 0, sizeof(unsigned int), st));
+  for (int i = 0; i < nseg; ++i)
+    CK(launch_tx_max(ctx->r_scores + seg_slot[i] * W, seg_n[i] * W, ctx->tx_max, st, &ctx->lc));
+  for (int i = 0, o = 0; i < nseg; o += (int)seg_n[i], ++i)
+    CK(launch_tx_encode(ctx->r_scores + seg_slot[i] * W, seg_n[i] * W, out + (int64_t)o * W, ctx->tx_max, st,
+                        &ctx->lc));
+  if (mem == HSAD_HOST)
+    CK(cudaMemcpyAsync(codes, out, (size_t)(n_lines * W * 2), cudaMemcpyDeviceToHost, st));
+  unsigned int bits = 0;
+  CK(cudaMemcpyAsync(&bits, ctx->tx_max, sizeof bits, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (max_score) memcpy(max_score, &bits, sizeof bits);
+  // the same status report as hsad_scores for the block's lines
+  return hsad_scores(ctx, first_line_id, n_lines, nullptr, nullptr, mem, 0);
 }
 
 int hsad_reset(hsad_ctx* ctx) {

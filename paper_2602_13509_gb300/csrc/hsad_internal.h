@@ -71,9 +71,14 @@ cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int i
 // K2 (tcgen05, uint16 input): exact s2 = sum (x - c)(x - c)^T per group into the lower
 // triangle of out[g] (row stride B); groups above 4096 pixels need accumulate != 0
 // (atomic adds into a zeroed out). err is set if a bounded wait expires.
+// max_pix: pixels one accumulation may sum exactly (4096 for 12-bit DN, fewer for wider
+// values); larger groups are cut into slices of max_pix that need accumulate != 0.
 cudaError_t launch_syrk_tc(const uint16_t* x, int64_t n_groups, int64_t pix_per_group, int B,
                            const int32_t* c_int, double* out, int64_t out_stride, int accumulate, int32_t* err,
-                           cudaStream_t st, LaunchCounter* lc);
+                           cudaStream_t st, LaunchCounter* lc, int64_t max_pix = 4096);
+// Front end (Sec. 3.2): out[p][b] = sum_{i < bin} raw[p][first + bin * b + i].
+cudaError_t launch_frontend(const uint16_t* raw, int64_t n_px, int raw_bands, int first, int bin, int bands,
+                            uint16_t* out, cudaStream_t st, LaunchCounter* lc);
 
 // K3c (cube): raw sums S2 (lower triangle) copied from the state into sigma and
 // m = S1 / N; status[0] becomes LS_OK or LS_NOT_READY (fewer than min_pixels pixels).
@@ -166,6 +171,12 @@ int fp32_form(bool cube);
 // the REL / ABS mask.
 cudaError_t launch_cube_normalize(ScoreOut out, int64_t n_lines, int W, int rel, int normalize,
                                   unsigned int* dmax_bits, cudaStream_t st, LaunchCounter* lc);
+
+// Transmit encoding (Sec. 3.5): max_bits (zeroed by the caller) receives the bits of the
+// largest finite positive score of s[0, n); then codes = binary16(sqrt(s / max)).
+cudaError_t launch_tx_max(const float* s, int64_t n, unsigned int* max_bits, cudaStream_t st, LaunchCounter* lc);
+cudaError_t launch_tx_encode(const float* s, int64_t n, uint16_t* codes, const unsigned int* max_bits,
+                             cudaStream_t st, LaunchCounter* lc);
 
 // f32 input validation: sets *bad = 1 if any value is NaN or Inf.
 cudaError_t launch_check_finite(const float* x, int64_t n, int32_t* bad, cudaStream_t st,

@@ -7,6 +7,8 @@
 //     S2 = 4096 H^T H + 64 (H^T R + R^T H) + R^T R,
 // three sums that stay exact in FP32 accumulators (TMEM) for up to 4096 pixels
 // (|h h| <= 4096, |h r + r h| <= 4096, |r r| <= 1024 per pixel, all below 2^24 in sum).
+// Wider values (binned 12-bit DN: |x'| < 2^14, |h| <= 256, h h <= 2^16) keep the same split,
+// exact in BF16, with slices of 2^24 / 2^16 = 256 pixels.
 // They are combined exactly (int64) in the epilogue and stored as FP64, so S2 is exact.
 //
 // One CTA: one 128 x N block (bands i in [i0, i0+128), j in [j0, j0+N), j-block >= i-block)
@@ -243,14 +245,15 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
 
 cudaError_t launch_syrk_tc(const uint16_t* x, int64_t n_groups, int64_t pix_per_group, int B,
                            const int32_t* c_int, double* out, int64_t out_stride, int accumulate, int32_t* err,
-                           cudaStream_t st, LaunchCounter* lc) {
+                           cudaStream_t st, LaunchCounter* lc, int64_t max_pix) {
   if (n_groups <= 0 || pix_per_group <= 0) return cudaSuccess;
+  if (max_pix < SK_KC || max_pix > SK_MAX_PIX || max_pix % SK_KC) return cudaErrorInvalidValue;
   const int nb = (B + SK_M - 1) / SK_M;
   const int tiles = nb * (nb + 1) / 2;
-  int64_t slices = (pix_per_group + SK_MAX_PIX - 1) / SK_MAX_PIX;
+  int64_t slices = (pix_per_group + max_pix - 1) / max_pix;
   if (slices > 1 && !accumulate) return cudaErrorInvalidValue;  // caller zeroes and accumulates
   if (slices > 65535 || n_groups > 65535) return cudaErrorInvalidValue;
-  const int64_t per = slices > 1 ? SK_MAX_PIX : pix_per_group;
+  const int64_t per = slices > 1 ? max_pix : pix_per_group;
   // Bulk copies need 16-byte aligned chunk starts and sizes: the input base, every group
   // start (pix_per_group * B * 2 bytes) and the last partial chunk of a group.
   const bool aligned = ((uintptr_t)x % 16 == 0) && ((pix_per_group * B) % 8 == 0) &&

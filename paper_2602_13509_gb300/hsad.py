@@ -39,6 +39,7 @@ class hsad_config(C.Structure):
         ("warmup_pixels", C.c_int64), ("device_budget_bytes", C.c_int64),
         ("flags", C.c_int32), ("device", C.c_int32),
         ("max_batch_lines", C.c_int32), ("result_lines", C.c_int32),
+        ("raw_bands", C.c_int32), ("band_first", C.c_int32), ("band_bin", C.c_int32),
     ]
 
 
@@ -61,6 +62,9 @@ def _load():
         "hsad_push_lines": (C.c_int, [P, P, C.c_int64, C.c_int32, C.POINTER(C.c_uint64)]),
         "hsad_flush": (C.c_int, [P]),
         "hsad_scores": (C.c_int, [P, C.c_uint64, C.c_int64, P, P, C.c_int32, C.c_int32]),
+        "hsad_scores_tx": (C.c_int, [P, C.c_uint64, C.c_int64, P, C.POINTER(C.c_float), C.c_int32, C.c_int32]),
+        "hsad_encode_scores": (C.c_int, [P, C.c_int64, P, C.POINTER(C.c_float), C.c_int32, P]),
+        "hsad_frontend": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, P]),
         "hsad_line_status": (C.c_int, [P, C.c_uint64, C.c_int64, P, C.c_int32]),
         "hsad_synchronize": (C.c_int, [P, C.c_int32]),
         "hsad_reset": (C.c_int, [P]),
@@ -166,6 +170,28 @@ def hsad_flush(ctx) -> int:
 def hsad_scores(ctx, first_line_id: int, n_lines: int, scores, mask, mem: int, timeout_ms: int) -> int:
     return _lib.hsad_scores(ctx, int(first_line_id), int(n_lines), _ptr(scores), _ptr(mask), int(mem),
                             int(timeout_ms))
+
+
+def hsad_scores_tx(ctx, first_line_id: int, n_lines: int, codes, mem: int, timeout_ms: int):
+    """Transmit codes (binary16 of sqrt(delta / delta_max)) of a block of lines into ``codes``
+    (uint16, n_lines x width). Returns ``(status, delta_max)``."""
+    mx = C.c_float(0.0)
+    rc = _lib.hsad_scores_tx(ctx, int(first_line_id), int(n_lines), _ptr(codes), C.byref(mx), int(mem),
+                             int(timeout_ms))
+    return rc, mx.value
+
+
+def hsad_frontend(raw, n_pixels: int, raw_bands: int, band_first: int, band_bin: int, bands: int, out,
+                  device: int = 0, stream=None) -> int:
+    return _lib.hsad_frontend(_ptr(raw), int(n_pixels), int(raw_bands), int(band_first), int(band_bin), int(bands),
+                              _ptr(out), int(device), _ptr(stream))
+
+
+def hsad_encode_scores(scores, n: int, codes, device: int = 0, stream=None):
+    """Transmit codes of n device scores into n device codes. Returns ``(status, delta_max)``."""
+    mx = C.c_float(0.0)
+    rc = _lib.hsad_encode_scores(_ptr(scores), int(n), _ptr(codes), C.byref(mx), int(device), _ptr(stream))
+    return rc, mx.value
 
 
 def hsad_line_status(ctx, first_line_id: int, n_lines: int, status, timeout_ms: int) -> int:
@@ -324,7 +350,8 @@ _NAMES = {
 
 def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="exclusive", cube_lines=0,
                 gain=None, offset=None, threshold_mode="abs", threshold=0.0, warmup_pixels=0,
-                device_budget_bytes=0, flags=0, device=0, max_batch_lines=0, result_lines=0):
+                device_budget_bytes=0, flags=0, device=0, max_batch_lines=0, result_lines=0,
+                raw_bands=0, band_first=0, band_bin=1):
     """Build an hsad_config; ``gain``/``offset`` arrays are kept alive on the struct."""
     import numpy as np
     cfg = hsad_config_init()
@@ -338,6 +365,7 @@ def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="excl
     cfg.warmup_pixels, cfg.device_budget_bytes = int(warmup_pixels), int(device_budget_bytes)
     cfg.flags, cfg.device = int(flags), int(device)
     cfg.max_batch_lines, cfg.result_lines = int(max_batch_lines), int(result_lines)
+    cfg.raw_bands, cfg.band_first, cfg.band_bin = int(raw_bands), int(band_first), int(band_bin)
     keep = []
     for name, arr in (("gain", gain), ("offset", offset)):
         if arr is not None:
@@ -385,6 +413,15 @@ class Detector:
         if rc2 not in (HSAD_OK,):
             raise HsadError(rc2, hsad_last_error(self.ctx))
         return rc, s, m, st
+
+    def scores_tx(self, first, n, timeout_ms=-1):
+        """Transmit codes (Sec. 3.5): ``(status, codes uint16 [n, W], delta_max)``."""
+        import numpy as np
+        codes = np.empty((n, self.width), dtype=np.uint16)
+        rc, mx = hsad_scores_tx(self.ctx, first, n, codes, HSAD_HOST, timeout_ms)
+        if rc in (HSAD_E_INVALID, HSAD_E_CUDA, HSAD_E_TIMEOUT):
+            raise HsadError(rc, hsad_last_error(self.ctx))
+        return rc, codes, mx
 
     def scores_device(self, first, n, scores, mask, timeout_ms=-1) -> int:
         return hsad_scores(self.ctx, first, n, scores, mask, HSAD_DEVICE, timeout_ms)

@@ -37,7 +37,8 @@ def test_config_defaults_and_struct_size(hs):
     cfg = hs.hsad_config_init()
     assert cfg.in_dtype == hs.HSAD_U16 and cfg.precision == hs.HSAD_FP32
     assert cfg.stats_mode == hs.HSAD_EXCLUSIVE and cfg.threshold_mode == hs.HSAD_ABS
-    assert C.sizeof(hs.hsad_config) == 80
+    assert C.sizeof(hs.hsad_config) == 96  # 80 + the three front-end fields, padded to 8
+    assert cfg.raw_bands == 0 and cfg.band_first == 0 and cfg.band_bin == 0   # front end off
 
 
 @pytest.mark.parametrize("field,value,msg", [
@@ -95,3 +96,16 @@ def test_budget_calls_are_host_only(hs):
     assert hs.hsad_set_device_budget(0, -1) == hs.HSAD_E_INVALID
     assert hs.hsad_set_device_budget(0, 0) == hs.HSAD_OK
     assert hs.hsad_device_budget_used(0) == 0
+
+
+def test_create_rejects_bad_front_end(hs):
+    def rc(**kw):
+        r, ctx = hs.hsad_create(hs.make_config(16, 8, **kw))
+        return r, hs.hsad_last_error(None)
+    assert rc(raw_bands=-1)[0] == hs.HSAD_E_INVALID
+    r, why = rc(raw_bands=40, band_bin=5)
+    assert r == hs.HSAD_E_INVALID and "band_bin" in why
+    r, why = rc(raw_bands=40, band_first=10, band_bin=4)          # 10 + 4 * 8 > 40
+    assert r == hs.HSAD_E_INVALID and "raw_bands" in why
+    r, why = rc(raw_bands=40, band_bin=4, in_dtype="f32")
+    assert r == hs.HSAD_E_INVALID and "U16" in why
