@@ -23,6 +23,9 @@ What it computes, and where the paper says so:
   reset (every ``cube_lines`` lines, or never when it is 0). A line whose
   statistics hold fewer than max(B+1, warmup_pixels) pixels is not ready
   (NaN score).
+* Factorisation cadence (an extension; the paper does not define one): with a
+  cadence of k lines, EXCLUSIVE statistics are taken only every k lines after the
+  reset, and line t is scored against the last snapshot, [r, r + k floor((t-r)/k)).
 
 * Transmit encoding, Sec. 3.5 ("Data Transmission"): each score is sent as an
   IEEE-754 half-precision value of its square root, normalised to the cube's
@@ -152,11 +155,17 @@ def _fetch(lines: LineSource, t0: int, n: int) -> np.ndarray:
     return lines[t0:t0 + n]
 
 
-def statistics_lines(t: int, mode: str, cube_lines: int, n_lines: int) -> tuple[int, int]:
-    """Half-open line range [a, b) whose pixels form the statistics for scoring line t."""
+def statistics_lines(t: int, mode: str, cube_lines: int, n_lines: int, every: int = 1) -> tuple[int, int]:
+    """Half-open line range [a, b) whose pixels form the statistics for scoring line t.
+
+    ``every`` (EXCLUSIVE only) is the factorisation cadence: the statistics are taken only
+    every ``every`` lines after the reset r, so line t uses the last such snapshot,
+    [r, r + every * floor((t - r) / every)); every = 1 is [r, t)."""
     r = (t // cube_lines) * cube_lines if cube_lines > 0 else 0
+    if every < 1 or (every > 1 and mode != EXCLUSIVE):
+        raise ValueError("a cadence needs EXCLUSIVE statistics and every >= 1")
     if mode == EXCLUSIVE:
-        return r, t
+        return r, r + every * ((t - r) // every)
     if mode == INCLUSIVE:
         return r, t + 1
     if mode == CUBE:
@@ -189,7 +198,7 @@ def _stats_over_lines(lines: LineSource, a: int, b: int, gain, offset, chunk: in
 
 def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines: int = 0,
                    warmup_pixels: int = 0, gain=None, offset=None, n_lines: int | None = None,
-                   chunk: int = 64):
+                   chunk: int = 64, every: int = 1):
     """Scores of line t under the given statistics window.
 
     Returns ``(delta [W], status)`` with status OK, NOT_READY (too few pixels;
@@ -199,7 +208,7 @@ def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines:
     W, B = line.shape
     if n_lines is None:
         n_lines = (t + 1) if callable(lines) else lines.shape[0]
-    a, b = statistics_lines(t, mode, cube_lines, n_lines)
+    a, b = statistics_lines(t, mode, cube_lines, n_lines, every)
     n_pix = (b - a) * W
     if n_pix < max(B + 1, int(warmup_pixels)):
         return np.full(W, np.nan), NOT_READY
@@ -211,14 +220,14 @@ def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines:
 
 
 def stream_rx(lines: np.ndarray, mode: str = EXCLUSIVE, cube_lines: int = 0, warmup_pixels: int = 0,
-              gain=None, offset=None):
+              gain=None, offset=None, every: int = 1):
     """Scores of every line of ``lines`` [T, W, B]: ``(delta [T, W], status [T])``."""
     T, W, B = lines.shape
     delta = np.full((T, W), np.nan)
     status = np.zeros(T, dtype=np.int32)
     for t in range(T):
         delta[t], status[t] = stream_rx_line(lines, t, mode, cube_lines, warmup_pixels,
-                                             gain, offset, n_lines=T)
+                                             gain, offset, n_lines=T, every=every)
     return delta, status
 
 

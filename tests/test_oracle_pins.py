@@ -356,3 +356,28 @@ def test_frontend_band_discard_and_binning():
     assert (oracle.frontend(raw, 0, 1, 12) == raw).all()
     with pytest.raises(ValueError):
         oracle.frontend(raw, 5, 4, 2)
+
+
+# ------------------------------------------------------------------ factorisation cadence (extension)
+def test_cadence_window_and_scores():
+    rng = np.random.default_rng(12)
+    T, W, B = 11, 6, 3
+    lines = rng.normal(size=(T, W, B)) @ np.diag([1.0, 2.0, 0.5]) + 10.0
+    k = 3
+    d1, s1 = orx.stream_rx(lines, oracle.EXCLUSIVE)
+    dk, sk = orx.stream_rx(lines, oracle.EXCLUSIVE, every=k)
+    for t in range(T):
+        snap = k * (t // k)              # the last multiple of k lines: the statistics of lines [0, snap)
+        if snap * W < B + 1:
+            assert sk[t] == orx.NOT_READY and np.isnan(dk[t]).all()
+            continue
+        X = lines[:snap].reshape(-1, B)
+        mu = X.mean(axis=0)
+        D = X - mu
+        Sigma = D.T @ D / (X.shape[0] - 1)
+        ref = np.einsum("pi,ij,pj->p", lines[t] - mu, np.linalg.inv(Sigma), lines[t] - mu)
+        np.testing.assert_allclose(dk[t], ref, rtol=1e-10)
+        if t % k == 0:                   # at a snapshot line the cadence changes nothing
+            np.testing.assert_array_equal(dk[t], d1[t])
+    with pytest.raises(ValueError):
+        orx.statistics_lines(4, oracle.INCLUSIVE, 0, 10, every=2)
