@@ -446,6 +446,9 @@ def main():
     ap.add_argument("--cube", default="", help="stress workload: one cube 'lines,width,bands' instead")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--batch", type=int, default=0, help="lines per internal batch (0 = workload default)")
+    ap.add_argument("--factor-every", type=int, default=0,
+                    help="factorisation cadence in lines (an extension: statistics up to k-1 lines old); "
+                         "0 = every line, the paper's detector")
     ap.add_argument("--lines", type=int, default=0, help="override the stream length (profiling captures)")
     ap.add_argument("--latency-lines", type=int, default=200)
     ap.add_argument("--skip-cpu", action="store_true")
@@ -494,7 +497,7 @@ def main():
         return hs.Detector(width=W, bands=B, stats_mode="exclusive", precision=prec, gain=sc.gain,
                            offset=sc.offset, max_batch_lines=wl["batch"], result_lines=T, device=local,
                            raw_bands=wl.get("raw_bands", 0), band_first=wl.get("band_first", 0),
-                           band_bin=wl.get("band_bin", 1))
+                           band_bin=wl.get("band_bin", 1), factor_every=args.factor_every)
 
     def step(det, host=False):
         det.reset()
@@ -629,7 +632,8 @@ def main():
         launches_per_step = n / prof_steps
         if dom == "factor":
             lines_per_launch = T / launches_per_step
-            work = lines_per_launch * factor_flops_per_line(B, form)
+            # with a cadence only every k-th line's statistics are factored
+            work = lines_per_launch / max(1, args.factor_every) * factor_flops_per_line(B, form)
             ach = work / (avg_ms / 1e3) / 1e12
             pk = fp64_peak_tflops(mhz)
             key = (B, form)
@@ -667,6 +671,7 @@ def main():
         "config": {"workload": args.workload, "width": W, "bands": B, "lines": T, "stats": "exclusive",
                    "input": "uint16 12-bit DN", "batch_lines": wl["batch"],
                    "whitening": "triangular solve" if form else "explicit inverse",
+                   **({"factor_every": args.factor_every} if args.factor_every > 1 else {}),
                    **({"front_end": {"raw_bands": wl["raw_bands"], "band_first": wl["band_first"],
                                      "band_bin": wl["band_bin"]}} if wl.get("raw_bands") else {}),
                    "parallelism": f"replicas x{world} (independent streams)" if world > 1 else "single stream",

@@ -111,6 +111,12 @@ typedef struct {
   int32_t raw_bands;
   int32_t band_first;
   int32_t band_bin;
+  /* Factorisation cadence (an extension; the paper does not define one): 0 or 1 (default)
+   * scores every line with the statistics of all lines before it; k in [2, 64] (EXCLUSIVE
+   * only) takes the statistics every k lines after a reset and scores line t against the
+   * last such snapshot, lines [r, r + k floor((t - r) / k)): k times fewer factorisations,
+   * with statistics up to k - 1 lines old. */
+  int32_t factor_every;
 } hsad_config;
 
 /* Fill *cfg with defaults: U16, FP32, EXCLUSIVE, cube_lines 0, ABS threshold

@@ -113,6 +113,7 @@ struct hsad_ctx {
   void* d_bin[2] = {nullptr, nullptr};
   int fe_idx = 0;
   int64_t syrk_max_pix = 4096;  // pixels one exact SYRK accumulation may hold
+  int every = 1;                // factorisation cadence in lines (EXCLUSIVE)
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   // pinned caller buffers are copied straight to d_stage on h2d_stream: copy_ev marks the
   // copy done, free_ev the end of the last batch that read d_stage[i]
@@ -292,6 +293,8 @@ int validate(const hsad_config* cfg, std::string* why) {
     for (int b = 0; b < cfg->bands; ++b)
       if (!std::isfinite(cfg->offset[b])) return bad("offset must be finite");
   if ((int64_t)cfg->width * cfg->bands > (int64_t)1 << 31) return bad("line too large");
+  if (cfg->factor_every < 0 || cfg->factor_every > 64) return bad("factor_every must be in [0, 64]");
+  if (cfg->factor_every > 1 && cfg->stats_mode != HSAD_EXCLUSIVE) return bad("factor_every > 1 needs EXCLUSIVE mode");
   if (cfg->raw_bands < 0) return bad("raw_bands must be >= 0");
   if (cfg->raw_bands > 0) {
     if (cfg->in_dtype != HSAD_U16) return bad("the front end (raw_bands > 0) needs HSAD_U16 input");
@@ -497,6 +500,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->line_elems = (int64_t)ctx->W * ctx->B;
   ctx->line_bytes = ctx->line_elems * ctx->elem;
   ctx->fe = cfg->raw_bands > 0;
+  ctx->every = cfg->factor_every > 1 ? cfg->factor_every : 1;
   ctx->raw_line_bytes = ctx->fe ? (int64_t)ctx->W * cfg->raw_bands * 2 : ctx->line_bytes;
   // sums of bin 12-bit DN: |x'| < 2^(12 + ceil(log2 bin)); an exact accumulation holds
   // 2^24 / (|x'| / 64)^2 pixels: 4096 (bin 1), 1024 (bin 2), 256 (bin 3, 4)
@@ -723,6 +727,9 @@ int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* ou
 // read from ctx->bdesc at run time, so that the launches can be captured once and replayed.
 int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   const int W = ctx->W, B = ctx->B, Bp = ctx->Bp;
+  // cadence phase of the batch's first line: slot j (statistics through line first + j - 1)
+  // is a snapshot iff (q0 + j) % every == 0
+  const int q0 = (int)((ctx->n_stats / W) % ctx->every);
   const int64_t BB = (int64_t)B * B;
   cudaStream_t st = ctx->stream;
   const int64_t* n0_dev = dev ? ctx->bdesc : nullptr;
@@ -737,20 +744,27 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc));
   KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, ctx->dgain, L, B, ctx->prec,
                              (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
-                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev));
+                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev, ctx->every, q0 + 1));
   if (L > 1) {
     ScoreOut o1 = score_out(ctx, first + 1, true);
     o1.factor_base = 1;
+    o1.every = ctx->every;
+    o1.q0 = q0;
     if (dev) o1.slot0_dev = ctx->bdesc + 1;
     int rc = whiten(ctx, (const char*)x + ctx->line_bytes, L - 1, 1, o1);
     if (rc != HSAD_OK) return rc;
   }
-  // carry the factor of all statistics so far to slot 0
-  const size_t wb = (size_t)Bp * Bp * 4;
-  CK(cudaMemcpyAsync(ctx->wmat, (char*)ctx->wmat + (size_t)L * wb, wb, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ctx->y0, ctx->y0 + (size_t)L * Bp, (size_t)Bp * 4, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ctx->inv_s2, ctx->inv_s2 + L, 4, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ctx->status, ctx->status + L, 4, cudaMemcpyDeviceToDevice, st));
+  // carry the factor of the last snapshot to slot 0 (every line: slot L, the statistics of all
+  // lines so far; with a cadence the last snapshot slot of the batch, or slot 0 unchanged if
+  // the batch holds none)
+  const int c = L - (q0 + L) % ctx->every;
+  if (c > 0) {
+    const size_t wb = (size_t)Bp * Bp * 4;
+    CK(cudaMemcpyAsync(ctx->wmat, (char*)ctx->wmat + (size_t)c * wb, wb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->y0, ctx->y0 + (size_t)c * Bp, (size_t)Bp * 4, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->inv_s2, ctx->inv_s2 + c, 4, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->status, ctx->status + c, 4, cudaMemcpyDeviceToDevice, st));
+  }
   return HSAD_OK;
 }
 
@@ -759,7 +773,9 @@ constexpr int kGraphMaxLines = 8;
 // The replayable graph of excl_tail for (L, staging buffer s), captured on first use.
 // Returns nullptr if capture or instantiation fails (the caller then launches directly).
 hsad_ctx::GraphEntry* excl_graph(hsad_ctx* ctx, const void* x, int L, int s, uint64_t first) {
-  auto key = std::make_pair(L, s);
+  // the cadence phase fixes which slots are factored and carried: part of the key
+  const int q0 = (int)((ctx->n_stats / ctx->W) % ctx->every);
+  auto key = std::make_pair(L, s + 2 * q0);
   auto it = ctx->graphs.find(key);
   if (it != ctx->graphs.end()) return it->second.exec ? &it->second : nullptr;
   hsad_ctx::GraphEntry ge;
@@ -1291,6 +1307,8 @@ int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const d
   if (ctx->failed) return HSAD_E_CUDA;
   if (ctx->mode == HSAD_CUBE) return fail(ctx, HSAD_E_INVALID, "statistics import is for stream modes");
   if (!shift || !s1 || !s2 || n_pixels < 0) return fail(ctx, HSAD_E_INVALID, "NULL array or negative n_pixels");
+  if (ctx->every > 1 && (n_pixels % ctx->W != 0 || (n_pixels / ctx->W) % ctx->every != 0))
+    return fail(ctx, HSAD_E_INVALID, "with a factorisation cadence the import must be at a snapshot (lines a multiple of it)");
   if (ctx->next_line != 0 || ctx->n_stats != 0)
     return fail(ctx, HSAD_E_INVALID, "import needs a context with no line pushed since creation or reset");
   const int B = ctx->B;

@@ -95,7 +95,7 @@ cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, 
 cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m, const double* dgain,
                                 int L, int B, int prec, void* wmat, float* y0, float* inv_s2, int32_t* status,
                                 int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
-                                const int64_t* n0_dev);
+                                const int64_t* n0_dev, int every = 1, int q_off = 0);
 // Measure the launch shapes for batch-size buckets 1, 2, 4, ..., max_lines and keep the
 // fastest per bucket for launch_factor (current device). report: rows of (bucket, cl, ft,
 // ms), up to cap rows. Returns the number of buckets or a negative value on failure.
@@ -107,10 +107,12 @@ int factor_wave_lines(int B, int prec);
 // factor kernel can run at once (host calls that must not land on a line's latency path).
 void factor_prepare(int B, int prec);
 // n0_dev: if set, n0 is read there at run time (replayed CUDA graphs).
+// every > 1: only lines t with (q_off + t) % every == 0 are factored (a cadence); the others
+// are left untouched.
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
                           int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
-                          const int64_t* n0_dev = nullptr);
+                          const int64_t* n0_dev = nullptr, int every = 1, int q_off = 0);
 
 // K6 (SIMT): delta_p = inv_s2 * || G (x_p - c) - y0 ||^2 for every pixel of every line,
 // threshold, and scatter into the result ring. factor_stride = 0 makes every line
@@ -125,9 +127,21 @@ struct ScoreOut {
   int write_mask;    // 1: mask = delta > tau here; 0: left to the cube normaliser
   int factor_base = 0;  // factor slot of line 0 (slots advance with factor_stride)
   const int64_t* slot0_dev = nullptr;  // if set, slot0 is read here (replayed CUDA graphs)
+  // factorisation cadence: only slots j with (q0 + j) % every == 0 hold a factor; a line
+  // whose own slot j does not uses the last such slot at or below j (slot 0 if none)
+  int every = 1;
+  int q0 = 0;
 };
 #ifdef __CUDACC__
 __device__ __forceinline__ int64_t slot0_of(const ScoreOut& o) { return o.slot0_dev ? *o.slot0_dev : o.slot0; }
+// Factor slot of line t of a whitening launch.
+__device__ __forceinline__ int factor_slot(const ScoreOut& o, int factor_stride, int t) {
+  if (!factor_stride) return o.factor_base;
+  const int j = o.factor_base + t;
+  if (o.every <= 1) return j;
+  const int s = j - (o.q0 + j) % o.every;
+  return s > 0 ? s : 0;
+}
 #endif
 cudaError_t launch_whiten_score_simt(const void* x, int L, int W, int B, int in_type,
                                      const int32_t* c_int, const float* c_flt, int prec,

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) whiten_score_kernel(
   __shared__ __align__(16) float Bs[2][2][WS_K][WS_N + 4];
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * WS_P;
-  const int f = out.factor_base + (factor_stride ? t : 0);
+  const int f = factor_slot(out, factor_stride, t);
   const int64_t slot = (slot0_of(out) + t) % out.ring;
   const int st = status[f];
   if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) whiten_fp32_kernel(
   __shared__ __align__(16) float Bs[2][WF_K][WF_N + 4];
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * WF_P;
-  const int f = out.factor_base + (factor_stride ? t : 0);
+  const int f = factor_slot(out, factor_stride, t);
   const int64_t slot = (slot0_of(out) + t) % out.ring;
   const int st = status[f];
   if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
     int32_t* __restrict__ err, long long limit, int stages, int raw_tile) {
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * WT_M;
-  const int f = out.factor_base + (factor_stride ? t : 0);
+  const int f = factor_slot(out, factor_stride, t);
   const int64_t slot = (slot0_of(out) + t) % out.ring;
   const int st = status[f];
   if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;

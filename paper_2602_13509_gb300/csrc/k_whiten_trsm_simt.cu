@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(TF_THREADS) whiten_trsm_simt_kernel(
   __shared__ __align__(16) float Hs[2][TF_K][TF_N + 4];
   const int t = blockIdx.y;
   const int p0 = blockIdx.x * TF_P;
-  const int f = out.factor_base + (factor_stride ? t : 0);
+  const int f = factor_slot(out, factor_stride, t);
   const int64_t slot = (slot0_of(out) + t) % out.ring;
   const int st = status[f];
   if (blockIdx.x == 0 && threadIdx.x == 0) out.ring_status[slot] = st;

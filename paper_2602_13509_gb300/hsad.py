@@ -40,6 +40,7 @@ class hsad_config(C.Structure):
         ("flags", C.c_int32), ("device", C.c_int32),
         ("max_batch_lines", C.c_int32), ("result_lines", C.c_int32),
         ("raw_bands", C.c_int32), ("band_first", C.c_int32), ("band_bin", C.c_int32),
+        ("factor_every", C.c_int32),
     ]
 
 
@@ -351,7 +352,7 @@ _NAMES = {
 def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="exclusive", cube_lines=0,
                 gain=None, offset=None, threshold_mode="abs", threshold=0.0, warmup_pixels=0,
                 device_budget_bytes=0, flags=0, device=0, max_batch_lines=0, result_lines=0,
-                raw_bands=0, band_first=0, band_bin=1):
+                raw_bands=0, band_first=0, band_bin=1, factor_every=0):
     """Build an hsad_config; ``gain``/``offset`` arrays are kept alive on the struct."""
     import numpy as np
     cfg = hsad_config_init()
@@ -366,6 +367,7 @@ def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="excl
     cfg.flags, cfg.device = int(flags), int(device)
     cfg.max_batch_lines, cfg.result_lines = int(max_batch_lines), int(result_lines)
     cfg.raw_bands, cfg.band_first, cfg.band_bin = int(raw_bands), int(band_first), int(band_bin)
+    cfg.factor_every = int(factor_every)
     keep = []
     for name, arr in (("gain", gain), ("offset", offset)):
         if arr is not None:

@@ -37,7 +37,7 @@ def test_config_defaults_and_struct_size(hs):
     cfg = hs.hsad_config_init()
     assert cfg.in_dtype == hs.HSAD_U16 and cfg.precision == hs.HSAD_FP32
     assert cfg.stats_mode == hs.HSAD_EXCLUSIVE and cfg.threshold_mode == hs.HSAD_ABS
-    assert C.sizeof(hs.hsad_config) == 96  # 80 + the three front-end fields, padded to 8
+    assert C.sizeof(hs.hsad_config) == 96  # 80 + the front-end and cadence fields
     assert cfg.raw_bands == 0 and cfg.band_first == 0 and cfg.band_bin == 0   # front end off
 
 
@@ -109,3 +109,9 @@ def test_create_rejects_bad_front_end(hs):
     assert r == hs.HSAD_E_INVALID and "raw_bands" in why
     r, why = rc(raw_bands=40, band_bin=4, in_dtype="f32")
     assert r == hs.HSAD_E_INVALID and "U16" in why
+
+
+def test_create_rejects_bad_cadence(hs):
+    for kw in (dict(factor_every=-1), dict(factor_every=65), dict(factor_every=2, stats_mode="inclusive")):
+        r, ctx = hs.hsad_create(hs.make_config(16, 8, **kw))
+        assert r == hs.HSAD_E_INVALID and "factor_every" in hs.hsad_last_error(None)
