@@ -165,7 +165,9 @@ int hsad_engine_open(hsad_engine* e, const hsad_config* cfg, int32_t* stream_id)
   if (rc != HSAD_OK) return rc;
   auto s = std::make_shared<EStream>();
   s->ctx = ctx;
-  s->line_bytes = (int64_t)cfg->width * cfg->bands * (cfg->in_dtype == HSAD_U16 ? 2 : 4);
+  // bytes of one submitted line: raw lines when the stream has the front end
+  s->line_bytes = (int64_t)cfg->width * (cfg->raw_bands > 0 ? cfg->raw_bands : cfg->bands) *
+                  (cfg->in_dtype == HSAD_U16 ? 2 : 4);
   s->max_batch = cfg->max_batch_lines > 0 ? cfg->max_batch_lines : 256;
   std::lock_guard<std::mutex> g(e->mu);
   e->streams.push_back(s);

@@ -133,3 +133,47 @@ def test_stream_closed_mid_flight_leaves_the_others_intact(hs):
     assert hs.hsad_destroy(det.ctx) == hs.HSAD_OK
     det.ctx = None
     assert hs.hsad_device_budget_used(0) == gc_base
+
+
+def test_front_end_and_cadence_streams_in_the_mix(hs):
+    """A front-end stream (raw 120-band lines binned to 28) and a cadence stream (k = 3) run
+    beside a plain one; each gives the results of the same configuration alone."""
+    from gen import PushbroomScene
+    T = 30
+    raw = PushbroomScene(72, 120, seed=61).lines(0, T)
+    sc2 = PushbroomScene(80, 32, seed=62)
+    plain = sc2.lines(0, T)
+    kws = [dict(width=72, bands=28, raw_bands=120, band_first=4, band_bin=4),
+           dict(width=80, bands=32, factor_every=3, gain=sc2.gain, offset=sc2.offset),
+           dict(width=80, bands=32, precision="bf16", gain=sc2.gain, offset=sc2.offset)]
+    inputs = [raw, plain, plain]
+    rc, eng = hs.hsad_engine_create(0, 0)
+    assert rc == hs.HSAD_OK
+    sids = []
+    for kw in kws:
+        rc, sid = hs.hsad_engine_open(eng, hs.make_config(max_batch_lines=8, **kw))
+        assert rc == hs.HSAD_OK, hs.hsad_status_string(rc)
+        sids.append(sid)
+    rng = np.random.default_rng(3)
+    pos = [0] * 3
+    while any(p < T for p in pos):
+        k = int(rng.integers(0, 3))
+        if pos[k] >= T:
+            continue
+        n = int(min(T - pos[k], rng.integers(1, 5)))
+        rc, first = hs.hsad_engine_submit(eng, sids[k], np.ascontiguousarray(inputs[k][pos[k]:pos[k] + n]), n)
+        assert rc == hs.HSAD_OK and first == pos[k]
+        pos[k] += n
+    for k, kw in enumerate(kws):
+        W = kw["width"]
+        s = np.empty((T, W), np.float32)
+        m = np.empty((T, W), np.uint8)
+        rc = hs.hsad_engine_results(eng, sids[k], 0, T, s, m, 20000)
+        assert rc in (hs.HSAD_OK, hs.HSAD_E_NOT_READY), hs.hsad_status_string(rc)
+        det = hs.Detector(**kw)
+        first = det.push(inputs[k])
+        _, s0, m0, _ = det.scores(first, T)
+        det.close()
+        np.testing.assert_array_equal(np.nan_to_num(s, nan=-1.0), np.nan_to_num(s0, nan=-1.0))
+        np.testing.assert_array_equal(m, m0)
+    assert hs.hsad_engine_destroy(eng) == hs.HSAD_OK
