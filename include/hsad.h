@@ -49,16 +49,17 @@ typedef enum {
 /* input element type */
 enum { HSAD_U16 = 0, HSAD_F32 = 1 };
 /* working precision of the whitening contraction (the covariance sums are exact
- * for HSAD_U16 input in every mode; the Cholesky factorisation and the triangular
- * inverses are always FP64) */
+ * for HSAD_U16 input in every mode; the covariance, the Cholesky pivots and panel solves
+ * are FP64 and the O(B^3) factor updates float-float, about 48 significant bits, in every
+ * precision) */
 enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
 /* whitening form of a context (Eq. 1, Sec. 3.3), see hsad_whitening_form:
- * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1} D, the full triangular
+ * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1}, the full triangular
  *                              inverse: CUBE mode (one factorisation per cube, where the
  *                              whitening dominates), FP16, BF16 with float input;
  * HSAD_FORM_TRIANGULAR_SOLVE   streamed statistics (EXCLUSIVE, INCLUSIVE: a factorisation
  *                              per line): L y = x' - m solved blockwise from L and the
- *                              inverses of its 64 x 64 diagonal blocks only, half the FP64
+ *                              inverses of its 64 x 64 diagonal blocks only, half the
  *                              factor work; on the tensor cores for BF16 (uint16 input), on
  *                              the SIMT cores for FP32. */
 enum { HSAD_FORM_INVERSE = 0, HSAD_FORM_TRIANGULAR_SOLVE = 1 };

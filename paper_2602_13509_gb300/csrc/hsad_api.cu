@@ -78,7 +78,6 @@ struct hsad_ctx {
   // device state
   int32_t* c_int = nullptr;
   float* c_flt = nullptr;
-  double* dgain = nullptr;
   double* state_s1 = nullptr;
   double* state_s2 = nullptr;
   // per-batch workspace
@@ -255,7 +254,7 @@ int64_t plan_bytes(const hsad_ctx* c) {
   const int64_t Lf = (c->mode == HSAD_CUBE) ? 1 : (c->mode == HSAD_EXCLUSIVE ? L + 1 : L);
   const int64_t Ls = (c->mode == HSAD_CUBE) ? c->cfg.cube_lines : L;  // lines per batch
   int64_t b = 0;
-  b += B * 4 + B * 4 + B * 8 + B * 8 + B * B * 8;                // c, dgain, S1, S2
+  b += B * 4 + B * 4 + B * 8 + B * B * 8;                        // c (int, float), S1, S2
   b += Ls * B * 8 * 2;                                           // s1_line, m_line
   b += Lf * B * B * 8 * 2;                                       // sigma, inv
   b += Lf * Bp * Bp * 4 + Lf * Bp * 4 + Lf * 4 + Ls * 4;        // wmat, y0, inv_s2, status
@@ -563,7 +562,6 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   const int64_t Ls = ctx->mode == HSAD_CUBE ? cfg->cube_lines : L;
   ctx->c_int = (int32_t*)dalloc(ctx, B * 4, &ok);
   ctx->c_flt = (float*)dalloc(ctx, B * 4, &ok);
-  ctx->dgain = (double*)dalloc(ctx, B * 8, &ok);
   ctx->state_s1 = (double*)dalloc(ctx, B * 8, &ok);
   ctx->state_s2 = (double*)dalloc(ctx, B * B * 8, &ok);
   ctx->s1_line = (double*)dalloc(ctx, Ls * B * 8, &ok);
@@ -616,12 +614,9 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     release(ctx);
     return fail(nullptr, HSAD_E_NOMEM, "device allocation failed");
   }
-  // calibration gain as FP64 (the offset cancels in the centring)
-  std::vector<double> g(B, 1.0);
-  if (cfg->gain)
-    for (int b = 0; b < B; ++b) g[b] = (double)cfg->gain[b];
-  if (cudaMemcpy(ctx->dgain, g.data(), B * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemsetAsync(ctx->state_s1, 0, B * 8, ctx->stream) != cudaSuccess ||
+  // the calibration gain and offset cancel from Eq. 1 (RX is invariant under a per-band
+  // affine map): validated above, not needed on the device
+  if (cudaMemsetAsync(ctx->state_s1, 0, B * 8, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->state_s2, 0, B * B * 8, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->r_status, 0xff, ctx->ring * 4, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->dmax_bits, 0, 64, ctx->stream) != cudaSuccess ||
@@ -742,7 +737,7 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, 1,
                                        ctx->min_pix, ctx->status + 1, st, &ctx->lc, n0_dev));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc));
-  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, ctx->dgain, L, B, ctx->prec,
+  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L, B, ctx->prec,
                              (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
                              ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev, ctx->every, q0 + 1));
   if (L > 1) {
@@ -858,7 +853,7 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, incl,
                         ctx->min_pix, ctx->status, st, &ctx->lc));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc));
-  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, L, B, ctx->prec, ctx->wmat, ctx->y0,
+  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, L, B, ctx->prec, ctx->wmat, ctx->y0,
                    ctx->inv_s2, ctx->status, ctx->n_stats, W, incl, st, &ctx->lc));
   {
     int rc = whiten(ctx, x, L, 1, score_out(ctx, first, true));
@@ -884,9 +879,9 @@ int cube_score(hsad_ctx* ctx, const void* x, int64_t n) {
     int rc = syrk(ctx, x, 1, N, ctx->state_s2, 0, true);
     if (rc != HSAD_OK) return rc;
   }
-  KL("finalize_cov", launch_finalize_cov(ctx->state_s1, ctx->state_s2, ctx->dgain, N, B, ctx->sigma, ctx->m_line,
+  KL("finalize_cov", launch_finalize_cov(ctx->state_s1, ctx->state_s2, N, B, ctx->sigma, ctx->m_line,
                          ctx->min_pix, ctx->status, st, &ctx->lc));
-  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, 1, B, ctx->prec, ctx->wmat, ctx->y0,
+  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, 1, B, ctx->prec, ctx->wmat, ctx->y0,
                    ctx->inv_s2, ctx->status, N, 0, 0, st, &ctx->lc));
   const bool rel = ctx->cfg.threshold_mode == HSAD_REL;
   const bool norm = (ctx->cfg.flags & HSAD_NORMALIZE_SCORES) != 0;
@@ -1342,7 +1337,7 @@ int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const d
     CK(cudaMemcpyAsync(ctx->sigma, s2, (size_t)B * B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->m_line, m.data(), (size_t)B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->status, &st0, 4, cudaMemcpyHostToDevice, st));
-    KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, ctx->dgain, 1, B, ctx->prec, ctx->wmat, ctx->y0,
+    KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, 1, B, ctx->prec, ctx->wmat, ctx->y0,
                                ctx->inv_s2, ctx->status, n_pixels, 0, 0, st, &ctx->lc));
     CK(cudaStreamSynchronize(st));  // the host vectors above are copied before they go out of scope
   } else {

@@ -5,7 +5,8 @@
 //   shift c         [B]         int32 (u16 input: integer DN) or float (f32 input)
 //   per-line sums   [L][B]      double   s1_t = sum_p (x_p - c)
 //   per-line SYRK   [L][B][B]   double   s2_t = sum_p (x_p - c)(x_p - c)^T, then Sigma_t in place
-//   factor          [L][Bp][Bp] whitening operand G_t = s_t L_t^{-1} D, row n = output coordinate
+//   factor          [L][Bp][Bp] whitening operand G_t = s_t L_t^{-1} (S_t = L_t L_t^T, the DN-frame
+//                               covariance), row n = output coordinate
 //                               (FP32: float; FP16/BF16: hi plane then lo plane, 16-bit)
 //   y0              [L][Bp]     float   s_t G_t (mu_t - c)
 //   inv_s2          [L]         float   1 / s_t^2 (s_t: power-of-two scale of G_t)
@@ -82,17 +83,18 @@ cudaError_t launch_frontend(const uint16_t* raw, int64_t n_px, int raw_bands, in
 
 // K3c (cube): raw sums S2 (lower triangle) copied from the state into sigma and
 // m = S1 / N; status[0] becomes LS_OK or LS_NOT_READY (fewer than min_pixels pixels).
-cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, const double* dgain,
-                                int64_t n, int B, double* sigma, double* m, int64_t min_pixels,
-                                int32_t* status, cudaStream_t st, LaunchCounter* lc);
+cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, int64_t n, int B, double* sigma,
+                                double* m, int64_t min_pixels, int32_t* status, cudaStream_t st, LaunchCounter* lc);
 
 // K4+K5: from each ready line's raw sums (lower triangle of sigma[t]) and mean offset
-// m[t]: Sigma_t = D (S2_t - n_t m_t m_t^T) D / (n_t - 1) with n_t = n0 + (t + incl) W,
-// FP64 Cholesky and triangular inverse in place, then G_t = s_t L^{-1} D cast to the
-// working precision, y0 and 1/s_t^2. scratch: [L][B][B] FP64.
+// m[t]: the DN-frame covariance S_t = (S2_t - n_t m_t m_t^T) / (n_t - 1) with
+// n_t = n0 + (t + incl) W (the calibration gains cancel from Eq. 1), Cholesky with FP64
+// pivots and panel solves and float-float trailing updates, and the triangular inverse,
+// in place (sigma and scratch then hold float-float pairs), then the whitening operand in
+// the working precision, y0 and 1/s_t^2. scratch: [L][B][B] 8-byte slots.
 // The factor kernel with a given launch shape: cl CTAs per line (1, 2, 4, 8, 16) and, for
 // cl = 1, ft threads per CTA (128 or 256).
-cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m, const double* dgain,
+cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m,
                                 int L, int B, int prec, void* wmat, float* y0, float* inv_s2, int32_t* status,
                                 int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
                                 const int64_t* n0_dev, int every = 1, int q_off = 0);
@@ -109,7 +111,7 @@ void factor_prepare(int B, int prec);
 // n0_dev: if set, n0 is read there at run time (replayed CUDA graphs).
 // every > 1: only lines t with (q_off + t) % every == 0 are factored (a cadence); the others
 // are left untouched.
-cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
+cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
                           int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
                           const int64_t* n0_dev = nullptr, int every = 1, int q_off = 0);

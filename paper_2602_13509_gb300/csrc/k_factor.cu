@@ -1,10 +1,15 @@
-// K4 + K5: FP64 Cholesky factorisation and triangular inverse of each line's
-// covariance, and the whitening operand in the working precision.
+// K4 + K5: Cholesky factorisation and triangular inverse of each line's covariance, and
+// the whitening operand in the working precision.
 //
-// Eq. 1 (Sec. 3.3) needs Sigma^{-1}. With Sigma = L L^T (Cholesky, FP64) the score is
-// delta = || L^{-1} (x - mu) ||^2. In the DN frame used by the statistics kernels the
-// calibrated deviation is x - mu = D (x' - m), with x' = DN - c and m = mu_DN - c, so
-//     y = G x' - G m,   G = L^{-1} D,   delta = || y ||^2.
+// Eq. 1 (Sec. 3.3) needs Sigma^{-1}. In the DN frame used by the statistics kernels the
+// calibrated deviation is x - mu = D (x' - m), with x' = DN - c, m = mu_DN - c and D the
+// per-band calibration gains, and Sigma = D S D with S the DN-frame covariance, so
+//     delta = (x' - m)^T S^{-1} (x' - m) = || L^{-1} (x' - m) ||^2,   S = L L^T:
+// the gains cancel and the factor works on S alone. Arithmetic: the covariance is formed
+// in FP64; the pivots, the 16 x 16 diagonal blocks and the panel solves run in FP64; the
+// two O(B^3) register-tiled updates (Cholesky trailing update, inverse block rows) run in
+// float-float (pairs of FP32 values, about 48 significant bits), as FP64 issues at 1/64
+// of the FP32 rate here. With G = L^{-1} the score is delta = || G x' - G m ||^2.
 // G is lower triangular. It is stored row-major ([n][k], n = output coordinate) as the
 // K-major operand of the whitening contraction, scaled by a power of two s so that
 // max |s G| is in [0.5, 1) (keeps FP16 in range; exact in every format), and
@@ -123,11 +128,6 @@ __device__ __forceinline__ void csync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
   }
 }
-// Global loads of data other CTAs of the cluster may have written: through L2.
-template <int CL>
-__device__ __forceinline__ double ldg_c(const double* p) {
-  return CL == 1 ? *p : __ldcg(p);
-}
 // A double in the shared memory of CTA `rank` of this cluster.
 __device__ __forceinline__ double ld_remote(const double* local, int rank) {
   uint32_t laddr = (uint32_t)__cvta_generic_to_shared(local), raddr;
@@ -137,11 +137,49 @@ __device__ __forceinline__ double ld_remote(const double* local, int rank) {
   return v;
 }
 
+// The O(B^3) updates run in float-float arithmetic: a value is an unevaluated pair
+// hi + lo of FP32 numbers (about 48 significant bits; FP32's exponent range), stored as a
+// float2 in the 8 bytes of a double. FP64 issues at 1/64 of the FP32 rate on this part,
+// while one float-float multiply-subtract costs 12 FP32 operations. Pivots, the panel
+// solves and everything outside the two register-tiled updates stay in FP64.
+__device__ __forceinline__ double ff_to_d(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ float2 d_to_ff(double d) {
+  const float h = __double2float_rn(d);
+  return make_float2(h, __double2float_rn(d - (double)h));  // d - h is exact in FP64
+}
+// Global loads of data other CTAs of the cluster may have written: through L2.
+template <int CL>
+__device__ __forceinline__ float2 ldg_c2(const float2* p) {
+  return CL == 1 ? *p : __ldcg(p);
+}
+// s + c -= x y: the product's rounding error from an FMA (Dekker's two-product, with the
+// hi x lo cross terms; lo x lo is below the format's precision), the sum's rounding error
+// from Knuth's two-sum, both errors gathered in c (compensated dot product, Ogita, Rump
+// and Oishi 2005). Explicitly rounded operations: the compiler may not fuse or reorder.
+__device__ __forceinline__ void ff_fms(float& s, float& c, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  const float t = __fsub_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(-p, z));
+  s = t;
+  c = __fsub_rn(__fadd_rn(c, q), e);
+}
+// The pair renormalised (two-sum: c may exceed s after cancellation).
+__device__ __forceinline__ float2 ff_norm(float s, float c) {
+  const float h = __fadd_rn(s, c);
+  const float z = __fsub_rn(h, s);
+  return make_float2(h, __fadd_rn(__fsub_rn(s, __fsub_rn(h, z)), __fsub_rn(c, z)));
+}
+
 // Trailing update of panel p: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B,
 // in TS x TS register tiles over the lower triangle (same operations per element for any
-// TS). The panel P (rows p.., kb columns) is in shared memory.
+// TS). A and the panel rows below its diagonal block (P, rows p.., kb columns, in shared
+// memory) are float-float.
 template <int CL, int TS>
-__device__ __forceinline__ void trailing_update(double* A, const double* P, int B, int p, int kb, int rows, int gtid,
+__device__ __forceinline__ void trailing_update(float2* A, const float2* P, int B, int p, int kb, int rows, int gtid,
                                                 int gthreads) {
   const int mt = (rows - kb + TS - 1) / TS;
   const int ntiles = mt * (mt + 1) / 2;
@@ -151,67 +189,75 @@ __device__ __forceinline__ void trailing_update(double* A, const double* P, int 
     while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
     const int tk = idx - ti * (ti + 1) / 2;
     const int r0 = kb + TS * ti, c0 = kb + TS * tk;  // panel-relative
-    double acc[TS][TS];
+    float s[TS][TS], c[TS][TS];
 #pragma unroll
     for (int a = 0; a < TS; ++a)
 #pragma unroll
       for (int b = 0; b < TS; ++b) {
-        const int r = r0 + a, c = c0 + b;
-        acc[a][b] = (r < rows && c <= r) ? ldg_c<CL>(A + (int64_t)(p + r) * B + p + c) : 0.0;
+        const int r = r0 + a, cc = c0 + b;
+        const float2 v =
+            (r < rows && cc <= r) ? ldg_c2<CL>(A + (int64_t)(p + r) * B + p + cc) : make_float2(0.f, 0.f);
+        s[a][b] = v.x;
+        c[a][b] = v.y;
       }
     for (int j = 0; j < kb; ++j) {
-      double x[TS], y[TS];
+      float2 x[TS], y[TS];
 #pragma unroll
       for (int a = 0; a < TS; ++a) {
-        x[a] = (r0 + a < rows) ? P[(r0 + a) * PS + j] : 0.0;
-        y[a] = (c0 + a < rows) ? P[(c0 + a) * PS + j] : 0.0;
+        x[a] = (r0 + a < rows) ? P[(r0 + a) * PS + j] : make_float2(0.f, 0.f);
+        y[a] = (c0 + a < rows) ? P[(c0 + a) * PS + j] : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int a = 0; a < TS; ++a)
 #pragma unroll
-        for (int b = 0; b < TS; ++b) acc[a][b] = fma(-x[a], y[b], acc[a][b]);
+        for (int b = 0; b < TS; ++b) ff_fms(s[a][b], c[a][b], x[a], y[b]);
     }
 #pragma unroll
     for (int a = 0; a < TS; ++a)
 #pragma unroll
       for (int b = 0; b < TS; ++b) {
-        const int r = r0 + a, c = c0 + b;
-        if (r < rows && c <= r) A[(int64_t)(p + r) * B + p + c] = acc[a][b];
+        const int r = r0 + a, cc = c0 + b;
+        if (r < rows && cc <= r) A[(int64_t)(p + r) * B + p + cc] = ff_norm(s[a][b], c[a][b]);
       }
   }
 }
 
 // Inverse update of block row p: R_j -= L_jp X_p for the rows below the block (panel-
-// relative kb..rows) and the columns c < ncols, in TS x TS register tiles.
+// relative kb..rows) and the columns c < ncols, in TS x TS register tiles, float-float.
 template <int CL, int TS>
-__device__ __forceinline__ void inverse_update(double* R, const double* P, int B, int p, int kb, int rows, int cbase,
+__device__ __forceinline__ void inverse_update(float2* R, const float2* P, int B, int p, int kb, int rows, int cbase,
                                                int ncols, int gtid, int gthreads) {
   const int mt = (rows - kb + TS - 1) / TS, nct = (ncols - cbase + TS - 1) / TS;
   for (int idx = gtid; idx < mt * nct; idx += gthreads) {
     const int tr = idx / nct, tcx = idx - tr * nct;
     const int j0 = kb + TS * tr, c0 = cbase + TS * tcx;  // j0 panel-relative row, c0 column
-    double acc[TS][TS];
+    float s[TS][TS], c[TS][TS];
 #pragma unroll
     for (int a = 0; a < TS; ++a)
 #pragma unroll
-      for (int b = 0; b < TS; ++b)
-        acc[a][b] = (j0 + a < rows && c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + j0 + a) * B + c0 + b) : 0.0;
+      for (int b = 0; b < TS; ++b) {
+        const float2 v = (j0 + a < rows && c0 + b < ncols) ? ldg_c2<CL>(R + (int64_t)(p + j0 + a) * B + c0 + b)
+                                                           : make_float2(0.f, 0.f);
+        s[a][b] = v.x;
+        c[a][b] = v.y;
+      }
     for (int q = 0; q < kb; ++q) {
-      double l[TS], xq[TS];
+      float2 l[TS], xq[TS];
 #pragma unroll
-      for (int a = 0; a < TS; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : 0.0;
+      for (int a = 0; a < TS; ++a) l[a] = (j0 + a < rows) ? P[(j0 + a) * PS + q] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int b = 0; b < TS; ++b) xq[b] = (c0 + b < ncols) ? ldg_c<CL>(R + (int64_t)(p + q) * B + c0 + b) : 0.0;
+      for (int b = 0; b < TS; ++b)
+        xq[b] = (c0 + b < ncols) ? ldg_c2<CL>(R + (int64_t)(p + q) * B + c0 + b) : make_float2(0.f, 0.f);
 #pragma unroll
       for (int a = 0; a < TS; ++a)
 #pragma unroll
-        for (int b = 0; b < TS; ++b) acc[a][b] = fma(-l[a], xq[b], acc[a][b]);
+        for (int b = 0; b < TS; ++b) ff_fms(s[a][b], c[a][b], l[a], xq[b]);
     }
 #pragma unroll
     for (int a = 0; a < TS; ++a)
 #pragma unroll
       for (int b = 0; b < TS; ++b)
-        if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(p + j0 + a) * B + c0 + b] = acc[a][b];
+        if (j0 + a < rows && c0 + b < ncols) R[(int64_t)(p + j0 + a) * B + c0 + b] = ff_norm(s[a][b], c[a][b]);
   }
 }
 
@@ -234,8 +280,7 @@ __device__ __forceinline__ void inverse_update(double* R, const double* P, int B
 template <int PREC, int CL, int FT, int MB = (CL == 1 ? 512 / FT : 1)>
 __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sigma_all,
                                                        double* __restrict__ inv_all,
-                                                       const double* __restrict__ m_all,
-                                                       const double* __restrict__ dgain, int B,
+                                                       const double* __restrict__ m_all, int B,
                                                        void* __restrict__ wmat,
                                                        float* __restrict__ y0_all,
                                                        float* __restrict__ inv_s2_all,
@@ -246,8 +291,9 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   if (status[t] != LS_OK) return;  // same for every CTA of the cluster
   if (every > 1 && (q_off + t) % every != 0) return;  // not a snapshot of the cadence
   const int64_t BB = (int64_t)B * B;
-  double* A = sigma_all + t * BB;
-  double* Inv = inv_all + t * BB;
+  double* A = sigma_all + t * BB;        // raw sums in, then Sigma and L as float-float
+  float2* A2 = reinterpret_cast<float2*>(A);
+  float2* Inv = reinterpret_cast<float2*>(inv_all + t * BB);  // the inverse, float-float
   const double* m = m_all + (int64_t)t * B;
   const int Bp = pad64(B);
   extern __shared__ double smem[];
@@ -261,25 +307,32 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   const int gtid = gwarp * 32 + lane, gthreads = CL * FT;
 
   // ---- covariance from the raw sums (lower triangle, in place) ----------------------
-  // Sigma_ij = d_i d_j (S2_ij - n m_i m_j) / (n - 1), n = pixels in this line's window.
-  // (triangular-solve form: the DN-frame covariance S_ij = (S2_ij - n m_i m_j) / (n - 1);
-  // the gains cancel from Eq. 1, delta = (x' - m)^T S^{-1} (x' - m))
+  // The DN-frame covariance S_ij = (S2_ij - n m_i m_j) / (n - 1), n = pixels in this
+  // line's window, in FP64, stored float-float. The calibration gains cancel from Eq. 1:
+  // with x - mu = D (x' - m) and Sigma = D S D, delta = (x' - m)^T S^{-1} (x' - m).
   constexpr bool TRSM = is_trsm(PREC);
   {
     const int64_t n = (n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W;
     const double nn = (double)n, inv_nm1 = 1.0 / (double)(n - 1);
     for (int i = gwarp; i < B; i += gwarps) {
-      const double ai = (TRSM ? 1.0 : dgain[i]) * inv_nm1, nmi = nn * m[i];
+      const double nmi = nn * m[i];
       double* row = A + (int64_t)i * B;
-      for (int j = lane; j <= i; j += 32) row[j] = ai * (TRSM ? 1.0 : dgain[j]) * fma(-nmi, m[j], row[j]);
+      for (int j = lane; j <= i; j += 32) {
+        const double v = inv_nm1 * fma(-nmi, m[j], row[j]);
+        A2[(int64_t)i * B + j] = d_to_ff(v);
+      }
     }
     // the inverse is built in place of R = I (entries above the diagonal stay zero)
-    for (int64_t e = gtid; e < BB; e += gthreads) Inv[e] = ((int)(e / B) == (int)(e % B)) ? 1.0 : 0.0;
+    for (int64_t e = gtid; e < BB; e += gthreads)
+      Inv[e] = make_float2(((int)(e / B) == (int)(e % B)) ? 1.f : 0.f, 0.f);
     csync<CL>();
   }
 
   // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
-  double* P = smem;  // panel: P[r * PS + j] = A[p + r][p + j]
+  // panel: element (r, j) = A[p + r][p + j] at r * PS + j; the kb x kb diagonal block in
+  // FP64 (P), the rows below it float-float (Pf), in the same 8-byte slots
+  double* P = smem;
+  float2* Pf = reinterpret_cast<float2*>(smem);
   __shared__ double rdg[NB];  // 1 / L[p + j][p + j] of the current panel
   __shared__ int notpd;       // a non-positive pivot in the diagonal block
   if (tid == 0) notpd = 0;
@@ -293,7 +346,9 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     const int frows = CL == 1 ? rows : kb;
     for (int e = tid; e < frows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
-      P[r * PS + j] = ldg_c<CL>(A + (int64_t)(p + r) * B + p + j);
+      const float2 v = ldg_c2<CL>(A2 + (int64_t)(p + r) * B + p + j);
+      if (r < kb) P[r * PS + j] = ff_to_d(v);
+      else Pf[r * PS + j] = v;
     }
     __syncthreads();
     {
@@ -335,7 +390,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       for (int r = kb + tid; r < rows; r += FT) {
         double v[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v[j] = j < kb ? P[r * PS + j] : 0.0;
+        for (int j = 0; j < NB; ++j) v[j] = j < kb ? ff_to_d(Pf[r * PS + j]) : 0.0;
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
           if (j < kb) {
@@ -347,7 +402,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
         }
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-          if (j < kb) P[r * PS + j] = v[j];
+          if (j < kb) Pf[r * PS + j] = d_to_ff(v[j]);
       }
       __syncthreads();
     }
@@ -356,9 +411,9 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       // the same factor), rows spread over the cluster
       for (int r = kb + gtid; r < rows; r += gthreads) {
         double v[NB];
-        const double* arow = A + (int64_t)(p + r) * B + p;
+        const float2* arow = A2 + (int64_t)(p + r) * B + p;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v[j] = j < kb ? ldg_c<CL>(arow + j) : 0.0;
+        for (int j = 0; j < NB; ++j) v[j] = j < kb ? ff_to_d(ldg_c2<CL>(arow + j)) : 0.0;
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
           if (j < kb) {
@@ -368,21 +423,21 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
             v[j] = a * rdg[j];
           }
         }
-        double* wrow = A + (int64_t)(p + r) * B + p;
+        float2* wrow = A2 + (int64_t)(p + r) * B + p;
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-          if (j < kb) wrow[j] = v[j];
+          if (j < kb) wrow[j] = d_to_ff(v[j]);
       }
       csync<CL>();
       for (int e = tid; e < (rows - kb) * kb; e += FT) {
         const int r = kb + e / kb, j = e - (r - kb) * kb;
-        P[r * PS + j] = ldg_c<CL>(A + (int64_t)(p + r) * B + p + j);
+        Pf[r * PS + j] = ldg_c2<CL>(A2 + (int64_t)(p + r) * B + p + j);
       }
       __syncthreads();
     }
     for (int e = tid; e < frows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
-      if (r >= j && rank == 0) A[(int64_t)(p + r) * B + p + j] = P[r * PS + j];
+      if (r >= j && rank == 0) A2[(int64_t)(p + r) * B + p + j] = r < kb ? d_to_ff(P[r * PS + j]) : Pf[r * PS + j];
     }
     // trailing update: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B. A cluster
     // switches to 2 x 2 tiles once the 4 x 4 tiles of a phase no longer cover all of its
@@ -391,9 +446,9 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     if (mrem > 0) {
       const int mt4 = (mrem + 3) >> 2;
       if (CL > 1 && mt4 * (mt4 + 1) / 2 < gthreads)
-        trailing_update<CL, 2>(A, P, B, p, kb, rows, gtid, gthreads);
+        trailing_update<CL, 2>(A2, Pf, B, p, kb, rows, gtid, gthreads);
       else
-        trailing_update<CL, 4>(A, P, B, p, kb, rows, gtid, gthreads);
+        trailing_update<CL, 4>(A2, Pf, B, p, kb, rows, gtid, gthreads);
     }
     // ---- triangular inverse, block row p, fused into the Cholesky step ----------------
     // X = L^{-1} is built right-looking in place of R = I: once panel p is factored, block
@@ -402,7 +457,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     // update R_j -= L_jp X_p (next phase, register tiles). R_p has received the
     // updates of every earlier block row, and the operations per element run in the same
     // order as in a separate inverse sweep after the whole factorisation.
-    double* R = Inv;
+    float2* R = Inv;
     {
       // triangular-solve form: only the inverses of the 64 x 64 diagonal blocks of L
       const int cbase = TRSM ? p / 64 * 64 : 0;
@@ -415,20 +470,20 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
         for (int r = 0; r < NB; ++r) {
           xr[r] = 0.0;
           if (r < kb) {
-            double v = ldg_c<CL>(R + (int64_t)(p + r) * B + c);
+            double v = ff_to_d(ldg_c2<CL>(R + (int64_t)(p + r) * B + c));
 #pragma unroll
             for (int q = 0; q < r; ++q) v = fma(-P[r * PS + q], xr[q], v);
             xr[r] = v * rdg[r];
-            R[(int64_t)(p + r) * B + c] = xr[r];
+            R[(int64_t)(p + r) * B + c] = d_to_ff(xr[r]);
           }
         }
       }
       csync<CL>();  // the trailing update of A and X_p are complete cluster-wide
       if (imrem > 0) {
         if (CL > 1 && ((imrem + 3) >> 2) * ((ncols - cbase + 3) >> 2) < gthreads)
-          inverse_update<CL, 2>(R, P, B, p, kb, irows, cbase, ncols, gtid, gthreads);
+          inverse_update<CL, 2>(R, Pf, B, p, kb, irows, cbase, ncols, gtid, gthreads);
         else
-          inverse_update<CL, 4>(R, P, B, p, kb, irows, cbase, ncols, gtid, gthreads);
+          inverse_update<CL, 4>(R, Pf, B, p, kb, irows, cbase, ncols, gtid, gthreads);
       }
       csync<CL>();  // panel p done: next panel (and its shared-memory buffer) may start
     }
@@ -443,8 +498,8 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       for (int k = lane; k < Bp; k += 32) {
         const int64_t idx = (int64_t)n * Bp + k;
         if (n < B && k <= n) {
-          const double* src = ((n >> 6) == (k >> 6)) ? Inv : A;
-          WOut<PREC>::store(w, plane, idx, ldg_c<CL>(src + (int64_t)n * B + k));
+          const float2* src = ((n >> 6) == (k >> 6)) ? Inv : A2;
+          WOut<PREC>::store(w, plane, idx, ff_to_d(ldg_c2<CL>(src + (int64_t)n * B + k)));
         } else {
           WOut<PREC>::zero(w, plane, idx);
         }
@@ -455,10 +510,10 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     if (CL > 1) csync<CL>();  // no CTA leaves while others may still read its shared memory
     return;
   }
-  // ---- G = Inv D, power-of-two scale, cast, y0 ------------------------------------
+  // ---- G = L^{-1} of the DN-frame covariance, power-of-two scale, cast, y0 ----------
   double mx = 0.0;
   for (int n = gwarp; n < B; n += gwarps)  // X is lower triangular
-    for (int k = lane; k <= n; k += 32) mx = fmax(mx, fabs(ldg_c<CL>(Inv + (int64_t)n * B + k) * dgain[k]));
+    for (int k = lane; k <= n; k += 32) mx = fmax(mx, fabs(ff_to_d(ldg_c2<CL>(Inv + (int64_t)n * B + k))));
   mx = block_max<FT>(mx, red);
   if (CL > 1) {  // maximum over the cluster: read every CTA's partial from its shared memory
     csync<CL>();
@@ -469,16 +524,13 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   const double s = (mx > 0.0) ? ldexp(1.0, -ex) : 1.0;
   const int64_t plane = (int64_t)Bp * Bp;
   void* w = (char*)wmat + (size_t)t * plane * 4;  // 4 bytes per element pair in every format
-  double* ds = P;  // the panel buffer is free: d_k s per band (s is a power of two: exact)
-  for (int k = tid; k < B; k += FT) ds[k] = dgain[k] * s;
-  __syncthreads();
   // one warp per output row n: write the row and accumulate y0[n] from the rounded values
   for (int n = gwarp; n < Bp; n += gwarps) {
     double acc = 0.0;
     for (int k = lane; k < Bp; k += 32) {
       const int64_t idx = (int64_t)n * Bp + k;
       if (n < B && k <= n) {
-        const float r = WOut<PREC>::store(w, plane, idx, ldg_c<CL>(Inv + (int64_t)n * B + k) * ds[k]);
+        const float r = WOut<PREC>::store(w, plane, idx, ff_to_d(ldg_c2<CL>(Inv + (int64_t)n * B + k)) * s);
         acc = fma((double)r, m[k], acc);
       } else {
         WOut<PREC>::zero(w, plane, idx);
@@ -531,7 +583,7 @@ int factor_cluster_capacity(size_t smem) {
 }
 
 template <int PREC, int CL, int FT = FT_CLUSTER, int MB = (CL == 1 ? 512 / FT : 1)>
-cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, const double* dgain, int L, int B,
+cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, int L, int B,
                             void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
                             cudaStream_t st, const int64_t* n0_dev, int every, int q_off) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
@@ -556,7 +608,7 @@ cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, con
   cfg.numAttrs = 1;
   // a non-portable size: launch only where the device can place such a cluster
   if (CL > 8 && factor_cluster_capacity<PREC, CL, FT, MB>(smem) <= 0) return cudaErrorInvalidConfiguration;
-  return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL, FT, MB>, sigma, scratch, m, dgain, B, wmat, y0, inv_s2, status,
+  return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL, FT, MB>, sigma, scratch, m, B, wmat, y0, inv_s2, status,
                             n0, W, incl, n0_dev, every, q_off);
 }
 
@@ -575,27 +627,27 @@ int factor_single_threads() {
 }
 
 template <int PREC>
-cudaError_t launch_factor_p(int cl, int ft, double* sigma, double* scratch, const double* m, const double* dgain, int L,
+cudaError_t launch_factor_p(int cl, int ft, double* sigma, double* scratch, const double* m, int L,
                             int B, void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
                             int incl, cudaStream_t st, const int64_t* n0_dev, int every, int q_off) {
   switch (cl) {
     case 16: {
       const cudaError_t e =
-          launch_factor_t<PREC, 16>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+          launch_factor_t<PREC, 16>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
       if (e != cudaErrorInvalidConfiguration) return e;
-      return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+      return launch_factor_t<PREC, 8>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
     }
-    case 8: return launch_factor_t<PREC, 8>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
-    case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
-    case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+    case 8: return launch_factor_t<PREC, 8>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+    case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+    case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
     default:
       if (ft == 96)  // 128 threads sized for 5 CTAs per SM
-        return launch_factor_t<PREC, 1, 128, 5>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W,
+        return launch_factor_t<PREC, 1, 128, 5>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W,
                                                 incl, st, n0_dev, every, q_off);
       if (ft == 128)
-        return launch_factor_t<PREC, 1, 128>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl,
+        return launch_factor_t<PREC, 1, 128>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl,
                                              st, n0_dev, every, q_off);
-      return launch_factor_t<PREC, 1, 256>(sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+      return launch_factor_t<PREC, 1, 256>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
   }
 }
 
@@ -707,7 +759,7 @@ void factor_prepare(int B, int prec) {
   factor_wave_lines(B, prec);
 }
 
-cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const double* dgain,
+cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
                           int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
                           const int64_t* n0_dev, int every, int q_off) {
@@ -722,22 +774,22 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m, const
                            : factor_cluster_size<P_BF16>(L, smem);
     ft = factor_single_threads();
   }
-  return launch_factor_shape(cl, ft, sigma, scratch, m, dgain, L, B, prec, wmat, y0, inv_s2, status, n0, W, incl,
+  return launch_factor_shape(cl, ft, sigma, scratch, m, L, B, prec, wmat, y0, inv_s2, status, n0, W, incl,
                              st, lc, n0_dev, every, q_off);
 }
 
-cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m, const double* dgain,
+cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m,
                                 int L, int B, int prec, void* wmat, float* y0, float* inv_s2, int32_t* status,
                                 int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
                                 const int64_t* n0_dev, int every, int q_off) {
   if (L <= 0) return cudaSuccess;
   cudaError_t e;
   switch (prec) {
-    case P_FP32: e = launch_factor_p<P_FP32>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    case P_FP16: e = launch_factor_p<P_FP16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    case P_BF16T: e = launch_factor_p<P_BF16T>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    case P_FP32T: e = launch_factor_p<P_FP32T>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    default: e = launch_factor_p<P_BF16>(cl, ft, sigma, scratch, m, dgain, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
+    case P_FP32: e = launch_factor_p<P_FP32>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
+    case P_FP16: e = launch_factor_p<P_FP16>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
+    case P_BF16T: e = launch_factor_p<P_BF16T>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
+    case P_FP32T: e = launch_factor_p<P_FP32T>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
+    default: e = launch_factor_p<P_BF16>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
   }
   if (lc) lc->n += 1;
   if (e != cudaSuccess) return e;
@@ -780,14 +832,14 @@ int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
   buckets.push_back(max_lines);
   const int Lt = max_lines, Bp = pad64(B);
   const int64_t BB = (int64_t)B * B;
-  double *sigma = nullptr, *inv = nullptr, *m = nullptr, *dgain = nullptr;
+  double *sigma = nullptr, *inv = nullptr, *m = nullptr;
   float *y0 = nullptr, *inv_s2 = nullptr;
   int32_t* status = nullptr;
   void* wmat = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   bool ok = cudaMalloc(&sigma, (size_t)Lt * BB * 8) == cudaSuccess && cudaMalloc(&inv, (size_t)Lt * BB * 8) == cudaSuccess &&
-            cudaMalloc(&m, (size_t)Lt * B * 8) == cudaSuccess && cudaMalloc(&dgain, (size_t)B * 8) == cudaSuccess &&
+            cudaMalloc(&m, (size_t)Lt * B * 8) == cudaSuccess &&
             cudaMalloc(&y0, (size_t)Lt * Bp * 4) == cudaSuccess && cudaMalloc(&inv_s2, (size_t)Lt * 4) == cudaSuccess &&
             cudaMalloc(&status, (size_t)Lt * 4) == cudaSuccess &&
             cudaMalloc(&wmat, (size_t)Lt * Bp * Bp * 4) == cudaSuccess &&
@@ -795,9 +847,7 @@ int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
             cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
   std::vector<TunedShape> result;
   if (ok) {
-    std::vector<double> ones(B, 1.0);
-    ok = cudaMemcpyAsync(dgain, ones.data(), (size_t)B * 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-         cudaMemsetAsync(m, 0, (size_t)Lt * B * 8, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+    ok = cudaMemsetAsync(m, 0, (size_t)Lt * B * 8, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
   }
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   for (size_t bi = 0; ok && bi < buckets.size(); ++bi) {
@@ -822,7 +872,7 @@ int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
         tune_identity_kernel<<<256, 256, 0, st>>>(sigma, L, B, 1.0e6);
         ok = cudaMemsetAsync(status, 0, (size_t)L * 4, st) == cudaSuccess;
         cudaEventRecord(e0, st);
-        if (launch_factor_shape(cf.first, cf.second, sigma, inv, m, dgain, L, B, prec, wmat, y0, inv_s2, status,
+        if (launch_factor_shape(cf.first, cf.second, sigma, inv, m, L, B, prec, wmat, y0, inv_s2, status,
                                 1000, 1, 0, st, nullptr, nullptr) != cudaSuccess)
           ok = false;
         cudaEventRecord(e1, st);
@@ -841,7 +891,6 @@ int factor_autotune(int B, int prec, int max_lines, float* report, int cap) {
   cudaFree(sigma);
   cudaFree(inv);
   cudaFree(m);
-  cudaFree(dgain);
   cudaFree(y0);
   cudaFree(inv_s2);
   cudaFree(status);

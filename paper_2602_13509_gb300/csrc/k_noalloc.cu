@@ -66,7 +66,7 @@ size_t scratch_need(int64_t n, int W, int B) {
   const size_t Bp = (size_t)pad64(B);
   auto r = [](size_t b) { return (b + 255) / 256 * 256; };
   (void)W;
-  return r(B * 4) + r(B * 4) + r(B * 8) + r(B * 8) + r((size_t)B * B * 8)  // c, dgain, S1, S2
+  return r(B * 4) + r(B * 4) + r(B * 8) + r((size_t)B * B * 8)  // c (int, float), S1, S2
          + 2 * r((size_t)n * B * 8)                                            // s1_line, m_line
          + 2 * r((size_t)B * B * 8)                                            // sigma, inv
          + r(Bp * Bp * 4) + r(Bp * 4) + r(4)                                   // wmat, y0, inv_s2
@@ -89,10 +89,9 @@ extern "C" int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t
   if (!(threshold >= 0.f) || threshold > 3.0e38f) return noalloc_fail(HSAD_E_INVALID, "bad threshold");
   if (flags & ~HSAD_NORMALIZE_SCORES) return noalloc_fail(HSAD_E_INVALID, "unknown flags");
   if (device < 0 || device >= kMaxDevices) return noalloc_fail(HSAD_E_INVALID, "bad device");
-  double g[512];
-  for (int b = 0; b < bands; ++b) {
-    g[b] = gain ? (double)gain[b] : 1.0;
-    if (!(g[b] == g[b]) || g[b] == 0.0 || g[b] > 1e308 || g[b] < -1e308)
+  for (int b = 0; b < bands; ++b) {  // the gains cancel from Eq. 1: validated, not used
+    const double g = gain ? (double)gain[b] : 1.0;
+    if (!(g == g) || g == 0.0 || g > 1e308 || g < -1e308)
       return noalloc_fail(HSAD_E_INVALID, "gain must be finite and non-zero");
   }
   const size_t need = scratch_need(n_lines, width, bands);
@@ -122,7 +121,6 @@ extern "C" int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t
     Carve cv{base};
     int32_t* c_int = cv.take<int32_t>(B);
     float* c_flt = cv.take<float>(B);
-    double* dgain = cv.take<double>(B);
     double* s1 = cv.take<double>(B);
     double* s2 = cv.take<double>((size_t)B * B);
     double* s1_line = cv.take<double>((size_t)n_lines * B);
@@ -139,8 +137,7 @@ extern "C" int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t
     // every region below is written before it is read except S1 / S2 and the status
     // words, which are cleared here; the array keeps the previous call's contents
     LaunchCounter lc;
-    cudaError_t e = cudaMemcpyAsync(dgain, g, (size_t)B * 8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s1, 0, (size_t)B * 8, st);
+    cudaError_t e = cudaMemsetAsync(s1, 0, (size_t)B * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s2, 0, (size_t)B * B * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, (size_t)n_lines * 4, st);
     if (e == cudaSuccess) e = launch_shift_init(cube, W, B, it, c_int, c_flt, st, &lc);
@@ -149,9 +146,9 @@ extern "C" int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t
       e = launch_prefix_mean(s1_line, m_line, s1, 0, W, (int)n_lines, B, 1, 0, status, st, &lc);
     if (e == cudaSuccess) e = launch_syrk_simt(cube, 1, N, B, it, c_int, c_flt, s2, 0, 1, st, &lc);
     if (e == cudaSuccess)
-      e = launch_finalize_cov(s1, s2, dgain, N, B, sigma, m_line, (int64_t)B + 1, status, st, &lc);
+      e = launch_finalize_cov(s1, s2, N, B, sigma, m_line, (int64_t)B + 1, status, st, &lc);
     if (e == cudaSuccess)
-      e = launch_factor(sigma, inv, m_line, dgain, 1, B, pr, wmat, y0, inv_s2, status, N, 0, 0, st, &lc);
+      e = launch_factor(sigma, inv, m_line, 1, B, pr, wmat, y0, inv_s2, status, N, 0, 0, st, &lc);
     const bool rel = threshold_mode == HSAD_REL, norm = (flags & HSAD_NORMALIZE_SCORES) != 0;
     ScoreOut o;
     o.scores = scores;

@@ -342,24 +342,22 @@ cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int i
 // K3c finalize_cov (cube mode): the cube's raw sums S2 (lower triangle, read from the
 // lower triangle of the state) and m = S1 / N; the factor kernel forms Sigma from them.
 __global__ void finalize_cov_kernel(const double* __restrict__ s1, const double* __restrict__ s2,
-                                    const double* __restrict__ dgain, int64_t n, int B,
+                                    int64_t n, int B,
                                     double* __restrict__ sigma, double* __restrict__ m,
                                     int64_t min_pixels, int32_t* __restrict__ status) {
   const int64_t BB = (int64_t)B * B;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= BB) return;
   const int i = (int)(e / B), j = (int)(e % B);
-  (void)dgain;
   if (j <= i) sigma[e] = s2[e];
   if (j == 0) m[i] = s1[i] / (double)n;
   if (e == 0) status[0] = (n >= min_pixels && n > 1) ? LS_OK : LS_NOT_READY;
 }
 
-cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, const double* dgain,
-                                int64_t n, int B, double* sigma, double* m, int64_t min_pixels,
+cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, int64_t n, int B, double* sigma, double* m, int64_t min_pixels,
                                 int32_t* status, cudaStream_t st, LaunchCounter* lc) {
   const int64_t BB = (int64_t)B * B;
-  finalize_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(state_s1, state_s2, dgain, n,
+  finalize_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(state_s1, state_s2, n,
                                                                     B, sigma, m, min_pixels, status);
   HSAD_LAUNCH_CHECK(lc);
 }
