@@ -6,10 +6,11 @@
 // per-band calibration gains, and Sigma = D S D with S the DN-frame covariance, so
 //     delta = (x' - m)^T S^{-1} (x' - m) = || L^{-1} (x' - m) ||^2,   S = L L^T:
 // the gains cancel and the factor works on S alone. Arithmetic: the covariance is formed
-// in FP64; the pivots, the 16 x 16 diagonal blocks and the panel solves run in FP64; the
-// two O(B^3) register-tiled updates (Cholesky trailing update, inverse block rows) run in
-// float-float (pairs of FP32 values, about 48 significant bits), as FP64 issues at 1/64
-// of the FP32 rate here. With G = L^{-1} the score is delta = || G x' - G m ||^2.
+// in FP64, and so are the 16 x 16 diagonal blocks with their pivots; the panel solves,
+// the O(B^3) register-tiled updates (Cholesky trailing update, inverse block rows) and the
+// inverse's forward substitutions run in float-float (pairs of FP32 values, about 48
+// significant bits), as FP64 issues at 1/64 of the FP32 rate here. With G = L^{-1} the
+// score is delta = || G x' - G m ||^2.
 // G is lower triangular. It is stored row-major ([n][k], n = output coordinate) as the
 // K-major operand of the whitening contraction, scaled by a power of two s so that
 // max |s G| is in [0.5, 1) (keeps FP16 in range; exact in every format), and
@@ -39,15 +40,14 @@ namespace hsad {
 namespace {
 constexpr int FT_CLUSTER = 256;  // threads per factorisation CTA in a cluster
 
-// Store one element of the whitening operand and return the value actually stored (the
-// sum of the stored planes, exact in FP32), converted once from FP64 to FP32: the hi / lo
-// split of the FP32 value keeps 16 (BF16) or 22 (FP16) of its 24 bits.
+// Store one element of the whitening operand, given in FP32, and return the value actually
+// stored (the sum of the stored planes, exact in FP32): the hi / lo split keeps 16 (BF16)
+// or 22 (FP16) of its 24 bits.
 template <int PREC>
 struct WOut;
 template <>
 struct WOut<P_FP32> {
-  __device__ static float store(void* w, int64_t, int64_t idx, double v) {
-    const float f = (float)v;
+  __device__ static float store(void* w, int64_t, int64_t idx, float f) {
     ((float*)w)[idx] = f;
     return f;
   }
@@ -55,8 +55,7 @@ struct WOut<P_FP32> {
 };
 template <>
 struct WOut<P_FP16> {
-  __device__ static float store(void* w, int64_t plane, int64_t idx, double v) {
-    const float f = (float)v;
+  __device__ static float store(void* w, int64_t plane, int64_t idx, float f) {
     const __half hi = __float2half_rn(f);
     const float hf = __half2float(hi);
     const __half lo = __float2half_rn(f - hf);
@@ -73,8 +72,7 @@ template <>
 struct WOut<P_BF16T>;
 template <>
 struct WOut<P_BF16> {
-  __device__ static float store(void* w, int64_t plane, int64_t idx, double v) {
-    const float f = (float)v;
+  __device__ static float store(void* w, int64_t plane, int64_t idx, float f) {
     const __nv_bfloat16 hi = __float2bfloat16_rn(f);
     const float hf = __bfloat162float(hi);
     const __nv_bfloat16 lo = __float2bfloat16_rn(f - hf);
@@ -137,11 +135,11 @@ __device__ __forceinline__ double ld_remote(const double* local, int rank) {
   return v;
 }
 
-// The O(B^3) updates run in float-float arithmetic: a value is an unevaluated pair
-// hi + lo of FP32 numbers (about 48 significant bits; FP32's exponent range), stored as a
-// float2 in the 8 bytes of a double. FP64 issues at 1/64 of the FP32 rate on this part,
-// while one float-float multiply-subtract costs 12 FP32 operations. Pivots, the panel
-// solves and everything outside the two register-tiled updates stay in FP64.
+// The factorisation runs in float-float arithmetic: a value is an unevaluated pair hi + lo
+// of FP32 numbers (about 48 significant bits; FP32's exponent range), stored as a float2
+// in the 8 bytes of a double. FP64 issues at 1/64 of the FP32 rate on this part, while
+// one float-float multiply-subtract costs 12 FP32 operations. The covariance, the 16 x 16
+// diagonal blocks and their pivots stay in FP64.
 __device__ __forceinline__ double ff_to_d(float2 v) { return (double)v.x + (double)v.y; }
 __device__ __forceinline__ float2 d_to_ff(double d) {
   const float h = __double2float_rn(d);
@@ -167,11 +165,38 @@ __device__ __forceinline__ void ff_fms(float& s, float& c, float2 x, float2 y) {
   s = t;
   c = __fsub_rn(__fadd_rn(c, q), e);
 }
+// a b in float-float (two-product with the cross terms), renormalised by fast two-sum
+// (the error term is below half an ulp of the product).
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+// The FP32 value nearest to hi + lo.
+__device__ __forceinline__ float ff_f(float2 v) { return __fadd_rn(v.x, v.y); }
 // The pair renormalised (two-sum: c may exceed s after cancellation).
 __device__ __forceinline__ float2 ff_norm(float s, float c) {
   const float h = __fadd_rn(s, c);
   const float z = __fsub_rn(h, s);
   return make_float2(h, __fadd_rn(__fsub_rn(s, __fsub_rn(h, z)), __fsub_rn(c, z)));
+}
+
+// One row of L21 = A21 L11^{-T} (forward substitution against the panel's factored
+// diagonal block L11 and the reciprocals of its pivots), float-float: each element takes
+// its updates in column order, then the pivot's reciprocal.
+__device__ __forceinline__ void row_solve(float2 (&v)[NB], const float2* L11, const float2* rdg, int kb) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < kb) {
+      float s = v[j].x, c = v[j].y;
+#pragma unroll
+      for (int q = 0; q < j; ++q) ff_fms(s, c, v[q], L11[j * PS + q]);
+      v[j] = ff_mul(ff_norm(s, c), rdg[j]);
+    }
+  }
 }
 
 // Trailing update of panel p: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B,
@@ -265,7 +290,8 @@ __device__ __forceinline__ void inverse_update(float2* R, const float2* P, int B
 // global memory with a blocked right-looking Cholesky: the NB-column panel is staged in
 // shared memory and factored there (its diagonal block by one warp, the rows below by
 // one thread each), and the trailing lower triangle is updated with 4 x 4 register tiles
-// (NB DFMA per element loaded and stored). The inverse X = L^{-1} (all of it, or only its
+// (NB float-float multiply-subtracts per element loaded and stored). The inverse
+// X = L^{-1} (all of it, or only its
 // 64 x 64 diagonal blocks in the triangular-solve form) is built NB rows at a time, fused
 // into the same loop: the contribution of earlier block rows is a register-tiled product,
 // and the within-block forward substitution runs per column, each thread owning whole
@@ -329,11 +355,11 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   }
 
   // ---- blocked Cholesky (right-looking, lower triangle in place) -------------------
-  // panel: element (r, j) = A[p + r][p + j] at r * PS + j; the kb x kb diagonal block in
-  // FP64 (P), the rows below it float-float (Pf), in the same 8-byte slots
+  // panel: element (r, j) = A[p + r][p + j] at r * PS + j, float-float (Pf); the kb x kb
+  // diagonal block is factored in FP64 (P, the same 8-byte slots) and then converted
   double* P = smem;
   float2* Pf = reinterpret_cast<float2*>(smem);
-  __shared__ double rdg[NB];  // 1 / L[p + j][p + j] of the current panel
+  __shared__ float2 rdg[NB];  // 1 / L[p + j][p + j] of the current panel
   __shared__ int notpd;       // a non-positive pivot in the diagonal block
   if (tid == 0) notpd = 0;
   __syncthreads();
@@ -355,10 +381,12 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       // the kb x kb diagonal block: one warp, column by column, warp-level syncs only
       // (pivot, reciprocal, column scaled by it, rank-1 update of the block's remainder)
       if (warp == 0) {
+        bool bad = false;
         for (int j = 0; j < kb; ++j) {
           const double piv = P[j * PS + j];
           if (!(piv > 0.0) || !isfinite(piv)) {  // same value in every lane
             if (lane == 0) notpd = 1;
+            bad = true;
             break;
           }
           const double l = sqrt(piv);
@@ -367,7 +395,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
           __syncwarp();
           if (lane == 0) {
             P[j * PS + j] = l;
-            rdg[j] = rl;
+            rdg[j] = d_to_ff(rl);
           }
           const int nc = kb - j - 1;
           for (int e = lane; e < nc * nc; e += 32) {
@@ -375,6 +403,12 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
             if (k <= r) P[r * PS + k] = fma(-P[r * PS + j], P[k * PS + j], P[r * PS + k]);
           }
           __syncwarp();
+        }
+        if (!bad) {  // the factored block to float-float, in place (lower triangle)
+          for (int e = lane; e < kb * kb; e += 32) {
+            const int r = e / kb, j = e - r * kb;
+            if (j <= r) Pf[r * PS + j] = d_to_ff(P[r * PS + j]);
+          }
         }
       }
       __syncthreads();
@@ -388,21 +422,13 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       // the order of a column-by-column sweep (each element takes its updates in column
       // order, then the pivot's reciprocal)
       for (int r = kb + tid; r < rows; r += FT) {
-        double v[NB];
+        float2 v[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v[j] = j < kb ? ff_to_d(Pf[r * PS + j]) : 0.0;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (j < kb) {
-            double a = v[j];
-#pragma unroll
-            for (int q = 0; q < j; ++q) a = fma(-v[q], P[j * PS + q], a);
-            v[j] = a * rdg[j];
-          }
-        }
+        for (int j = 0; j < NB; ++j) v[j] = j < kb ? Pf[r * PS + j] : make_float2(0.f, 0.f);
+        row_solve(v, Pf, rdg, kb);
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-          if (j < kb) Pf[r * PS + j] = d_to_ff(v[j]);
+          if (j < kb) Pf[r * PS + j] = v[j];
       }
       __syncthreads();
     }
@@ -410,23 +436,15 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       // L21 = A21 L11^{-T}: the same forward substitution as the one-CTA form (bitwise
       // the same factor), rows spread over the cluster
       for (int r = kb + gtid; r < rows; r += gthreads) {
-        double v[NB];
+        float2 v[NB];
         const float2* arow = A2 + (int64_t)(p + r) * B + p;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) v[j] = j < kb ? ff_to_d(ldg_c2<CL>(arow + j)) : 0.0;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (j < kb) {
-            double a = v[j];
-#pragma unroll
-            for (int q = 0; q < j; ++q) a = fma(-v[q], P[j * PS + q], a);
-            v[j] = a * rdg[j];
-          }
-        }
+        for (int j = 0; j < NB; ++j) v[j] = j < kb ? ldg_c2<CL>(arow + j) : make_float2(0.f, 0.f);
+        row_solve(v, Pf, rdg, kb);
         float2* wrow = A2 + (int64_t)(p + r) * B + p;
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-          if (j < kb) wrow[j] = d_to_ff(v[j]);
+          if (j < kb) wrow[j] = v[j];
       }
       csync<CL>();
       for (int e = tid; e < (rows - kb) * kb; e += FT) {
@@ -437,7 +455,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     }
     for (int e = tid; e < frows * kb; e += FT) {
       const int r = e / kb, j = e - r * kb;
-      if (r >= j && rank == 0) A2[(int64_t)(p + r) * B + p + j] = r < kb ? d_to_ff(P[r * PS + j]) : Pf[r * PS + j];
+      if (r >= j && rank == 0) A2[(int64_t)(p + r) * B + p + j] = Pf[r * PS + j];
     }
     // trailing update: A[i][k] -= sum_j P[i][j] P[k][j] for p + kb <= k <= i < B. A cluster
     // switches to 2 x 2 tiles once the 4 x 4 tiles of a phase no longer cover all of its
@@ -465,16 +483,17 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
       const int imrem = irows - kb;
       const int ncols = p + kb;
       for (int c = cbase + gtid; c < ncols; c += gthreads) {
-        double xr[NB];
+        float2 xr[NB];
 #pragma unroll
         for (int r = 0; r < NB; ++r) {
-          xr[r] = 0.0;
+          xr[r] = make_float2(0.f, 0.f);
           if (r < kb) {
-            double v = ff_to_d(ldg_c2<CL>(R + (int64_t)(p + r) * B + c));
+            const float2 v = ldg_c2<CL>(R + (int64_t)(p + r) * B + c);
+            float sv = v.x, cv = v.y;
 #pragma unroll
-            for (int q = 0; q < r; ++q) v = fma(-P[r * PS + q], xr[q], v);
-            xr[r] = v * rdg[r];
-            R[(int64_t)(p + r) * B + c] = d_to_ff(xr[r]);
+            for (int q = 0; q < r; ++q) ff_fms(sv, cv, Pf[r * PS + q], xr[q]);
+            xr[r] = ff_mul(ff_norm(sv, cv), rdg[r]);
+            R[(int64_t)(p + r) * B + c] = xr[r];
           }
         }
       }
@@ -499,7 +518,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
         const int64_t idx = (int64_t)n * Bp + k;
         if (n < B && k <= n) {
           const float2* src = ((n >> 6) == (k >> 6)) ? Inv : A2;
-          WOut<PREC>::store(w, plane, idx, ff_to_d(ldg_c2<CL>(src + (int64_t)n * B + k)));
+          WOut<PREC>::store(w, plane, idx, ff_f(ldg_c2<CL>(src + (int64_t)n * B + k)));
         } else {
           WOut<PREC>::zero(w, plane, idx);
         }
@@ -511,10 +530,10 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     return;
   }
   // ---- G = L^{-1} of the DN-frame covariance, power-of-two scale, cast, y0 ----------
-  double mx = 0.0;
+  float mxf = 0.f;
   for (int n = gwarp; n < B; n += gwarps)  // X is lower triangular
-    for (int k = lane; k <= n; k += 32) mx = fmax(mx, fabs(ff_to_d(ldg_c2<CL>(Inv + (int64_t)n * B + k))));
-  mx = block_max<FT>(mx, red);
+    for (int k = lane; k <= n; k += 32) mxf = fmaxf(mxf, fabsf(ff_f(ldg_c2<CL>(Inv + (int64_t)n * B + k))));
+  double mx = block_max<FT>((double)mxf, red);
   if (CL > 1) {  // maximum over the cluster: read every CTA's partial from its shared memory
     csync<CL>();
     for (int r = 0; r < CL; ++r) mx = fmax(mx, ld_remote(&red[0], r));
@@ -522,6 +541,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   int ex = 0;
   frexp(mx, &ex);
   const double s = (mx > 0.0) ? ldexp(1.0, -ex) : 1.0;
+  const float sf = (float)s;  // a power of two within FP32's range (mx is an FP32 value)
   const int64_t plane = (int64_t)Bp * Bp;
   void* w = (char*)wmat + (size_t)t * plane * 4;  // 4 bytes per element pair in every format
   // one warp per output row n: write the row and accumulate y0[n] from the rounded values
@@ -530,7 +550,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     for (int k = lane; k < Bp; k += 32) {
       const int64_t idx = (int64_t)n * Bp + k;
       if (n < B && k <= n) {
-        const float r = WOut<PREC>::store(w, plane, idx, ff_to_d(ldg_c2<CL>(Inv + (int64_t)n * B + k)) * s);
+        const float r = WOut<PREC>::store(w, plane, idx, __fmul_rn(ff_f(ldg_c2<CL>(Inv + (int64_t)n * B + k)), sf));
         acc = fma((double)r, m[k], acc);
       } else {
         WOut<PREC>::zero(w, plane, idx);
