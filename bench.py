@@ -57,11 +57,11 @@ def load_peaks():
 # to a launch by its lines; keyed by (band count, whitening form: 1 = triangular solve), and
 # to be refreshed whenever the kernel changes (a form without a capture of the current
 # kernel reports null).
-FACTOR_DRAM_BYTES_PER_LINE = {(270, 1): (0.945713e9 + 1.386916e9) / 512}
+FACTOR_DRAM_BYTES_PER_LINE = {(270, 1): (0.960198e9 + 1.425162e9) / 512}
 
 
 def factor_flops_per_line(B, form):
-    """Algorithmic FP64 flops of one line's factorisation: the Cholesky factor (B^3 / 3)
+    """Algorithmic flops of one line's factorisation: the Cholesky factor (B^3 / 3)
     plus the full triangular inverse (B^3 / 3) for the explicit-inverse form, or plus only
     the inverses of the 64 x 64 diagonal blocks (b^3 / 3 each) for the triangular solve."""
     if form == 0:
@@ -79,6 +79,17 @@ def fp64_peak_tflops(mhz):
 
 def fp32_peak_tflops(mhz):
     return 152 * mhz * 1e6 * 256 / 1e12
+
+
+# The factor's O(B^3) updates run in float-float: one multiply-subtract of two pairs into a
+# compensated sum is 12 FP32-pipe instructions (product, three FMAs for its error, six for
+# the two-sum, two to gather the errors) for 2 flops of the algorithm, so its ALU ceiling is
+# the FP32 instruction rate x 2 / 12.
+FF_INSTR_PER_MAC = 12
+
+
+def ff_peak_tflops(mhz):
+    return 152 * mhz * 1e6 * 128 * 2 / FF_INSTR_PER_MAC / 1e12
 
 
 class ClockSampler:
@@ -635,18 +646,21 @@ def main():
             # with a cadence only every k-th line's statistics are factored
             work = lines_per_launch / max(1, args.factor_every) * factor_flops_per_line(B, form)
             ach = work / (avg_ms / 1e3) / 1e12
-            pk = fp64_peak_tflops(mhz)
+            pk = ff_peak_tflops(mhz)
             key = (B, form)
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                     "traffic": (FACTOR_DRAM_BYTES_PER_LINE[key] * lines_per_launch
                                 if key in FACTOR_DRAM_BYTES_PER_LINE else None),
                     "traffic_source": "ncu dram bytes per line of a 512-line capture x lines per launch",
-                    "kernel": ("factor (FP64 Cholesky + inverses of the 64 x 64 diagonal blocks)" if form
-                               else "factor (FP64 Cholesky + triangular inverse)"),
-                    "work_per_launch": (f"{lines_per_launch:.0f} lines x (B^3/3 + sum of 64-block b^3/3) FP64 flop"
-                                        if form else f"{lines_per_launch:.0f} lines x 2B^3/3 FP64 flop"),
-                    "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk (nominal 1.25 TF/s; "
-                                   "a DFMA probe measured 1.20 TF/s)"}
+                    "kernel": ("factor (Cholesky + inverses of the 64 x 64 diagonal blocks; FP64 pivots "
+                               "and panels, float-float updates)" if form
+                               else "factor (Cholesky + triangular inverse; FP64 pivots and panels, "
+                                    "float-float updates)"),
+                    "work_per_launch": (f"{lines_per_launch:.0f} lines x (B^3/3 + sum of 64-block b^3/3) flop"
+                                        if form else f"{lines_per_launch:.0f} lines x 2B^3/3 flop"),
+                    "peak_source": "derived: 152 SMs x 2070 MHz x 128 FP32 lanes x 2 flop / 12 FP32 "
+                                   "instructions per float-float multiply-subtract",
+                    "fp64_peak_derived": fp64_peak_tflops(mhz)}
         else:
             per_launch_px = px_step / launches_per_step
             byts = per_launch_px * (2 * B + (5 if dom == "whiten_score" else 0))
