@@ -20,6 +20,7 @@ from .rx import (  # noqa: F401
     encode_tx,
     forward_substitution,
     frontend,
+    gain_correct,
     global_rx,
     rx_scores,
     sample_covariance,

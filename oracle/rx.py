@@ -36,6 +36,10 @@ What it computes, and where the paper says so:
 * Front end, Sec. 3.2 ("Data Acquisition"): the out-of-specification bands are
   discarded and four consecutive bands are summed into one. Reading: keep raw bands
   [first, first + bin * B) and sum groups of ``bin`` consecutive bands (integers, exact).
+* Per-line gain correction, Sec. 3.2 ("Data Acquisition"): the imager's gain is changed
+  for every line to avoid saturation, and the data is corrected for the varying gain
+  before the radiometric calibration. Reading: one positive scalar g_t per line, every
+  value of line t divided by it (u = v / g_t), then the per-band calibration above.
 
 Pins (tests/test_oracle_*.py): exact rational brute force on tiny inputs, the
 in-sample identity mean(delta) = B (N-1)/N, invariance under invertible affine
@@ -70,6 +74,17 @@ def calibrate(v, gain=None, offset=None) -> np.ndarray:
     if gain is not None:
         x = x * np.asarray(gain, dtype=np.float64)
     return x
+
+
+def gain_correct(v, line_gain) -> np.ndarray:
+    """Per-line gain correction (Sec. 3.2): u[t] = v[t] / g_t for lines v [T, ...] and
+    gains g [T], in FP64. Pinned by the invariance of scores when each line holds its gain
+    times a common scene (tests/test_oracle_pins.py)."""
+    v = np.asarray(v, dtype=np.float64)
+    g = np.asarray(line_gain, dtype=np.float64).reshape(-1)
+    if g.shape[0] != v.shape[0] or not np.all(np.isfinite(g)) or not np.all(g > 0):
+        raise ValueError("one finite positive gain per line")
+    return v / g.reshape((-1,) + (1,) * (v.ndim - 1))
 
 
 def sample_mean(X: np.ndarray) -> np.ndarray:
@@ -198,12 +213,22 @@ def _stats_over_lines(lines: LineSource, a: int, b: int, gain, offset, chunk: in
 
 def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines: int = 0,
                    warmup_pixels: int = 0, gain=None, offset=None, n_lines: int | None = None,
-                   chunk: int = 64, every: int = 1):
+                   chunk: int = 64, every: int = 1, line_gain=None):
     """Scores of line t under the given statistics window.
 
     Returns ``(delta [W], status)`` with status OK, NOT_READY (too few pixels;
     delta is NaN) or NOT_PD (covariance not positive definite; delta is NaN).
+    ``line_gain`` (one gain per line of ``lines``): every line is gain-corrected
+    (``gain_correct``) before the calibration.
     """
+    if line_gain is not None:
+        raw, g = lines, np.asarray(line_gain, dtype=np.float64).reshape(-1)
+
+        def lines(t0, n):  # noqa: F811 (the gain-corrected source)
+            return gain_correct(_fetch(raw, t0, n), g[t0:t0 + n])
+
+        if n_lines is None:
+            n_lines = (t + 1) if callable(raw) else raw.shape[0]
     line = calibrate(_fetch(lines, t, 1), gain, offset)[0]
     W, B = line.shape
     if n_lines is None:
@@ -220,14 +245,14 @@ def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines:
 
 
 def stream_rx(lines: np.ndarray, mode: str = EXCLUSIVE, cube_lines: int = 0, warmup_pixels: int = 0,
-              gain=None, offset=None, every: int = 1):
+              gain=None, offset=None, every: int = 1, line_gain=None):
     """Scores of every line of ``lines`` [T, W, B]: ``(delta [T, W], status [T])``."""
     T, W, B = lines.shape
     delta = np.full((T, W), np.nan)
     status = np.zeros(T, dtype=np.int32)
     for t in range(T):
         delta[t], status[t] = stream_rx_line(lines, t, mode, cube_lines, warmup_pixels,
-                                             gain, offset, n_lines=T, every=every)
+                                             gain, offset, n_lines=T, every=every, line_gain=line_gain)
     return delta, status
 
 

@@ -108,3 +108,34 @@ def test_encoding_and_front_end_pins_reject_mutant(monkeypatch, target, mutant):
     monkeypatch.setattr(orx, target, mutant)
     monkeypatch.setattr(oracle, target, mutant)
     assert fails(), f"mutant {mutant.__name__} of {target} was not caught"
+
+
+def _gain_multiplied(v, line_gain):             # multiplies by the gain instead of dividing
+    v = np.asarray(v, dtype=np.float64)
+    return v * np.asarray(line_gain, dtype=np.float64).reshape((-1,) + (1,) * (v.ndim - 1))
+
+
+def _gain_of_next_line(v, line_gain):           # line t corrected with the gain of line t + 1
+    v = np.asarray(v, dtype=np.float64)
+    g = np.roll(np.asarray(line_gain, dtype=np.float64).reshape(-1), -1)
+    return v / g.reshape((-1,) + (1,) * (v.ndim - 1))
+
+
+@pytest.mark.parametrize("mutant", [_gain_multiplied, _gain_of_next_line])
+def test_gain_correction_pins_reject_mutant(monkeypatch, mutant):
+    import tests.test_oracle_pins as pins
+    checks = [pins.test_gain_correct_hand_values,
+              lambda: pins.test_line_gain_recovers_the_scene(oracle.EXCLUSIVE)]
+
+    def fails():
+        for c in checks:
+            try:
+                c()
+            except AssertionError:
+                return True
+        return False
+
+    assert not fails(), "pins must accept the unmodified oracle"
+    monkeypatch.setattr(orx, "gain_correct", mutant)
+    monkeypatch.setattr(oracle, "gain_correct", mutant)
+    assert fails(), f"mutant {mutant.__name__} of gain_correct was not caught"

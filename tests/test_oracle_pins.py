@@ -381,3 +381,52 @@ def test_cadence_window_and_scores():
             np.testing.assert_array_equal(dk[t], d1[t])
     with pytest.raises(ValueError):
         orx.statistics_lines(4, oracle.INCLUSIVE, 0, 10, every=2)
+
+
+# ------------------------------------------------------------------ per-line gain correction (Sec. 3.2)
+def test_gain_correct_hand_values():
+    v = np.array([[[2.0, 4.0]], [[6.0, 8.0]], [[3.0, 9.0]]])        # 3 lines x 1 pixel x 2 bands
+    u = oracle.gain_correct(v, [2.0, 4.0, 0.5])
+    np.testing.assert_array_equal(u[:, 0, :], [[1.0, 2.0], [1.5, 2.0], [6.0, 18.0]])
+    for bad in ([1.0, 0.0, 1.0], [1.0, -2.0, 1.0], [1.0, np.nan, 1.0], [1.0, 1.0]):
+        with pytest.raises(ValueError):
+            oracle.gain_correct(v, bad)
+
+
+def _gain_scene(seed=21, T=14, W=9, B=3):
+    rng = np.random.default_rng(seed)
+    R = rng.integers(40, 400, size=(T, W, B)).astype(np.float64)
+    g = rng.choice([0.5, 1.0, 2.0, 4.0], size=T)          # powers of two: g_t R_t is exact
+    return R, g, R * g[:, None, None]
+
+
+@pytest.mark.parametrize("mode", [oracle.EXCLUSIVE, oracle.INCLUSIVE])
+def test_line_gain_recovers_the_scene(mode):
+    """A line recorded at gain g_t holds g_t times the scene; after the correction the
+    scores are those of the scene itself, line by line and with every line's statistics."""
+    R, g, DN = _gain_scene()
+    d_ref, s_ref = orx.stream_rx(R, mode)
+    d_g, s_g = orx.stream_rx(DN, mode, line_gain=g)
+    np.testing.assert_array_equal(s_g, s_ref)
+    ok = s_ref == orx.OK
+    assert ok.sum() >= 10
+    np.testing.assert_allclose(d_g[ok], d_ref[ok], rtol=1e-11)
+    # without the correction the varying gain changes the scores
+    d_raw, _ = orx.stream_rx(DN, mode)
+    assert np.max(np.abs(d_raw[ok] - d_ref[ok]) / d_ref[ok]) > 1e-2
+
+
+def test_line_gain_precedes_the_band_calibration():
+    """Sec. 3.2 corrects the gain first and calibrates after: a per-band affine map after
+    the correction leaves the scores unchanged; the offset subtracted before the division
+    (the other order) does not."""
+    R, g, DN = _gain_scene(seed=22)
+    off = np.array([30.0, 55.0, 17.0])
+    bg = np.array([0.5, 2.0, 1.25])
+    d0, s0 = orx.stream_rx(DN, oracle.EXCLUSIVE, line_gain=g)
+    d1, s1 = orx.stream_rx(DN, oracle.EXCLUSIVE, line_gain=g, gain=bg, offset=off)
+    ok = s0 == orx.OK
+    np.testing.assert_array_equal(s0, s1)
+    np.testing.assert_allclose(d1[ok], d0[ok], rtol=1e-9)
+    d2, _ = orx.stream_rx(DN - off, oracle.EXCLUSIVE, line_gain=g)
+    assert np.max(np.abs(d2[ok] - d0[ok]) / d0[ok]) > 1e-3
