@@ -462,6 +462,8 @@ def main():
                          "0 = every line, the paper's detector")
     ap.add_argument("--lines", type=int, default=0, help="override the stream length (profiling captures)")
     ap.add_argument("--latency-lines", type=int, default=200)
+    ap.add_argument("--line-gain", action="store_true",
+                    help="push every line with its own gain (per-line gain correction)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32-arm", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
@@ -510,14 +512,23 @@ def main():
                            raw_bands=wl.get("raw_bands", 0), band_first=wl.get("band_first", 0),
                            band_bin=wl.get("band_bin", 1), factor_every=args.factor_every)
 
+    # per-line gain correction (Sec. 3.2): every line pushed with its own gain
+    line_gain = (np.random.default_rng(7).uniform(0.8, 1.25, size=T).astype(np.float32)
+                 if args.line_gain else None)
+
+    def push(det, x, mem):
+        if line_gain is None:
+            return hs.hsad_push_lines(det.ctx, x, T, mem)
+        return hs.hsad_push_lines_gain(det.ctx, x, line_gain, T, mem)
+
     def step(det, host=False):
         det.reset()
         if host:
-            rc, first = hs.hsad_push_lines(det.ctx, x_host, T, hs.HSAD_HOST)
+            rc, first = push(det, x_host, hs.HSAD_HOST)
             assert rc == hs.HSAD_OK, hs.hsad_last_error(det.ctx)
             rc = hs.hsad_scores(det.ctx, first, T, s_host, m_host, hs.HSAD_HOST, -1)
         else:
-            rc, first = hs.hsad_push_lines(det.ctx, x_dev, T, hs.HSAD_DEVICE)
+            rc, first = push(det, x_dev, hs.HSAD_DEVICE)
             assert rc == hs.HSAD_OK, hs.hsad_last_error(det.ctx)
             rc = hs.hsad_scores(det.ctx, first, T, s_dev, m_dev, hs.HSAD_DEVICE, -1)
         assert rc in (hs.HSAD_OK, hs.HSAD_E_NOT_READY), hs.hsad_status_string(rc)
@@ -686,6 +697,7 @@ def main():
                    "input": "uint16 12-bit DN", "batch_lines": wl["batch"],
                    "whitening": "triangular solve" if form else "explicit inverse",
                    **({"factor_every": args.factor_every} if args.factor_every > 1 else {}),
+                   **({"line_gain": "per-line gains U[0.8, 1.25] (hsad_push_lines_gain)"} if args.line_gain else {}),
                    **({"front_end": {"raw_bands": wl["raw_bands"], "band_first": wl["band_first"],
                                      "band_bin": wl["band_bin"]}} if wl.get("raw_bands") else {}),
                    "parallelism": f"replicas x{world} (independent streams)" if world > 1 else "single stream",

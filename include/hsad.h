@@ -151,6 +151,29 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out);
 int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem,
                     uint64_t* first_line_id);
 
+/* Push lines recorded at varying gain (Sec. 3.2, "Data Acquisition": the imager adjusts
+ * its gain for every line to avoid saturation, and the data is corrected for the varying
+ * gain before the radiometric calibration). As hsad_push_lines, plus line_gain: host
+ * memory, n_lines floats, line_gain[i] > 0 the gain of line i of this push (of the binned
+ * line when the context has a front end: binning commutes with the correction). The
+ * detector then works on u = DN / g_t: every line's statistics and scores are those of its
+ * values divided by its gain, and the per-band calibration still cancels from Eq. 1.
+ * The covariance sums stay exact integers per line; the correction is applied to them in
+ * FP64 when the running statistics are formed, and to the mean and the score of each line
+ * in the whitening (d = ||L^{-1}(DN - g (mu + c) + c)||^2 / g^2 with the integer shift c).
+ * The gains are copied before the call returns. Contexts mix both calls freely (a push
+ * without gains has gain 1 on every line). Supported for streamed statistics (EXCLUSIVE,
+ * INCLUSIVE) with HSAD_U16 input in the triangular-solve whitening form (HSAD_FP32, or
+ * HSAD_BF16); pushes with gains run without CUDA-graph replay. The first call allocates
+ * the per-batch gain buffers (Lmax x (4 Bp + 68) bytes of device memory, two pinned slots
+ * of Lmax x 32 bytes), outside the context's admission budget.
+ * Errors: those of hsad_push_lines; HSAD_E_INVALID for a NULL line_gain with n_lines > 0,
+ * a gain outside [2^-16, 2^16] or NaN (checked before anything is enqueued), a CUBE-mode,
+ * float-input or explicit-inverse context; HSAD_E_NOMEM if the gain buffers cannot be
+ * allocated. */
+int hsad_push_lines_gain(hsad_ctx* ctx, const void* lines, const float* line_gain, int64_t n_lines,
+                         int32_t mem, uint64_t* first_line_id);
+
 /* CUBE mode: close the current partial cube (fewer than cube_lines lines) and score
  * it as a cube of its own. No-op when no partial cube is open or in stream modes. */
 int hsad_flush(hsad_ctx* ctx);

@@ -121,6 +121,21 @@ struct hsad_ctx {
   int stage_idx = 0;
   void* cube_buf = nullptr;
   int32_t* h_small = nullptr;  // pinned scratch for small host->device values
+  // per-line gain correction (hsad_push_lines_gain), allocated on first use. A batch's
+  // per-line factors go through pinned slot h_gain[i] to device slot d_gain + i Lmax
+  // kGainStride (slots alternate): gain_ev[i] marks the copy out of h_gain[i] done,
+  // gfree_ev[i] the end of the last batch that read device slot i. d_gain_cur is the
+  // slot of the batch being enqueued (batch_gain set meanwhile); d_mgain [Lmax][Bp] and
+  // d_gscale [Lmax] hold the gain-corrected mean offsets and score scales of a whitening
+  // launch.
+  double* d_gain = nullptr;  // 2 x [Lmax][kGainStride]: g, 1 / g, 1 / g^2, 1 - g
+  double* d_gain_cur = nullptr;
+  float* d_mgain = nullptr;
+  float* d_gscale = nullptr;
+  double* h_gain[2] = {nullptr, nullptr};
+  cudaEvent_t gain_ev[2] = {nullptr, nullptr}, gfree_ev[2] = {nullptr, nullptr};
+  int gain_idx = 0;
+  bool batch_gain = false;
 
   // host-side stream state
   uint64_t next_line = 0;   // id of the next line to be pushed
@@ -320,6 +335,8 @@ void release(hsad_ctx* ctx) {
   }
   if (ctx->h2d_stream) cudaStreamSynchronize(ctx->h2d_stream);
   for (int i = 0; i < 2; ++i) {
+    if (ctx->gain_ev[i]) cudaEventDestroy(ctx->gain_ev[i]);
+    if (ctx->gfree_ev[i]) cudaEventDestroy(ctx->gfree_ev[i]);
     if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
     if (ctx->copy_ev[i]) cudaEventDestroy(ctx->copy_ev[i]);
     if (ctx->free_ev[i]) cudaEventDestroy(ctx->free_ev[i]);
@@ -674,8 +691,17 @@ int add_record(hsad_ctx* ctx, uint64_t first, uint64_t n) {
 }
 
 // K6: tensor cores (tcgen05, G by TMA) for the FP16 / BF16 forms, FFMA for FP32.
-int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o) {
+// gain_off: with a gain-corrected batch, the index of the launch's first line among the
+// batch's gains.
+int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o, int gain_off = 0) {
   cudaStream_t st = ctx->stream;
+  if (ctx->batch_gain) {
+    if (ctx->prec != P_BF16T && ctx->prec != P_FP32T) return fail(ctx, HSAD_E_INVALID, "gains need the triangular-solve form");
+    KL("gain_mean", launch_gain_mean(ctx->d_gain_cur + (size_t)kGainStride * gain_off, L, ctx->B, ctx->y0, ctx->c_int, factor_stride, o,
+                                     ctx->d_mgain, ctx->d_gscale, st, &ctx->lc));
+    o.m_line = ctx->d_mgain;
+    o.line_scale = ctx->d_gscale;
+  }
   if (ctx->prec == P_BF16T) {
     KL("whiten_score", launch_whiten_trsm((const uint16_t*)x, L, ctx->W, ctx->B, ctx->c_int, &ctx->gmap, ctx->y0,
                                           ctx->inv_s2, ctx->status, factor_stride, o, ctx->dev_err, st, &ctx->lc));
@@ -734,9 +760,11 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
     int rc = syrk(ctx, x, L, W, ctx->sigma + BB, BB, false);
     if (rc != HSAD_OK) return rc;
   }
+  const double* gain = ctx->batch_gain ? ctx->d_gain_cur : nullptr;
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, 1,
-                                       ctx->min_pix, ctx->status + 1, st, &ctx->lc, n0_dev));
-  KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc));
+                                       ctx->min_pix, ctx->status + 1, st, &ctx->lc, n0_dev, gain, ctx->c_int));
+  KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc, gain, ctx->s1_line,
+                                     ctx->c_int, W));
   KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L, B, ctx->prec,
                              (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
                              ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev, ctx->every, q0 + 1));
@@ -746,7 +774,7 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
     o1.every = ctx->every;
     o1.q0 = q0;
     if (dev) o1.slot0_dev = ctx->bdesc + 1;
-    int rc = whiten(ctx, (const char*)x + ctx->line_bytes, L - 1, 1, o1);
+    int rc = whiten(ctx, (const char*)x + ctx->line_bytes, L - 1, 1, o1, 1);
     if (rc != HSAD_OK) return rc;
   }
   // carry the factor of the last snapshot to slot 0 (every line: slot L, the statistics of all
@@ -818,7 +846,7 @@ int stream_batch_excl(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
   hsad_ctx::GraphEntry* ge = nullptr;
   // graphs for small batches only: their launch overhead is what a graph saves, and a
   // backlog (large batches of many sizes) must not turn into a capture per new size
-  if (ctx->use_graphs && !ctx->prof_on && ctx->n_stats > 0 && s >= 0 && L <= kGraphMaxLines)
+  if (ctx->use_graphs && !ctx->prof_on && !ctx->batch_gain && ctx->n_stats > 0 && s >= 0 && L <= kGraphMaxLines)
     ge = excl_graph(ctx, x, L, s, first);
   if (ge) {
     KL("set_batch_desc", launch_set_batch_desc(ctx->bdesc, ctx->n_stats,
@@ -850,9 +878,11 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
     int rc = syrk(ctx, x, L, W, ctx->sigma, (int64_t)B * B, false);
     if (rc != HSAD_OK) return rc;
   }
+  const double* gain = ctx->batch_gain ? ctx->d_gain_cur : nullptr;
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, incl,
-                        ctx->min_pix, ctx->status, st, &ctx->lc));
-  KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc));
+                        ctx->min_pix, ctx->status, st, &ctx->lc, nullptr, gain, ctx->c_int));
+  KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc, gain, ctx->s1_line,
+                                     ctx->c_int, W));
   KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, L, B, ctx->prec, ctx->wmat, ctx->y0,
                    ctx->inv_s2, ctx->status, ctx->n_stats, W, incl, st, &ctx->lc));
   {
@@ -921,9 +951,55 @@ bool is_device_ptr(const void* p, int device) {
 
 extern "C" {
 
-static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem);
+static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem, const float* gain);
+static int push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem, uint64_t* first_line_id,
+                      const float* gain);
 
 int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem, uint64_t* first_line_id) {
+  return push_lines(ctx, lines, n_lines, mem, first_line_id, nullptr);
+}
+
+int hsad_push_lines_gain(hsad_ctx* ctx, const void* lines, const float* line_gain, int64_t n_lines, int32_t mem,
+                         uint64_t* first_line_id) {
+  if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
+  if (ctx->failed) return HSAD_E_CUDA;
+  if (n_lines < 0) return fail(ctx, HSAD_E_INVALID, "n_lines < 0");
+  if (n_lines > 0 && !line_gain) return fail(ctx, HSAD_E_INVALID, "line_gain is NULL");
+  if (ctx->mode == HSAD_CUBE) return fail(ctx, HSAD_E_INVALID, "per-line gains need streamed statistics");
+  if (ctx->in_type != IN_U16) return fail(ctx, HSAD_E_INVALID, "per-line gains need uint16 input");
+  if (ctx->prec != P_BF16T && ctx->prec != P_FP32T)
+    return fail(ctx, HSAD_E_INVALID, "per-line gains need the triangular-solve whitening form (FP32 or BF16)");
+  for (int64_t i = 0; i < n_lines; ++i) {
+    const float g = line_gain[i];
+    if (!(g >= 1.0f / 65536.0f && g <= 65536.0f)) return fail(ctx, HSAD_E_INVALID, "gain outside [2^-16, 2^16]");
+  }
+  if (n_lines > 0 && !ctx->d_gain) {  // first use: per-batch gain buffers
+    DeviceGuard dg(ctx->device);
+    bool ok = true;
+    const int64_t L = ctx->Lmax;
+    ctx->d_gain = (double*)dalloc(ctx, 2 * L * kGainStride * 8, &ok);
+    ctx->d_mgain = (float*)dalloc(ctx, L * ctx->Bp * 4, &ok);
+    ctx->d_gscale = (float*)dalloc(ctx, L * 4, &ok);
+    for (int i = 0; i < 2 && ok; ++i) {
+      void* h = nullptr;
+      if (cudaHostAlloc(&h, (size_t)L * kGainStride * 8, cudaHostAllocDefault) != cudaSuccess) ok = false;
+      else ctx->host_allocs.push_back(h);
+      ctx->h_gain[i] = (double*)h;
+      if (ok && (cudaEventCreateWithFlags(&ctx->gain_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&ctx->gfree_ev[i], cudaEventDisableTiming) != cudaSuccess))
+        ok = false;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      ctx->d_gain = nullptr;  // the partial allocations stay with the context until destroy
+      return fail(ctx, HSAD_E_NOMEM, "allocation of the gain buffers failed");
+    }
+  }
+  return push_lines(ctx, lines, n_lines, mem, first_line_id, line_gain);
+}
+
+static int push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem, uint64_t* first_line_id,
+                      const float* gain) {
   if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
   if (ctx->failed) return HSAD_E_CUDA;
   if (n_lines < 0) return fail(ctx, HSAD_E_INVALID, "n_lines < 0");
@@ -937,7 +1013,7 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
     return fail(ctx, HSAD_E_INVALID, "lines is not device memory of this context's device");
   if (mem == HSAD_HOST && is_device_ptr(lines, ctx->device))
     return fail(ctx, HSAD_E_INVALID, "lines is device memory but mem = HSAD_HOST");
-  if (!ctx->fe) return push_impl(ctx, lines, n_lines, mem);
+  if (!ctx->fe) return push_impl(ctx, lines, n_lines, mem, gain);
   // front end: raw lines to the device (host pushes), binned on the context's stream, then
   // pushed as device lines; chunks of at most Lmax lines alternate between two buffers
   const char* raw = (const char*)lines;
@@ -952,7 +1028,7 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
     ctx->fe_idx ^= 1;
     KL("frontend", launch_frontend((const uint16_t*)src, k * ctx->W, ctx->cfg.raw_bands, ctx->cfg.band_first,
                                    ctx->cfg.band_bin, ctx->B, (uint16_t*)bin, ctx->stream, &ctx->lc));
-    const int rc = push_impl(ctx, bin, k, HSAD_DEVICE);
+    const int rc = push_impl(ctx, bin, k, HSAD_DEVICE, gain ? gain + done : nullptr);
     if (rc != HSAD_OK) return rc;
     done += k;
   }
@@ -968,7 +1044,7 @@ int hsad_push_lines(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t m
   return HSAD_OK;
 }
 
-static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem) {
+static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t mem, const float* gain) {
 
   // float input: reject non-finite values before anything is enqueued
   if (ctx->in_type == IN_F32) {
@@ -1060,15 +1136,41 @@ static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t 
       const int64_t into = (int64_t)(ctx->next_line % (uint64_t)CLr);
       take = std::min<int64_t>(take, CLr - into);
     }
+    // the batch's per-line gain factors into a pinned slot whose previous copy has landed
+    int gs = -1;
+    double* dg = nullptr;
+    if (gain) {
+      gs = ctx->gain_idx;
+      ctx->gain_idx ^= 1;
+      int rc = wait_event(ctx, ctx->gain_ev[gs], 10000);
+      if (rc != HSAD_OK) return rc == HSAD_E_NOT_READY ? fail(ctx, HSAD_E_TIMEOUT, "gain staging busy") : rc;
+      double* hg = ctx->h_gain[gs];
+      for (int64_t i = 0; i < take; ++i) {
+        const double gi = (double)gain[done + i];
+        hg[kGainStride * i] = gi;
+        hg[kGainStride * i + 1] = 1.0 / gi;
+        hg[kGainStride * i + 2] = 1.0 / (gi * gi);
+        hg[kGainStride * i + 3] = 1.0 - gi;
+      }
+      dg = ctx->d_gain + (size_t)gs * ctx->Lmax * kGainStride;
+    }
+    const size_t gbytes = (size_t)take * kGainStride * 8;
     const void* x;
     int s = -1;
     if (mem == HSAD_DEVICE) {
       x = src + done * ctx->line_bytes;
     } else if (pinned) {
       // DMA straight from the caller's pinned buffer, on its own stream, once the batch that
-      // last read d_stage[s] is done; the kernels wait for the copy
+      // last read d_stage[s] is done; the kernels wait for the copy. The gains go first on
+      // the same stream (the copy engine runs copies in order: queued on the kernels' stream
+      // instead, they would wait behind the next batch's lines).
       s = ctx->stage_idx;
       CK(cudaStreamWaitEvent(ctx->h2d_stream, ctx->free_ev[s], 0));
+      if (gain) {
+        CK(cudaStreamWaitEvent(ctx->h2d_stream, ctx->gfree_ev[gs], 0));
+        CK(cudaMemcpyAsync(dg, ctx->h_gain[gs], gbytes, cudaMemcpyHostToDevice, ctx->h2d_stream));
+        CK(cudaEventRecord(ctx->gain_ev[gs], ctx->h2d_stream));
+      }
       CK(cudaMemcpyAsync(ctx->d_stage[s], src + done * ctx->line_bytes, (size_t)(take * ctx->line_bytes),
                          cudaMemcpyHostToDevice, ctx->h2d_stream));
       CK(cudaEventRecord(ctx->copy_ev[s], ctx->h2d_stream));
@@ -1087,10 +1189,18 @@ static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t 
       ctx->stage_idx ^= 1;
       x = ctx->d_stage[s];
     }
+    if (gain && !pinned) {  // in order on the kernels' stream
+      CK(cudaMemcpyAsync(dg, ctx->h_gain[gs], gbytes, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaEventRecord(ctx->gain_ev[gs], ctx->stream));
+    }
     const uint64_t first = ctx->next_line;
     ctx->next_line += (uint64_t)take;
+    ctx->batch_gain = gain != nullptr;
+    ctx->d_gain_cur = dg;
     int rc = stream_batch(ctx, x, (int)take, first);
+    ctx->batch_gain = false;
     if (rc != HSAD_OK) return rc;
+    if (gain) CK(cudaEventRecord(ctx->gfree_ev[gs], ctx->stream));
     if (s >= 0) CK(cudaEventRecord(ctx->free_ev[s], ctx->stream));
     done += take;
     if (CLr > 0 && ctx->next_line % (uint64_t)CLr == 0) {  // statistics reset

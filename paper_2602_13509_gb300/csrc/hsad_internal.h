@@ -55,10 +55,17 @@ cudaError_t launch_syrk_simt(const void* x, int64_t n_groups, int64_t pix_per_gr
 
 // K3a: running per-band sums -> per-line mean offset m_t = S1_t / N_t (FP64), line
 // readiness, and the updated state S1.
+// Per-line gain correction (Sec. 3.2): gain[4 t .. 4 t + 3] = {g_t, 1 / g_t, 1 / g_t^2,
+// 1 - g_t} in FP64 (formed on the host, so that no kernel divides). Line t's values are
+// u = DN / g_t; with the fixed shift c its sums about c are (s1_t + W e_t) / g_t and
+// (s2_t + s1_t e_t^T + e_t s1_t^T + W e_t e_t^T) / g_t^2 with e_t = c (1 - g_t), formed in
+// FP64 from the exact integer sums (c_int: the shift, needed with gain).
+constexpr int kGainStride = 4;
 cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
                                int W, int L, int B, int inclusive, int64_t min_pixels,
                                int32_t* status, cudaStream_t st, LaunchCounter* lc,
-                               const int64_t* n0_dev = nullptr);
+                               const int64_t* n0_dev = nullptr, const double* gain = nullptr,
+                               const int32_t* c_int = nullptr);
 // Writes the per-batch values a replayed CUDA graph reads: desc[0] = pixels in the
 // statistics before the batch, desc[1] = ring slot of the batch's second line.
 cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1, cudaStream_t st,
@@ -66,8 +73,11 @@ cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1,
 
 // K3b: running raw sums S2_t (lower triangle) written in place over the per-line SYRK
 // results, and the updated state S2. The factor kernel turns them into Sigma_t.
+// gain, s1_line, c_int, W (optional): the per-line gain correction of launch_prefix_mean,
+// applied to each line's s2 before it is summed.
 cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int inclusive, cudaStream_t st,
-                              LaunchCounter* lc);
+                              LaunchCounter* lc, const double* gain = nullptr, const double* s1_line = nullptr,
+                              const int32_t* c_int = nullptr, int W = 0);
 
 // K2 (tcgen05, uint16 input): exact s2 = sum (x - c)(x - c)^T per group into the lower
 // triangle of out[g] (row stride B); groups above 4096 pixels need accumulate != 0
@@ -133,6 +143,11 @@ struct ScoreOut {
   // whose own slot j does not uses the last such slot at or below j (slot 0 if none)
   int every = 1;
   int q0 = 0;
+  // per-line gain correction (triangular-solve forms only): if set, line t of the launch is
+  // centred with m_line[t * Bp ..] instead of its factor slot's mean, and its score is
+  // multiplied by line_scale[t] = 1 / g_t^2 (see launch_gain_mean)
+  const float* m_line = nullptr;
+  const float* line_scale = nullptr;
 };
 #ifdef __CUDACC__
 __device__ __forceinline__ int64_t slot0_of(const ScoreOut& o) { return o.slot0_dev ? *o.slot0_dev : o.slot0; }
@@ -145,6 +160,14 @@ __device__ __forceinline__ int factor_slot(const ScoreOut& o, int factor_stride,
   return s > 0 ? s : 0;
 }
 #endif
+// Per-line gain correction of a whitening launch of L lines (gain + kGainStride t: line t of
+// the launch): the score of a pixel x of line t is ||L^{-1}(x/g - c - m_f)||^2
+// = ||L^{-1}(x' - m'_t)||^2 / g^2 with x' = x - c and m'_t = g (m_f + c) - c, m_f the mean
+// offset of line t's factor slot f (y0 of the triangular-solve form). Writes m'_t to
+// m_out[t * Bp ..] (zero past B) and 1 / g^2 to scale_out[t].
+cudaError_t launch_gain_mean(const double* gain, int L, int B, const float* y0, const int32_t* c_int,
+                             int factor_stride, ScoreOut out, float* m_out, float* scale_out, cudaStream_t st,
+                             LaunchCounter* lc);
 cudaError_t launch_whiten_score_simt(const void* x, int L, int W, int B, int in_type,
                                      const int32_t* c_int, const float* c_flt, int prec,
                                      const void* wmat, const float* y0, const float* inv_s2,

@@ -6,10 +6,12 @@
 // The data are shifted by an integer per-band value c (the rounded mean of the
 // first line after a reset), so for uint16 input every sum below is an exact
 // integer: s1 = sum (x - c), s2 = sum (x - c)(x - c)^T. The covariance then
-// follows as Sigma = (S2 - S1 S1^T / N) / (N - 1) (N-1 sample covariance), scaled
-// by the calibration gain D on both sides: Sigma_cal = D Sigma D, because the
-// calibrated spectrum is D (DN - offset) (Sec. 3.2, gain and radiometric
-// correction); the offset cancels in the centring.
+// follows as Sigma = (S2 - S1 S1^T / N) / (N - 1) (N-1 sample covariance). The
+// calibrated spectrum is D (DN - offset) (Sec. 3.2, radiometric correction), a per-band
+// affine map under which Eq. 1 is invariant, so the statistics stay in the DN frame.
+// With the per-line gain correction (Sec. 3.2: each line divided by its gain g_t before
+// the calibration) the prefix kernels turn each line's exact sums into the sums of
+// DN / g_t about c, in FP64.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -254,7 +256,8 @@ cudaError_t launch_syrk_simt(const void* x, int64_t n_groups, int64_t pix_per_gr
 __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* __restrict__ m_out,
                                    double* __restrict__ state_s1, int64_t n0_arg, int W, int L, int B,
                                    int inclusive, int64_t min_pixels, int32_t* __restrict__ status,
-                                   const int64_t* __restrict__ n0_dev) {
+                                   const int64_t* __restrict__ n0_dev, const double* __restrict__ gain,
+                                   const int32_t* __restrict__ c_int) {
   const int64_t n0 = n0_dev ? *n0_dev : n0_arg;
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -262,7 +265,11 @@ __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* _
     double carry = state_s1[b];
     for (int t0 = 0; t0 < L; t0 += 32) {
       const int t = t0 + lane;
-      const double v = t < L ? s1_line[(int64_t)t * B + b] : 0.0;
+      double v = t < L ? s1_line[(int64_t)t * B + b] : 0.0;
+      if (gain && t < L) {  // sum of (DN / g - c) = (s1 + W e) / g, e = c (1 - g)
+        const double* gt = gain + kGainStride * t;
+        v = fma((double)W * (double)c_int[b], gt[3], v) * gt[1];
+      }
       double x = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -287,9 +294,11 @@ __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* _
 
 cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
                                int W, int L, int B, int inclusive, int64_t min_pixels,
-                               int32_t* status, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev) {
+                               int32_t* status, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev,
+                               const double* gain, const int32_t* c_int) {
+  if (gain && !c_int) return cudaErrorInvalidValue;
   prefix_mean_kernel<<<(B + 7) / 8, 256, 0, st>>>(s1_line, m_out, state_s1, n0, W, L, B, inclusive,
-                                                  min_pixels, status, n0_dev);
+                                                  min_pixels, status, n0_dev, gain, c_int);
   HSAD_LAUNCH_CHECK(lc);
 }
 
@@ -309,7 +318,8 @@ cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1,
 // One FP64 add per entry and line; the covariance itself is formed by the factor
 // kernel, which reads each entry once anyway.
 __global__ void prefix_cov_kernel(double* __restrict__ buf, double* __restrict__ state_s2, int L, int B,
-                                  int inclusive) {
+                                  int inclusive, const double* __restrict__ gain,
+                                  const double* __restrict__ s1_line, const int32_t* __restrict__ c_int, int W) {
   const int64_t BB = (int64_t)B * B;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= BB) return;
@@ -321,6 +331,22 @@ __global__ void prefix_cov_kernel(double* __restrict__ buf, double* __restrict__
     double v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = (t0 + u < L) ? buf[(int64_t)(t0 + u) * BB + e] : 0.0;
+    if (gain) {
+      // sum of (DN/g - c)_i (DN/g - c)_j = (s2 + s1_i e_j + e_i s1_j + W e_i e_j) / g^2
+      const double ci = (double)c_int[i], cj = (double)c_int[j], wci = (double)W * ci;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + u;
+        if (t < L) {
+          const double* gt = gain + kGainStride * t;
+          const double h = gt[3];
+          const double* s1 = s1_line + (int64_t)t * B;
+          // h (s1_i c_j + c_i s1_j + W h c_i c_j)
+          const double x = fma(s1[i], cj, fma(ci, s1[j], wci * h * cj));
+          v[u] = fma(h, x, v[u]) * gt[2];
+        }
+      }
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (t0 + u >= L) break;
@@ -333,9 +359,40 @@ __global__ void prefix_cov_kernel(double* __restrict__ buf, double* __restrict__
 }
 
 cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int inclusive, cudaStream_t st,
-                              LaunchCounter* lc) {
+                              LaunchCounter* lc, const double* gain, const double* s1_line, const int32_t* c_int,
+                              int W) {
+  if (gain && (!s1_line || !c_int)) return cudaErrorInvalidValue;
   const int64_t BB = (int64_t)B * B;
-  prefix_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(buf, state_s2, L, B, inclusive);
+  prefix_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(buf, state_s2, L, B, inclusive, gain, s1_line,
+                                                                  c_int, W);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// Per-line gain correction of a whitening launch: m'_t = g (m_f + c) - c in FP64 from the
+// FP32 mean offset of line t's factor slot, and 1 / g^2.
+__global__ void gain_mean_kernel(const double* __restrict__ gain, int B, const float* __restrict__ y0,
+                                 const int32_t* __restrict__ c_int, int factor_stride, ScoreOut out,
+                                 float* __restrict__ m_out, float* __restrict__ scale_out) {
+  const int t = blockIdx.y;
+  const int Bp = pad64(B);
+  const int f = factor_slot(out, factor_stride, t);
+  const double g = gain[kGainStride * t], q = gain[kGainStride * t + 2];
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < Bp; b += gridDim.x * blockDim.x) {
+    float v = 0.f;
+    if (b < B) {
+      const double c = (double)c_int[b];
+      v = (float)(fma(g, (double)y0[(int64_t)f * Bp + b] + c, -c));
+    }
+    m_out[(int64_t)t * Bp + b] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) scale_out[t] = (float)q;
+}
+
+cudaError_t launch_gain_mean(const double* gain, int L, int B, const float* y0, const int32_t* c_int,
+                             int factor_stride, ScoreOut out, float* m_out, float* scale_out, cudaStream_t st,
+                             LaunchCounter* lc) {
+  if (L <= 0) return cudaSuccess;
+  gain_mean_kernel<<<dim3(1, L), 256, 0, st>>>(gain, B, y0, c_int, factor_stride, out, m_out, scale_out);
   HSAD_LAUNCH_CHECK(lc);
 }
 

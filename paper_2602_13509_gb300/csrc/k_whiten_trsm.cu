@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     tc::mbar_init(done, 1);
     tc::mbar_init_fence();
   }
-  const float* mf = m_all + (int64_t)f * Bp;
+  // mean offset: the factor slot's, or the gain-corrected one of this line
+  const float* mf = out.m_line ? out.m_line + (int64_t)t * Bp : m_all + (int64_t)f * Bp;
   for (int n = tid; n < Bp; n += TS_THREADS)
     cmS[n] = make_int2(0x4B400000 - (n < B ? c_int[n] : 0), __float_as_int(n < B ? mf[n] : 0.f));
   if (warp == 5) tc::tmem_alloc(tc::smem_u32(tslot), tcols);
@@ -293,7 +294,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     if (!ok) atomicExch(err, 1);
     const int p = p0 + r;
     if (p < W) {
-      const float dlt = ok ? dsum * inv_s2_all[f] : __int_as_float(0x7fc00000);
+      float dlt = ok ? dsum * inv_s2_all[f] : __int_as_float(0x7fc00000);
+      if (out.line_scale) dlt *= out.line_scale[t];
       out.scores[slot * W + p] = dlt;
       if (out.write_mask) out.mask[slot * W + p] = dlt > out.tau ? 1 : 0;
     }

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(TF_THREADS) whiten_trsm_simt_kernel(
   const int Bp = pad64(B), nkb = Bp / TF_N;
   const int npx = min(TF_P, W - p0);
   const float* H = H_all + (size_t)f * Bp * Bp;
-  const float* m = m_all + (int64_t)f * Bp;
+  // mean offset: the factor slot's, or the gain-corrected one of this line
+  const float* m = out.m_line ? out.m_line + (int64_t)t * Bp : m_all + (int64_t)f * Bp;
   const In* xt = x + ((int64_t)t * W + p0) * B;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tx = tid & 15, ty = tid >> 4;  // bands tx + 16 c, pixels ty*4..
@@ -188,12 +189,13 @@ __global__ void __launch_bounds__(TF_THREADS) whiten_trsm_simt_kernel(
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) dsum[r] += __shfl_xor_sync(0xffffffffu, dsum[r], o);
   if (tx == 0) {
-    const float is2 = inv_s2_all[f];
+    const float is2 = inv_s2_all[f], ls = out.line_scale ? out.line_scale[t] : 1.f;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int p = p0 + ty * 4 + r;
       if (p < W) {
-        const float d = dsum[r] * is2;
+        float d = dsum[r] * is2;
+        if (out.line_scale) d *= ls;
         out.scores[slot * W + p] = d;
         if (out.write_mask) out.mask[slot * W + p] = d > out.tau ? 1 : 0;
       }

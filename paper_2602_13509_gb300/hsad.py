@@ -61,6 +61,7 @@ def _load():
         "hsad_config_init": (C.c_int, [C.POINTER(hsad_config)]),
         "hsad_create": (C.c_int, [C.POINTER(hsad_config), C.POINTER(P)]),
         "hsad_push_lines": (C.c_int, [P, P, C.c_int64, C.c_int32, C.POINTER(C.c_uint64)]),
+        "hsad_push_lines_gain": (C.c_int, [P, P, P, C.c_int64, C.c_int32, C.POINTER(C.c_uint64)]),
         "hsad_flush": (C.c_int, [P]),
         "hsad_scores": (C.c_int, [P, C.c_uint64, C.c_int64, P, P, C.c_int32, C.c_int32]),
         "hsad_scores_tx": (C.c_int, [P, C.c_uint64, C.c_int64, P, C.POINTER(C.c_float), C.c_int32, C.c_int32]),
@@ -161,6 +162,14 @@ def hsad_push_lines(ctx, lines, n_lines: int, mem: int):
     """Returns ``(status, first_line_id)``."""
     first = C.c_uint64(0)
     rc = _lib.hsad_push_lines(ctx, _ptr(lines), int(n_lines), int(mem), C.byref(first))
+    return rc, first.value
+
+
+def hsad_push_lines_gain(ctx, lines, line_gain, n_lines: int, mem: int):
+    """Push lines recorded at per-line gains ``line_gain`` (host float32, one per line).
+    Returns ``(status, first_line_id)``."""
+    first = C.c_uint64(0)
+    rc = _lib.hsad_push_lines_gain(ctx, _ptr(lines), _ptr(line_gain), int(n_lines), int(mem), C.byref(first))
     return rc, first.value
 
 
@@ -388,11 +397,19 @@ class Detector:
             raise HsadError(rc, hsad_last_error(None))
         self.width, self.bands = self.cfg.width, self.cfg.bands
 
-    def push(self, lines, mem=None) -> int:
-        """Push lines ([n, W, B] numpy array or contiguous tensor); returns the first line id."""
+    def push(self, lines, mem=None, gains=None) -> int:
+        """Push lines ([n, W, B] numpy array or contiguous tensor); returns the first line id.
+        ``gains``: optional per-line gains (n floats; ``hsad_push_lines_gain``)."""
         if mem is None:
             mem = HSAD_DEVICE if (hasattr(lines, "is_cuda") and lines.is_cuda) else HSAD_HOST
-        rc, first = hsad_push_lines(self.ctx, lines, lines.shape[0], mem)
+        if gains is None:
+            rc, first = hsad_push_lines(self.ctx, lines, lines.shape[0], mem)
+        else:
+            import numpy as np
+            g = np.ascontiguousarray(np.asarray(gains, dtype=np.float32).reshape(-1))
+            if g.shape[0] != lines.shape[0]:
+                raise ValueError("one gain per line")
+            rc, first = hsad_push_lines_gain(self.ctx, lines, g, lines.shape[0], mem)
         if rc != HSAD_OK:
             raise HsadError(rc, hsad_last_error(self.ctx))
         return first
