@@ -19,6 +19,7 @@ from .rx import (  # noqa: F401
     cholesky_lower,
     encode_tx,
     forward_substitution,
+    forget_weights,
     frontend,
     gain_correct,
     global_rx,

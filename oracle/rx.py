@@ -36,6 +36,12 @@ What it computes, and where the paper says so:
 * Front end, Sec. 3.2 ("Data Acquisition"): the out-of-specification bands are
   discarded and four consecutive bands are summed into one. Reading: keep raw bands
   [first, first + bin * B) and sum groups of ``bin`` consecutive bands (integers, exact).
+* Exponential forgetting (an extension; the paper does not define one, and names drift
+  and cloud shadow as open problems for the statistics in Sec. 6.1). Reading: with a
+  factor lam in (0, 1], every pixel of a window line tau counts with frequency weight
+  lam^(b - 1 - tau), b the end of the window (the newest line weighs 1); N = sum of the
+  weights, mu the weighted mean, Sigma = sum_p w_p (x_p - mu)(x_p - mu)^T / (N - 1), and a
+  line is scored once N >= max(B + 1, warmup_pixels). lam = 1 is the unweighted window.
 * Per-line gain correction, Sec. 3.2 ("Data Acquisition"): the imager's gain is changed
   for every line to avoid saturation, and the data is corrected for the varying gain
   before the radiometric calibration. Reading: one positive scalar g_t per line, every
@@ -190,37 +196,53 @@ def statistics_lines(t: int, mode: str, cube_lines: int, n_lines: int, every: in
     raise ValueError(mode)
 
 
-def _stats_over_lines(lines: LineSource, a: int, b: int, gain, offset, chunk: int):
-    """Two-pass mean and N-1 covariance over the pixels of lines [a, b).
+def forget_weights(a: int, b: int, lam: float) -> np.ndarray:
+    """Per-line weights of window lines [a, b) under exponential forgetting: line tau
+    weighs lam^(b - 1 - tau) (the newest line 1). Pinned by exact brute force on
+    replicated pixels (tests/test_oracle_pins.py)."""
+    return np.asarray([float(lam) ** (b - 1 - tau) for tau in range(a, b)], dtype=np.float64)
+
+
+def _stats_over_lines(lines: LineSource, a: int, b: int, gain, offset, chunk: int, lam: float = 1.0):
+    """Two-pass mean and N-1 covariance over the pixels of lines [a, b), every pixel of
+    line tau weighted by forget_weights (all 1 for lam = 1); N is the sum of the weights.
 
     The sums run over line chunks only to bound host memory; each pass is the
     same sum as the unchunked definition, in a different rounding order.
     """
-    s1, n = None, 0
+    w = forget_weights(a, b, lam)
+    s1, n = None, 0.0
     for t0 in range(a, b, chunk):
         X = calibrate(_fetch(lines, t0, min(chunk, b - t0)), gain, offset)
-        X = X.reshape(-1, X.shape[-1])
-        s1 = X.sum(axis=0) if s1 is None else s1 + X.sum(axis=0)
-        n += X.shape[0]
+        wl = w[t0 - a:t0 - a + X.shape[0]]
+        # lam = 1: the plain sum (every weight is 1)
+        s = X.reshape(-1, X.shape[-1]).sum(axis=0) if lam == 1.0 else np.einsum("l,lwb->b", wl, X)
+        s1 = s if s1 is None else s1 + s
+        n += float(wl.sum()) * X.shape[1]
     mu = s1 / n
     m2 = None
     for t0 in range(a, b, chunk):
         X = calibrate(_fetch(lines, t0, min(chunk, b - t0)), gain, offset)
-        D = X.reshape(-1, X.shape[-1]) - mu
-        m2 = D.T @ D if m2 is None else m2 + D.T @ D
+        wl = w[t0 - a:t0 - a + X.shape[0]]
+        D = (X - mu).reshape(-1, X.shape[-1])
+        c = D.T @ D if lam == 1.0 else (D * np.repeat(wl, X.shape[1])[:, None]).T @ D
+        m2 = c if m2 is None else m2 + c
     return mu, m2 / (n - 1), n
 
 
 def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines: int = 0,
                    warmup_pixels: int = 0, gain=None, offset=None, n_lines: int | None = None,
-                   chunk: int = 64, every: int = 1, line_gain=None):
+                   chunk: int = 64, every: int = 1, line_gain=None, forget: float = 1.0):
     """Scores of line t under the given statistics window.
 
     Returns ``(delta [W], status)`` with status OK, NOT_READY (too few pixels;
     delta is NaN) or NOT_PD (covariance not positive definite; delta is NaN).
     ``line_gain`` (one gain per line of ``lines``): every line is gain-corrected
-    (``gain_correct``) before the calibration.
+    (``gain_correct``) before the calibration. ``forget`` in (0, 1]: exponential forgetting
+    of the streamed window (``forget_weights``).
     """
+    if not (0.0 < forget <= 1.0) or (forget < 1.0 and (mode == CUBE or every > 1)):
+        raise ValueError("forgetting needs 0 < forget <= 1, streamed statistics and no cadence")
     if line_gain is not None:
         raw, g = lines, np.asarray(line_gain, dtype=np.float64).reshape(-1)
 
@@ -234,10 +256,10 @@ def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines:
     if n_lines is None:
         n_lines = (t + 1) if callable(lines) else lines.shape[0]
     a, b = statistics_lines(t, mode, cube_lines, n_lines, every)
-    n_pix = (b - a) * W
+    n_pix = float(forget_weights(a, b, forget).sum()) * W
     if n_pix < max(B + 1, int(warmup_pixels)):
         return np.full(W, np.nan), NOT_READY
-    mu, Sigma, _ = _stats_over_lines(lines, a, b, gain, offset, chunk)
+    mu, Sigma, _ = _stats_over_lines(lines, a, b, gain, offset, chunk, forget)
     try:
         return rx_scores(line, mu, Sigma), OK
     except NotPositiveDefinite:
@@ -245,14 +267,15 @@ def stream_rx_line(lines: LineSource, t: int, mode: str = EXCLUSIVE, cube_lines:
 
 
 def stream_rx(lines: np.ndarray, mode: str = EXCLUSIVE, cube_lines: int = 0, warmup_pixels: int = 0,
-              gain=None, offset=None, every: int = 1, line_gain=None):
+              gain=None, offset=None, every: int = 1, line_gain=None, forget: float = 1.0):
     """Scores of every line of ``lines`` [T, W, B]: ``(delta [T, W], status [T])``."""
     T, W, B = lines.shape
     delta = np.full((T, W), np.nan)
     status = np.zeros(T, dtype=np.int32)
     for t in range(T):
         delta[t], status[t] = stream_rx_line(lines, t, mode, cube_lines, warmup_pixels,
-                                             gain, offset, n_lines=T, every=every, line_gain=line_gain)
+                                             gain, offset, n_lines=T, every=every, line_gain=line_gain,
+                                             forget=forget)
     return delta, status
 
 

@@ -139,3 +139,28 @@ def test_gain_correction_pins_reject_mutant(monkeypatch, mutant):
     monkeypatch.setattr(orx, "gain_correct", mutant)
     monkeypatch.setattr(oracle, "gain_correct", mutant)
     assert fails(), f"mutant {mutant.__name__} of gain_correct was not caught"
+
+
+def _weights_age_off_by_one(a, b, lam):       # the newest line already decayed once
+    return np.asarray([float(lam) ** (b - tau) for tau in range(a, b)], dtype=np.float64)
+
+
+def _weights_reversed(a, b, lam):             # the oldest line weighs 1
+    return np.asarray([float(lam) ** (tau - a) for tau in range(a, b)], dtype=np.float64)
+
+
+@pytest.mark.parametrize("mutant", [_weights_age_off_by_one, _weights_reversed])
+def test_forgetting_pin_rejects_mutant(monkeypatch, mutant):
+    import tests.test_oracle_pins as pins
+
+    def fails():
+        try:
+            pins.test_forgetting_equals_replicated_pixels_exactly(oracle.EXCLUSIVE)
+        except AssertionError:
+            return True
+        return False
+
+    assert not fails(), "pins must accept the unmodified oracle"
+    monkeypatch.setattr(orx, "forget_weights", mutant)
+    monkeypatch.setattr(oracle, "forget_weights", mutant)
+    assert fails(), f"mutant {mutant.__name__} of forget_weights was not caught"

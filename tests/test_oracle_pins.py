@@ -430,3 +430,53 @@ def test_line_gain_precedes_the_band_calibration():
     np.testing.assert_allclose(d1[ok], d0[ok], rtol=1e-9)
     d2, _ = orx.stream_rx(DN - off, oracle.EXCLUSIVE, line_gain=g)
     assert np.max(np.abs(d2[ok] - d0[ok]) / d0[ok]) > 1e-3
+
+
+# ------------------------------------------------------------------ exponential forgetting (extension)
+@pytest.mark.parametrize("mode", [oracle.EXCLUSIVE, oracle.INCLUSIVE])
+def test_forgetting_equals_replicated_pixels_exactly(mode):
+    """With lam = 1/2 the weights of the window's lines are 2^-age; scaling them by 2^K makes
+    them integers, i.e. line tau's pixels repeated 2^(K - age) times. The weighted mean is
+    that of the repeated set, and the weighted N-1 covariance is the repeated set's times
+    (N' - 1) / (N' - 2^K) (N' repeated pixels): checked against exact rational arithmetic."""
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    T, W, B = 6, 3, 2
+    lines = rng.integers(-9, 10, size=(T, W, B)).astype(np.float64)
+    d, st = orx.stream_rx(lines, mode, forget=0.5)
+    checked = 0
+    for t in range(T):
+        a, b = orx.statistics_lines(t, mode, 0, T)
+        K = b - 1 - a                                   # the oldest line's age
+        rows = []
+        for tau in range(a, b):
+            rows += [list(p) for p in lines[tau]] * (2 ** (K - (b - 1 - tau)))
+        n_w = Fraction(W) * sum(Fraction(1, 2 ** (b - 1 - tau)) for tau in range(a, b))
+        if n_w < B + 1:
+            assert st[t] == orx.NOT_READY and np.isnan(d[t]).all()
+            continue
+        ex = exact_scores(rows, lines[t].tolist())
+        n_rep = len(rows)
+        f = Fraction(n_rep - 2 ** K, n_rep - 1)
+        ref = np.array([float(v * f) for v in ex])
+        np.testing.assert_allclose(d[t], ref, rtol=1e-11)
+        checked += 1
+    assert checked >= 3
+
+
+def test_forgetting_limits():
+    rng = np.random.default_rng(18)
+    lines = rng.normal(size=(9, 5, 3)) + 4.0
+    d1, s1 = orx.stream_rx(lines, oracle.EXCLUSIVE)
+    df, sf = orx.stream_rx(lines, oracle.EXCLUSIVE, forget=1.0)
+    np.testing.assert_array_equal(s1, sf)
+    np.testing.assert_array_equal(d1, df)
+    # N saturates at W / (1 - lam) = 4 = B + 1 from below: no line is ever ready
+    _, s = orx.stream_rx(rng.normal(size=(30, 2, 3)), oracle.EXCLUSIVE, forget=0.5)
+    assert (s == orx.NOT_READY).all()
+    np.testing.assert_allclose(oracle.forget_weights(3, 7, 0.5), [0.125, 0.25, 0.5, 1.0])
+    for bad in (dict(forget=0.0), dict(forget=1.5), dict(forget=0.9, every=2)):
+        with pytest.raises(ValueError):
+            orx.stream_rx(lines, oracle.EXCLUSIVE, **bad)
+    with pytest.raises(ValueError):
+        orx.stream_rx(lines, oracle.CUBE, cube_lines=9, forget=0.9)
