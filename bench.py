@@ -462,6 +462,8 @@ def main():
                          "0 = every line, the paper's detector")
     ap.add_argument("--lines", type=int, default=0, help="override the stream length (profiling captures)")
     ap.add_argument("--latency-lines", type=int, default=200)
+    ap.add_argument("--forget", type=float, default=0.0,
+                    help="exponential forgetting factor of the statistics (0 = off)")
     ap.add_argument("--line-gain", action="store_true",
                     help="push every line with its own gain (per-line gain correction)")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -510,7 +512,7 @@ def main():
         return hs.Detector(width=W, bands=B, stats_mode="exclusive", precision=prec, gain=sc.gain,
                            offset=sc.offset, max_batch_lines=wl["batch"], result_lines=T, device=local,
                            raw_bands=wl.get("raw_bands", 0), band_first=wl.get("band_first", 0),
-                           band_bin=wl.get("band_bin", 1), factor_every=args.factor_every)
+                           band_bin=wl.get("band_bin", 1), factor_every=args.factor_every, forget=args.forget)
 
     # per-line gain correction (Sec. 3.2): every line pushed with its own gain
     line_gain = (np.random.default_rng(7).uniform(0.8, 1.25, size=T).astype(np.float32)
@@ -698,6 +700,7 @@ def main():
                    "whitening": "triangular solve" if form else "explicit inverse",
                    **({"factor_every": args.factor_every} if args.factor_every > 1 else {}),
                    **({"line_gain": "per-line gains U[0.8, 1.25] (hsad_push_lines_gain)"} if args.line_gain else {}),
+                   **({"forget": args.forget} if 0.0 < args.forget < 1.0 else {}),
                    **({"front_end": {"raw_bands": wl["raw_bands"], "band_first": wl["band_first"],
                                      "band_bin": wl["band_bin"]}} if wl.get("raw_bands") else {}),
                    "parallelism": f"replicas x{world} (independent streams)" if world > 1 else "single stream",

@@ -118,6 +118,17 @@ typedef struct {
    * last such snapshot, lines [r, r + k floor((t - r) / k)): k times fewer factorisations,
    * with statistics up to k - 1 lines old. */
   int32_t factor_every;
+  /* Exponential forgetting (an extension; the paper does not define one, and names drift and
+   * cloud shadow as open problems for the statistics, Sec. 6.1): 0 or 1 (default) keeps every
+   * line since the last reset at full weight; forget in (0, 1) (EXCLUSIVE or INCLUSIVE, not
+   * with factor_every > 1) weighs the pixels of a line forget^age, age = the number of window
+   * lines newer than it (the newest line weighs 1). The mean is the weighted mean and the
+   * covariance the weighted centred sum over (N - 1), N = the sum of the weights, which also
+   * replaces the pixel count of the warm-up rule: the window saturates at W / (1 - forget)
+   * pixels, so a forget with W / (1 - forget) < max(B + 1, warmup_pixels) scores no line.
+   * The running sums are then FP64 instead of exact integers; statistics export and import
+   * (hsad_get_stats, hsad_set_stats) and CUDA-graph replay are not available. */
+  float forget;
 } hsad_config;
 
 /* Fill *cfg with defaults: U16, FP32, EXCLUSIVE, cube_lines 0, ABS threshold
@@ -233,7 +244,8 @@ int hsad_reset(hsad_ctx* ctx);
  * uint16 input, cast to double; float input: the float shift); s1[B] = sum (x - c);
  * s2[B*B] = sum (x - c)(x - c)^T, row-major, lower triangle (row >= column) valid.
  * All arguments are host arrays and may be NULL. For uint16 input every value is an
- * exact integer. Synchronises the context's stream (bounded, 10 s). */
+ * exact integer. Synchronises the context's stream (bounded, 10 s). HSAD_E_INVALID for a
+ * context with forgetting (its sums are weighted, not counts of pixels). */
 int hsad_get_stats(hsad_ctx* ctx, int64_t* n_pixels, double* shift, double* s1, double* s2);
 
 /* Import running statistics exported by hsad_get_stats (checkpoint / resume of a stream;
@@ -244,8 +256,8 @@ int hsad_get_stats(hsad_ctx* ctx, int64_t* n_pixels, double* shift, double* s1, 
  * lines in one stream (for uint16 input the sums are exact, so the scores are bitwise the
  * same); EXCLUSIVE mode also rebuilds the carried factor here (enqueued on the context's
  * stream). Line ids and the reset schedule (cube_lines) count from 0 in the new context.
- * Returns HSAD_E_INVALID for CUBE mode, a context already in use, NULL arrays or a bad
- * shift. */
+ * Returns HSAD_E_INVALID for CUBE mode, a context with forgetting, a context already in
+ * use, NULL arrays or a bad shift. */
 int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const double* s1, const double* s2);
 
 /* Block until all work enqueued on the context has finished (bounded by timeout_ms,

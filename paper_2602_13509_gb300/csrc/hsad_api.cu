@@ -140,6 +140,11 @@ struct hsad_ctx {
   // host-side stream state
   uint64_t next_line = 0;   // id of the next line to be pushed
   int64_t n_stats = 0;      // pixels in the running statistics (stream modes)
+  // exponential forgetting (lam < 1): the window's weight after the last pushed line and the
+  // per-line weights of a batch [Lmax] (device)
+  double lam = 1.0;
+  double n_eff = 0.0;
+  double* d_nline = nullptr;
   int64_t cube_fill = 0;    // lines in the open cube (CUBE mode)
   uint64_t cube_first = 0;  // id of the open cube's first line
   int64_t last_cube_lines = 0;  // lines of the most recently scored cube
@@ -271,6 +276,7 @@ int64_t plan_bytes(const hsad_ctx* c) {
   int64_t b = 0;
   b += B * 4 + B * 4 + B * 8 + B * B * 8;                        // c (int, float), S1, S2
   b += Ls * B * 8 * 2;                                           // s1_line, m_line
+  if (c->lam != 1.0) b += Ls * 8;                                // forgetting weights per line
   b += Lf * B * B * 8 * 2;                                       // sigma, inv
   b += Lf * Bp * Bp * 4 + Lf * Bp * 4 + Lf * 4 + Ls * 4;        // wmat, y0, inv_s2, status
   b += c->ring * c->W * 5 + c->ring * 4 + 64;                    // result ring
@@ -309,6 +315,11 @@ int validate(const hsad_config* cfg, std::string* why) {
   if ((int64_t)cfg->width * cfg->bands > (int64_t)1 << 31) return bad("line too large");
   if (cfg->factor_every < 0 || cfg->factor_every > 64) return bad("factor_every must be in [0, 64]");
   if (cfg->factor_every > 1 && cfg->stats_mode != HSAD_EXCLUSIVE) return bad("factor_every > 1 needs EXCLUSIVE mode");
+  if (!(cfg->forget >= 0.f && cfg->forget <= 1.f)) return bad("forget must be in [0, 1]");
+  if (cfg->forget > 0.f && cfg->forget < 1.f) {
+    if (cfg->stats_mode == HSAD_CUBE) return bad("forgetting needs streamed statistics");
+    if (cfg->factor_every > 1) return bad("forgetting and factor_every > 1 do not combine");
+  }
   if (cfg->raw_bands < 0) return bad("raw_bands must be >= 0");
   if (cfg->raw_bands > 0) {
     if (cfg->in_dtype != HSAD_U16) return bad("the front end (raw_bands > 0) needs HSAD_U16 input");
@@ -510,7 +521,8 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->prec = cfg->precision == HSAD_FP32 ? fp32_form(cube)
               : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type, cube)
                                             : P_FP16;
-  ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE;
+  ctx->lam = (cfg->forget > 0.f && cfg->forget < 1.f) ? (double)cfg->forget : 1.0;
+  ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE && ctx->lam == 1.0;
   ctx->mode = cfg->stats_mode;
   ctx->elem = ctx->in_type == IN_U16 ? 2 : 4;
   ctx->line_elems = (int64_t)ctx->W * ctx->B;
@@ -582,6 +594,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->state_s1 = (double*)dalloc(ctx, B * 8, &ok);
   ctx->state_s2 = (double*)dalloc(ctx, B * B * 8, &ok);
   ctx->s1_line = (double*)dalloc(ctx, Ls * B * 8, &ok);
+  if (ctx->lam != 1.0) ctx->d_nline = (double*)dalloc(ctx, Ls * 8, &ok);
   ctx->m_line = (double*)dalloc(ctx, Ls * B * 8, &ok);
   ctx->sigma = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
   ctx->inv = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
@@ -761,13 +774,16 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
     if (rc != HSAD_OK) return rc;
   }
   const double* gain = ctx->batch_gain ? ctx->d_gain_cur : nullptr;
+  const double* n_line = ctx->lam != 1.0 ? ctx->d_nline : nullptr;
+  if (n_line) KL("forget_n", launch_forget_n(ctx->n_eff, ctx->lam, W, L, 1, ctx->d_nline, st, &ctx->lc));
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, 1,
-                                       ctx->min_pix, ctx->status + 1, st, &ctx->lc, n0_dev, gain, ctx->c_int));
+                                       ctx->min_pix, ctx->status + 1, st, &ctx->lc, n0_dev, gain, ctx->c_int,
+                                       ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc, gain, ctx->s1_line,
-                                     ctx->c_int, W));
+                                     ctx->c_int, W, ctx->lam));
   KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L, B, ctx->prec,
                              (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
-                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev, ctx->every, q0 + 1));
+                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev, ctx->every, q0 + 1, n_line));
   if (L > 1) {
     ScoreOut o1 = score_out(ctx, first + 1, true);
     o1.factor_base = 1;
@@ -862,6 +878,7 @@ int stream_batch_excl(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
     if (rc != HSAD_OK) return rc;
   }
   ctx->n_stats += (int64_t)L * W;
+  if (ctx->lam != 1.0) ctx->n_eff = forget_weight(ctx->n_eff, ctx->lam, W, L);
   return HSAD_OK;
 }
 
@@ -879,17 +896,20 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
     if (rc != HSAD_OK) return rc;
   }
   const double* gain = ctx->batch_gain ? ctx->d_gain_cur : nullptr;
+  const double* n_line = ctx->lam != 1.0 ? ctx->d_nline : nullptr;
+  if (n_line) KL("forget_n", launch_forget_n(ctx->n_eff, ctx->lam, W, L, incl, ctx->d_nline, st, &ctx->lc));
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, incl,
-                        ctx->min_pix, ctx->status, st, &ctx->lc, nullptr, gain, ctx->c_int));
+                        ctx->min_pix, ctx->status, st, &ctx->lc, nullptr, gain, ctx->c_int, ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc, gain, ctx->s1_line,
-                                     ctx->c_int, W));
+                                     ctx->c_int, W, ctx->lam));
   KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, L, B, ctx->prec, ctx->wmat, ctx->y0,
-                   ctx->inv_s2, ctx->status, ctx->n_stats, W, incl, st, &ctx->lc));
+                   ctx->inv_s2, ctx->status, ctx->n_stats, W, incl, st, &ctx->lc, nullptr, 1, 0, n_line));
   {
     int rc = whiten(ctx, x, L, 1, score_out(ctx, first, true));
     if (rc != HSAD_OK) return rc;
   }
   ctx->n_stats += (int64_t)L * W;
+  if (ctx->lam != 1.0) ctx->n_eff = forget_weight(ctx->n_eff, ctx->lam, W, L);
   return add_record(ctx, first, (uint64_t)L);
 }
 
@@ -1207,6 +1227,7 @@ static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t 
       CK(cudaMemsetAsync(ctx->state_s1, 0, (size_t)ctx->B * 8, ctx->stream));
       CK(cudaMemsetAsync(ctx->state_s2, 0, (size_t)ctx->B * ctx->B * 8, ctx->stream));
       ctx->n_stats = 0;
+      ctx->n_eff = 0.0;
     }
   }
   // the caller may reuse its buffer once the copies from it have landed
@@ -1371,6 +1392,7 @@ int hsad_reset(hsad_ctx* ctx) {
   ctx->records.clear();
   ctx->next_line = 0;
   ctx->n_stats = 0;
+  ctx->n_eff = 0.0;
   ctx->cube_fill = 0;
   ctx->cube_first = 0;
   ctx->last_cube_lines = 0;
@@ -1380,6 +1402,7 @@ int hsad_reset(hsad_ctx* ctx) {
 int hsad_get_stats(hsad_ctx* ctx, int64_t* n_pixels, double* shift, double* s1, double* s2) {
   if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
   if (ctx->failed) return HSAD_E_CUDA;
+  if (ctx->lam != 1.0) return fail(ctx, HSAD_E_INVALID, "no statistics export with forgetting");
   DeviceGuard dg(ctx->device);
   int rc = hsad_synchronize(ctx, 10000);
   if (rc != HSAD_OK) return rc;
@@ -1411,6 +1434,7 @@ int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const d
   if (!ctx) return fail(nullptr, HSAD_E_INVALID, "ctx is NULL");
   if (ctx->failed) return HSAD_E_CUDA;
   if (ctx->mode == HSAD_CUBE) return fail(ctx, HSAD_E_INVALID, "statistics import is for stream modes");
+  if (ctx->lam != 1.0) return fail(ctx, HSAD_E_INVALID, "no statistics import with forgetting");
   if (!shift || !s1 || !s2 || n_pixels < 0) return fail(ctx, HSAD_E_INVALID, "NULL array or negative n_pixels");
   if (ctx->every > 1 && (n_pixels % ctx->W != 0 || (n_pixels / ctx->W) % ctx->every != 0))
     return fail(ctx, HSAD_E_INVALID, "with a factorisation cadence the import must be at a snapshot (lines a multiple of it)");

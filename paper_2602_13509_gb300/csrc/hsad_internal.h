@@ -65,7 +65,14 @@ cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* sta
                                int W, int L, int B, int inclusive, int64_t min_pixels,
                                int32_t* status, cudaStream_t st, LaunchCounter* lc,
                                const int64_t* n0_dev = nullptr, const double* gain = nullptr,
-                               const int32_t* c_int = nullptr);
+                               const int32_t* c_int = nullptr, double lam = 1.0, const double* n_line = nullptr);
+// Exponential forgetting (an extension: lam in (0, 1), every line's sums decay by lam per
+// later line): n_line[t] = the forgetting weight of the window after t + incl more lines,
+// lam^k n_prev + W (1 - lam^k) / (1 - lam) with k = t + incl; the prefix kernels take lam
+// (running sums R_t = lam R_{t-1} + line t) and n_line in place of the pixel count.
+cudaError_t launch_forget_n(double n_prev, double lam, int W, int L, int incl, double* n_line, cudaStream_t st,
+                            LaunchCounter* lc);
+double forget_weight(double n_prev, double lam, int W, int64_t k);
 // Writes the per-batch values a replayed CUDA graph reads: desc[0] = pixels in the
 // statistics before the batch, desc[1] = ring slot of the batch's second line.
 cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1, cudaStream_t st,
@@ -77,7 +84,7 @@ cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1,
 // applied to each line's s2 before it is summed.
 cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int inclusive, cudaStream_t st,
                               LaunchCounter* lc, const double* gain = nullptr, const double* s1_line = nullptr,
-                              const int32_t* c_int = nullptr, int W = 0);
+                              const int32_t* c_int = nullptr, int W = 0, double lam = 1.0);
 
 // K2 (tcgen05, uint16 input): exact s2 = sum (x - c)(x - c)^T per group into the lower
 // triangle of out[g] (row stride B); groups above 4096 pixels need accumulate != 0
@@ -107,7 +114,8 @@ cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, 
 cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m,
                                 int L, int B, int prec, void* wmat, float* y0, float* inv_s2, int32_t* status,
                                 int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
-                                const int64_t* n0_dev, int every = 1, int q_off = 0);
+                                const int64_t* n0_dev, int every = 1, int q_off = 0,
+                                const double* n_line = nullptr);
 // Measure the launch shapes for batch-size buckets 1, 2, 4, ..., max_lines and keep the
 // fastest per bucket for launch_factor (current device). report: rows of (bucket, cl, ft,
 // ms), up to cap rows. Returns the number of buckets or a negative value on failure.
@@ -124,7 +132,8 @@ void factor_prepare(int B, int prec);
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
                           int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
-                          const int64_t* n0_dev = nullptr, int every = 1, int q_off = 0);
+                          const int64_t* n0_dev = nullptr, int every = 1, int q_off = 0,
+                          const double* n_line = nullptr);
 
 // K6 (SIMT): delta_p = inv_s2 * || G (x_p - c) - y0 ||^2 for every pixel of every line,
 // threshold, and scatter into the result ring. factor_stride = 0 makes every line

@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
                                                        float* __restrict__ inv_s2_all,
                                                        int32_t* __restrict__ status, int64_t n0_arg, int W,
                                                        int incl, const int64_t* __restrict__ n0_dev,
-                                                       int every, int q_off) {
+                                                       int every, int q_off,
+                                                       const double* __restrict__ n_line) {
   const int t = blockIdx.x / CL;
   if (status[t] != LS_OK) return;  // same for every CTA of the cluster
   if (every > 1 && (q_off + t) % every != 0) return;  // not a snapshot of the cadence
@@ -338,8 +339,9 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
   // with x - mu = D (x' - m) and Sigma = D S D, delta = (x' - m)^T S^{-1} (x' - m).
   constexpr bool TRSM = is_trsm(PREC);
   {
+    // pixels in the window, or their forgetting weight (n_line: one value per line)
     const int64_t n = (n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W;
-    const double nn = (double)n, inv_nm1 = 1.0 / (double)(n - 1);
+    const double nn = n_line ? n_line[t] : (double)n, inv_nm1 = 1.0 / (nn - 1.0);
     for (int i = gwarp; i < B; i += gwarps) {
       const double nmi = nn * m[i];
       double* row = A + (int64_t)i * B;
@@ -605,7 +607,7 @@ int factor_cluster_capacity(size_t smem) {
 template <int PREC, int CL, int FT = FT_CLUSTER, int MB = (CL == 1 ? 512 / FT : 1)>
 cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, int L, int B,
                             void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
-                            cudaStream_t st, const int64_t* n0_dev, int every, int q_off) {
+                            cudaStream_t st, const int64_t* n0_dev, int every, int q_off, const double* n_line) {
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<PREC, CL, FT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -629,7 +631,7 @@ cudaError_t launch_factor_t(double* sigma, double* scratch, const double* m, int
   // a non-portable size: launch only where the device can place such a cluster
   if (CL > 8 && factor_cluster_capacity<PREC, CL, FT, MB>(smem) <= 0) return cudaErrorInvalidConfiguration;
   return cudaLaunchKernelEx(&cfg, factor_kernel<PREC, CL, FT, MB>, sigma, scratch, m, B, wmat, y0, inv_s2, status,
-                            n0, W, incl, n0_dev, every, q_off);
+                            n0, W, incl, n0_dev, every, q_off, n_line);
 }
 
 // Threads of a one-CTA-per-line factorisation: 128 threads with registers for 5 CTAs per
@@ -649,25 +651,25 @@ int factor_single_threads() {
 template <int PREC>
 cudaError_t launch_factor_p(int cl, int ft, double* sigma, double* scratch, const double* m, int L,
                             int B, void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
-                            int incl, cudaStream_t st, const int64_t* n0_dev, int every, int q_off) {
+                            int incl, cudaStream_t st, const int64_t* n0_dev, int every, int q_off, const double* n_line) {
   switch (cl) {
     case 16: {
       const cudaError_t e =
-          launch_factor_t<PREC, 16>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+          launch_factor_t<PREC, 16>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line);
       if (e != cudaErrorInvalidConfiguration) return e;
-      return launch_factor_t<PREC, 8>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+      return launch_factor_t<PREC, 8>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line);
     }
-    case 8: return launch_factor_t<PREC, 8>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
-    case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
-    case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+    case 8: return launch_factor_t<PREC, 8>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line);
+    case 4: return launch_factor_t<PREC, 4>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line);
+    case 2: return launch_factor_t<PREC, 2>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line);
     default:
       if (ft == 96)  // 128 threads sized for 5 CTAs per SM
         return launch_factor_t<PREC, 1, 128, 5>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W,
-                                                incl, st, n0_dev, every, q_off);
+                                                incl, st, n0_dev, every, q_off, n_line);
       if (ft == 128)
         return launch_factor_t<PREC, 1, 128>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl,
-                                             st, n0_dev, every, q_off);
-      return launch_factor_t<PREC, 1, 256>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off);
+                                             st, n0_dev, every, q_off, n_line);
+      return launch_factor_t<PREC, 1, 256>(sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line);
   }
 }
 
@@ -782,7 +784,7 @@ void factor_prepare(int B, int prec) {
 cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
                           int L, int B, int prec, void* wmat, float* y0, float* inv_s2,
                           int32_t* status, int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
-                          const int64_t* n0_dev, int every, int q_off) {
+                          const int64_t* n0_dev, int every, int q_off, const double* n_line) {
   if (L <= 0) return cudaSuccess;
   const size_t smem = (size_t)factor_smem_doubles(B) * sizeof(double);
   int cl = 0, ft = 0;
@@ -795,21 +797,21 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
     ft = factor_single_threads();
   }
   return launch_factor_shape(cl, ft, sigma, scratch, m, L, B, prec, wmat, y0, inv_s2, status, n0, W, incl,
-                             st, lc, n0_dev, every, q_off);
+                             st, lc, n0_dev, every, q_off, n_line);
 }
 
 cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m,
                                 int L, int B, int prec, void* wmat, float* y0, float* inv_s2, int32_t* status,
                                 int64_t n0, int W, int incl, cudaStream_t st, LaunchCounter* lc,
-                                const int64_t* n0_dev, int every, int q_off) {
+                                const int64_t* n0_dev, int every, int q_off, const double* n_line) {
   if (L <= 0) return cudaSuccess;
   cudaError_t e;
   switch (prec) {
-    case P_FP32: e = launch_factor_p<P_FP32>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    case P_FP16: e = launch_factor_p<P_FP16>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    case P_BF16T: e = launch_factor_p<P_BF16T>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    case P_FP32T: e = launch_factor_p<P_FP32T>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
-    default: e = launch_factor_p<P_BF16>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off); break;
+    case P_FP32: e = launch_factor_p<P_FP32>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line); break;
+    case P_FP16: e = launch_factor_p<P_FP16>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line); break;
+    case P_BF16T: e = launch_factor_p<P_BF16T>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line); break;
+    case P_FP32T: e = launch_factor_p<P_FP32T>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line); break;
+    default: e = launch_factor_p<P_BF16>(cl, ft, sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off, n_line); break;
   }
   if (lc) lc->n += 1;
   if (e != cudaSuccess) return e;

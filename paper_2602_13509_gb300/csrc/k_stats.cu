@@ -257,10 +257,12 @@ __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* _
                                    double* __restrict__ state_s1, int64_t n0_arg, int W, int L, int B,
                                    int inclusive, int64_t min_pixels, int32_t* __restrict__ status,
                                    const int64_t* __restrict__ n0_dev, const double* __restrict__ gain,
-                                   const int32_t* __restrict__ c_int) {
+                                   const int32_t* __restrict__ c_int, double lam,
+                                   const double* __restrict__ n_line) {
   const int64_t n0 = n0_dev ? *n0_dev : n0_arg;
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const double lam_lane = lam == 1.0 ? 1.0 : pow(lam, (double)(lane + 1));
   if (b < B) {
     double carry = state_s1[b];
     for (int t0 = 0; t0 < L; t0 += 32) {
@@ -271,34 +273,55 @@ __global__ void prefix_mean_kernel(const double* __restrict__ s1_line, double* _
         v = fma((double)W * (double)c_int[b], gt[3], v) * gt[1];
       }
       double x = v;
+      if (lam == 1.0) {
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        for (int o = 1; o < 32; o <<= 1) {
+          const double y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        const double incl = carry + x;
+        const double run = inclusive ? incl : incl - v;
+        if (t < L) {
+          const int64_t n = n0 + (int64_t)(t + inclusive) * W;
+          m_out[(int64_t)t * B + b] = n > 0 ? run / (double)n : 0.0;
+        }
+        carry = __shfl_sync(0xffffffffu, incl, 31);
+      } else {
+        // forgetting: incl_t = lam incl_{t-1} + v_t, a scan of the affine steps (the
+        // partial sum of a lane o places back decays by lam^o)
+        double lo = lam;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const double y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x = fma(lo, y, x);
+          lo *= lo;
+        }
+        const double incl = fma(lam_lane, carry, x);  // carry decayed over lanes 0..lane
+        const double prev = __shfl_up_sync(0xffffffffu, incl, 1);
+        const double run = inclusive ? incl : (lane == 0 ? carry : prev);
+        if (t < L) {
+          const double n = n_line[t];
+          m_out[(int64_t)t * B + b] = n > 0.0 ? run / n : 0.0;
+        }
+        carry = __shfl_sync(0xffffffffu, incl, min(31, L - 1 - t0));  // the last real line
       }
-      const double incl = carry + x;
-      const double run = inclusive ? incl : incl - v;
-      if (t < L) {
-        const int64_t n = n0 + (int64_t)(t + inclusive) * W;
-        m_out[(int64_t)t * B + b] = n > 0 ? run / (double)n : 0.0;
-      }
-      carry = __shfl_sync(0xffffffffu, incl, 31);
     }
     if (lane == 0) state_s1[b] = carry;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L; t += gridDim.x * blockDim.x) {
     const int64_t n = n0 + (int64_t)(t + inclusive) * W;
-    if (n < min_pixels && status[t] == LS_OK) status[t] = LS_NOT_READY;
+    const bool few = n_line ? n_line[t] < (double)min_pixels : n < min_pixels;
+    if (few && status[t] == LS_OK) status[t] = LS_NOT_READY;
   }
 }
 
 cudaError_t launch_prefix_mean(const double* s1_line, double* m_out, double* state_s1, int64_t n0,
                                int W, int L, int B, int inclusive, int64_t min_pixels,
                                int32_t* status, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev,
-                               const double* gain, const int32_t* c_int) {
-  if (gain && !c_int) return cudaErrorInvalidValue;
+                               const double* gain, const int32_t* c_int, double lam, const double* n_line) {
+  if ((gain && !c_int) || (lam != 1.0 && !n_line)) return cudaErrorInvalidValue;
   prefix_mean_kernel<<<(B + 7) / 8, 256, 0, st>>>(s1_line, m_out, state_s1, n0, W, L, B, inclusive,
-                                                  min_pixels, status, n0_dev, gain, c_int);
+                                                  min_pixels, status, n0_dev, gain, c_int, lam, n_line);
   HSAD_LAUNCH_CHECK(lc);
 }
 
@@ -319,7 +342,8 @@ cudaError_t launch_set_batch_desc(int64_t* desc, int64_t n_stats, int64_t slot1,
 // kernel, which reads each entry once anyway.
 __global__ void prefix_cov_kernel(double* __restrict__ buf, double* __restrict__ state_s2, int L, int B,
                                   int inclusive, const double* __restrict__ gain,
-                                  const double* __restrict__ s1_line, const int32_t* __restrict__ c_int, int W) {
+                                  const double* __restrict__ s1_line, const int32_t* __restrict__ c_int, int W,
+                                  double lam) {
   const int64_t BB = (int64_t)B * B;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= BB) return;
@@ -351,7 +375,7 @@ __global__ void prefix_cov_kernel(double* __restrict__ buf, double* __restrict__
     for (int u = 0; u < U; ++u) {
       if (t0 + u >= L) break;
       const double before = run;
-      run += v[u];
+      run = lam == 1.0 ? run + v[u] : fma(lam, run, v[u]);
       buf[(int64_t)(t0 + u) * BB + e] = inclusive ? run : before;
     }
   }
@@ -360,11 +384,34 @@ __global__ void prefix_cov_kernel(double* __restrict__ buf, double* __restrict__
 
 cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int inclusive, cudaStream_t st,
                               LaunchCounter* lc, const double* gain, const double* s1_line, const int32_t* c_int,
-                              int W) {
+                              int W, double lam) {
   if (gain && (!s1_line || !c_int)) return cudaErrorInvalidValue;
   const int64_t BB = (int64_t)B * B;
   prefix_cov_kernel<<<(unsigned)((BB + 255) / 256), 256, 0, st>>>(buf, state_s2, L, B, inclusive, gain, s1_line,
-                                                                  c_int, W);
+                                                                  c_int, W, lam);
+  HSAD_LAUNCH_CHECK(lc);
+}
+
+// Forgetting weight of a window after k more lines of W pixels, from n_prev:
+// lam^k n_prev + W (1 - lam^k) / (1 - lam), the geometric sum by expm1 (no cancellation
+// for lam near 1). The host uses the same function for the state it carries.
+__host__ __device__ double forget_weight_hd(double n_prev, double lam, int W, int64_t k) {
+  const double ll = log(lam);
+  const double lk = exp((double)k * ll);
+  return fma(lk, n_prev, (double)W * (expm1((double)k * ll) / expm1(ll)));
+}
+
+double forget_weight(double n_prev, double lam, int W, int64_t k) { return forget_weight_hd(n_prev, lam, W, k); }
+
+__global__ void forget_n_kernel(double n_prev, double lam, int W, int L, int incl, double* __restrict__ n_line) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < L) n_line[t] = forget_weight_hd(n_prev, lam, W, (int64_t)(t + incl));
+}
+
+cudaError_t launch_forget_n(double n_prev, double lam, int W, int L, int incl, double* n_line, cudaStream_t st,
+                            LaunchCounter* lc) {
+  if (L <= 0) return cudaSuccess;
+  forget_n_kernel<<<(L + 255) / 256, 256, 0, st>>>(n_prev, lam, W, L, incl, n_line);
   HSAD_LAUNCH_CHECK(lc);
 }
 

@@ -41,6 +41,7 @@ class hsad_config(C.Structure):
         ("max_batch_lines", C.c_int32), ("result_lines", C.c_int32),
         ("raw_bands", C.c_int32), ("band_first", C.c_int32), ("band_bin", C.c_int32),
         ("factor_every", C.c_int32),
+        ("forget", C.c_float),
     ]
 
 
@@ -361,7 +362,7 @@ _NAMES = {
 def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="exclusive", cube_lines=0,
                 gain=None, offset=None, threshold_mode="abs", threshold=0.0, warmup_pixels=0,
                 device_budget_bytes=0, flags=0, device=0, max_batch_lines=0, result_lines=0,
-                raw_bands=0, band_first=0, band_bin=1, factor_every=0):
+                raw_bands=0, band_first=0, band_bin=1, factor_every=0, forget=0.0):
     """Build an hsad_config; ``gain``/``offset`` arrays are kept alive on the struct."""
     import numpy as np
     cfg = hsad_config_init()
@@ -377,6 +378,7 @@ def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="excl
     cfg.max_batch_lines, cfg.result_lines = int(max_batch_lines), int(result_lines)
     cfg.raw_bands, cfg.band_first, cfg.band_bin = int(raw_bands), int(band_first), int(band_bin)
     cfg.factor_every = int(factor_every)
+    cfg.forget = float(forget)
     keep = []
     for name, arr in (("gain", gain), ("offset", offset)):
         if arr is not None:

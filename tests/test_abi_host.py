@@ -37,8 +37,9 @@ def test_config_defaults_and_struct_size(hs):
     cfg = hs.hsad_config_init()
     assert cfg.in_dtype == hs.HSAD_U16 and cfg.precision == hs.HSAD_FP32
     assert cfg.stats_mode == hs.HSAD_EXCLUSIVE and cfg.threshold_mode == hs.HSAD_ABS
-    assert C.sizeof(hs.hsad_config) == 96  # 80 + the front-end and cadence fields
+    assert C.sizeof(hs.hsad_config) == 104  # 80 + the front-end, cadence and forgetting fields
     assert cfg.raw_bands == 0 and cfg.band_first == 0 and cfg.band_bin == 0   # front end off
+    assert cfg.forget == 0.0                                                  # forgetting off
 
 
 @pytest.mark.parametrize("field,value,msg", [
@@ -46,6 +47,7 @@ def test_config_defaults_and_struct_size(hs):
     ("precision", 9, "precision"), ("stats_mode", 5, "stats_mode"), ("cube_lines", -1, "cube_lines"),
     ("threshold_mode", 4, "threshold_mode"), ("threshold", -1.0, "threshold"),
     ("warmup_pixels", -5, "warmup"), ("max_batch_lines", 70000, "max_batch_lines"), ("flags", 64, "flags"),
+    ("forget", 1.5, "forget"), ("forget", -0.25, "forget"), ("forget", float("nan"), "forget"),
 ])
 def test_create_rejects_bad_fields(hs, field, value, msg):
     cfg = hs.make_config(64, 32)
@@ -61,6 +63,10 @@ def test_create_rejects_inconsistent_modes(hs):
     assert hs.hsad_create(hs.make_config(8, 4, flags=hs.HSAD_NORMALIZE_SCORES))[0] == hs.HSAD_E_INVALID
     assert hs.hsad_create(hs.make_config(8, 4, gain=[1, 0, 1, 1]))[0] == hs.HSAD_E_INVALID        # zero gain
     assert hs.hsad_create(hs.make_config(8, 4, gain=[1, float("nan"), 1, 1]))[0] == hs.HSAD_E_INVALID
+    # forgetting needs streamed statistics and does not combine with a cadence
+    assert hs.hsad_create(hs.make_config(8, 4, stats_mode="cube", cube_lines=4, forget=0.9))[0] == hs.HSAD_E_INVALID
+    assert hs.hsad_create(hs.make_config(8, 4, factor_every=2, forget=0.9))[0] == hs.HSAD_E_INVALID
+    assert "forget" in hs.hsad_last_error(None)
 
 
 def test_null_handling(hs):
