@@ -49,9 +49,9 @@ typedef enum {
 /* input element type */
 enum { HSAD_U16 = 0, HSAD_F32 = 1 };
 /* working precision of the whitening contraction (the covariance sums are exact
- * for HSAD_U16 input in every mode; the covariance, the Cholesky pivots and panel solves
- * are FP64 and the O(B^3) factor updates float-float, about 48 significant bits, in every
- * precision) */
+ * for HSAD_U16 input in every mode; the covariance, the Cholesky pivots and the 16 x 16
+ * diagonal blocks are FP64 and the O(B^3) factor work (trailing updates, row solves,
+ * inverse substitutions) float-float, about 48 significant bits, in every precision) */
 enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
 /* whitening form of a context (Eq. 1, Sec. 3.3), see hsad_whitening_form:
  * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1}, the full triangular
@@ -325,7 +325,7 @@ int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int
                            uint8_t* mask, void* stream, int32_t device);
 
 /* Factor-kernel autotuner (no counterpart in the paper). Times every launch shape of the
- * FP64 factorisation (one 128-thread CTA per line with registers for 4 or 5 CTAs per SM,
+ * factorisation (one 128-thread CTA per line with registers for 4 or 5 CTAs per SM,
  * one 256-thread CTA per line, or a 2/4/8/16-CTA cluster per line) on synthetic
  * positive definite problems of `bands` bands, for batches of 1, 2, 4, ..., max_lines
  * lines (1 .. 4096), and makes contexts on `device` with that band count and precision

@@ -8,7 +8,8 @@
 // Per batch in the stream modes (Sec. 6.1's line-based detector; EXCLUSIVE scores line t
 // against lines [r, t), INCLUSIVE against [r, t]):
 //   K1 shift (first line after a reset) -> K1 column sums -> K2 per-line SYRK
-//   -> K3 running mean / covariance per line -> K4+K5 FP64 Cholesky + inverse per line
+//   -> K3 running mean / covariance per line -> K4+K5 Cholesky + inverse per line (FP64
+//   pivots and diagonal blocks, float-float updates)
 //   -> K6 whitening + score + threshold.
 // In CUBE mode (global RX per cube of cube_lines lines, Sec. 3.3) the cube's lines are
 // kept on the device; when the cube is complete: K1, K2 over the whole cube, K3 once,

@@ -204,7 +204,7 @@ cudaError_t launch_whiten_trsm_simt(const void* x, int L, int W, int B, int in_t
                                     LaunchCounter* lc);
 // Ring depth the triangular-solve whitening runs with for B bands; 0 if it does not fit.
 int whiten_trsm_stages(int B);
-// Working form of a context. The triangular solve halves the FP64 factor work but its
+// Working form of a context. The triangular solve halves the factor work but its
 // whitening is a chain of dependent block steps: it pays where a factorisation per line
 // dominates (streamed statistics), not in CUBE mode (one factorisation per cube, the
 // whitening dominates), which keeps the explicit inverse.
