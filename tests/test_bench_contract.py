@@ -24,3 +24,14 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_roofline_work_and_peaks():
+    """The factor's algorithmic work per line and the derived ceilings the bench divides by."""
+    sys.path.insert(0, ROOT)
+    import bench
+    # B^3/3 + five 64-band diagonal blocks (64^3/3 x 4 + 14^3/3) at B = 270: 6.93 MFLOP
+    assert abs(bench.factor_flops_per_line(270, 1) - (270 ** 3 + 4 * 64 ** 3 + 14 ** 3) / 3) < 1e-6
+    assert abs(bench.factor_flops_per_line(270, 0) - 2 * 270 ** 3 / 3) < 1e-6
+    assert abs(bench.fp64_peak_tflops(2070) - 1.25856) < 1e-9                    # 152 x 2070 MHz x 4
+    assert abs(bench.ff_peak_tflops(2070) - 152 * 2070e6 * 128 * 2 / 12 / 1e12) < 1e-12
