@@ -57,7 +57,9 @@ def load_peaks():
 # to a launch by its lines; keyed by (band count, whitening form: 1 = triangular solve), and
 # to be refreshed whenever the kernel changes (a form without a capture of the current
 # kernel reports null).
-FACTOR_DRAM_BYTES_PER_LINE = {(270, 1): (0.960198e9 + 1.425162e9) / 512}
+# (The last capture, 4.66 MB per line, was taken before the kernel gained the optional
+# per-line window weights of exponential forgetting, so no form has a current figure.)
+FACTOR_DRAM_BYTES_PER_LINE = {}
 
 
 def factor_flops_per_line(B, form):
@@ -664,7 +666,10 @@ def main():
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                     "traffic": (FACTOR_DRAM_BYTES_PER_LINE[key] * lines_per_launch
                                 if key in FACTOR_DRAM_BYTES_PER_LINE else None),
-                    "traffic_source": "ncu dram bytes per line of a 512-line capture x lines per launch",
+                    "traffic_source": ("ncu dram bytes per line of a 512-line capture x lines per launch"
+                                       if key in FACTOR_DRAM_BYTES_PER_LINE else
+                                       "null: the kernel changed after its last capture (4.66 MB per line, "
+                                       "profiles/factor_trsm_512x640x270.md)"),
                     "kernel": ("factor (Cholesky + inverses of the 64 x 64 diagonal blocks; FP64 pivots "
                                "and panels, float-float updates)" if form
                                else "factor (Cholesky + triangular inverse; FP64 pivots and panels, "
