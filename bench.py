@@ -1,17 +1,19 @@
 #!/usr/bin/env python
 """Throughput / latency benchmark of streaming RX on one GB300 (or N replicas).
 
-Workload (default): the 640-pixel x 270-band push-broom stream, 4000 lines of
-uint16 12-bit DN, EXCLUSIVE running statistics (each line scored against all
-earlier lines, Sec. 6.1's line-based form of the global RX of Sec. 3.3), ABS
-threshold. One step = restart the stream and push all 4000 lines (resident in
-HBM) through the C ABI, then read every score and mask back into device memory.
+Workload (default): the precision form, 1024 pixels x 448 bands x 8000 lines of uint16
+12-bit DN pushed in batches of 2000, EXCLUSIVE running statistics (each line scored
+against all earlier lines, Sec. 6.1's line-based form of the global RX of Sec. 3.3), ABS
+threshold. One step = restart the stream and push all 8000 lines (resident in HBM)
+through the C ABI, then read every score and mask back into device memory.
 
-Printed: one JSON line with pixel-spectra scored / s (whole job), the same
-metric end to end from pinned host memory, p50/p99 single-line latency, a
-roofline entry for the dominant kernel timed live with CUDA events on the
-launching stream, the FP32 path next to the BF16 path, clocks sampled during
-the timed region, and the FP64 oracle timed on a bounded sample on the host.
+Printed: one JSON line whose headline is the FP32 path (the paper's detector computes in
+FP32), in pixel-spectra scored / s (whole job); the same metric end to end from pinned
+host memory; the BF16 path and the FP32 path with the FP64 factor on the same workload and
+step count beside it, each with its error against the FP64 oracle on a sampled line;
+p50/p99 single-line latency; roofline entries of the factor, covariance and whitening
+kernels timed live with CUDA events on the launching stream; clocks sampled during the
+timed region; and the FP64 oracle timed on a bounded sample on the host.
 
 ``--impl reference`` times the oracle itself (the only reference that exists).
 """
@@ -53,12 +55,9 @@ def load_peaks():
 
 
 # DRAM bytes per line of the factor kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of a 512-line launch, profiles/factor_trsm_512x640x270.md), scaled
-# to a launch by its lines; keyed by (band count, whitening form: 1 = triangular solve), and
-# to be refreshed whenever the kernel changes (a form without a capture of the current
-# kernel reports null).
-# (The last capture, 4.66 MB per line, was taken before the kernel gained the optional
-# per-line window weights of exponential forgetting, so no form has a current figure.)
+# dram__bytes_write.sum of a small launch divided by its lines), scaled to a launch by its
+# lines; keyed by (band count, whitening form: 1 = triangular solve). A form without a
+# capture of the current kernel reports null.
 FACTOR_DRAM_BYTES_PER_LINE = {}
 
 
@@ -152,6 +151,86 @@ def oracle_sample(lines, t_list, gain, offset):
         d, st = orx.stream_rx_line(lines, t, oracle.EXCLUSIVE, gain=gain, offset=offset)
         px += d.size
     return px, time.perf_counter() - t0
+
+
+def oracle_sample_scores(lines, t, gain, offset):
+    """The FP64 oracle scoring line t of the stream (EXCLUSIVE): pixels, seconds, scores."""
+    import oracle
+    from oracle import rx as orx
+    t0 = time.perf_counter()
+    d, st = orx.stream_rx_line(lines, t, oracle.EXCLUSIVE, gain=gain, offset=offset)
+    return d.size, time.perf_counter() - t0, d
+
+
+# Score tolerances and mask margins of the parity tests (relative error |d - ref| / max(ref, 1)).
+TOL = {"fp32": 1e-4, "bf16": 1e-2, "fp16": 1e-2}
+MARGIN = {"fp32": 2e-4, "bf16": 2e-2, "fp16": 2e-2}
+
+
+def accuracy_vs_oracle(s, m, ref, B, prec, t):
+    """Error of one arm's scores of line t against the oracle's, and mask disagreement."""
+    import numpy as np
+    s = np.asarray(s, np.float64)
+    ok = np.isfinite(ref)
+    e = np.abs(s[ok] - ref[ok]) / np.maximum(ref[ok], 1.0)
+    tau = B + 6 * math.sqrt(2 * B)
+    band = np.abs(ref - tau) <= MARGIN[prec] * tau
+    diff = (np.asarray(m).astype(bool) != (ref > tau))
+    return {"line": int(t), "pixels": int(ok.sum()), "max_rel_err": float(e.max()) if e.size else None,
+            "p999_rel_err": float(np.percentile(e, 99.9)) if e.size else None, "tolerance": TOL[prec],
+            "mask_diff_outside_margin": int((diff & ~band).sum()), "mask_diff_total": int(diff.sum())}
+
+
+def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
+    """Roofline entries of the factor, covariance (SYRK) and whitening kernels of one arm:
+    algorithmic work per launch (SURVEY-style per-unit figures x units per launch) over the
+    launch's average CUDA-event duration, against the peak of the unit that bounds it."""
+    out = {}
+    px_step = T * W
+    for name, (n, tot) in prof.items():
+        if name not in ("factor", "syrk", "whiten_score") or n == 0:
+            continue
+        avg_ms = tot / n
+        lps = n / prof_steps                       # launches per step
+        if name == "factor":
+            lines_per_launch = T / lps
+            work = lines_per_launch / max(1, every) * factor_flops_per_line(B, form)
+            ach = work / (avg_ms / 1e3) / 1e12
+            pk = ff_peak_tflops(mhz)
+            key = (B, form)
+            r = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                 "traffic": (FACTOR_DRAM_BYTES_PER_LINE[key] * lines_per_launch
+                             if key in FACTOR_DRAM_BYTES_PER_LINE else None),
+                 "traffic_algorithmic": lines_per_launch * (B * B * 8 + B * 8 + pad64(B) ** 2 * 4),
+                 "kernel": "factor (Cholesky + inverses of the 64 x 64 diagonal blocks)" if form
+                           else "factor (Cholesky + triangular inverse)",
+                 "work_per_launch": (f"{lines_per_launch:.0f} lines x (B^3/3 + sum of 64-block b^3/3) flop"
+                                     if form else f"{lines_per_launch:.0f} lines x 2B^3/3 flop"),
+                 "peak_source": "derived: 152 SMs x %.0f MHz x 128 FP32 lanes x 2 flop / 12 FP32 instructions "
+                                "per float-float multiply-subtract" % mhz,
+                 "fp64_peak_derived": fp64_peak_tflops(mhz), "frac_of_fp64_peak": ach / fp64_peak_tflops(mhz)}
+        else:
+            px = px_step / lps
+            flops = px * B * (B + 1)               # B(B+1)/2 multiply-adds per pixel
+            byts = px * (2 * B + (5 if name == "whiten_score" else 0))
+            ach = flops / (avg_ms / 1e3) / 1e12
+            if name == "whiten_score" and prec == "fp32":
+                pk, bound, src = fp32_peak_tflops(mhz), "alu", "derived: 152 SMs x %.0f MHz x 128 FFMA x 2" % mhz
+            else:
+                pk, bound, src = peaks["bf16_tflops"], "tensor", f"{peaks['source']} bf16 burst"
+            r = {"bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                 "traffic": None, "traffic_algorithmic": byts,
+                 "kernel": name, "work_per_launch": f"{px:.0f} px x B(B+1) flop", "peak_source": src,
+                 "hbm_achieved_gbs": byts / (avg_ms / 1e3) / 1e9, "hbm_frac": byts / (avg_ms / 1e3) / 1e9 /
+                 peaks["hbm_gbs"]}
+        r["avg_launch_ms"] = avg_ms
+        r["launches_per_step"] = lps
+        out[name] = r
+    return out
+
+
+def pad64(b):
+    return (b + 63) // 64 * 64
 
 
 def gpu_local_cpus(index):
@@ -419,21 +498,36 @@ def oracle_lines(wl, lines):
 
 
 def run_reference(args, wl, rank, world):
+    """The FP64 oracle timed on the host: each step scores one line against all lines before
+    it (EXCLUSIVE). Its cost grows with the line index, so the sampled line is the stream
+    midpoint (the stream average) unless warm-up + steps lines there would not finish in
+    about two minutes; then an earlier line, which overstates the oracle's average rate."""
     if rank != 0:
         return
-    sc, lines = make_inputs(wl, 0)
-    lines = oracle_lines(wl, lines)
     T = wl["lines"]
-    cores = len(os.sched_getaffinity(0))
     mid = T // 2
+    n_oracle = args.warmup + args.steps
+    sc, lines = make_inputs(dict(wl, lines=min(T, 65)), 0)
+    lines = oracle_lines(wl, lines)
+    # calibrate: the cost of a line against 64 earlier lines, scaled linearly in the index
+    _, c64 = oracle_sample(lines, [64 if T > 64 else T - 1], sc.gain, sc.offset)
+    budget = 120.0 / max(1, n_oracle)
+    t_s = int(min(mid, max(64, 64 * budget / max(c64, 1e-6))))
+    sc, lines = make_inputs(dict(wl, lines=min(T, t_s + args.steps + 1)), 0)
+    lines = oracle_lines(wl, lines)
+    cores = len(os.sched_getaffinity(0))
     for i in range(args.warmup):
-        oracle_sample(lines, [mid - 1 - i], sc.gain, sc.offset)
+        oracle_sample(lines, [t_s - 1 - i], sc.gain, sc.offset)
     px_total, secs = 0, 0.0
     for i in range(args.steps):
-        px, s = oracle_sample(lines, [mid + i], sc.gain, sc.offset)
+        px, s = oracle_sample(lines, [t_s + i], sc.gain, sc.offset)
         px_total += px
         secs += s
     v = px_total / secs
+    where = ("the stream midpoint, whose cost equals the stream average" if t_s >= mid else
+             f"before the stream midpoint ({mid}) so that {n_oracle} lines finish in minutes: the oracle's "
+             f"cost per line grows with the index, so this overstates its stream-average rate about "
+             f"{mid / t_s:.1f}x")
     out = {
         "metric": "pixel-spectra scored/s", "value": v, "unit": "pixel-spectra/s", "impl": "reference",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -441,8 +535,8 @@ def run_reference(args, wl, rank, world):
         "config": {"workload": args.workload, "width": wl["width"], "bands": wl["bands"], "lines": T,
                    "stats": "exclusive", "parallelism": "none (host oracle)"},
         "cpu_baseline": {"value": v, "unit": "pixel-spectra/s", "cores": cores, "kind": "oracle",
-                         "sample": f"one line per step at the stream midpoint (t = {mid}..{mid + args.steps - 1}),"
-                                   " whose cost equals the stream average"},
+                         "sample": f"one line per step (t = {t_s}..{t_s + args.steps - 1}) scored against all "
+                                   f"lines before it; {where}"},
         "e2e": {"value": v, "unit": "pixel-spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -454,10 +548,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stream_640x270", choices=sorted(WORKLOADS) + ["stress"])
+    ap.add_argument("--workload", default="precision_1024x448", choices=sorted(WORKLOADS) + ["stress"])
     ap.add_argument("--stress-cubes", type=int, default=0, help="score only the first k of the 32 cubes")
     ap.add_argument("--cube", default="", help="stress workload: one cube 'lines,width,bands' instead")
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32"],
+                    help="the headline arm (the paper's detector computes in FP32, Sec. 3.4)")
+    ap.add_argument("--factor-precision", default="ff", choices=["ff", "fp64"],
+                    help="arithmetic of the factor's O(B^3) work: float-float (default) or FP64")
     ap.add_argument("--batch", type=int, default=0, help="lines per internal batch (0 = workload default)")
     ap.add_argument("--factor-every", type=int, default=0,
                     help="factorisation cadence in lines (an extension: statistics up to k-1 lines old); "
@@ -469,7 +566,8 @@ def main():
     ap.add_argument("--line-gain", action="store_true",
                     help="push every line with its own gain (per-line gain correction)")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--skip-fp32-arm", action="store_true")
+    ap.add_argument("--skip-other-arm", action="store_true",
+                    help="skip the second precision (and the FP64-factor) arms")
     ap.add_argument("--serving-seconds", type=float, default=5.0,
                     help="measured seconds of the 16-stream serving run (0 = skip)")
     args = ap.parse_args()
@@ -510,8 +608,9 @@ def main():
     s_host = torch.empty((T, W), dtype=torch.float32).pin_memory()
     m_host = torch.empty((T, W), dtype=torch.uint8).pin_memory()
 
-    def detector(prec):
-        return hs.Detector(width=W, bands=B, stats_mode="exclusive", precision=prec, gain=sc.gain,
+    def detector(prec, factor="ff"):
+        return hs.Detector(width=W, bands=B, stats_mode="exclusive", precision=prec, factor_precision=factor,
+                           gain=sc.gain,
                            offset=sc.offset, max_batch_lines=wl["batch"], result_lines=T, device=local,
                            raw_bands=wl.get("raw_bands", 0), band_first=wl.get("band_first", 0),
                            band_bin=wl.get("band_bin", 1), factor_every=args.factor_every, forget=args.forget)
@@ -559,20 +658,36 @@ def main():
         return ms, det.kernel_launches - n0
 
     px_step = T * W
-    det = detector(args.precision)
-    form = det.whitening_form
-    with ClockSampler(local) as clk:
-        ms, launches = timed(det)
-    value = weak_value(px_step, world, ms)
+    other = "bf16" if args.precision != "bf16" else "fp32"
 
-    # per-kernel times, CUDA events on the library's stream (separate pass)
+    def measure(prec, factor="ff", clocks=False):
+        """Device-resident throughput of one arm, then per-kernel CUDA-event times (separate
+        pass) and the scores of the accuracy sample line. Leaves the detector open."""
+        det = detector(prec, factor)
+        form = det.whitening_form
+        if clocks:
+            with ClockSampler(local) as clk:
+                ms, launches = timed(det)
+            clk_summary = clk.summary()
+        else:
+            ms, launches = timed(det)
+            clk_summary = None
+        # per-kernel times, CUDA events on the library's stream (separate pass)
+        det.profile(True)
+        det.profile_reset()
+        for _ in range(prof_steps):
+            step(det)
+        prof = det.profile_totals()
+        det.profile(False)
+        sample = s_dev[t_acc].cpu().numpy().copy(), m_dev[t_acc].cpu().numpy().copy()
+        return det, dict(value=weak_value(px_step, world, ms), ms=ms, launches=launches, form=form, prof=prof,
+                         sample=sample, clocks=clk_summary)
+
     prof_steps = 2
-    det.profile(True)
-    det.profile_reset()
-    for _ in range(prof_steps):
-        step(det)
-    prof = det.profile_totals()
-    det.profile(False)
+    t_acc = T // 2   # the accuracy sample: scored by the oracle once, compared with every arm
+    det, head = measure(args.precision, args.factor_precision, clocks=True)
+    ms, launches, form, prof = head["ms"], head["launches"], head["form"], head["prof"]
+    value = head["value"]
     per_kernel = {k: {"launches_per_step": n / prof_steps, "ms_per_step": t / prof_steps}
                   for k, (n, t) in prof.items()}
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
@@ -617,7 +732,7 @@ def main():
     if rank == 0 and args.serving_seconds > 0:
         serving = {p: run_serving(hs, local, p, args.serving_seconds, 1.0) for p in ("bf16", "fp32")}
 
-    # transmit encoding (Sec. 3.5) of the step's last full ring of scores, through the
+    # transmit encoding (Sec. 3.4) of the step's last full ring of scores, through the
     # public API into device memory (a full call: launches, copy stream sync included)
     tx = None
     if rank == 0:
@@ -642,59 +757,46 @@ def main():
            "h2d_bytes_per_step": int(x_host.numel() * 2), "d2h_bytes_per_step": int(T * W * 5)}
     det.close()
 
-    fp32_arm = None
-    if args.precision != "fp32" and not args.skip_fp32_arm:
-        d32 = detector("fp32")
-        ms32, _ = timed(d32)
-        d32.close()
-        fp32_arm = {"value": px_step * world / (ms32 / 1e3), "ms_per_step": ms32}
+    # the other precision on the same workload and step count, and the FP32 path with the
+    # FP64 factor (precision forms side by side)
+    arms = {}
+    if not args.skip_other_arm:
+        d2, arm = measure(other, args.factor_precision)
+        e2_ms, _ = timed(d2, host=True)
+        d2.close()
+        arm["e2e"] = {"value": px_step * world / (e2_ms / 1e3), "unit": "pixel-spectra/s"}
+        arms[other] = arm
+        if args.precision == "fp32" and args.factor_precision == "ff":
+            d3, arm3 = measure("fp32", "fp64")
+            d3.close()
+            arms["fp32_fp64_factor"] = arm3
 
-    # roofline of the dominant kernel
-    roof = None
-    if dom is not None:
-        n, tot = prof[dom]
-        avg_ms = tot / n
-        mhz = peaks["sm_max_mhz"]
-        launches_per_step = n / prof_steps
-        if dom == "factor":
-            lines_per_launch = T / launches_per_step
-            # with a cadence only every k-th line's statistics are factored
-            work = lines_per_launch / max(1, args.factor_every) * factor_flops_per_line(B, form)
-            ach = work / (avg_ms / 1e3) / 1e12
-            pk = ff_peak_tflops(mhz)
-            key = (B, form)
-            roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": (FACTOR_DRAM_BYTES_PER_LINE[key] * lines_per_launch
-                                if key in FACTOR_DRAM_BYTES_PER_LINE else None),
-                    "traffic_source": ("ncu dram bytes per line of a 512-line capture x lines per launch"
-                                       if key in FACTOR_DRAM_BYTES_PER_LINE else
-                                       "null: the kernel changed after its last capture (4.66 MB per line, "
-                                       "profiles/factor_trsm_512x640x270.md)"),
-                    "kernel": ("factor (Cholesky + inverses of the 64 x 64 diagonal blocks; FP64 pivots "
-                               "and panels, float-float updates)" if form
-                               else "factor (Cholesky + triangular inverse; FP64 pivots and panels, "
-                                    "float-float updates)"),
-                    "work_per_launch": (f"{lines_per_launch:.0f} lines x (B^3/3 + sum of 64-block b^3/3) flop"
-                                        if form else f"{lines_per_launch:.0f} lines x 2B^3/3 flop"),
-                    "peak_source": "derived: 152 SMs x 2070 MHz x 128 FP32 lanes x 2 flop / 12 FP32 "
-                                   "instructions per float-float multiply-subtract",
-                    "fp64_peak_derived": fp64_peak_tflops(mhz)}
-        else:
-            per_launch_px = px_step / launches_per_step
-            byts = per_launch_px * (2 * B + (5 if dom == "whiten_score" else 0))
-            ach = byts / (avg_ms / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
-                    "peak_source": peaks["source"]}
-        roof["avg_launch_ms"] = avg_ms
+    mhz = peaks["sm_max_mhz"]
+    head_roofs = kernel_rooflines(prof, prof_steps, T, W, B, form, args.precision, args.factor_every, peaks, mhz)
+    roof = dict(head_roofs[dom]) if dom in head_roofs else None
 
-    cpu = None
+    cpu, ref_line = None, None
     if rank == 0 and not args.skip_cpu:
-        mid = T // 2
-        px, secs = oracle_sample(oracle_lines(wl, lines[:mid + 1]), [mid], sc.gain, sc.offset)
+        px, secs, ref_line = oracle_sample_scores(oracle_lines(wl, lines[:t_acc + 1]), t_acc, sc.gain, sc.offset)
         cpu = {"value": px / secs, "unit": "pixel-spectra/s", "cores": len(os.sched_getaffinity(0)),
-               "kind": "oracle", "sample": f"line {mid} of the stream ({W} pixels) scored against lines "
-                                           f"0..{mid - 1}; its cost equals the stream average"}
+               "kind": "oracle", "sample": f"line {t_acc} of the stream ({W} pixels) scored against lines "
+                                           f"0..{t_acc - 1}; its cost equals the stream average"}
+
+    def accuracy(arm, prec):
+        if ref_line is None:
+            return None
+        s_, m_ = arm["sample"]
+        return accuracy_vs_oracle(s_, m_, ref_line, B, prec, t_acc)
+
+    def arm_json(arm, prec):
+        pk = {k: {"launches_per_step": n / prof_steps, "ms_per_step": t / prof_steps}
+              for k, (n, t) in arm["prof"].items()}
+        return {"value": arm["value"], "unit": "pixel-spectra/s", "ms_per_step": arm["ms"], "dtype": prec,
+                "gpu_launches": arm["launches"], "e2e": arm.get("e2e"),
+                "whitening": "triangular solve" if arm["form"] else "explicit inverse",
+                "accuracy_vs_oracle": accuracy(arm, prec), "kernels": pk,
+                "rooflines": kernel_rooflines(arm["prof"], prof_steps, T, W, B, arm["form"], prec,
+                                              args.factor_every, peaks, mhz)}
 
     out = {
         "metric": "pixel-spectra scored/s", "value": value, "unit": "pixel-spectra/s", "n_gpus": world,
@@ -703,6 +805,7 @@ def main():
         "config": {"workload": args.workload, "width": W, "bands": B, "lines": T, "stats": "exclusive",
                    "input": "uint16 12-bit DN", "batch_lines": wl["batch"],
                    "whitening": "triangular solve" if form else "explicit inverse",
+                   "factor": "FP64" if args.factor_precision == "fp64" else "float-float",
                    **({"factor_every": args.factor_every} if args.factor_every > 1 else {}),
                    **({"line_gain": "per-line gains U[0.8, 1.25] (hsad_push_lines_gain)"} if args.line_gain else {}),
                    **({"forget": args.forget} if 0.0 < args.forget < 1.0 else {}),
@@ -711,9 +814,11 @@ def main():
                    "parallelism": f"replicas x{world} (independent streams)" if world > 1 else "single stream",
                    "l2": "inputs larger than L2 (%.2f GB per step)" % (x_dev.numel() * 2 / 1e9),
                    "host": host_cpus},
-        "latency": lat, "e2e": e2e, "gpu_launches": launches, "fp32_path": fp32_arm,
-        "roofline": roof, "kernels": per_kernel, "cpu_baseline": cpu, "clocks": clk.summary(),
-        "serving": serving, "tx_encode": tx,
+        "accuracy_vs_oracle": accuracy(head, args.precision),
+        "latency": lat, "e2e": e2e, "gpu_launches": launches,
+        **{f"{k}_path": arm_json(a, "fp32" if k == "fp32_fp64_factor" else k) for k, a in arms.items()},
+        "roofline": roof, "rooflines": head_roofs, "kernels": per_kernel, "cpu_baseline": cpu,
+        "clocks": head["clocks"], "serving": serving, "tx_encode": tx,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

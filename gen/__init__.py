@@ -7,6 +7,7 @@ can both consume it without sharing any of the method's computation.
 from .cubes import (  # noqa: F401
     SEED_BASE,
     GaussianMixtureCube,
+    IllConditionedScene,
     PushbroomScene,
     config1_cube,
     config_scene,

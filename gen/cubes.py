@@ -248,6 +248,41 @@ class PushbroomScene:
         return out
 
 
+class IllConditionedScene:
+    """Lines whose band covariance has a prescribed, very large condition number.
+
+    Every pixel is ``2048 + U diag(a) z`` (DN units) with U a Haar orthogonal B x B matrix,
+    z ~ N(0, I_B) drawn per pixel and a_j = 500 sqrt(B) 10^(-decades j / (B - 1)): the
+    bands are strongly correlated (about 500 DN of spread per band along the leading
+    direction) and the population covariance U diag(a^2) U^T has condition number
+    10^(2 decades). ``dtype="f32"``: the values divided by 4096, as float32 (nothing else
+    bounds the conditioning); ``dtype="u16"``: rounded and clamped 12-bit DN, where the
+    rounding noise (variance 1/12 per band) caps the sample covariance's condition number
+    near 10^6. No anomalies are implanted. Stands in for a scene dominated by one material
+    under a low-noise sensor, the hardest case for the factorisation.
+    """
+
+    def __init__(self, width: int, bands: int, seed: int, decades: float = 5.0, dtype: str = "f32"):
+        self.width, self.bands, self.seed = int(width), int(bands), int(seed)
+        self.decades, self.dtype = float(decades), dtype
+        B = self.bands
+        self.U = haar_orthogonal(rng_for(self.seed, 0), B)
+        self.a = 500.0 * np.sqrt(B) * 10.0 ** (-self.decades * np.arange(B) / max(B - 1, 1))
+        self.gain = None
+        self.offset = None
+
+    def lines(self, t0: int, n: int) -> np.ndarray:
+        """Lines [t0, t0 + n) as [n, W, B] float32 or uint16 (one generator block per line)."""
+        W, B = self.width, self.bands
+        out = np.empty((n, W, B), dtype=np.float64)
+        for i in range(n):
+            z = rng_for(self.seed, 1, t0 + i).standard_normal((W, B))
+            out[i] = 2048.0 + (z * self.a) @ self.U.T
+        if self.dtype == "u16":
+            return np.clip(np.rint(out), 0, FULL_SCALE).astype(np.uint16)
+        return (out / 4096.0).astype(np.float32)
+
+
 # Named workloads (seed SEED_BASE + k for workload k).
 SCENES = {
     "stream_640x270": dict(width=640, bands=270, lines=4000, seed=SEED_BASE + 2),

@@ -50,9 +50,15 @@ typedef enum {
 enum { HSAD_U16 = 0, HSAD_F32 = 1 };
 /* working precision of the whitening contraction (the covariance sums are exact
  * for HSAD_U16 input in every mode; the covariance, the Cholesky pivots and the 16 x 16
- * diagonal blocks are FP64 and the O(B^3) factor work (trailing updates, row solves,
- * inverse substitutions) float-float, about 48 significant bits, in every precision) */
+ * diagonal blocks are FP64 in every precision, and the O(B^3) factor work follows
+ * factor_precision) */
 enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
+/* arithmetic of the factor's O(B^3) work (trailing updates, row solves, inverse
+ * substitutions; Sec. 3.3 needs Sigma^{-1}): float-float, pairs of FP32 values with about
+ * 48 significant bits and FP32's exponent range, on the FP32 pipe (default); or FP64 (53
+ * bits), at about half the factor throughput on this GPU, whose FP64 rate is 1/64 of its
+ * FP32 rate. */
+enum { HSAD_FACTOR_FF = 0, HSAD_FACTOR_FP64 = 1 };
 /* whitening form of a context (Eq. 1, Sec. 3.3), see hsad_whitening_form:
  * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1}, the full triangular
  *                              inverse: CUBE mode (one factorisation per cube, where the
@@ -77,11 +83,14 @@ enum { HSAD_HOST = 0, HSAD_DEVICE = 1 };
 enum {
   HSAD_CREATE_WAIT = 1,      /* hsad_create blocks (bounded) until the device budget admits the context */
   HSAD_NORMALIZE_SCORES = 2, /* CUBE mode: report delta / cube max instead of delta (Sec. 3.3) */
-  HSAD_CUDA_GRAPHS = 4       /* EXCLUSIVE mode, host pushes: the statistics, factor and scoring
+  HSAD_CUDA_GRAPHS = 4,      /* EXCLUSIVE mode, host pushes: the statistics, factor and scoring
                                 launches of a batch of up to 8 lines are captured once per batch
                                 size and replayed as a CUDA graph (same kernels, same results;
                                 fewer host calls); larger batches launch directly. No counterpart
                                 in the paper. Ignored while profiling is on. */
+  HSAD_FORCE_INVERSE = 8     /* use the explicit-inverse whitening form (HSAD_FORM_INVERSE) also
+                                for streamed statistics, where the triangular solve is the
+                                default (comparisons of the two forms) */
 };
 
 typedef struct {
@@ -99,7 +108,8 @@ typedef struct {
   int64_t warmup_pixels;       /* a line is scored only once its statistics hold at least
                                   max(B + 1, warmup_pixels) pixels */
   int64_t device_budget_bytes; /* 0 = no cap for this context */
-  int32_t flags;               /* HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES | HSAD_CUDA_GRAPHS */
+  int32_t flags;               /* HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES | HSAD_CUDA_GRAPHS |
+                                  HSAD_FORCE_INVERSE */
   int32_t device;              /* CUDA device ordinal */
   int32_t max_batch_lines;     /* lines processed per internal batch (0 = default 256) */
   int32_t result_lines;        /* lines of scores kept for hsad_scores (0 = default) */
@@ -129,9 +139,10 @@ typedef struct {
    * The running sums are then FP64 instead of exact integers; statistics export and import
    * (hsad_get_stats, hsad_set_stats) and CUDA-graph replay are not available. */
   float forget;
+  int32_t factor_precision;    /* HSAD_FACTOR_FF (default) | HSAD_FACTOR_FP64 */
 } hsad_config;
 
-/* Fill *cfg with defaults: U16, FP32, EXCLUSIVE, cube_lines 0, ABS threshold
+/* Fill *cfg with defaults: U16, FP32, float-float factor, EXCLUSIVE, cube_lines 0, ABS threshold
  * B + 6 sqrt(2B) once bands is known (threshold 0 here means "use that default"),
  * device 0. Returns HSAD_E_INVALID for NULL. */
 int hsad_config_init(hsad_config* cfg);
@@ -205,7 +216,7 @@ int hsad_scores(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines, float* s
 int hsad_line_status(hsad_ctx* ctx, uint64_t first_line_id, int64_t n_lines,
                      int32_t* status, int32_t timeout_ms);
 
-/* Transmit encoding (Sec. 3.5, data transmission) of lines [first_line_id, first_line_id +
+/* Transmit encoding (Sec. 3.4, data transmission) of lines [first_line_id, first_line_id +
  * n_lines): code = IEEE binary16 of sqrt(delta / delta_max), delta_max the largest finite
  * score of the block (the cube maximum of the paper when the block is one cube), the
  * division and square root in FP32 (correctly rounded) and the conversion rounded to nearest
@@ -313,8 +324,10 @@ int64_t hsad_device_budget_used(int device);
  *   16 n_lines B + 24 B^2 + 4 pad64(B)^2 + 8 n_lines bytes <= 16 MiB
  * (e.g. B = 270 up to ~3300 lines, B = 70 up to ~14000 lines), else HSAD_E_INVALID
  * before anything runs. The first call on a device looks up the array's address
- * (cudaGetSymbolAddress, with that device current) and loads the module: make it
- * before any stream capture. Calls share the array and keep its last contents (the
+ * (cudaGetSymbolAddress, with that device current), which loads the module and commits
+ * the array: make it before any stream capture. A call with n_lines = 0 does only that
+ * set-up (every other argument is ignored and may be NULL) and returns HSAD_OK:
+ * callers that must not allocate after start-up make it once per device at start-up. Calls share the array and keep its last contents (the
  * sums and status words are cleared at the start of each call): calls that overlap
  * on the GPU, from any thread or stream, race and must not be issued. The call
  * returns after the cube is scored: HSAD_OK, HSAD_E_NOT_PD, HSAD_E_NOT_READY (fewer

@@ -27,7 +27,7 @@ What it computes, and where the paper says so:
   cadence of k lines, EXCLUSIVE statistics are taken only every k lines after the
   reset, and line t is scored against the last snapshot, [r, r + k floor((t-r)/k)).
 
-* Transmit encoding, Sec. 3.5 ("Data Transmission"): each score is sent as an
+* Transmit encoding, Sec. 3.4 ("Data Transmission"): each score is sent as an
   IEEE-754 half-precision value of its square root, normalised to the cube's
   maximum; the scores themselves are computed in single precision. Reading: code =
   binary16(sqrt(delta / delta_max)) with the division and the square root in FP32
@@ -280,7 +280,7 @@ def stream_rx(lines: np.ndarray, mode: str = EXCLUSIVE, cube_lines: int = 0, war
 
 
 def encode_tx(scores):
-    """Transmit encoding of a block of scores (Sec. 3.5): ``(codes uint16, delta_max)``.
+    """Transmit encoding of a block of scores (Sec. 3.4): ``(codes uint16, delta_max)``.
 
     code = binary16(sqrt(delta / delta_max)) with the division and square root in FP32
     (the paper computes scores in single precision) and round-to-nearest-even to

@@ -32,6 +32,15 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the hsad CUDA library cannot be built")
 
 
+# Sources compiled more than once, with different macro definitions: the factor kernel,
+# once per arithmetic (0 float-float, 1 FP64) and working precision (0..4), so that its
+# instances compile in parallel.
+VARIANTS = {
+    "k_factor_inst.cu": [(f"k_factor_inst_a{a}_p{p}", [f"-DHSAD_FI_AR={a}", f"-DHSAD_FI_PREC={p}"])
+                         for a in (0, 1) for p in range(5)],
+}
+
+
 def _headers():
     return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(INCLUDE, "*.h"))
@@ -52,10 +61,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
-        objs.append(o)
-        if force or _stale(o, [s] + hdrs):
-            jobs.append([cc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o])
+        base = os.path.basename(s)
+        for name, defs in VARIANTS.get(base, [(base[:-3], [])]):
+            o = os.path.join(BUILD, name + ".o")
+            objs.append(o)
+            if force or _stale(o, [s] + hdrs):
+                jobs.append([cc, *ARCH, *NVCC_FLAGS, *defs, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,7 +75,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and (r.stdout or r.stderr):
             sys.stderr.write(r.stdout + r.stderr)
 
+    # stale objects of sources or variants that no longer exist must not be linked
+    for o in glob.glob(os.path.join(BUILD, "*.o")):
+        if o not in objs:
+            os.remove(o)
     if jobs:
+        jobs.sort(key=lambda c: "k_factor_inst" not in c[-3])  # longest first
         with ThreadPoolExecutor(max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
             list(ex.map(run, jobs))
     if jobs or force or _stale(LIB, objs):

@@ -61,6 +61,7 @@ using Clock = std::chrono::steady_clock;
 struct hsad_ctx {
   hsad_config cfg{};
   int W = 0, B = 0, Bp = 0, in_type = 0, prec = 0, mode = 0;
+  int fprec = 0;  // prec, or'ed with kFactorF64 for the FP64 factor (launch_factor's argument)
   int64_t min_pix = 0, elem = 2, line_elems = 0, line_bytes = 0;
   float tau = 0.f;
   int Lmax = 256;
@@ -305,7 +306,10 @@ int validate(const hsad_config* cfg, std::string* why) {
   if (cfg->device_budget_bytes < 0) return bad("device_budget_bytes must be >= 0");
   if (cfg->max_batch_lines < 0 || cfg->max_batch_lines > 65535) return bad("max_batch_lines must be in [0, 65535]");
   if (cfg->result_lines < 0) return bad("result_lines must be >= 0");
-  if (cfg->flags & ~(HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES | HSAD_CUDA_GRAPHS)) return bad("unknown flags");
+  if (cfg->flags & ~(HSAD_CREATE_WAIT | HSAD_NORMALIZE_SCORES | HSAD_CUDA_GRAPHS | HSAD_FORCE_INVERSE))
+    return bad("unknown flags");
+  if (cfg->factor_precision != HSAD_FACTOR_FF && cfg->factor_precision != HSAD_FACTOR_FP64)
+    return bad("factor_precision must be HSAD_FACTOR_FF or HSAD_FACTOR_FP64");
   if ((cfg->flags & HSAD_NORMALIZE_SCORES) && cfg->stats_mode != HSAD_CUBE) return bad("HSAD_NORMALIZE_SCORES needs CUBE mode");
   if (cfg->gain)
     for (int b = 0; b < cfg->bands; ++b)
@@ -448,8 +452,8 @@ int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32
   }
   DeviceGuard dg(device);
   // the form of a streamed uint16-input context (the case with a factorisation per line)
-  const int prec = precision == HSAD_FP32 ? fp32_form(false)
-                   : precision == HSAD_BF16 ? bf16_form(bands, IN_U16, false)
+  const int prec = precision == HSAD_FP32 ? fp32_form(false, false)
+                   : precision == HSAD_BF16 ? bf16_form(bands, IN_U16, false, false)
                                             : P_FP16;
   factor_prepare(bands, prec);
   const int cap = report ? *n_rows : 0;
@@ -519,9 +523,11 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->Bp = pad64(cfg->bands);
   ctx->in_type = cfg->in_dtype == HSAD_U16 ? IN_U16 : IN_F32;
   const bool cube = cfg->stats_mode == HSAD_CUBE;
-  ctx->prec = cfg->precision == HSAD_FP32 ? fp32_form(cube)
-              : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type, cube)
+  const bool force_inverse = (cfg->flags & HSAD_FORCE_INVERSE) != 0;
+  ctx->prec = cfg->precision == HSAD_FP32 ? fp32_form(cube, force_inverse)
+              : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type, cube, force_inverse)
                                             : P_FP16;
+  ctx->fprec = ctx->prec | (cfg->factor_precision == HSAD_FACTOR_FP64 ? kFactorF64 : 0);
   ctx->lam = (cfg->forget > 0.f && cfg->forget < 1.f) ? (double)cfg->forget : 1.0;
   ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE && ctx->lam == 1.0;
   ctx->mode = cfg->stats_mode;
@@ -665,7 +671,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     }
     ctx->have_gmap = true;
   }
-  factor_prepare(ctx->B, ctx->prec);  // cluster capacities: off the first line's latency path
+  factor_prepare(ctx->B, ctx->fprec);  // cluster capacities: off the first line's latency path
   cudaGetLastError();
   *out = ctx;
   return HSAD_OK;
@@ -782,7 +788,7 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
                                        ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc, gain, ctx->s1_line,
                                      ctx->c_int, W, ctx->lam));
-  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L, B, ctx->prec,
+  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L, B, ctx->fprec,
                              (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
                              ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev, ctx->every, q0 + 1, n_line));
   if (L > 1) {
@@ -903,7 +909,7 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
                         ctx->min_pix, ctx->status, st, &ctx->lc, nullptr, gain, ctx->c_int, ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc, gain, ctx->s1_line,
                                      ctx->c_int, W, ctx->lam));
-  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, L, B, ctx->prec, ctx->wmat, ctx->y0,
+  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, L, B, ctx->fprec, ctx->wmat, ctx->y0,
                    ctx->inv_s2, ctx->status, ctx->n_stats, W, incl, st, &ctx->lc, nullptr, 1, 0, n_line));
   {
     int rc = whiten(ctx, x, L, 1, score_out(ctx, first, true));
@@ -932,7 +938,7 @@ int cube_score(hsad_ctx* ctx, const void* x, int64_t n) {
   }
   KL("finalize_cov", launch_finalize_cov(ctx->state_s1, ctx->state_s2, N, B, ctx->sigma, ctx->m_line,
                          ctx->min_pix, ctx->status, st, &ctx->lc));
-  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, 1, B, ctx->prec, ctx->wmat, ctx->y0,
+  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, 1, B, ctx->fprec, ctx->wmat, ctx->y0,
                    ctx->inv_s2, ctx->status, N, 0, 0, st, &ctx->lc));
   const bool rel = ctx->cfg.threshold_mode == HSAD_REL;
   const bool norm = (ctx->cfg.flags & HSAD_NORMALIZE_SCORES) != 0;
@@ -1143,7 +1149,7 @@ static int push_impl(hsad_ctx* ctx, const void* lines, int64_t n_lines, int32_t 
   // boundaries do not change any score.
   int64_t first_batch = ctx->Lmax, pinned_batch = ctx->Lmax;
   if (pinned) {
-    const int64_t wave = factor_wave_lines(ctx->B, ctx->prec);
+    const int64_t wave = factor_wave_lines(ctx->B, ctx->fprec);
     if (wave > 0 && n_lines >= 2 * wave && ctx->Lmax >= 2 * wave) {
       first_batch = wave;
       pinned_batch = ctx->Lmax / wave * wave;
@@ -1472,7 +1478,7 @@ int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const d
     CK(cudaMemcpyAsync(ctx->sigma, s2, (size_t)B * B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->m_line, m.data(), (size_t)B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->status, &st0, 4, cudaMemcpyHostToDevice, st));
-    KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, 1, B, ctx->prec, ctx->wmat, ctx->y0,
+    KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, 1, B, ctx->fprec, ctx->wmat, ctx->y0,
                                ctx->inv_s2, ctx->status, n_pixels, 0, 0, st, &ctx->lc));
     CK(cudaStreamSynchronize(st));  // the host vectors above are copied before they go out of scope
   } else {

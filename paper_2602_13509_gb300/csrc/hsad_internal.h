@@ -103,12 +103,36 @@ cudaError_t launch_frontend(const uint16_t* raw, int64_t n_px, int raw_bands, in
 cudaError_t launch_finalize_cov(const double* state_s1, const double* state_s2, int64_t n, int B, double* sigma,
                                 double* m, int64_t min_pixels, int32_t* status, cudaStream_t st, LaunchCounter* lc);
 
+// Arguments of one factor launch (see launch_factor).
+struct FactorArgs {
+  double* sigma;
+  double* scratch;
+  const double* m;
+  int L, B;
+  void* wmat;
+  float* y0;
+  float* inv_s2;
+  int32_t* status;
+  int64_t n0;
+  int W, incl;
+  cudaStream_t st;
+  const int64_t* n0_dev;
+  int every, q_off;
+  const double* n_line;
+};
+// launch_factor's prec argument: the working precision of the whitening operand (a Prec),
+// or'ed with kFactorF64 for FP64 arithmetic in the factor's O(B^3) work (float-float
+// otherwise).
+constexpr int kFactorF64 = 0x100;
+__host__ __device__ constexpr int out_prec(int fprec) { return fprec & 0xff; }
+
 // K4+K5: from each ready line's raw sums (lower triangle of sigma[t]) and mean offset
 // m[t]: the DN-frame covariance S_t = (S2_t - n_t m_t m_t^T) / (n_t - 1) with
 // n_t = n0 + (t + incl) W (the calibration gains cancel from Eq. 1), Cholesky with FP64
-// pivots and panel solves and float-float trailing updates, and the triangular inverse,
-// in place (sigma and scratch then hold float-float pairs), then the whitening operand in
-// the working precision, y0 and 1/s_t^2. scratch: [L][B][B] 8-byte slots.
+// pivots and 16 x 16 diagonal blocks and float-float (or, with kFactorF64, FP64) panel
+// solves and updates, and the triangular inverse, in place (sigma and scratch then hold
+// 8-byte float-float pairs or doubles), then the whitening operand in the working
+// precision, y0 and 1/s_t^2. scratch: [L][B][B] 8-byte slots.
 // The factor kernel with a given launch shape: cl CTAs per line (1, 2, 4, 8, 16) and, for
 // cl = 1, ft threads per CTA (128 or 256).
 cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, const double* m,
@@ -210,17 +234,17 @@ int whiten_trsm_stages(int B);
 // whitening dominates), which keeps the explicit inverse.
 // BF16: P_BF16T for uint16 input, else P_BF16.
 // FP32: P_FP32T (triangular solve on the SIMT cores), else P_FP32.
-// HSAD_BF16_FORM=inverse / HSAD_FP32_FORM=inverse in the environment keep the explicit
-// inverse everywhere (comparisons).
-int bf16_form(int B, int in_type, bool cube);
-int fp32_form(bool cube);
+// force_inverse (the HSAD_FORCE_INVERSE configuration flag) keeps the explicit inverse
+// everywhere (comparisons).
+int bf16_form(int B, int in_type, bool cube, bool force_inverse);
+int fp32_form(bool cube, bool force_inverse);
 
 // K7: cube maximum of delta over n_lines ring lines, then optional normalisation and
 // the REL / ABS mask.
 cudaError_t launch_cube_normalize(ScoreOut out, int64_t n_lines, int W, int rel, int normalize,
                                   unsigned int* dmax_bits, cudaStream_t st, LaunchCounter* lc);
 
-// Transmit encoding (Sec. 3.5): max_bits (zeroed by the caller) receives the bits of the
+// Transmit encoding (Sec. 3.4): max_bits (zeroed by the caller) receives the bits of the
 // largest finite positive score of s[0, n); then codes = binary16(sqrt(s / max)).
 cudaError_t launch_tx_max(const float* s, int64_t n, unsigned int* max_bits, cudaStream_t st, LaunchCounter* lc);
 cudaError_t launch_tx_encode(const float* s, int64_t n, uint16_t* codes, const unsigned int* max_bits,

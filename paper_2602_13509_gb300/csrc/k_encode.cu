@@ -1,4 +1,4 @@
-// Transmit encoding (Sec. 3.5, "Data Transmission"): every score is sent as an IEEE-754
+// Transmit encoding (Sec. 3.4, "Data Transmission"): every score is sent as an IEEE-754
 // half-precision value of its square root, normalised to the block's maximum:
 //   code = binary16(sqrt(delta / delta_max)),
 // in FP32 as the paper computes its scores (the division and square root correctly

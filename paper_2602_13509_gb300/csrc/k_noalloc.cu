@@ -79,6 +79,20 @@ extern "C" int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t
                                       int32_t in_dtype, int32_t precision, const float* gain,
                                       int32_t threshold_mode, float threshold, int32_t flags, float* scores,
                                       uint8_t* mask, void* stream, int32_t device) {
+  if (n_lines == 0) {
+    // start-up warm-up: only the one-time set-up of `device` (the module load that commits
+    // the scratch array, and its address lookup), so that no later call pays for it
+    if (device < 0 || device >= kMaxDevices) return noalloc_fail(HSAD_E_INVALID, "bad device");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != device && cudaSetDevice(device) != cudaSuccess) {
+      cudaGetLastError();
+      return noalloc_fail(HSAD_E_CUDA, "cudaSetDevice failed");
+    }
+    const int rc = scratch_address(device) ? HSAD_OK : noalloc_fail(HSAD_E_CUDA, "cudaGetSymbolAddress failed");
+    if (prev >= 0 && prev != device) cudaSetDevice(prev);
+    return rc;
+  }
   if (!cube || !scores || !mask) return noalloc_fail(HSAD_E_INVALID, "cube, scores and mask are required");
   if (n_lines < 1 || width < 1 || bands < 1 || bands > 512) return noalloc_fail(HSAD_E_INVALID, "bad sizes");
   if (n_lines > 0x7fffffff || (int64_t)width * bands > ((int64_t)1 << 31))

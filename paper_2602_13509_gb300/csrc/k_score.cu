@@ -9,7 +9,8 @@
 //
 // Operand terms per working precision (products exact in FP32, FP32 accumulation):
 //   FP32 : x' (exact for uint16) times G (float)
-//   FP16 : h(x') times G_hi, h(x') times G_lo           (h: round to FP16)
+//   FP16 : h(x') times G_hi, h(x') times G_lo           (h: round to FP16; integer input)
+//          H times G_hi, H times G_lo, R times G_hi      (float input: H = h(x'), R = h(x' - H))
 //   BF16 : H times G_hi, H times G_lo, R times G_hi      (x' = H + R, both exact in BF16:
 //          integer input H = 64 rint(x'/64); float input H = bf16(x'), R = bf16(x' - H))
 #include <cuda_bf16.h>
@@ -44,7 +45,7 @@ __device__ __forceinline__ void split_x(float x, float& a0, float& a1) {
     a1 = 0.f;
   } else if (PREC == P_FP16) {
     a0 = __half2float(__float2half_rn(x));
-    a1 = 0.f;
+    a1 = sizeof(In) == 4 ? __half2float(__float2half_rn(x - a0)) : 0.f;
   } else {
     if (sizeof(In) == 2) {
       const float h = 64.f * rintf(x * (1.f / 64.f));
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256) whiten_score_kernel(
 #pragma unroll
           for (int s2 = 0; s2 < 4; ++s2) acc[r][s2] = fmaf(a0[r], b1[s2], acc[r][s2]);
       }
-      if (PREC == P_BF16) {
+      if (PREC == P_BF16 || (PREC == P_FP16 && sizeof(In) == 4)) {
         float a1[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) a1[r] = As[cur][1][kk][ty * 4 + r];

@@ -18,8 +18,9 @@
 //                      128-byte row, conflict free); afterwards the same 128 threads are
 //                      the epilogue, one pixel (TMEM lane) each.
 //   warp 5 (one lane)  issues tcgen05.mma (M = 128, N = 128 or 64, K = 16) into a 128 x Bp FP32
-//                      accumulator in TMEM: FP16 terms x'.G_hi + x'.G_lo, BF16 terms
-//                      H.G_hi + H.G_lo + R.G_hi; commits free the smem stages.
+//                      accumulator in TMEM: FP16 terms x'.G_hi + x'.G_lo (integer input),
+//                      BF16 (and FP16 with float input) terms H.G_hi + H.G_lo + R.G_hi;
+//                      commits free the smem stages.
 // Every wait is bounded; a timeout sets *err and the CTA drains and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -119,7 +120,10 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   bool ok = true;
-  constexpr int NT = (PREC == P_BF16) ? 3 : 2;
+  // terms: BF16 H.G_hi + H.G_lo + R.G_hi; FP16 x'.G_hi + x'.G_lo for integer input (x' exact
+  // in FP16 up to 2048), and H.G_hi + H.G_lo + R.G_hi with x' = H + R (two FP16 values, 22
+  // bits) for float input, whose centred values a single FP16 keeps to only 11 bits
+  constexpr int NT = (PREC == P_BF16 || sizeof(In) == 4) ? 3 : 2;
 
   if (warp == 4) {
     // ---------------- copy engine: raw tile, then G blocks ----------------
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
             if (PREC != P_FP16) *(uint4*)(A1 + off) = make_uint4(p1w[0], p1w[1], p1w[2], p1w[3]);
           }
         } else {
-          // float input: one value at a time (BF16: H = bf16(v), R = bf16(v - H))
+          // float input: one value at a time (H = rn(v), R = rn(v - H) in BF16 or FP16)
           for (int u = tid; u < WT_M * 8; u += WT_M) {
             const int r = u >> 3;
 #pragma unroll
@@ -290,7 +294,9 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
               if (r < npx && k < B) v = centred_tc<In>(src[(int64_t)r * B + k], c_int, c_flt, k);
               const uint32_t off = tc::sw128_offset(r, kg * 8 + j);
               if (PREC == P_FP16) {
-                *(__half*)(A0 + off) = __float2half_rn(v);
+                const __half h = __float2half_rn(v);
+                *(__half*)(A0 + off) = h;
+                *(__half*)(A1 + off) = __float2half_rn(v - __half2float(h));
               } else {
                 const float h = __bfloat162float(__float2bfloat16_rn(v));
                 *(__nv_bfloat16*)(A0 + off) = __float2bfloat16_rn(h);

@@ -309,15 +309,13 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   }
 }
 
-int bf16_form(int B, int in_type, bool cube) {
-  const char* v = getenv("HSAD_BF16_FORM");
-  if (cube || (v && strcmp(v, "inverse") == 0)) return P_BF16;
+int bf16_form(int B, int in_type, bool cube, bool force_inverse) {
+  if (cube || force_inverse) return P_BF16;
   return in_type == IN_U16 && whiten_trsm_stages(B) > 0 ? P_BF16T : P_BF16;
 }
 
-int fp32_form(bool cube) {
-  const char* v = getenv("HSAD_FP32_FORM");
-  return cube || (v && strcmp(v, "inverse") == 0) ? P_FP32 : P_FP32T;
+int fp32_form(bool cube, bool force_inverse) {
+  return cube || force_inverse ? P_FP32 : P_FP32T;
 }
 
 int whiten_trsm_stages(int B) {

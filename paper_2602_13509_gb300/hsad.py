@@ -25,7 +25,8 @@ HSAD_FORM_INVERSE, HSAD_FORM_TRIANGULAR_SOLVE = 0, 1
 HSAD_EXCLUSIVE, HSAD_INCLUSIVE, HSAD_CUBE = 0, 1, 2
 HSAD_ABS, HSAD_REL = 0, 1
 HSAD_HOST, HSAD_DEVICE = 0, 1
-HSAD_CREATE_WAIT, HSAD_NORMALIZE_SCORES, HSAD_CUDA_GRAPHS = 1, 2, 4
+HSAD_CREATE_WAIT, HSAD_NORMALIZE_SCORES, HSAD_CUDA_GRAPHS, HSAD_FORCE_INVERSE = 1, 2, 4, 8
+HSAD_FACTOR_FF, HSAD_FACTOR_FP64 = 0, 1
 # per-line status
 LS_OK, LS_NOT_READY, LS_NOT_PD, LS_INVALID_DATA = 0, 1, 2, 3
 
@@ -42,6 +43,7 @@ class hsad_config(C.Structure):
         ("raw_bands", C.c_int32), ("band_first", C.c_int32), ("band_bin", C.c_int32),
         ("factor_every", C.c_int32),
         ("forget", C.c_float),
+        ("factor_precision", C.c_int32),
     ]
 
 
@@ -362,7 +364,7 @@ _NAMES = {
 def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="exclusive", cube_lines=0,
                 gain=None, offset=None, threshold_mode="abs", threshold=0.0, warmup_pixels=0,
                 device_budget_bytes=0, flags=0, device=0, max_batch_lines=0, result_lines=0,
-                raw_bands=0, band_first=0, band_bin=1, factor_every=0, forget=0.0):
+                raw_bands=0, band_first=0, band_bin=1, factor_every=0, forget=0.0, factor_precision="ff"):
     """Build an hsad_config; ``gain``/``offset`` arrays are kept alive on the struct."""
     import numpy as np
     cfg = hsad_config_init()
@@ -379,6 +381,7 @@ def make_config(width, bands, in_dtype="u16", precision="fp32", stats_mode="excl
     cfg.raw_bands, cfg.band_first, cfg.band_bin = int(raw_bands), int(band_first), int(band_bin)
     cfg.factor_every = int(factor_every)
     cfg.forget = float(forget)
+    cfg.factor_precision = {"ff": HSAD_FACTOR_FF, "fp64": HSAD_FACTOR_FP64}.get(factor_precision, factor_precision)
     keep = []
     for name, arr in (("gain", gain), ("offset", offset)):
         if arr is not None:
@@ -436,7 +439,7 @@ class Detector:
         return rc, s, m, st
 
     def scores_tx(self, first, n, timeout_ms=-1):
-        """Transmit codes (Sec. 3.5): ``(status, codes uint16 [n, W], delta_max)``."""
+        """Transmit codes (Sec. 3.4): ``(status, codes uint16 [n, W], delta_max)``."""
         import numpy as np
         codes = np.empty((n, self.width), dtype=np.uint16)
         rc, mx = hsad_scores_tx(self.ctx, first, n, codes, HSAD_HOST, timeout_ms)

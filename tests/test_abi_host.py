@@ -37,9 +37,13 @@ def test_config_defaults_and_struct_size(hs):
     cfg = hs.hsad_config_init()
     assert cfg.in_dtype == hs.HSAD_U16 and cfg.precision == hs.HSAD_FP32
     assert cfg.stats_mode == hs.HSAD_EXCLUSIVE and cfg.threshold_mode == hs.HSAD_ABS
-    assert C.sizeof(hs.hsad_config) == 104  # 80 + the front-end, cadence and forgetting fields
+    # 80 + the front-end, cadence, forgetting and factor-precision fields (the last fills
+    # the 4-byte tail padding of the 8-byte aligned struct)
+    assert C.sizeof(hs.hsad_config) == 104
+    assert hs.hsad_config.factor_precision.offset == 100
     assert cfg.raw_bands == 0 and cfg.band_first == 0 and cfg.band_bin == 0   # front end off
     assert cfg.forget == 0.0                                                  # forgetting off
+    assert cfg.factor_precision == hs.HSAD_FACTOR_FF                          # float-float factor
 
 
 @pytest.mark.parametrize("field,value,msg", [
@@ -48,6 +52,8 @@ def test_config_defaults_and_struct_size(hs):
     ("threshold_mode", 4, "threshold_mode"), ("threshold", -1.0, "threshold"),
     ("warmup_pixels", -5, "warmup"), ("max_batch_lines", 70000, "max_batch_lines"), ("flags", 64, "flags"),
     ("forget", 1.5, "forget"), ("forget", -0.25, "forget"), ("forget", float("nan"), "forget"),
+    ("factor_precision", 2, "factor_precision"), ("factor_precision", -1, "factor_precision"),
+    ("flags", 16, "flags"),
 ])
 def test_create_rejects_bad_fields(hs, field, value, msg):
     cfg = hs.make_config(64, 32)

@@ -20,7 +20,7 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["metric"] == "pixel-spectra scored/s" and d["unit"] == "pixel-spectra/s"
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] >= 3 and d["higher_is_better"] is True
-    assert d["vs_baseline"] is None and d["config"]["workload"] == "stream_640x270"
+    assert d["vs_baseline"] is None and d["config"]["workload"] == "precision_1024x448"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
@@ -35,3 +35,30 @@ def test_roofline_work_and_peaks():
     assert abs(bench.factor_flops_per_line(270, 0) - 2 * 270 ** 3 / 3) < 1e-6
     assert abs(bench.fp64_peak_tflops(2070) - 1.25856) < 1e-9                    # 152 x 2070 MHz x 4
     assert abs(bench.ff_peak_tflops(2070) - 152 * 2070e6 * 128 * 2 / 12 / 1e12) < 1e-12
+
+
+def test_kernel_rooflines_from_a_profile():
+    """Per-kernel roofline entries: algorithmic work per launch over the launch's time,
+    against the peak of the unit that bounds each kernel."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peaks = {"hbm_gbs": 6753.4, "bf16_tflops": 1849.2, "source": "measured"}
+    T, W, B = 8000, 1024, 448
+    # two steps profiled: factor 4 launches of 2000 lines, syrk 4 launches, whitening 8
+    prof = {"factor": (8, 8 * 30.0), "syrk": (8, 8 * 5.0), "whiten_score": (16, 16 * 2.0), "colsum": (8, 1.0)}
+    r = bench.kernel_rooflines(prof, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)
+    assert set(r) == {"factor", "syrk", "whiten_score"}
+    f = r["factor"]
+    assert f["launches_per_step"] == 4 and abs(f["avg_launch_ms"] - 30.0) < 1e-12
+    assert abs(f["achieved"] - 2000 * bench.factor_flops_per_line(B, 1) / 0.030 / 1e12) < 1e-9
+    assert f["bound"] == "alu" and abs(f["frac"] - f["achieved"] / bench.ff_peak_tflops(2070.0)) < 1e-12
+    s = r["syrk"]
+    px = T * W / 4
+    assert s["bound"] == "tensor" and abs(s["achieved"] - px * B * (B + 1) / 0.005 / 1e12) < 1e-9
+    assert abs(s["frac"] - s["achieved"] / 1849.2) < 1e-12
+    assert abs(s["traffic_algorithmic"] - px * 2 * B) < 1e-6
+    w = r["whiten_score"]
+    assert w["bound"] == "alu" and abs(w["peak"] - bench.fp32_peak_tflops(2070.0)) < 1e-12
+    assert abs(w["traffic_algorithmic"] - T * W / 8 * (2 * B + 5)) < 1e-6
+    wb = bench.kernel_rooflines(prof, 2, T, W, B, 1, "bf16", 1, peaks, 2070.0)["whiten_score"]
+    assert wb["bound"] == "tensor" and wb["peak"] == 1849.2

@@ -1,4 +1,4 @@
-"""Transmit encoding (Sec. 3.5) on the GPU against the oracle (needs a GB300).
+"""Transmit encoding (Sec. 3.4) on the GPU against the oracle (needs a GB300).
 
 The encoding is integer-valued (binary16 codes), so given the same FP32 scores both sides
 must agree bit for bit; against the oracle's own FP64 scores the codes may differ by one

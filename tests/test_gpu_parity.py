@@ -50,14 +50,12 @@ def test_config1_cube_global_rx(hs, prec):
     rc, s, m, st, nl = _run(hs, cube, in_dtype="f32", precision=prec, stats_mode="cube", cube_lines=64,
                             threshold_mode="rel", threshold=0.110)
     assert rc == hs.HSAD_OK and (st == 0).all() and nl > 0
+    # float input: the centred values are split into two BF16 (or two FP16) terms, 16 (22)
+    # of their 24 bits, and G into hi + lo; the scores still meet each precision's tolerance
     emax, _ = rel_err(s, dref)
-    if prec == "fp32":
-        assert emax <= TOL["fp32"], emax
-        assert mask_mismatch(m, dnorm, 0.110, 2 * MARGIN["fp32"]) == 0
-    else:
-        # float input is not integer, so the BF16/FP16 operand split is approximate:
-        # only the ranking property is required here
-        assert np.median(s[anom]) > np.percentile(s[~anom], 99)
+    assert emax <= TOL[prec], emax
+    assert mask_mismatch(m, dnorm, 0.110, 2 * MARGIN[prec]) == 0
+    assert np.median(s[anom]) > np.percentile(s[~anom], 99)
 
 
 def test_config1_normalized_scores(hs):
@@ -142,6 +140,67 @@ def test_whitening_form_per_context(hs, prec, dtype, B, mode, form):
     det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype, stats_mode=mode, **kw)
     assert det.whitening_form == form
     det.close()
+    # HSAD_FORCE_INVERSE keeps the explicit inverse everywhere
+    det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype, stats_mode=mode,
+                      flags=hs.HSAD_FORCE_INVERSE, **kw)
+    assert det.whitening_form == hs.HSAD_FORM_INVERSE
+    det.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_forced_inverse_form_matches_oracle(hs, prec):
+    """A streamed context forced to the explicit-inverse form (full L^{-1}, one GEMM) scores
+    the same lines as the oracle within each precision's tolerance."""
+    sc, lines = _scene_lines(30, 130, 200, seed=31)
+    rc, s, m, st, _ = _run(hs, lines, stats_mode="exclusive", precision=prec, gain=sc.gain, offset=sc.offset,
+                           flags=hs.HSAD_FORCE_INVERSE, max_batch_lines=11)
+    ref, rst = orx.stream_rx(lines, oracle.EXCLUSIVE, gain=sc.gain, offset=sc.offset)
+    np.testing.assert_array_equal(st, rst)
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL[prec], emax
+    assert mask_mismatch(m, ref, 200 + 6 * np.sqrt(400), MARGIN[prec]) == 0
+
+
+# ------------------------------------------------------------------ FP64 factor form
+@pytest.mark.parametrize("prec,mode,W,B,batch", [("fp32", "exclusive", 33, 127, 0), ("fp32", "exclusive", 130, 270, 1),
+                                                 ("fp32", "inclusive", 130, 448, 5), ("bf16", "exclusive", 300, 130, 0),
+                                                 ("bf16", "exclusive", 130, 270, 1), ("fp16", "exclusive", 65, 65, 0),
+                                                 ("fp32", "cube", 64, 100, 0), ("bf16", "cube", 64, 100, 0)])
+def test_fp64_factor_matches_oracle(hs, prec, mode, W, B, batch):
+    """factor_precision = HSAD_FACTOR_FP64: the factor's O(B^3) work in FP64 instead of
+    float-float, in one-CTA (whole pushes) and cluster (one-line pushes) launch shapes, in
+    both whitening forms; same tolerances, and the scores differ from the float-float
+    factor's only in the last bits."""
+    T = max(8, (B + 1) // W + 5)
+    sc, lines = _scene_lines(T, W, B, seed=W * 7 + B)
+    kw = dict(stats_mode=mode, precision=prec, gain=sc.gain, offset=sc.offset)
+    if mode == "cube":
+        kw["cube_lines"] = T
+    out = {}
+    for fp in ("fp64", "ff"):
+        det = hs.Detector(width=W, bands=B, factor_precision=fp, **kw)
+        if batch:
+            for t in range(0, T, batch):
+                det.push(lines[t:t + batch])
+        else:
+            det.push(lines)
+        if mode == "cube":
+            det.flush()
+        rc, s, m, st = det.scores(0, T)
+        det.close()
+        out[fp] = (s, m, st)
+    if mode == "cube":
+        ref, rst = orx.stream_rx(lines, oracle.CUBE, cube_lines=T, gain=sc.gain, offset=sc.offset)
+    else:
+        ref, rst = orx.stream_rx(lines, getattr(oracle, mode.upper()), gain=sc.gain, offset=sc.offset)
+    s, m, st = out["fp64"]
+    np.testing.assert_array_equal(st, rst)
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL[prec], emax
+    assert mask_mismatch(m, ref, B + 6 * np.sqrt(2 * B), MARGIN[prec]) == 0
+    ok = np.isfinite(ref)
+    d = np.abs(out["ff"][0][ok].astype(np.float64) - s[ok]) / np.maximum(ref[ok], 1.0)
+    assert d.max() <= (1e-5 if prec == "fp32" else 1e-3), d.max()
 
 
 def test_stream_resets_and_warmup(hs):

@@ -303,7 +303,7 @@ def test_pushbroom_anomalies_rank_above_background():
     assert np.median(dd[mm]) > np.percentile(dd[~mm], 99)
 
 
-# ------------------------------------------------------------------ transmit encoding (Sec. 3.5)
+# ------------------------------------------------------------------ transmit encoding (Sec. 3.4)
 def _binary16_value(c):
     """Value of a binary16 bit pattern, decoded field by field (sign, exponent, mantissa)."""
     c = int(c)

@@ -3,8 +3,9 @@
 hsad_global_rx_noalloc serves callers that cannot allocate device memory: it keeps
 its intermediates in one static device array instead. Its scores and mask must
 agree with a CUBE-mode context scoring the same cube, on two calls in a row (the
-second call reuses the array with the first call's contents still in it). This
-file is collected last on purpose.
+second call reuses the array with the first call's contents still in it), also when the
+earlier call left a larger layout (more lines, more bands, another padded width) or
+stopped at a warm-up status. This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -90,3 +91,37 @@ def test_noalloc_rejects_oversize_and_bad_arguments(hs):
                                      s, m, None, 0) == hs.HSAD_E_INVALID
     assert hs.hsad_global_rx_noalloc(None, 4, 8, 512, hs.HSAD_U16, hs.HSAD_FP32, None, hs.HSAD_ABS, 0.0, 0,
                                      s, m, None, 0) == hs.HSAD_E_INVALID
+
+
+def test_noalloc_startup_warmup_call(hs):
+    """n_lines = 0 only sets the device up (module load, array address) and succeeds with
+    every pointer NULL; a bad device is still rejected."""
+    assert hs.hsad_global_rx_noalloc(None, 0, 0, 0, 0, 0, None, 0, 0.0, 0, None, None, None, 0) == hs.HSAD_OK
+    assert hs.hsad_global_rx_noalloc(None, 0, 0, 0, 0, 0, None, 0, 0.0, 0, None, None, None, -1) == \
+        hs.HSAD_E_INVALID
+
+
+def test_noalloc_after_larger_layout_and_warmup_status(hs):
+    """Each region of the shared array is written before it is read: a call on a smaller
+    cube (fewer lines, fewer bands, a smaller padded band count) after a larger one, and a
+    good call after one that stopped at HSAD_E_NOT_READY, both match a fresh CUBE-mode
+    context."""
+    from gen import PushbroomScene
+    big_sc = PushbroomScene(96, 130, seed=33)
+    big = big_sc.lines(0, 60).view(np.int16)
+    small_sc = PushbroomScene(64, 40, seed=34)
+    small = small_sc.lines(0, 20).view(np.int16)
+    rc, s_big, _ = _noalloc(hs, big, "u16", "fp32", big_sc.gain, "abs", 0.0, 0)
+    assert rc == hs.HSAD_OK
+    rc0, s0, m0 = _context_scores(hs, small, "u16", "fp32", small_sc.gain, "abs", 0.0, 0)
+    assert rc0 == hs.HSAD_OK
+    tau = 40 + 6 * np.sqrt(80)
+    rc, s, m = _noalloc(hs, small, "u16", "fp32", small_sc.gain, "abs", 0.0, 0)
+    assert rc == hs.HSAD_OK
+    assert rel_err(s, s0)[0] <= TOL["fp32"] and mask_mismatch(m, s0, tau, MARGIN["fp32"]) == 0
+    # 8 pixels of 40 bands: fewer than B + 1, nothing to score
+    rc, s_nr, m_nr = _noalloc(hs, np.ascontiguousarray(small[:1, :8]), "u16", "bf16", small_sc.gain, "abs", 0.0, 0)
+    assert rc == hs.HSAD_E_NOT_READY and np.isnan(s_nr).all() and (m_nr == 0).all()
+    rc, s, m = _noalloc(hs, small, "u16", "fp32", small_sc.gain, "abs", 0.0, 0)
+    assert rc == hs.HSAD_OK
+    assert rel_err(s, s0)[0] <= TOL["fp32"] and mask_mismatch(m, s0, tau, MARGIN["fp32"]) == 0
