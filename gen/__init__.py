@@ -13,4 +13,5 @@ from .cubes import (  # noqa: F401
     config_scene,
     serving_streams,
     stress_cubes,
+    subsample_indices,
 )

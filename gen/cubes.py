@@ -283,6 +283,14 @@ class IllConditionedScene:
         return (out / 4096.0).astype(np.float32)
 
 
+def subsample_indices(n_pixels: int, m: int, seed: int) -> np.ndarray:
+    """m distinct pixel indices in [0, n_pixels), uniform without replacement, sorted: the
+    random background subsample of subsampled kernel RX (drawn here, passed to both sides)."""
+    if not 0 < m <= n_pixels:
+        raise ValueError("need 0 < m <= n_pixels")
+    return np.sort(rng_for(seed, 2).choice(n_pixels, size=m, replace=False)).astype(np.int64)
+
+
 # Named workloads (seed SEED_BASE + k for workload k).
 SCENES = {
     "stream_640x270": dict(width=640, bands=270, lines=4000, seed=SEED_BASE + 2),

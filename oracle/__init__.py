@@ -1,4 +1,5 @@
-"""Plain FP64 CPU oracle for global and streaming RX anomaly detection.
+"""Plain FP64 CPU oracle for global and streaming RX anomaly detection, and subsampled
+kernel RX (``oracle.krx``).
 
 TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference arm of ``bench.py`` may import this package. The
@@ -31,3 +32,4 @@ from .rx import (  # noqa: F401
     stream_rx_line,
     threshold_mask,
 )
+from . import krx  # noqa: F401,E402
