@@ -337,6 +337,36 @@ int hsad_global_rx_noalloc(const void* cube, int64_t n_lines, int32_t width, int
                            int32_t threshold_mode, float threshold, int32_t flags, float* scores,
                            uint8_t* mask, void* stream, int32_t device);
 
+/* Subsampled kernel RX (Sec. 2.2, Table tab:results: the kernel RX variant the paper's prior
+ * work compared with global RX, citing Kwon and Nasrabadi's kernel RX and Hidalgo et al.'s
+ * subsampled form) of one cube already in device memory of `device`. The background is the m
+ * pixels subsample[0 .. m) (distinct flat pixel indices, host array, drawn by the caller);
+ * every pixel r of the cube is scored
+ *     delta(r) = (m - 1) || (K~ + lam I)^{-1} H (k_r - K 1 / m) ||^2
+ * with the Gaussian kernel k(x, y) = exp(-||x - y||^2 / c) on the calibrated bands
+ * (x_b = v_b gain_b: offsets cancel), K the m x m kernel matrix of the background,
+ * H = I - 1 1^T / m, K~ = H K H, (k_r)_i = k(s_i, r), lam = ridge tr(K~) / m, and
+ * c = kernel_width, or the mean squared distance between distinct background pixels when
+ * kernel_width is 0.
+ *   cube       device [n_pixels][bands], in_dtype (HSAD_U16 | HSAD_F32), bands contiguous
+ *   m          2 .. 512, <= n_pixels
+ *   ridge      > 0 (relative ridge eps; 1e-2 is a sound default: the scores' sensitivity to
+ *              rounding grows with kappa(K~ + lam I), about 1 / eps)
+ *   gain       host array of `bands` floats or NULL (all 1), finite and non-zero
+ *   threshold_mode / threshold / flags (HSAD_NORMALIZE_SCORES only) as in hsad_config
+ *              (threshold 0 with HSAD_ABS means bands + 6 sqrt(2 bands))
+ *   scores     device float [n_pixels], mask device uint8 [n_pixels]
+ *   stream     cudaStream_t to run on (NULL = legacy default stream)
+ * The background statistics are FP64 (Cholesky factor and inverse by the factor kernel);
+ * the per-pixel squared distances and the product with (K~ + lam I)^{-1} H carry float-float
+ * sums on the FP32 pipe. Allocates its scratch (stream-ordered, about 40 m^2 + 8 m B bytes)
+ * and frees it before returning; the call returns after the scores are written: HSAD_OK,
+ * HSAD_E_NOT_PD (K~ + lam I not positive definite), HSAD_E_INVALID (bad argument, repeated or
+ * out-of-range indices), HSAD_E_INVALID_DATA (non-finite float input) or HSAD_E_CUDA. */
+int hsad_krx(const void* cube, int64_t n_pixels, int32_t bands, int32_t in_dtype, const int64_t* subsample,
+             int32_t m, float kernel_width, float ridge, const float* gain, int32_t threshold_mode,
+             float threshold, int32_t flags, float* scores, uint8_t* mask, void* stream, int32_t device);
+
 /* Factor-kernel autotuner (no counterpart in the paper). Times every launch shape of the
  * factorisation (one 128-thread CTA per line with registers for 4 or 5 CTAs per SM,
  * one 256-thread CTA per line, or a 2/4/8/16-CTA cluster per line) on synthetic

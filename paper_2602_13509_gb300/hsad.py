@@ -87,6 +87,8 @@ def _load():
         "hsad_global_rx_noalloc": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                              C.POINTER(C.c_float), C.c_int32, C.c_float, C.c_int32, P, P, P,
                                              C.c_int32]),
+        "hsad_krx": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, P, C.c_int32, C.c_float, C.c_float,
+                               C.POINTER(C.c_float), C.c_int32, C.c_float, C.c_int32, P, P, P, C.c_int32]),
         "hsad_engine_create": (C.c_int, [C.c_int32, C.c_int64, C.POINTER(P)]),
         "hsad_engine_open": (C.c_int, [P, C.POINTER(hsad_config), C.POINTER(C.c_int32)]),
         "hsad_engine_submit": (C.c_int, [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_uint64)]),
@@ -268,6 +270,21 @@ def hsad_profile_read(ctx, index: int):
 
 def hsad_profile_reset(ctx) -> int:
     return _lib.hsad_profile_reset(ctx)
+
+
+def hsad_krx(cube, n_pixels, bands, in_dtype, subsample, kernel_width, ridge, gain, threshold_mode, threshold,
+             flags, scores, mask, stream=None, device=0) -> int:
+    """Subsampled kernel RX of one device cube (see include/hsad.h); ``subsample``: host
+    int64 pixel indices."""
+    import numpy as np
+    idx = np.ascontiguousarray(np.asarray(subsample, dtype=np.int64).reshape(-1))
+    g = None
+    if gain is not None:
+        keep = np.ascontiguousarray(np.asarray(gain, dtype=np.float32))
+        g = keep.ctypes.data_as(C.POINTER(C.c_float))
+    return _lib.hsad_krx(_ptr(cube), int(n_pixels), int(bands), int(in_dtype), idx.ctypes.data, int(idx.size),
+                         float(kernel_width), float(ridge), g, int(threshold_mode), float(threshold), int(flags),
+                         _ptr(scores), _ptr(mask), stream, int(device))
 
 
 def hsad_global_rx_noalloc(cube, n_lines, width, bands, in_dtype, precision, gain, threshold_mode,
