@@ -15,12 +15,14 @@
 //     float-float pairs (G transposed, [j][i], for coalesced rows);
 //   per pixel (krx_score_kernel, SIMT): squared distances to the m samples (exact
 //     differences times the band's gain, FP32 partial sums of 8 bands gathered in
-//     float-float), k = expf(-d / c), y = G k - ybar accumulated in float-float, and
-//     delta = (m - 1) ||y||^2 (FP32 squares, FP64 sum over the outputs).
+//     float-float), k = exp(-d / c) as a float-float pair (ff_exp_neg), y = G k - ybar
+//     accumulated in float-float, and delta = (m - 1) ||y||^2 (FP32 squares, FP64 sum over
+//     the outputs).
 // The map k -> y amplifies rounding by up to kappa(K~ + lam I) (about 1e4 at eps = 1e-2):
 // a CPU emulation with FP32 distances and FP32 accumulation of G k gave 1.7e-4 relative
-// error, with float-float distance sums and accumulation 1.7e-5; that is why those two
-// steps carry a second FP32 word.
+// error, with float-float distance sums and accumulation 1.7e-5, and the FP32 rounding
+// of k alone left 1e-4 on a float cube with a narrow kernel (exact k: 6e-6); that is why
+// these steps carry a second FP32 word.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -50,6 +52,74 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float p) {
   const float z = __fsub_rn(t, s);
   c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)));
   s = t;
+}
+
+// Float-float product of a pair and a pair (two-product of the high words with the cross
+// terms), renormalised.
+__device__ __forceinline__ float2 ffm(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+// a + b in float-float (two-sum of the high words, low words added, renormalised).
+__device__ __forceinline__ float2 ffa(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float z = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.x, __fsub_rn(s, z)), __fsub_rn(b.x, z)), __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+// Constants of the float-float exponential, formed once per CTA in FP64: 1/i! for
+// i = 0 .. 12 and ln 2 in three parts (Cody and Waite's reduction: the first part has
+// 11 significant bits, so n ln2_1 is exact for the integers n used here).
+struct ExpConsts {
+  float2 inv_fact[13];
+  float ln2[3];
+};
+__device__ void exp_consts_init(ExpConsts* ec) {
+  if (threadIdx.x == 0) {
+    double f = 1.0;
+    for (int i = 0; i <= 12; ++i) {
+      if (i > 0) f *= i;
+      const double v = 1.0 / f;
+      const float h = __double2float_rn(v);
+      ec->inv_fact[i] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+    const double ln2 = 0.69314718055994530942;
+    const double l1 = rint(ln2 * 2048.0) / 2048.0;
+    const float l2 = __double2float_rn(ln2 - l1);
+    ec->ln2[0] = (float)l1;
+    ec->ln2[1] = l2;
+    ec->ln2[2] = __double2float_rn(ln2 - l1 - (double)l2);
+  }
+}
+// exp(-t) for a float-float t >= 0, as a float-float pair (about 45 correct bits): with
+// n = rint(t / ln 2) and r = t - n ln 2 (|r| <= ln(2) / 2, formed exactly enough from the
+// three parts of ln 2), exp(-t) = 2^-n exp(-r), exp(-r) by its Taylor polynomial of degree
+// 12 (truncation below 2^-46) in Horner form. Zero once 2^-n leaves FP32's normal range.
+__device__ __forceinline__ float2 ff_exp_neg(float2 t, const ExpConsts& ec) {
+  const float n = rintf(__fmul_rn(t.x, 1.4426950408889634f));
+  if (n > 120.f) return make_float2(0.f, 0.f);
+  const float r1 = __fmaf_rn(-n, ec.ln2[0], t.x);      // exact: n ln2_1 has at most 18 bits
+  const float p = __fmul_rn(n, ec.ln2[1]);
+  const float pe = __fmaf_rn(n, ec.ln2[1], -p);
+  float2 r = ffa(make_float2(r1, 0.f), make_float2(-p, -pe));
+  r = ffa(r, make_float2(__fsub_rn(t.y, __fmul_rn(n, ec.ln2[2])), 0.f));
+  const float2 mr = make_float2(-r.x, -r.y);
+  float2 acc = ec.inv_fact[12];
+#pragma unroll
+  for (int i = 11; i >= 0; --i) acc = ffa(ffm(acc, mr), ec.inv_fact[i]);
+  const float sc = ldexpf(1.f, -(int)n);
+  return make_float2(__fmul_rn(acc.x, sc), __fmul_rn(acc.y, sc));
+}
+
+__device__ __forceinline__ float2 fk_norm(float s, float c) {
+  const float h = __fadd_rn(s, c);
+  return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
 }
 
 template <typename In>
@@ -202,15 +272,19 @@ __global__ void __launch_bounds__(KX_T, 2) krx_score_kernel(const In* __restrict
                                                          float* __restrict__ scores, uint8_t* __restrict__ mask,
                                                          float tau, int write_mask) {
   extern __shared__ __align__(16) float sm[];
-  float* kS = sm;                              // [mj][KX_P]
-  float* Xs = kS + (size_t)mj * KX_P;          // [KX_BC][KX_P]
+  float* kS = sm;                              // [mj][KX_P] high words of the kernel values
+  float* kL = kS + (size_t)mj * KX_P;          // [mj][KX_P] low words
+  float* Xs = kL + (size_t)mj * KX_P;          // [KX_BC][KX_P]
   float* Ss = Xs + KX_BC * KX_P;               // [KX_BC][KX_JC]
   float* gs = Ss + KX_BC * KX_JC;              // [round_up(B, 4)]
   double* red = (double*)(gs + round_up(B, 4)); // [KX_T / 8][KX_P]
   const int tid = threadIdx.x;
   const int64_t p0 = (int64_t)blockIdx.x * KX_P;
   const int npx = (int)min((int64_t)KX_P, n_px - p0);
-  const float rc = (float)(1.0 / scal[0]);
+  __shared__ ExpConsts ec;
+  exp_consts_init(&ec);
+  const double rcd = 1.0 / scal[0];
+  const float2 rc = make_float2(__double2float_rn(rcd), __double2float_rn(rcd - (double)__double2float_rn(rcd)));
   for (int b = tid; b < B; b += KX_T) gs[b] = gw[b];
 
   // ---- phase A: kernel values -------------------------------------------------------
@@ -262,9 +336,11 @@ __global__ void __launch_bounds__(KX_T, 2) krx_score_kernel(const In* __restrict
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
           two_sum_acc(s[u][v], c[u][v], a[u][v]);
-          const float d = __fadd_rn(s[u][v], c[u][v]);
           const int j = j0 + 2 * tj + v;
-          kS[j * KX_P + 4 * tp + u] = (j < m) ? expf(-__fmul_rn(d, rc)) : 0.f;
+          // k = exp(-d / c) with d and 1 / c as float-float pairs
+          const float2 kv = (j < m) ? ff_exp_neg(ffm(fk_norm(s[u][v], c[u][v]), rc), ec) : make_float2(0.f, 0.f);
+          kS[j * KX_P + 4 * tp + u] = kv.x;
+          kL[j * KX_P + 4 * tp + u] = kv.y;
         }
     }
   }
@@ -296,15 +372,17 @@ __global__ void __launch_bounds__(KX_T, 2) krx_score_kernel(const In* __restrict
         l1 = *(const float4*)(nl + 4);
       }
       const float4 kv = *(const float4*)&kS[j * KX_P + 4 * tp];
-      const float ka[4] = {kv.x, kv.y, kv.z, kv.w};
+      const float4 kw = *(const float4*)&kL[j * KX_P + 4 * tp];
+      const float ka[4] = {kv.x, kv.y, kv.z, kv.w}, kb[4] = {kw.x, kw.y, kw.z, kw.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-          // G_ij k_j: product error by FMA (two-product) with the lo word's term, sum by two-sum
+          // G_ij k_j: product error by FMA (two-product) with the cross terms, sum by two-sum
           const float p = __fmul_rn(hv[v], ka[u]);
           float e = __fmaf_rn(hv[v], ka[u], -p);
           e = __fmaf_rn(lv[v], ka[u], e);
+          e = __fmaf_rn(hv[v], kb[u], e);
           two_sum_acc(s[u][v], c[u][v], p);
           c[u][v] = __fadd_rn(c[u][v], e);
         }
@@ -334,7 +412,7 @@ __global__ void __launch_bounds__(KX_T, 2) krx_score_kernel(const In* __restrict
 }
 
 size_t score_smem(int B, int mj) {
-  return ((size_t)mj * KX_P + KX_BC * KX_P + KX_BC * KX_JC + round_up(B, 4)) * sizeof(float) +
+  return ((size_t)2 * mj * KX_P + KX_BC * KX_P + KX_BC * KX_JC + round_up(B, 4)) * sizeof(float) +
          (size_t)(KX_T / 8) * KX_P * sizeof(double);
 }
 
