@@ -62,6 +62,7 @@ struct hsad_ctx {
   hsad_config cfg{};
   int W = 0, B = 0, Bp = 0, in_type = 0, prec = 0, mode = 0;
   int fprec = 0;  // prec, or'ed with kFactorF64 for the FP64 factor (launch_factor's argument)
+  bool tc_factor = false;  // streamed statistics factored by the tensor-core factor (launch_factor_tc)
   int64_t min_pix = 0, elem = 2, line_elems = 0, line_bytes = 0;
   float tau = 0.f;
   int Lmax = 256;
@@ -528,6 +529,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
               : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type, cube, force_inverse)
                                             : P_FP16;
   ctx->fprec = ctx->prec | (cfg->factor_precision == HSAD_FACTOR_FP64 ? kFactorF64 : 0);
+  ctx->tc_factor = !cube && cfg->factor_precision == HSAD_FACTOR_FF && factor_tc_supported(ctx->B, ctx->prec);
   ctx->lam = (cfg->forget > 0.f && cfg->forget < 1.f) ? (double)cfg->forget : 1.0;
   ctx->use_graphs = (cfg->flags & HSAD_CUDA_GRAPHS) && cfg->stats_mode == HSAD_EXCLUSIVE && ctx->lam == 1.0;
   ctx->mode = cfg->stats_mode;
@@ -762,6 +764,19 @@ int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* ou
   return HSAD_OK;
 }
 
+// The factor of L lines of streamed statistics: the tensor-core factor where the context
+// uses it, else the factor kernel (same output layout; the choice depends only on the
+// context, so a line's factor does not depend on how lines are batched).
+cudaError_t factor_lines(hsad_ctx* ctx, double* sigma, double* inv, const double* m, int L, void* wmat, float* y0,
+                         float* inv_s2, int32_t* status, int64_t n0, int W, int incl, const int64_t* n0_dev,
+                         int every, int q_off, const double* n_line) {
+  if (ctx->tc_factor)
+    return launch_factor_tc(sigma, inv, m, L, ctx->B, ctx->prec, wmat, y0, inv_s2, status, n0, W, incl, ctx->stream,
+                            &ctx->lc, n0_dev, every, q_off, n_line, ctx->dev_err);
+  return launch_factor(sigma, inv, m, L, ctx->B, ctx->fprec, wmat, y0, inv_s2, status, n0, W, incl, ctx->stream,
+                       &ctx->lc, n0_dev, every, q_off, n_line);
+}
+
 // Everything of an EXCLUSIVE batch after its first line is scored: the batch's statistics,
 // the factors of slots 1..L, the scores of lines 1..L-1 and the carry of slot L to slot 0.
 // With dev = true the per-batch values (pixels before the batch, ring slot of line 1) are
@@ -788,9 +803,9 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
                                        ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc, gain, ctx->s1_line,
                                      ctx->c_int, W, ctx->lam));
-  KL("factor", launch_factor(ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L, B, ctx->fprec,
-                             (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1,
-                             ctx->status + 1, ctx->n_stats, W, 1, st, &ctx->lc, n0_dev, ctx->every, q0 + 1, n_line));
+  KL("factor", factor_lines(ctx, ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L,
+                            (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1, ctx->status + 1,
+                            ctx->n_stats, W, 1, n0_dev, ctx->every, q0 + 1, n_line));
   if (L > 1) {
     ScoreOut o1 = score_out(ctx, first + 1, true);
     o1.factor_base = 1;
@@ -909,8 +924,8 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
                         ctx->min_pix, ctx->status, st, &ctx->lc, nullptr, gain, ctx->c_int, ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc, gain, ctx->s1_line,
                                      ctx->c_int, W, ctx->lam));
-  KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, L, B, ctx->fprec, ctx->wmat, ctx->y0,
-                   ctx->inv_s2, ctx->status, ctx->n_stats, W, incl, st, &ctx->lc, nullptr, 1, 0, n_line));
+  KL("factor", factor_lines(ctx, ctx->sigma, ctx->inv, ctx->m_line, L, ctx->wmat, ctx->y0, ctx->inv_s2,
+                            ctx->status, ctx->n_stats, W, incl, nullptr, 1, 0, n_line));
   {
     int rc = whiten(ctx, x, L, 1, score_out(ctx, first, true));
     if (rc != HSAD_OK) return rc;
@@ -1478,8 +1493,8 @@ int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const d
     CK(cudaMemcpyAsync(ctx->sigma, s2, (size_t)B * B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->m_line, m.data(), (size_t)B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->status, &st0, 4, cudaMemcpyHostToDevice, st));
-    KL("factor", launch_factor(ctx->sigma, ctx->inv, ctx->m_line, 1, B, ctx->fprec, ctx->wmat, ctx->y0,
-                               ctx->inv_s2, ctx->status, n_pixels, 0, 0, st, &ctx->lc));
+    KL("factor", factor_lines(ctx, ctx->sigma, ctx->inv, ctx->m_line, 1, ctx->wmat, ctx->y0, ctx->inv_s2,
+                              ctx->status, n_pixels, 0, 0, nullptr, 1, 0, nullptr));
     CK(cudaStreamSynchronize(st));  // the host vectors above are copied before they go out of scope
   } else {
     CK(cudaStreamSynchronize(st));

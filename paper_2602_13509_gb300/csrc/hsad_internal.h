@@ -159,6 +159,16 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
                           const int64_t* n0_dev = nullptr, int every = 1, int q_off = 0,
                           const double* n_line = nullptr);
 
+// K4 + K5 on the tensor cores (k_factor_tc.cu): the same factor output as launch_factor for
+// the triangular-solve forms with the float-float factor, the trailing updates as exact
+// digit-split BF16 contractions. Needs B >= 192 (the slices live in the inverse scratch);
+// err is set if a bounded wait expires.
+bool factor_tc_supported(int B, int prec);
+cudaError_t launch_factor_tc(double* sigma, double* scratch, const double* m, int L, int B, int prec, void* wmat,
+                             float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
+                             cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev, int every, int q_off,
+                             const double* n_line, int32_t* err);
+
 // K6 (SIMT): delta_p = inv_s2 * || G (x_p - c) - y0 ||^2 for every pixel of every line,
 // threshold, and scatter into the result ring. factor_stride = 0 makes every line
 // use factor 0 (cube mode).

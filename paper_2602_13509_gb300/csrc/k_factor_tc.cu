@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
       } else {
         tc::mbar_arrive(done);
         atomicExch(err, 1);
+        tc::mbar_wait(full, 0, limit);  // copies still in flight land before the CTA may exit
       }
     }
   } else {

@@ -257,6 +257,34 @@ def test_cluster_and_single_cta_factors_agree_bitwise(hs, B):
     np.testing.assert_array_equal(m, a[2])
 
 
+@pytest.mark.parametrize("prec,B", [("fp32", 270), ("bf16", 448), ("fp32", 192)])
+def test_tensor_core_factor_is_batch_invariant(hs, prec, B):
+    """From B = 192 the streamed factor runs on the tensor cores (64-column panels, exact
+    digit-split trailing updates); each line's factor is computed the same way whatever the
+    batch holds, so one-line pushes, uneven pushes and one whole push give identical scores,
+    and they match the oracle."""
+    sc, lines = _scene_lines(24, 64, B, seed=B + 3)
+    a = _run(hs, lines, stats_mode="exclusive", precision=prec, gain=sc.gain, offset=sc.offset)
+    outs = []
+    for chunks in ([1] * 24, [5, 1, 7, 2, 9]):
+        det = hs.Detector(width=64, bands=B, stats_mode="exclusive", precision=prec, gain=sc.gain,
+                          offset=sc.offset)
+        t = 0
+        for n in chunks:
+            det.push(lines[t:t + n])
+            t += n
+        rc, s, m, st = det.scores(0, 24)
+        det.close()
+        outs.append((s, m))
+    for s, m in outs:
+        np.testing.assert_array_equal(s, a[1])
+        np.testing.assert_array_equal(m, a[2])
+    ref, rst = orx.stream_rx(lines, oracle.EXCLUSIVE, gain=sc.gain, offset=sc.offset)
+    np.testing.assert_array_equal(a[3], rst)
+    emax, _ = rel_err(a[1], ref)
+    assert emax <= TOL[prec], emax
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
 def test_cuda_graph_replay_matches_direct_launches(hs, prec):
     """HSAD_CUDA_GRAPHS replays a captured launch sequence per batch size; the kernels and
