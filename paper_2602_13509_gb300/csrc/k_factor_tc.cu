@@ -6,9 +6,9 @@
 //
 // Blocked right-looking Cholesky in 64-column panels, one launch per step for a whole
 // batch of lines:
-//   tcf_form_kernel      S = (S2 - n m m^T) / (n - 1) in FP64, stored float-float in place;
-//   tcf_panel_kernel(k)  one CTA per line: the 64 x 64 diagonal block factored (FP64
-//                        pivots, float-float updates) and inverted, the rows below solved
+//   tcf_form_kernel      S = (S2 - n m m^T) / (n - 1) as float-float, in place;
+//   tcf_panel_kernel(k)  one CTA per line: the 64 x 64 diagonal block factored and inverted
+//                        together (float-float, pivots by Newton steps), the rows below solved
 //                        as L_ik = A_ik L_kk^{-T} (float-float product with the inverse), the
 //                        whitening operand's block column k written (L_kk^{-1} on the diagonal,
 //                        L_ik below), and every panel row split into six signed base-256
@@ -49,7 +49,9 @@ constexpr int TU_M = 128, TU_N = 64, TU_K = 64;
 constexpr int TU_T = 160;          // 4 epilogue warps + 1 copy / MMA warp
 constexpr uint32_t TU_A_PLANE = TU_M * TU_K * 2;   // 16 KB
 constexpr uint32_t TU_B_PLANE = TU_N * TU_K * 2;   // 8 KB
-constexpr uint32_t TU_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + 256 + 64;
+constexpr int TU_AS = TU_N + 1;    // row stride (float2) of the staged trailing tile
+constexpr uint32_t TU_TILE = TU_M * TU_AS * 8;
+constexpr uint32_t TU_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + TU_TILE + 256 + 64;
 
 // Byte layout of one line's slice region (in the inverse scratch): NDIG planes of
 // (Bp + 64) rows x 128 bytes, then (Bp + 64) int32 exponents.
@@ -87,11 +89,46 @@ __device__ __forceinline__ bool skip_line(const int32_t* status, int t, int ever
 }  // namespace
 
 // ---- covariance -----------------------------------------------------------------------
+namespace {
+// A double holding an integer of magnitude below 2^53 (the exact covariance sums of uint16
+// input) as a float-float pair, by integer operations on its bits only (the FP64 pipe
+// issues at 1/64 of the FP32 rate here). Returns false for any other value.
+__device__ __forceinline__ bool int_double_to_ff(double v, float2& out) {
+  const long long bits = __double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7ff) - 1075;  // v = mant * 2^ex
+  if (v == 0.0) {
+    out = make_float2(0.f, 0.f);
+    return true;
+  }
+  if (ex > 0 || ex < -52) return false;
+  const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const long long ival = mant >> (-ex);
+  if ((ival << (-ex)) != mant) return false;  // a fractional part
+  // ival < 2^53: a = ival >> 24 (< 2^29) rounded to 24 significant bits, b = the rest
+  long long a = ival >> 24;
+  int sh = 0;
+  while ((a >> sh) >= (1LL << 24)) ++sh;
+  const long long ar = sh ? ((a + (1LL << (sh - 1))) >> sh) << sh : a;
+  const float fa = ldexpf((float)(int)(ar >> sh), 24 + sh);  // exact: < 2^24 significant bits
+  const float fb = (float)(int)(ival - (ar << 24));         // |.| < 2^29: rounded only past 2^48
+  const float h = __fadd_rn(fa, fb);
+  const float z = __fsub_rn(h, fa);
+  const float l = __fadd_rn(__fsub_rn(fa, __fsub_rn(h, z)), __fsub_rn(fb, z));
+  out = (bits < 0) ? make_float2(-h, -l) : make_float2(h, l);
+  return true;
+}
+}  // namespace
+
+// S = (S2 - n m m^T) / (n - 1), lower triangle, in place as float-float: one warp per row.
+// Integer sums (uint16 input without gains or forgetting) take the float-float route
+// (exact split of S2, n m_i m_j and the scale as float-float products); any other value
+// is formed in FP64 and split.
 __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __restrict__ m_all, int B,
                                 const int32_t* __restrict__ status, int64_t n0_arg, int W, int incl,
                                 const int64_t* __restrict__ n0_dev, int every, int q_off,
                                 const double* __restrict__ n_line) {
-  const int t = blockIdx.y, i = blockIdx.x;
+  const int t = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
   if (i >= B || skip_line(status, t, every, q_off)) return;
   const int64_t n = (n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W;
   const double nn = n_line ? n_line[t] : (double)n, inv_nm1 = 1.0 / (nn - 1.0);
@@ -99,7 +136,17 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
   double* row = sigma_all + (int64_t)t * B * B + (int64_t)i * B;
   float2* row2 = reinterpret_cast<float2*>(row);
   const double nmi = nn * m[i];
-  for (int j = threadIdx.x; j <= i; j += blockDim.x) row2[j] = dff(inv_nm1 * fma(-nmi, m[j], row[j]));
+  const float2 nmi_f = dff(nmi), sc_f = dff(inv_nm1);
+  for (int j = lane; j <= i; j += 32) {
+    const double v = row[j];
+    float2 s2;
+    if (int_double_to_ff(v, s2)) {
+      const float2 p = ff_mul(nmi_f, dff(m[j]));
+      row2[j] = ff_mul(ff_sub(s2, p), sc_f);
+    } else {
+      row2[j] = dff(inv_nm1 * fma(-nmi, m[j], v));
+    }
+  }
 }
 
 // ---- panel ------------------------------------------------------------------------------
@@ -138,16 +185,30 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
   }
   __syncthreads();
 
-  // ---- L_kk: column by column (FP64 pivot and reciprocal, float-float updates) ----------
+  // ---- L_kk and X = L_kk^{-1} together, right-looking, column by column -------------------
+  // Step j: the pivot l = sqrt(A_jj) and 1 / l (float-float Newton steps from FP32
+  // seeds); column j of L = A_.j / l, row j of X = R_j. / l with R the running right-hand
+  // sides (I at the start); then the rank-1 updates A_rc -= L_rj L_cj (j < c <= r) and
+  // R_rc -= L_rj X_jc (r > j, c <= j). Iv holds R, then X.
+  for (int e = tid; e < 64; e += TP_T) Iv[e * DS + e] = make_float2(1.f, 0.f);
+  __syncthreads();
   for (int j = 0; j < kb; ++j) {
     if (tid == 0) {
-      const double piv = ffd(Dg[j * DS + j]);
-      if (!(piv > 0.0) || !isfinite(piv)) {
+      const float2 a = Dg[j * DS + j];
+      if (!(a.x > 0.f) || !isfinite(a.x)) {
         notpd = 1;
       } else {
-        const double l = sqrt(piv);
-        Dg[j * DS + j] = dff(l);
-        rdg[j] = dff(1.0 / l);
+        // sqrt: s0 = sqrt(a_hi), l = s0 + (a - s0^2) / (2 s0) with s0^2 exact (two-product)
+        const float s0 = __fsqrt_rn(a.x);
+        const float q = __fmul_rn(s0, s0), qe = __fmaf_rn(s0, s0, -q);
+        const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.x, q), qe), a.y);
+        const float2 l = ff_norm(s0, __fdiv_rn(res, __fmul_rn(2.f, s0)));
+        // 1 / l: r0 = 1 / l_hi, r = r0 + r0 (1 - l r0) with l r0 as float-float
+        const float r0 = __frcp_rn(l.x);
+        const float p = __fmul_rn(l.x, r0), pe = __fmaf_rn(l.x, r0, -p);
+        const float d = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(l.y, r0));
+        Dg[j * DS + j] = l;
+        rdg[j] = ff_norm(r0, __fmul_rn(r0, d));
       }
     }
     __syncthreads();
@@ -155,27 +216,30 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
       if (tid == 0) status[t] = LS_NOT_PD;
       return;
     }
-    for (int r = j + 1 + tid; r < kb; r += TP_T) Dg[r * DS + j] = ff_mul(Dg[r * DS + j], rdg[j]);
-    __syncthreads();
-    const int nc = kb - j - 1;
-    for (int e = tid; e < nc * nc; e += TP_T) {
-      const int r = j + 1 + e / nc, c = j + 1 + e % nc;
-      if (c <= r) {
-        float2 v = Dg[r * DS + c];
-        ff_fms(v.x, v.y, Dg[r * DS + j], Dg[c * DS + j]);
-        Dg[r * DS + c] = ff_norm(v.x, v.y);
-      }
+    const float2 rj = rdg[j];
+    for (int e = tid; e < 64; e += TP_T) {
+      if (e > j && e < kb) Dg[e * DS + j] = ff_mul(Dg[e * DS + j], rj);   // column j of L
+      if (e <= j) Iv[j * DS + e] = ff_mul(Iv[j * DS + e], rj);            // row j of X
     }
     __syncthreads();
-  }
-
-  // ---- L_kk^{-1}: row by row, the columns of a row in parallel ---------------------------
-  // X[r][c] = (delta_rc - sum_{c <= q < r} L[r][q] X[q][c]) / L[r][r]
-  for (int r = 0; r < kb; ++r) {
-    for (int c = tid; c <= r; c += TP_T) {
-      float s = (c == r) ? 1.f : 0.f, cc = 0.f;
-      for (int q = c; q < r; ++q) ff_fms(s, cc, Dg[r * DS + q], Iv[q * DS + c]);
-      Iv[r * DS + c] = ff_mul(ff_norm(s, cc), rdg[r]);
+    const int nr = kb - j - 1;                 // rows below j
+    const int na = nr * (nr + 1) / 2;          // trailing lower triangle of A
+    const int nx = nr * (j + 1);               // R rows below j, columns <= j
+    for (int e = tid; e < na + nx; e += TP_T) {
+      if (e < na) {
+        int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while (r * (r + 1) / 2 > e) --r;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        const int c = e - r * (r + 1) / 2;     // 0 <= c <= r < nr
+        float2 v = Dg[(j + 1 + r) * DS + j + 1 + c];
+        ff_fms(v.x, v.y, Dg[(j + 1 + r) * DS + j], Dg[(j + 1 + c) * DS + j]);
+        Dg[(j + 1 + r) * DS + j + 1 + c] = ff_norm(v.x, v.y);
+      } else {
+        const int f = e - na, r = j + 1 + f / (j + 1), c = f % (j + 1);
+        float2 v = Iv[r * DS + c];
+        ff_fms(v.x, v.y, Dg[r * DS + j], Iv[j * DS + c]);
+        Iv[r * DS + c] = ff_norm(v.x, v.y);
+      }
     }
     __syncthreads();
   }
@@ -203,7 +267,8 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) s[a][b] = cc[a][b] = 0.f;
-    for (int q = 0; q < kb; ++q) {
+    const int qmax = min(kb, 4 * tcg + 4);  // X[c][q] = 0 for q > c
+    for (int q = 0; q < qmax; ++q) {
       float2 av[4], xv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -290,7 +355,8 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
   uint8_t* sm = (uint8_t*)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = sm;                                  // NDIG planes of 128 x 64 BF16 (swizzled)
   uint8_t* sB = sm + NDIG * TU_A_PLANE;              // NDIG planes of 64 x 64 BF16
-  uint64_t* bars = (uint64_t*)(sB + NDIG * TU_B_PLANE);
+  float2* As = (float2*)(sB + NDIG * TU_B_PLANE);   // the trailing tile A[i0 ..][j0 ..], [128][TU_AS]
+  uint64_t* bars = (uint64_t*)((uint8_t*)As + TU_TILE);
   uint32_t* tslot = (uint32_t*)(bars + 4);
   int* ej = (int*)(bars + 8);                        // exponents of the 64 columns
   const uint32_t full = tc::smem_u32(bars), done = full + 8;
@@ -342,14 +408,22 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
       }
     }
   } else {
-    // epilogue: thread = TMEM lane = tile row
+    // epilogue warps: stage the trailing tile (coalesced rows, while the digits load and the
+    // MMAs run), then one tile row per thread (= its TMEM lane), then store it back coalesced
+    float2* A = reinterpret_cast<float2*>(sigma_all + (int64_t)t * B * B);
+    for (int r = warp * 32; r < warp * 32 + 32; ++r) {
+      const int i = i0 + r;
+      for (int c = lane; c < TU_N; c += 32) {
+        const int j = j0 + c;
+        As[r * TU_AS + c] = (i < B && j < B && j <= i) ? A[(int64_t)i * B + j] : make_float2(0.f, 0.f);
+      }
+    }
     const bool dok = tc::mbar_wait(done, 0, limit);
     __syncwarp();
     tc::fence_after_sync();
     if (!dok) atomicExch(err, 1);
     const int row = 32 * warp + lane, i = i0 + row;
-    const int ei = (i < Bp + 64) ? expo[i] : 0;
-    float2* Arow = reinterpret_cast<float2*>(sigma_all + (int64_t)t * B * B) + (int64_t)i * B;
+    const int ei = expo[i];  // i < Bp + 64: the region's exponent rows
     const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
     for (int c0 = 0; c0 < TU_N; c0 += 16) {
       float lev[NDIG][16];
@@ -372,8 +446,18 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
             }
             const float sc = ldexpf(1.f, ei + ej[c0 + c] - 16);
             const float2 upd = ff_norm(__fmul_rn(hs, sc), __fmul_rn(hc, sc));
-            Arow[j] = ff_sub(Arow[j], upd);
+            As[row * TU_AS + c0 + c] = ff_sub(As[row * TU_AS + c0 + c], upd);
           }
+        }
+      }
+    }
+    __syncwarp();  // the warp's 32 rows are complete
+    if (dok) {
+      for (int r = warp * 32; r < warp * 32 + 32; ++r) {
+        const int i2 = i0 + r;
+        for (int c = lane; c < TU_N; c += 32) {
+          const int j = j0 + c;
+          if (i2 < B && j < B && j <= i2) A[(int64_t)i2 * B + j] = As[r * TU_AS + c];
         }
       }
     }
@@ -400,7 +484,8 @@ cudaError_t launch_factor_tc(double* sigma, double* scratch, const double* m, in
   if (slice_region_bytes(Bp) + 1024 > stride) return cudaErrorInvalidValue;
   uint8_t* slices = reinterpret_cast<uint8_t*>(scratch);
   const long long limit = 4000000000LL;  // ~2 s of clock cycles
-  tcf_form_kernel<<<dim3(B, L), 128, 0, st>>>(sigma, m, B, status, n0, W, incl, n0_dev, every, q_off, n_line);
+  tcf_form_kernel<<<dim3((B + 7) / 8, L), 256, 0, st>>>(sigma, m, B, status, n0, W, incl, n0_dev, every, q_off,
+                                                         n_line);
   cudaError_t e = cudaGetLastError();
   if (lc) lc->n += 1;
   const size_t psmem = (size_t)3 * 64 * DS * sizeof(float2);
