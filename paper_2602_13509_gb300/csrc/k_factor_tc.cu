@@ -8,7 +8,8 @@
 // batch of lines:
 //   tcf_form_kernel      S = (S2 - n m m^T) / (n - 1) as float-float, in place;
 //   tcf_panel_kernel(k)  one CTA per line: the 64 x 64 diagonal block factored and inverted
-//                        together (float-float, pivots by Newton steps), the rows below solved
+//                        in 16-column sub-panels (float-float, pivots by Newton steps), the
+//                        rows below solved
 //                        as L_ik = A_ik L_kk^{-T} (float-float product with the inverse), the
 //                        whitening operand's block column k written (L_kk^{-1} on the diagonal,
 //                        L_ik below), and every panel row split into six signed base-256
@@ -137,14 +138,25 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
   float2* row2 = reinterpret_cast<float2*>(row);
   const double nmi = nn * m[i];
   const float2 nmi_f = dff(nmi), sc_f = dff(inv_nm1);
-  for (int j = lane; j <= i; j += 32) {
-    const double v = row[j];
-    float2 s2;
-    if (int_double_to_ff(v, s2)) {
-      const float2 p = ff_mul(nmi_f, dff(m[j]));
-      row2[j] = ff_mul(ff_sub(s2, p), sc_f);
-    } else {
-      row2[j] = dff(inv_nm1 * fma(-nmi, m[j], v));
+  for (int j0 = 0; j0 <= i; j0 += 128) {
+    double v[4], mj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {  // four independent loads per lane
+      const int j = j0 + lane + 32 * u;
+      v[u] = j <= i ? row[j] : 0.0;
+      mj[u] = j <= i ? m[j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + lane + 32 * u;
+      if (j > i) continue;
+      float2 s2;
+      if (int_double_to_ff(v[u], s2)) {
+        const float2 p = ff_mul(nmi_f, dff(mj[u]));
+        row2[j] = ff_mul(ff_sub(s2, p), sc_f);
+      } else {
+        row2[j] = dff(inv_nm1 * fma(-nmi, mj[u], v[u]));
+      }
     }
   }
 }
@@ -185,30 +197,59 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
   }
   __syncthreads();
 
-  // ---- L_kk and X = L_kk^{-1} together, right-looking, column by column -------------------
-  // Step j: the pivot l = sqrt(A_jj) and 1 / l (float-float Newton steps from FP32
-  // seeds); column j of L = A_.j / l, row j of X = R_j. / l with R the running right-hand
-  // sides (I at the start); then the rank-1 updates A_rc -= L_rj L_cj (j < c <= r) and
-  // R_rc -= L_rj X_jc (r > j, c <= j). Iv holds R, then X.
+  // ---- L_kk and X = L_kk^{-1}, in 16-column sub-panels ------------------------------------
+  // Per sub-panel at p0: one warp factors its 16 x 16 diagonal block and inverts it (X16),
+  // with warp-level syncs only (pivots by float-float Newton steps from FP32 seeds); then
+  // the whole CTA solves the rows below it, L[r][p0 + c] = sum_q A[r][p0 + q] X16[c][q],
+  // forms block row p0 of X from the running right-hand sides R (I at the start; Iv holds R,
+  // then X), and applies the rank-16 updates to the rest of the block (A) and of R.
+  __shared__ float2 X16[16][17];
   for (int e = tid; e < 64; e += TP_T) Iv[e * DS + e] = make_float2(1.f, 0.f);
   __syncthreads();
-  for (int j = 0; j < kb; ++j) {
-    if (tid == 0) {
-      const float2 a = Dg[j * DS + j];
-      if (!(a.x > 0.f) || !isfinite(a.x)) {
-        notpd = 1;
-      } else {
-        // sqrt: s0 = sqrt(a_hi), l = s0 + (a - s0^2) / (2 s0) with s0^2 exact (two-product)
-        const float s0 = __fsqrt_rn(a.x);
-        const float q = __fmul_rn(s0, s0), qe = __fmaf_rn(s0, s0, -q);
-        const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.x, q), qe), a.y);
-        const float2 l = ff_norm(s0, __fdiv_rn(res, __fmul_rn(2.f, s0)));
-        // 1 / l: r0 = 1 / l_hi, r = r0 + r0 (1 - l r0) with l r0 as float-float
-        const float r0 = __frcp_rn(l.x);
-        const float p = __fmul_rn(l.x, r0), pe = __fmaf_rn(l.x, r0, -p);
-        const float d = __fsub_rn(__fsub_rn(__fsub_rn(1.f, p), pe), __fmul_rn(l.y, r0));
-        Dg[j * DS + j] = l;
-        rdg[j] = ff_norm(r0, __fmul_rn(r0, d));
+  for (int p0 = 0; p0 < kb; p0 += 16) {
+    const int nb = min(16, kb - p0);
+    if (warp == 0) {
+      for (int e = lane; e < 256; e += 32) X16[e >> 4][e & 15] = make_float2((e >> 4) == (e & 15) ? 1.f : 0.f, 0.f);
+      __syncwarp();
+      for (int j = 0; j < nb; ++j) {
+        if (lane == 0) {
+          const float2 a = Dg[(p0 + j) * DS + p0 + j];
+          if (!(a.x > 0.f) || !isfinite(a.x)) {
+            notpd = 1;
+          } else {
+            // sqrt: s0 = sqrt(a_hi), l = s0 + (a - s0^2) / (2 s0) with s0^2 exact (two-product)
+            const float s0 = __fsqrt_rn(a.x);
+            const float q = __fmul_rn(s0, s0), qe = __fmaf_rn(s0, s0, -q);
+            const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.x, q), qe), a.y);
+            const float2 l = ff_norm(s0, __fdiv_rn(res, __fmul_rn(2.f, s0)));
+            // 1 / l: r0 = 1 / l_hi, r = r0 + r0 (1 - l r0) with l r0 as float-float
+            const float r0 = __frcp_rn(l.x);
+            const float pp = __fmul_rn(l.x, r0), pe = __fmaf_rn(l.x, r0, -pp);
+            const float d = __fsub_rn(__fsub_rn(__fsub_rn(1.f, pp), pe), __fmul_rn(l.y, r0));
+            Dg[(p0 + j) * DS + p0 + j] = l;
+            rdg[p0 + j] = ff_norm(r0, __fmul_rn(r0, d));
+          }
+        }
+        __syncwarp();
+        if (notpd) break;  // shared, the same for the whole warp
+        const float2 rj = rdg[p0 + j];
+        if (lane > j && lane < nb) Dg[(p0 + lane) * DS + p0 + j] = ff_mul(Dg[(p0 + lane) * DS + p0 + j], rj);
+        if (lane >= 16 && lane - 16 <= j) X16[j][lane - 16] = ff_mul(X16[j][lane - 16], rj);
+        __syncwarp();
+        for (int e = lane; e < 256; e += 32) {
+          const int r = e >> 4, c = e & 15;
+          if (r <= j || r >= nb) continue;
+          if (c > j && c <= r) {
+            float2 v = Dg[(p0 + r) * DS + p0 + c];
+            ff_fms(v.x, v.y, Dg[(p0 + r) * DS + p0 + j], Dg[(p0 + c) * DS + p0 + j]);
+            Dg[(p0 + r) * DS + p0 + c] = ff_norm(v.x, v.y);
+          } else if (c <= j) {
+            float2 v = X16[r][c];
+            ff_fms(v.x, v.y, Dg[(p0 + r) * DS + p0 + j], X16[j][c]);
+            X16[r][c] = ff_norm(v.x, v.y);
+          }
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
@@ -216,29 +257,60 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
       if (tid == 0) status[t] = LS_NOT_PD;
       return;
     }
-    const float2 rj = rdg[j];
-    for (int e = tid; e < 64; e += TP_T) {
-      if (e > j && e < kb) Dg[e * DS + j] = ff_mul(Dg[e * DS + j], rj);   // column j of L
-      if (e <= j) Iv[j * DS + e] = ff_mul(Iv[j * DS + e], rj);            // row j of X
+    // rows below the sub-panel (o < nbel * 16) and block row p0 of X for columns < p0
+    // (o >= nbel * 16), computed into registers, written after a barrier
+    const int nbel = kb - p0 - nb;
+    const int n_l = nbel * 16, n_x = 16 * p0;
+    float2 res[6];
+    int cnt = 0;
+    for (int o = tid; o < n_l + n_x; o += TP_T, ++cnt) {
+      float s = 0.f, cc = 0.f;
+      if (o < n_l) {
+        const int r = p0 + nb + (o >> 4), c = o & 15;
+        for (int q = 0; q <= c && q < nb; ++q) {
+          const float2 x = X16[c][q];
+          ff_fms(s, cc, Dg[r * DS + p0 + q], make_float2(-x.x, -x.y));  // s += A X16^T
+        }
+      } else {
+        const int f = o - n_l, r = f / p0, c = f % p0;  // X[p0 + r][c], c < p0
+        for (int q = 0; q <= r && q < nb; ++q) {
+          const float2 x = X16[r][q];
+          ff_fms(s, cc, Iv[(p0 + q) * DS + c], make_float2(-x.x, -x.y));  // s += X16 R
+        }
+      }
+      res[cnt] = ff_norm(s, cc);
     }
     __syncthreads();
-    const int nr = kb - j - 1;                 // rows below j
-    const int na = nr * (nr + 1) / 2;          // trailing lower triangle of A
-    const int nx = nr * (j + 1);               // R rows below j, columns <= j
-    for (int e = tid; e < na + nx; e += TP_T) {
+    cnt = 0;
+    for (int o = tid; o < n_l + n_x; o += TP_T, ++cnt) {
+      if (o < n_l) {
+        Dg[(p0 + nb + (o >> 4)) * DS + p0 + (o & 15)] = res[cnt];
+      } else {
+        const int f = o - n_l;
+        Iv[(p0 + f / p0) * DS + f % p0] = res[cnt];
+      }
+    }
+    for (int e = tid; e < 256; e += TP_T)  // the diagonal part of block row p0 of X
+      if ((e >> 4) < nb && (e & 15) < nb) Iv[(p0 + (e >> 4)) * DS + p0 + (e & 15)] = X16[e >> 4][e & 15];
+    __syncthreads();
+    // rank-nb updates: A[r][c] -= sum_q L[r][p0 + q] L[c][p0 + q] (p0 + nb <= c <= r < kb) and
+    // R[r][c] -= sum_q L[r][p0 + q] X[p0 + q][c] (r >= p0 + nb, c < p0 + nb)
+    const int na = nbel * (nbel + 1) / 2, nr = nbel * (p0 + nb);
+    for (int e = tid; e < na + nr; e += TP_T) {
       if (e < na) {
         int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
         while (r * (r + 1) / 2 > e) --r;
         while ((r + 1) * (r + 2) / 2 <= e) ++r;
-        const int c = e - r * (r + 1) / 2;     // 0 <= c <= r < nr
-        float2 v = Dg[(j + 1 + r) * DS + j + 1 + c];
-        ff_fms(v.x, v.y, Dg[(j + 1 + r) * DS + j], Dg[(j + 1 + c) * DS + j]);
-        Dg[(j + 1 + r) * DS + j + 1 + c] = ff_norm(v.x, v.y);
+        const int c = e - r * (r + 1) / 2;
+        const int ri = p0 + nb + r, ci = p0 + nb + c;
+        float2 v = Dg[ri * DS + ci];
+        for (int q = 0; q < nb; ++q) ff_fms(v.x, v.y, Dg[ri * DS + p0 + q], Dg[ci * DS + p0 + q]);
+        Dg[ri * DS + ci] = ff_norm(v.x, v.y);
       } else {
-        const int f = e - na, r = j + 1 + f / (j + 1), c = f % (j + 1);
-        float2 v = Iv[r * DS + c];
-        ff_fms(v.x, v.y, Dg[r * DS + j], Iv[j * DS + c]);
-        Iv[r * DS + c] = ff_norm(v.x, v.y);
+        const int f = e - na, ri = p0 + nb + f / (p0 + nb), c = f % (p0 + nb);
+        float2 v = Iv[ri * DS + c];
+        for (int q = 0; q < nb; ++q) ff_fms(v.x, v.y, Dg[ri * DS + p0 + q], Iv[(p0 + q) * DS + c]);
+        Iv[ri * DS + c] = ff_norm(v.x, v.y);
       }
     }
     __syncthreads();
@@ -411,12 +483,22 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
     // epilogue warps: stage the trailing tile (coalesced rows, while the digits load and the
     // MMAs run), then one tile row per thread (= its TMEM lane), then store it back coalesced
     float2* A = reinterpret_cast<float2*>(sigma_all + (int64_t)t * B * B);
-    for (int r = warp * 32; r < warp * 32 + 32; ++r) {
-      const int i = i0 + r;
-      for (int c = lane; c < TU_N; c += 32) {
-        const int j = j0 + c;
-        As[r * TU_AS + c] = (i < B && j < B && j <= i) ? A[(int64_t)i * B + j] : make_float2(0.f, 0.f);
+    // 16 rows per round: 32 independent loads in flight per lane
+    for (int r0w = warp * 32; r0w < warp * 32 + 32; r0w += 16) {
+      float2 v[16][2];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int i = i0 + r0w + q;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = j0 + lane + 32 * h;
+          v[q][h] = (i < B && j < B && j <= i) ? A[(int64_t)i * B + j] : make_float2(0.f, 0.f);
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) As[(r0w + q) * TU_AS + lane + 32 * h] = v[q][h];
     }
     const bool dok = tc::mbar_wait(done, 0, limit);
     __syncwarp();
