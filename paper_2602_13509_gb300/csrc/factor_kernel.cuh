@@ -94,6 +94,14 @@ struct WOut<P_BF16T> : WOut<P_BF16> {};
 template <>
 struct WOut<P_FP32T> : WOut<P_FP32> {};
 
+// Element (n, k) of the triangular-solve operand H: row n = output band (n-major) for the
+// tensor-core form, whose TMA boxes are K-major rows; column k major (transposed) for the
+// FP32 SIMT form, whose K-slices then load as contiguous rows.
+template <int PREC>
+__host__ __device__ __forceinline__ int64_t h_index(int n, int k, int Bp) {
+  return PREC == P_FP32T ? (int64_t)k * Bp + n : (int64_t)n * Bp + k;
+}
+
 template <int FT>
 __device__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -540,7 +548,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     void* w = (char*)wmat + (size_t)t * plane * 4;
     for (int n = gwarp; n < Bp; n += gwarps) {
       for (int k = lane; k < Bp; k += 32) {
-        const int64_t idx = (int64_t)n * Bp + k;
+        const int64_t idx = h_index<PREC>(n, k, Bp);
         if (n < B && k <= n) {
           const T* src = ((n >> 6) == (k >> 6)) ? Inv : A2;
           WOut<PREC>::store(w, plane, idx, AR::to_f(ldg_c<CL>(src + (int64_t)n * B + k)));

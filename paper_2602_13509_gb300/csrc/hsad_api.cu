@@ -89,6 +89,7 @@ struct hsad_ctx {
   double* sigma = nullptr;
   double* inv = nullptr;
   void* wmat = nullptr;
+  float* yscratch = nullptr;  // whitened blocks of the FP32 triangular solve's items in flight
   float* y0 = nullptr;
   float* inv_s2 = nullptr;
   int32_t* status = nullptr;
@@ -282,6 +283,7 @@ int64_t plan_bytes(const hsad_ctx* c) {
   if (c->lam != 1.0) b += Ls * 8;                                // forgetting weights per line
   b += Lf * B * B * 8 * 2;                                       // sigma, inv
   b += Lf * Bp * Bp * 4 + Lf * Bp * 4 + Lf * 4 + Ls * 4;        // wmat, y0, inv_s2, status
+  if (c->prec == P_FP32T) b += (int64_t)whiten_trsm_simt_scratch_bytes(c->B);  // FP32 solve scratch
   b += c->ring * c->W * 5 + c->ring * 4 + 64;                    // result ring
   b += c->ring * c->W * 2 + 64;                                  // transmit codes scratch
   if (c->mode == HSAD_CUBE) b += (int64_t)c->cfg.cube_lines * c->line_bytes;
@@ -608,6 +610,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->sigma = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
   ctx->inv = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
   ctx->wmat = dalloc(ctx, Lf * Bp * Bp * 4, &ok);
+  if (ctx->prec == P_FP32T) ctx->yscratch = (float*)dalloc(ctx, (int64_t)whiten_trsm_simt_scratch_bytes(B), &ok);
   ctx->y0 = (float*)dalloc(ctx, Lf * Bp * 4, &ok);
   ctx->inv_s2 = (float*)dalloc(ctx, Lf * 4, &ok);
   ctx->status = (int32_t*)dalloc(ctx, std::max(Ls, Lf) * 4, &ok);
@@ -730,7 +733,7 @@ int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o, i
   } else if (ctx->prec == P_FP32T) {
     KL("whiten_score", launch_whiten_trsm_simt(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt,
                                                (const float*)ctx->wmat, ctx->y0, ctx->inv_s2, ctx->status,
-                                               factor_stride, o, st, &ctx->lc));
+                                               factor_stride, o, ctx->yscratch, st, &ctx->lc));
   } else if (ctx->prec != P_FP32) {
     KL("whiten_score", launch_whiten_tc(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->prec,
                                         &ctx->gmap, ctx->y0, ctx->inv_s2, ctx->status, factor_stride, o,

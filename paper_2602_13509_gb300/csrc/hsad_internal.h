@@ -231,11 +231,14 @@ cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, const int
                                const float* m, const float* inv_s2, const int32_t* status, int factor_stride,
                                ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc);
 // K6, triangular-solve form on the SIMT cores (P_FP32T factors): the same blocked forward
-// substitution in FP32 with H in FP32, 64 pixels per CTA.
+// substitution in FP32 with H in FP32 (stored transposed, see h_index), 128 pixels per
+// item of a persistent grid; yscratch: whiten_trsm_simt_scratch_bytes(B) of device memory
+// (one slot per resident CTA) for the whitened blocks of the items in flight.
 cudaError_t launch_whiten_trsm_simt(const void* x, int L, int W, int B, int in_type, const int32_t* c_int,
                                     const float* c_flt, const float* H, const float* m, const float* inv_s2,
-                                    const int32_t* status, int factor_stride, ScoreOut out, cudaStream_t st,
-                                    LaunchCounter* lc);
+                                    const int32_t* status, int factor_stride, ScoreOut out, float* yscratch,
+                                    cudaStream_t st, LaunchCounter* lc);
+size_t whiten_trsm_simt_scratch_bytes(int B);
 // Ring depth the triangular-solve whitening runs with for B bands; 0 if it does not fit.
 int whiten_trsm_stages(int B);
 // Working form of a context. The triangular solve halves the factor work but its

@@ -129,22 +129,27 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
                                 const int64_t* __restrict__ n0_dev, int every, int q_off,
                                 const double* __restrict__ n_line) {
   const int t = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (skip_line(status, t, every, q_off)) return;  // the same for the whole block
   const int i = blockIdx.x * 8 + warp;
-  if (i >= B || skip_line(status, t, every, q_off)) return;
+  const double* m = m_all + (int64_t)t * B;
+  // the means as float-float pairs, once per block (FP64 conversions are slow here)
+  __shared__ float2 mf[512];
+  const int jmax = min(B, blockIdx.x * 8 + 8);
+  for (int j = threadIdx.x; j < jmax; j += blockDim.x) mf[j] = dff(m[j]);
+  __syncthreads();
+  if (i >= B) return;
   const int64_t n = (n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W;
   const double nn = n_line ? n_line[t] : (double)n, inv_nm1 = 1.0 / (nn - 1.0);
-  const double* m = m_all + (int64_t)t * B;
   double* row = sigma_all + (int64_t)t * B * B + (int64_t)i * B;
   float2* row2 = reinterpret_cast<float2*>(row);
   const double nmi = nn * m[i];
   const float2 nmi_f = dff(nmi), sc_f = dff(inv_nm1);
   for (int j0 = 0; j0 <= i; j0 += 128) {
-    double v[4], mj[4];
+    double v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {  // four independent loads per lane
       const int j = j0 + lane + 32 * u;
       v[u] = j <= i ? row[j] : 0.0;
-      mj[u] = j <= i ? m[j] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -152,10 +157,10 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
       if (j > i) continue;
       float2 s2;
       if (int_double_to_ff(v[u], s2)) {
-        const float2 p = ff_mul(nmi_f, dff(mj[u]));
+        const float2 p = ff_mul(nmi_f, mf[j]);
         row2[j] = ff_mul(ff_sub(s2, p), sc_f);
       } else {
-        row2[j] = dff(inv_nm1 * fma(-nmi, mj[u], v[u]));
+        row2[j] = dff(inv_nm1 * fma(-nmi, m[j], v[u]));
       }
     }
   }
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
   // ---- whitening operand, block column k: zero above the diagonal block, L_kk^{-1} on it
   for (int e = tid; e < (p + 64) * 64; e += TP_T) {
     const int n = e >> 6, c = e & 63;
-    const int64_t idx = (int64_t)n * Bp + p + c;
+    const int64_t idx = fk::h_index<PREC>(n, p + c, Bp);
     if (n >= p && c <= n - p && n - p < kb && c < kb)
       fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Iv[(n - p) * DS + c]));
     else
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
     // the operand's rows c0 .. c0 + 63 of block column k
     for (int e = tid; e < 64 * 64; e += TP_T) {
       const int r = e >> 6, c = e & 63;
-      const int64_t idx = (int64_t)(c0 + r) * Bp + p + c;
+      const int64_t idx = fk::h_index<PREC>(c0 + r, p + c, Bp);
       if (c0 + r < B && c < kb) fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Ch[r * DS + c]));
       else fk::WOut<PREC>::zero(w, plane, idx);
     }
