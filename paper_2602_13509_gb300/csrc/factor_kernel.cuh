@@ -546,8 +546,12 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
     // 64 x 64 blocks, H_ii = L_ii^{-1}; y0 = m (the whitening forms x' - m in FP32); no scale
     const int64_t plane = (int64_t)Bp * Bp;
     void* w = (char*)wmat + (size_t)t * plane * 4;
-    for (int n = gwarp; n < Bp; n += gwarps) {
-      for (int k = lane; k < Bp; k += 32) {
+    // (u, v) = (row n, column k), or (column k, row n) for the transposed FP32 layout, so
+    // that the lanes of a warp write consecutive addresses
+    constexpr bool TR = PREC == P_FP32T;
+    for (int u = gwarp; u < Bp; u += gwarps) {
+      for (int v = lane; v < Bp; v += 32) {
+        const int n = TR ? v : u, k = TR ? u : v;
         const int64_t idx = h_index<PREC>(n, k, Bp);
         if (n < B && k <= n) {
           const T* src = ((n >> 6) == (k >> 6)) ? Inv : A2;
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(FT, MB) factor_kernel(double* __restrict__ sig
           WOut<PREC>::zero(w, plane, idx);
         }
       }
-      if (lane == 0) y0_all[(int64_t)t * Bp + n] = (n < B) ? (float)m[n] : 0.0f;
+      if (lane == 0) y0_all[(int64_t)t * Bp + u] = (u < B) ? (float)m[u] : 0.0f;
     }
     if (gtid == 0) inv_s2_all[t] = 1.0f;
     if (CL > 1) csync<CL>();  // no CTA leaves while others may still read its shared memory

@@ -322,8 +322,9 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
   }
 
   // ---- whitening operand, block column k: zero above the diagonal block, L_kk^{-1} on it
+  constexpr bool TR = PREC == P_FP32T;  // transposed operand: consecutive threads on consecutive rows n
   for (int e = tid; e < (p + 64) * 64; e += TP_T) {
-    const int n = e >> 6, c = e & 63;
+    const int n = TR ? e % (p + 64) : e >> 6, c = TR ? e / (p + 64) : e & 63;
     const int64_t idx = fk::h_index<PREC>(n, p + c, Bp);
     if (n >= p && c <= n - p && n - p < kb && c < kb)
       fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Iv[(n - p) * DS + c]));
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
     __syncthreads();
     // the operand's rows c0 .. c0 + 63 of block column k
     for (int e = tid; e < 64 * 64; e += TP_T) {
-      const int r = e >> 6, c = e & 63;
+      const int r = TR ? e & 63 : e >> 6, c = TR ? e >> 6 : e & 63;
       const int64_t idx = fk::h_index<PREC>(c0 + r, p + c, Bp);
       if (c0 + r < B && c < kb) fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Ch[r * DS + c]));
       else fk::WOut<PREC>::zero(w, plane, idx);
