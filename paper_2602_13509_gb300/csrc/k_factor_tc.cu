@@ -168,7 +168,7 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
 
 // ---- panel ------------------------------------------------------------------------------
 template <int PREC>
-__global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__ sigma_all,
+__global__ void __launch_bounds__(TP_T, 3) tcf_panel_kernel(double* __restrict__ sigma_all,
                                                             uint8_t* __restrict__ slice_all, size_t slice_stride,
                                                             const double* __restrict__ m_all, int B, int k,
                                                             int32_t* __restrict__ status, int every, int q_off,
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
   extern __shared__ __align__(16) float2 psm[];
   float2* Dg = psm;             // [64][DS] the diagonal block, then L_kk
   float2* Iv = Dg + 64 * DS;    // [64][DS] L_kk^{-1}
-  float2* Ch = Iv + 64 * DS;    // [64][DS] a chunk of 64 rows below: A_ik, then L_ik
+  float2* Ch = Dg;              // [64][DS] a chunk of 64 rows below: A_ik, then L_ik (L_kk is dead by then)
   __shared__ float2 rdg[64];
   __shared__ int notpd;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -222,17 +222,16 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
           if (!(a.x > 0.f) || !isfinite(a.x)) {
             notpd = 1;
           } else {
-            // sqrt: s0 = sqrt(a_hi), l = s0 + (a - s0^2) / (2 s0) with s0^2 exact (two-product)
-            const float s0 = __fsqrt_rn(a.x);
-            const float q = __fmul_rn(s0, s0), qe = __fmaf_rn(s0, s0, -q);
-            const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.x, q), qe), a.y);
-            const float2 l = ff_norm(s0, __fdiv_rn(res, __fmul_rn(2.f, s0)));
-            // 1 / l: r0 = 1 / l_hi, r = r0 + r0 (1 - l r0) with l r0 as float-float
-            const float r0 = __frcp_rn(l.x);
-            const float pp = __fmul_rn(l.x, r0), pe = __fmaf_rn(l.x, r0, -pp);
-            const float d = __fsub_rn(__fsub_rn(__fsub_rn(1.f, pp), pe), __fmul_rn(l.y, r0));
-            Dg[(p0 + j) * DS + p0 + j] = l;
-            rdg[p0 + j] = ff_norm(r0, __fmul_rn(r0, d));
+            // r = 1 / sqrt(a) from the FP32 seed by two Newton steps r += r (1 - a r^2) / 2 in
+            // float-float; then l = a r (= sqrt(a)) and 1 / l = r
+            float2 r = make_float2(rsqrtf(a.x), 0.f);
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+              const float2 e = ff_sub(make_float2(1.f, 0.f), ff_mul(a, ff_mul(r, r)));
+              r = ff_sub(r, ff_mul(r, make_float2(-0.5f * e.x, -0.5f * e.y)));
+            }
+            Dg[(p0 + j) * DS + p0 + j] = ff_mul(a, r);
+            rdg[p0 + j] = r;
           }
         }
         __syncwarp();
@@ -255,6 +254,22 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
           }
         }
         __syncwarp();
+      }
+    } else if (p0 == 0) {
+      // meanwhile the other warps write what does not depend on the factor: the operand's
+      // block column k above the diagonal block (zero) and the zero digit rows past Bp
+      constexpr bool TRz = PREC == P_FP32T;
+      const int t2 = tid - 32, nt2 = TP_T - 32;
+      for (int e = t2; e < p * 64; e += nt2) {
+        const int n = TRz ? e % p : e >> 6, c = TRz ? e / p : e & 63;
+        fk::WOut<PREC>::zero(w, plane, fk::h_index<PREC>(n, p + c, Bp));
+      }
+      for (int e = t2; e < 64 * 64; e += nt2) {
+        const int r = Bp + (e >> 6), c = e & 63;
+        const uint32_t off = tc::sw128_offset(r, c);
+#pragma unroll
+        for (int d = 0; d < NDIG; ++d) *(uint16_t*)(sl + d * plane_bytes(Bp) + off) = 0;
+        if (c == 0) expo[r] = 0;
       }
     }
     __syncthreads();
@@ -323,10 +338,10 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
 
   // ---- whitening operand, block column k: zero above the diagonal block, L_kk^{-1} on it
   constexpr bool TR = PREC == P_FP32T;  // transposed operand: consecutive threads on consecutive rows n
-  for (int e = tid; e < (p + 64) * 64; e += TP_T) {
-    const int n = TR ? e % (p + 64) : e >> 6, c = TR ? e / (p + 64) : e & 63;
+  for (int e = tid; e < 64 * 64; e += TP_T) {  // rows p .. p + 63 (those above were zeroed)
+    const int n = p + (TR ? e & 63 : e >> 6), c = TR ? e >> 6 : e & 63;
     const int64_t idx = fk::h_index<PREC>(n, p + c, Bp);
-    if (n >= p && c <= n - p && n - p < kb && c < kb)
+    if (c <= n - p && n - p < kb && c < kb)
       fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Iv[(n - p) * DS + c]));
     else
       fk::WOut<PREC>::zero(w, plane, idx);
@@ -400,14 +415,6 @@ __global__ void __launch_bounds__(TP_T, 2) tcf_panel_kernel(double* __restrict__
       }
     }
     __syncthreads();  // before the next chunk overwrites Ch
-  }
-  // rows past the last chunk up to Bp + 64 (the update kernel's 128-row tiles may read them)
-  for (int e = tid; e < 64 * 64; e += TP_T) {
-    const int r = Bp + (e >> 6), c = e & 63;
-    const uint32_t off = tc::sw128_offset(r, c);
-#pragma unroll
-    for (int d = 0; d < NDIG; ++d) *(uint16_t*)(sl + d * plane_bytes(Bp) + off) = 0;
-    if (c == 0) expo[r] = 0;
   }
 }
 
@@ -576,7 +583,7 @@ cudaError_t launch_factor_tc(double* sigma, double* scratch, const double* m, in
                                                          n_line);
   cudaError_t e = cudaGetLastError();
   if (lc) lc->n += 1;
-  const size_t psmem = (size_t)3 * 64 * DS * sizeof(float2);
+  const size_t psmem = (size_t)2 * 64 * DS * sizeof(float2);
   auto panel = prec == P_BF16T ? tcf_panel_kernel<P_BF16T> : tcf_panel_kernel<P_FP32T>;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
   if (e == cudaSuccess)
