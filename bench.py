@@ -181,50 +181,86 @@ def accuracy_vs_oracle(s, m, ref, B, prec, t):
             "mask_diff_outside_margin": int((diff & ~band).sum()), "mask_diff_total": int(diff.sum())}
 
 
+def factor_parts_per_line(B):
+    """Algorithmic flops of one line's blocked factorisation in 64-column panels (the
+    tensor-core factor): per panel k (kb columns, r rows below) the diagonal block's Cholesky
+    kb^3/3 and inverse kb^3/3 and the rows' triangular solve r kb^2 (the panel kernel), and
+    the rest of the Cholesky's B^3/3, the trailing updates (the update kernel)."""
+    panel, chol_panel = 0.0, 0.0
+    for p0 in range(0, B, 64):
+        kb = min(64, B - p0)
+        r = B - p0 - kb
+        panel += 2 * kb ** 3 / 3.0 + r * kb * kb
+        chol_panel += kb ** 3 / 3.0 + r * kb * kb
+    return panel, B ** 3 / 3.0 - chol_panel
+
+
 def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
-    """Roofline entries of the factor, covariance (SYRK) and whitening kernels of one arm:
-    algorithmic work per launch (SURVEY-style per-unit figures x units per launch) over the
-    launch's average CUDA-event duration, against the peak of the unit that bounds it."""
+    """Roofline entries of the factor (whole, or its covariance, panel and update kernels),
+    covariance (SYRK) and whitening kernels of one arm: algorithmic work per step (per-unit
+    figures x units per step) over the kernel class's CUDA-event time per step, against the
+    peak of the unit that bounds it."""
     out = {}
     px_step = T * W
+    lines = T / max(1, every)                    # factorisations per step
+    ffp = ff_peak_tflops(mhz)
     for name, (n, tot) in prof.items():
-        if name not in ("factor", "syrk", "whiten_score") or n == 0:
+        if n == 0 or name not in ("factor", "factor_form", "factor_panel", "factor_update", "syrk", "whiten_score"):
             continue
-        avg_ms = tot / n
-        lps = n / prof_steps                       # launches per step
+        ms = tot / prof_steps
+        r = None
         if name == "factor":
-            lines_per_launch = T / lps
-            work = lines_per_launch / max(1, every) * factor_flops_per_line(B, form)
-            ach = work / (avg_ms / 1e3) / 1e12
-            pk = ff_peak_tflops(mhz)
-            key = (B, form)
-            r = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                 "traffic": (FACTOR_DRAM_BYTES_PER_LINE[key] * lines_per_launch
-                             if key in FACTOR_DRAM_BYTES_PER_LINE else None),
-                 "traffic_algorithmic": lines_per_launch * (B * B * 8 + B * 8 + pad64(B) ** 2 * 4),
-                 "kernel": "factor (Cholesky + inverses of the 64 x 64 diagonal blocks)" if form
+            work = lines * factor_flops_per_line(B, form)
+            ach = work / (ms / 1e3) / 1e12
+            r = {"bound": "alu", "achieved": ach, "peak": ffp, "unit": "TFLOP/s", "frac": ach / ffp,
+                 "traffic_algorithmic": lines * (B * B * 8 + B * 8 + pad64(B) ** 2 * 4),
+                 "kernel": "factor (CUDA cores: Cholesky + inverses of the 64 x 64 diagonal blocks)" if form
                            else "factor (Cholesky + triangular inverse)",
-                 "work_per_launch": (f"{lines_per_launch:.0f} lines x (B^3/3 + sum of 64-block b^3/3) flop"
-                                     if form else f"{lines_per_launch:.0f} lines x 2B^3/3 flop"),
+                 "work_per_step": (f"{lines:.0f} lines x (B^3/3 + sum of 64-block b^3/3) flop" if form
+                                   else f"{lines:.0f} lines x 2B^3/3 flop"),
                  "peak_source": "derived: 152 SMs x %.0f MHz x 128 FP32 lanes x 2 flop / 12 FP32 instructions "
                                 "per float-float multiply-subtract" % mhz,
                  "fp64_peak_derived": fp64_peak_tflops(mhz), "frac_of_fp64_peak": ach / fp64_peak_tflops(mhz)}
+        elif name == "factor_panel":
+            work = lines * factor_parts_per_line(B)[0]
+            ach = work / (ms / 1e3) / 1e12
+            r = {"bound": "alu", "achieved": ach, "peak": ffp, "unit": "TFLOP/s", "frac": ach / ffp,
+                 "kernel": "factor panels (64 x 64 diagonal block Cholesky + inverse, rows' triangular solve; "
+                           "float-float on the CUDA cores)",
+                 "work_per_step": f"{lines:.0f} lines x sum over panels (2 kb^3/3 + r kb^2) flop",
+                 "peak_source": "derived: 152 SMs x %.0f MHz x 128 FP32 lanes x 2 flop / 12 FP32 instructions "
+                                "per float-float multiply-subtract" % mhz}
+        elif name == "factor_update":
+            work = lines * factor_parts_per_line(B)[1]
+            ach = work / (ms / 1e3) / 1e12
+            pk = peaks["bf16_tflops"]
+            r = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                 "kernel": "factor trailing updates (tcgen05, six-digit exact BF16 split: 21 digit-product "
+                           "MMAs per algorithmic product)",
+                 "work_per_step": f"{lines:.0f} lines x (B^3/3 - panel Cholesky flops) algorithmic flop",
+                 "issued_tflops": 21 * ach, "peak_source": f"{peaks['source']} bf16 burst"}
+        elif name == "factor_form":
+            byts = lines * B * (B + 1) / 2 * 16
+            ach = byts / (ms / 1e3) / 1e9
+            r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": ach / peaks["hbm_gbs"], "kernel": "covariance formation (FP64 sums in, float-float out)",
+                 "work_per_step": f"{lines:.0f} lines x B(B+1)/2 x 16 bytes", "peak_source": peaks["source"]}
         else:
-            px = px_step / lps
-            flops = px * B * (B + 1)               # B(B+1)/2 multiply-adds per pixel
-            byts = px * (2 * B + (5 if name == "whiten_score" else 0))
-            ach = flops / (avg_ms / 1e3) / 1e12
+            flops = px_step * B * (B + 1)               # B(B+1)/2 multiply-adds per pixel
+            byts = px_step * (2 * B + (5 if name == "whiten_score" else 0))
+            ach = flops / (ms / 1e3) / 1e12
             if name == "whiten_score" and prec == "fp32":
                 pk, bound, src = fp32_peak_tflops(mhz), "alu", "derived: 152 SMs x %.0f MHz x 128 FFMA x 2" % mhz
             else:
                 pk, bound, src = peaks["bf16_tflops"], "tensor", f"{peaks['source']} bf16 burst"
             r = {"bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                 "traffic": None, "traffic_algorithmic": byts,
-                 "kernel": name, "work_per_launch": f"{px:.0f} px x B(B+1) flop", "peak_source": src,
-                 "hbm_achieved_gbs": byts / (avg_ms / 1e3) / 1e9, "hbm_frac": byts / (avg_ms / 1e3) / 1e9 /
-                 peaks["hbm_gbs"]}
-        r["avg_launch_ms"] = avg_ms
-        r["launches_per_step"] = lps
+                 "traffic_algorithmic": byts, "kernel": name, "work_per_step": f"{px_step} px x B(B+1) flop",
+                 "peak_source": src, "hbm_achieved_gbs": byts / (ms / 1e3) / 1e9,
+                 "hbm_frac": byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+        r["traffic"] = None
+        r["ms_per_step"] = ms
+        r["launches_per_step"] = n / prof_steps
+        r["avg_launch_ms"] = tot / n
         out[name] = r
     return out
 

@@ -658,6 +658,14 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   }
   // the calibration gain and offset cancel from Eq. 1 (RX is invariant under a per-band
   // affine map): validated above, not needed on the device
+  // the tensor-core factor writes only the lower part of the whitening operand and never the
+  // zero padding rows of its digit planes: both start (and stay) zero
+  if (ctx->tc_factor && (cudaMemsetAsync(ctx->wmat, 0, (size_t)Lf * Bp * Bp * 4, ctx->stream) != cudaSuccess ||
+                         cudaMemsetAsync(ctx->inv, 0, (size_t)Lf * B * B * 8, ctx->stream) != cudaSuccess)) {
+    cudaGetLastError();
+    release(ctx);
+    return fail(nullptr, HSAD_E_CUDA, "device initialisation failed");
+  }
   if (cudaMemsetAsync(ctx->state_s1, 0, B * 8, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->state_s2, 0, B * B * 8, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->r_status, 0xff, ctx->ring * 4, ctx->stream) != cudaSuccess ||
@@ -770,14 +778,20 @@ int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* ou
 // The factor of L lines of streamed statistics: the tensor-core factor where the context
 // uses it, else the factor kernel (same output layout; the choice depends only on the
 // context, so a line's factor does not depend on how lines are batched).
-cudaError_t factor_lines(hsad_ctx* ctx, double* sigma, double* inv, const double* m, int L, void* wmat, float* y0,
-                         float* inv_s2, int32_t* status, int64_t n0, int W, int incl, const int64_t* n0_dev,
-                         int every, int q_off, const double* n_line) {
-  if (ctx->tc_factor)
-    return launch_factor_tc(sigma, inv, m, L, ctx->B, ctx->prec, wmat, y0, inv_s2, status, n0, W, incl, ctx->stream,
-                            &ctx->lc, n0_dev, every, q_off, n_line, ctx->dev_err);
-  return launch_factor(sigma, inv, m, L, ctx->B, ctx->fprec, wmat, y0, inv_s2, status, n0, W, incl, ctx->stream,
-                       &ctx->lc, n0_dev, every, q_off, n_line);
+int factor_lines(hsad_ctx* ctx, double* sigma, double* inv, const double* m, int L, void* wmat, float* y0,
+                 float* inv_s2, int32_t* status, int64_t n0, int W, int incl, const int64_t* n0_dev, int every,
+                 int q_off, const double* n_line) {
+  if (ctx->tc_factor) {
+    static const char* names[3] = {"factor_form", "factor_panel", "factor_update"};
+    for (int s = 0; s < factor_tc_steps(ctx->B); ++s)
+      KL(names[s == 0 ? 0 : (s & 1) ? 1 : 2],
+         launch_factor_tc_step(s, sigma, inv, m, L, ctx->B, ctx->prec, wmat, y0, inv_s2, status, n0, W, incl,
+                               ctx->stream, &ctx->lc, n0_dev, every, q_off, n_line, ctx->dev_err));
+    return HSAD_OK;
+  }
+  KL("factor", launch_factor(sigma, inv, m, L, ctx->B, ctx->fprec, wmat, y0, inv_s2, status, n0, W, incl,
+                             ctx->stream, &ctx->lc, n0_dev, every, q_off, n_line));
+  return HSAD_OK;
 }
 
 // Everything of an EXCLUSIVE batch after its first line is scored: the batch's statistics,
@@ -806,9 +820,12 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
                                        ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc, gain, ctx->s1_line,
                                      ctx->c_int, W, ctx->lam));
-  KL("factor", factor_lines(ctx, ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L,
-                            (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1, ctx->status + 1,
-                            ctx->n_stats, W, 1, n0_dev, ctx->every, q0 + 1, n_line));
+  {
+    const int rc_f = factor_lines(ctx, ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L,
+                                    (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1, ctx->status + 1,
+                                    ctx->n_stats, W, 1, n0_dev, ctx->every, q0 + 1, n_line);
+    if (rc_f != HSAD_OK) return rc_f;
+  }
   if (L > 1) {
     ScoreOut o1 = score_out(ctx, first + 1, true);
     o1.factor_base = 1;
@@ -927,8 +944,11 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
                         ctx->min_pix, ctx->status, st, &ctx->lc, nullptr, gain, ctx->c_int, ctx->lam, n_line));
   KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc, gain, ctx->s1_line,
                                      ctx->c_int, W, ctx->lam));
-  KL("factor", factor_lines(ctx, ctx->sigma, ctx->inv, ctx->m_line, L, ctx->wmat, ctx->y0, ctx->inv_s2,
-                            ctx->status, ctx->n_stats, W, incl, nullptr, 1, 0, n_line));
+  {
+    const int rc_f = factor_lines(ctx, ctx->sigma, ctx->inv, ctx->m_line, L, ctx->wmat, ctx->y0, ctx->inv_s2,
+                                    ctx->status, ctx->n_stats, W, incl, nullptr, 1, 0, n_line);
+    if (rc_f != HSAD_OK) return rc_f;
+  }
   {
     int rc = whiten(ctx, x, L, 1, score_out(ctx, first, true));
     if (rc != HSAD_OK) return rc;
@@ -1496,8 +1516,11 @@ int hsad_set_stats(hsad_ctx* ctx, int64_t n_pixels, const double* shift, const d
     CK(cudaMemcpyAsync(ctx->sigma, s2, (size_t)B * B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->m_line, m.data(), (size_t)B * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->status, &st0, 4, cudaMemcpyHostToDevice, st));
-    KL("factor", factor_lines(ctx, ctx->sigma, ctx->inv, ctx->m_line, 1, ctx->wmat, ctx->y0, ctx->inv_s2,
-                              ctx->status, n_pixels, 0, 0, nullptr, 1, 0, nullptr));
+    {
+    const int rc_f = factor_lines(ctx, ctx->sigma, ctx->inv, ctx->m_line, 1, ctx->wmat, ctx->y0, ctx->inv_s2,
+                                      ctx->status, n_pixels, 0, 0, nullptr, 1, 0, nullptr);
+    if (rc_f != HSAD_OK) return rc_f;
+  }
     CK(cudaStreamSynchronize(st));  // the host vectors above are copied before they go out of scope
   } else {
     CK(cudaStreamSynchronize(st));

@@ -163,11 +163,14 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
 // the triangular-solve forms with the float-float factor, the trailing updates as exact
 // digit-split BF16 contractions. Needs B >= 192 (the slices live in the inverse scratch);
 // err is set if a bounded wait expires.
+// Its launches, in order: step 0 forms the covariance; steps 2k + 1 and 2k + 2 are the panel
+// and the trailing update of 64-column panel k (the last panel has no update).
 bool factor_tc_supported(int B, int prec);
-cudaError_t launch_factor_tc(double* sigma, double* scratch, const double* m, int L, int B, int prec, void* wmat,
-                             float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
-                             cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev, int every, int q_off,
-                             const double* n_line, int32_t* err);
+int factor_tc_steps(int B);
+cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, const double* m, int L, int B, int prec,
+                                  void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
+                                  int incl, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev, int every,
+                                  int q_off, const double* n_line, int32_t* err);
 
 // K6 (SIMT): delta_p = inv_s2 * || G (x_p - c) - y0 ||^2 for every pixel of every line,
 // threshold, and scatter into the result ring. factor_stride = 0 makes every line

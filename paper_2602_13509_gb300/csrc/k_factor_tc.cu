@@ -222,11 +222,12 @@ __global__ void __launch_bounds__(TP_T, 3) tcf_panel_kernel(double* __restrict__
           if (!(a.x > 0.f) || !isfinite(a.x)) {
             notpd = 1;
           } else {
-            // r = 1 / sqrt(a) from the FP32 seed by two Newton steps r += r (1 - a r^2) / 2 in
+            // r = 1 / sqrt(a) from the FP32 seed by a Newton step r += r (1 - a r^2) / 2 in
             // float-float; then l = a r (= sqrt(a)) and 1 / l = r
+            // (the seed's relative error, below 2^-22, squares to below 2^-44 in one step: the
+            // order of the six-digit updates' 2^-45)
             float2 r = make_float2(rsqrtf(a.x), 0.f);
-#pragma unroll
-            for (int it = 0; it < 2; ++it) {
+            {
               const float2 e = ff_sub(make_float2(1.f, 0.f), ff_mul(a, ff_mul(r, r)));
               r = ff_sub(r, ff_mul(r, make_float2(-0.5f * e.x, -0.5f * e.y)));
             }
@@ -254,22 +255,6 @@ __global__ void __launch_bounds__(TP_T, 3) tcf_panel_kernel(double* __restrict__
           }
         }
         __syncwarp();
-      }
-    } else if (p0 == 0) {
-      // meanwhile the other warps write what does not depend on the factor: the operand's
-      // block column k above the diagonal block (zero) and the zero digit rows past Bp
-      constexpr bool TRz = PREC == P_FP32T;
-      const int t2 = tid - 32, nt2 = TP_T - 32;
-      for (int e = t2; e < p * 64; e += nt2) {
-        const int n = TRz ? e % p : e >> 6, c = TRz ? e / p : e & 63;
-        fk::WOut<PREC>::zero(w, plane, fk::h_index<PREC>(n, p + c, Bp));
-      }
-      for (int e = t2; e < 64 * 64; e += nt2) {
-        const int r = Bp + (e >> 6), c = e & 63;
-        const uint32_t off = tc::sw128_offset(r, c);
-#pragma unroll
-        for (int d = 0; d < NDIG; ++d) *(uint16_t*)(sl + d * plane_bytes(Bp) + off) = 0;
-        if (c == 0) expo[r] = 0;
       }
     }
     __syncthreads();
@@ -315,19 +300,17 @@ __global__ void __launch_bounds__(TP_T, 3) tcf_panel_kernel(double* __restrict__
     __syncthreads();
     // rank-nb updates: A[r][c] -= sum_q L[r][p0 + q] L[c][p0 + q] (p0 + nb <= c <= r < kb) and
     // R[r][c] -= sum_q L[r][p0 + q] X[p0 + q][c] (r >= p0 + nb, c < p0 + nb)
-    const int na = nbel * (nbel + 1) / 2, nr = nbel * (p0 + nb);
-    for (int e = tid; e < na + nr; e += TP_T) {
-      if (e < na) {
-        int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-        while (r * (r + 1) / 2 > e) --r;
-        while ((r + 1) * (r + 2) / 2 <= e) ++r;
-        const int c = e - r * (r + 1) / 2;
+    const int nr = nbel * (p0 + nb);
+    for (int e = tid; e < 64 * nbel + nr; e += TP_T) {
+      if (e < 64 * nbel) {  // (r, c) on a 64-wide grid, the lower triangle only
+        const int r = e >> 6, c = e & 63;
+        if (c > r) continue;
         const int ri = p0 + nb + r, ci = p0 + nb + c;
         float2 v = Dg[ri * DS + ci];
         for (int q = 0; q < nb; ++q) ff_fms(v.x, v.y, Dg[ri * DS + p0 + q], Dg[ci * DS + p0 + q]);
         Dg[ri * DS + ci] = ff_norm(v.x, v.y);
       } else {
-        const int f = e - na, ri = p0 + nb + f / (p0 + nb), c = f % (p0 + nb);
+        const int f = e - 64 * nbel, ri = p0 + nb + f / (p0 + nb), c = f % (p0 + nb);
         float2 v = Iv[ri * DS + c];
         for (int q = 0; q < nb; ++q) ff_fms(v.x, v.y, Dg[ri * DS + p0 + q], Iv[(p0 + q) * DS + c]);
         Iv[ri * DS + c] = ff_norm(v.x, v.y);
@@ -338,7 +321,7 @@ __global__ void __launch_bounds__(TP_T, 3) tcf_panel_kernel(double* __restrict__
 
   // ---- whitening operand, block column k: zero above the diagonal block, L_kk^{-1} on it
   constexpr bool TR = PREC == P_FP32T;  // transposed operand: consecutive threads on consecutive rows n
-  for (int e = tid; e < 64 * 64; e += TP_T) {  // rows p .. p + 63 (those above were zeroed)
+  for (int e = tid; e < 64 * 64; e += TP_T) {  // rows p .. p + 63 (those above stay zero from creation)
     const int n = p + (TR ? e & 63 : e >> 6), c = TR ? e >> 6 : e & 63;
     const int64_t idx = fk::h_index<PREC>(n, p + c, Bp);
     if (c <= n - p && n - p < kb && c < kb)
@@ -568,40 +551,42 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
 
 bool factor_tc_supported(int B, int prec) { return is_trsm(prec) && B >= 192; }
 
-cudaError_t launch_factor_tc(double* sigma, double* scratch, const double* m, int L, int B, int prec, void* wmat,
-                             float* y0, float* inv_s2, int32_t* status, int64_t n0, int W, int incl,
-                             cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev, int every, int q_off,
-                             const double* n_line, int32_t* err) {
+int factor_tc_steps(int B) { return 2 * (pad64(B) / 64); }
+
+cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, const double* m, int L, int B, int prec,
+                                  void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
+                                  int incl, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev, int every,
+                                  int q_off, const double* n_line, int32_t* err) {
   if (L <= 0) return cudaSuccess;
-  if (!factor_tc_supported(B, prec)) return cudaErrorInvalidValue;
-  const int Bp = pad64(B), nb = Bp / 64;
+  if (!factor_tc_supported(B, prec) || step < 0 || step >= factor_tc_steps(B)) return cudaErrorInvalidValue;
+  const int Bp = pad64(B);
   const size_t stride = (size_t)B * B * 8;  // the inverse scratch per line holds the slices
   if (slice_region_bytes(Bp) + 1024 > stride) return cudaErrorInvalidValue;
   uint8_t* slices = reinterpret_cast<uint8_t*>(scratch);
-  const long long limit = 4000000000LL;  // ~2 s of clock cycles
-  tcf_form_kernel<<<dim3((B + 7) / 8, L), 256, 0, st>>>(sigma, m, B, status, n0, W, incl, n0_dev, every, q_off,
-                                                         n_line);
-  cudaError_t e = cudaGetLastError();
-  if (lc) lc->n += 1;
-  const size_t psmem = (size_t)2 * 64 * DS * sizeof(float2);
-  auto panel = prec == P_BF16T ? tcf_panel_kernel<P_BF16T> : tcf_panel_kernel<P_FP32T>;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tcf_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TU_SMEM);
-  for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+  cudaError_t e = cudaSuccess;
+  if (step == 0) {
+    tcf_form_kernel<<<dim3((B + 7) / 8, L), 256, 0, st>>>(sigma, m, B, status, n0, W, incl, n0_dev, every, q_off,
+                                                           n_line);
+  } else if (step & 1) {
+    const int k = step / 2;
+    const size_t psmem = (size_t)2 * 64 * DS * sizeof(float2);
+    auto panel = prec == P_BF16T ? tcf_panel_kernel<P_BF16T> : tcf_panel_kernel<P_FP32T>;
+    e = cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    if (e != cudaSuccess) return e;
     panel<<<L, TP_T, psmem, st>>>(sigma, slices, stride, m, B, k, status, every, q_off, wmat, y0, inv_s2);
-    e = cudaGetLastError();
-    if (lc) lc->n += 1;
-    if (e != cudaSuccess || k == nb - 1) break;
+  } else {
+    const int k = step / 2 - 1;
+    const long long limit = 4000000000LL;  // ~2 s of clock cycles
+    e = cudaFuncSetAttribute(tcf_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TU_SMEM);
+    if (e != cudaSuccess) return e;
     const int r0 = 64 * (k + 1), nbr = (Bp - r0 + TU_M - 1) / TU_M, nbc = (Bp - r0) / TU_N;
     int tiles = 0;
     for (int a = 0; a < nbr; ++a) tiles += (2 * a + 2 < nbc) ? 2 * a + 2 : nbc;
     tcf_update_kernel<<<dim3(tiles, L), TU_T, TU_SMEM, st>>>(sigma, slices, stride, B, k, status, every, q_off, err,
                                                                limit);
-    e = cudaGetLastError();
-    if (lc) lc->n += 1;
   }
-  return e;
+  if (lc) lc->n += 1;
+  return cudaGetLastError();
 }
 
 }  // namespace hsad

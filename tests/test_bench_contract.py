@@ -38,8 +38,8 @@ def test_roofline_work_and_peaks():
 
 
 def test_kernel_rooflines_from_a_profile():
-    """Per-kernel roofline entries: algorithmic work per launch over the launch's time,
-    against the peak of the unit that bounds each kernel."""
+    """Per-kernel roofline entries: algorithmic work per step over the class's time per
+    step, against the peak of the unit that bounds each kernel."""
     sys.path.insert(0, ROOT)
     import bench
     peaks = {"hbm_gbs": 6753.4, "bf16_tflops": 1849.2, "source": "measured"}
@@ -49,16 +49,24 @@ def test_kernel_rooflines_from_a_profile():
     r = bench.kernel_rooflines(prof, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)
     assert set(r) == {"factor", "syrk", "whiten_score"}
     f = r["factor"]
-    assert f["launches_per_step"] == 4 and abs(f["avg_launch_ms"] - 30.0) < 1e-12
-    assert abs(f["achieved"] - 2000 * bench.factor_flops_per_line(B, 1) / 0.030 / 1e12) < 1e-9
+    assert f["launches_per_step"] == 4 and abs(f["avg_launch_ms"] - 30.0) < 1e-12 and abs(f["ms_per_step"] - 120) < 1e-9
+    assert abs(f["achieved"] - 8000 * bench.factor_flops_per_line(B, 1) / 0.120 / 1e12) < 1e-9
     assert f["bound"] == "alu" and abs(f["frac"] - f["achieved"] / bench.ff_peak_tflops(2070.0)) < 1e-12
     s = r["syrk"]
-    px = T * W / 4
-    assert s["bound"] == "tensor" and abs(s["achieved"] - px * B * (B + 1) / 0.005 / 1e12) < 1e-9
+    assert s["bound"] == "tensor" and abs(s["achieved"] - T * W * B * (B + 1) / 0.020 / 1e12) < 1e-9
     assert abs(s["frac"] - s["achieved"] / 1849.2) < 1e-12
-    assert abs(s["traffic_algorithmic"] - px * 2 * B) < 1e-6
+    assert abs(s["traffic_algorithmic"] - T * W * 2 * B) < 1e-6
     w = r["whiten_score"]
     assert w["bound"] == "alu" and abs(w["peak"] - bench.fp32_peak_tflops(2070.0)) < 1e-12
-    assert abs(w["traffic_algorithmic"] - T * W / 8 * (2 * B + 5)) < 1e-6
+    assert abs(w["traffic_algorithmic"] - T * W * (2 * B + 5)) < 1e-6
     wb = bench.kernel_rooflines(prof, 2, T, W, B, 1, "bf16", 1, peaks, 2070.0)["whiten_score"]
     assert wb["bound"] == "tensor" and wb["peak"] == 1849.2
+    # the tensor-core factor's three classes: their algorithmic parts add up to the Cholesky
+    panel, upd = bench.factor_parts_per_line(B)
+    blocks = [min(64, B - p) for p in range(0, B, 64)]
+    assert abs((upd + panel - sum(b ** 3 / 3 for b in blocks)) - B ** 3 / 3) < 1e-3
+    prof2 = {"factor_form": (8, 8.0), "factor_panel": (56, 40.0), "factor_update": (48, 30.0)}
+    r2 = bench.kernel_rooflines(prof2, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)
+    assert r2["factor_update"]["bound"] == "tensor" and r2["factor_panel"]["bound"] == "alu"
+    assert abs(r2["factor_update"]["achieved"] - 8000 * upd / 0.015 / 1e12) < 1e-9
+    assert abs(r2["factor_form"]["achieved"] - 8000 * B * (B + 1) / 2 * 16 / 0.004 / 1e9) < 1e-6
