@@ -184,15 +184,17 @@ def accuracy_vs_oracle(s, m, ref, B, prec, t):
 def factor_parts_per_line(B):
     """Algorithmic flops of one line's blocked factorisation in 64-column panels (the
     tensor-core factor): per panel k (kb columns, r rows below) the diagonal block's Cholesky
-    kb^3/3 and inverse kb^3/3 and the rows' triangular solve r kb^2 (the panel kernel), and
-    the rest of the Cholesky's B^3/3, the trailing updates (the update kernel)."""
-    panel, chol_panel = 0.0, 0.0
+    kb^3/3 and inverse kb^3/3 (the diagonal-block kernel), the rows' triangular solve r kb^2
+    (the panel kernel), and the rest of the Cholesky's B^3/3, the trailing updates (the update
+    kernel)."""
+    diag, trsm, chol_panel = 0.0, 0.0, 0.0
     for p0 in range(0, B, 64):
         kb = min(64, B - p0)
         r = B - p0 - kb
-        panel += 2 * kb ** 3 / 3.0 + r * kb * kb
+        diag += 2 * kb ** 3 / 3.0
+        trsm += r * kb * kb
         chol_panel += kb ** 3 / 3.0 + r * kb * kb
-    return panel, B ** 3 / 3.0 - chol_panel
+    return diag, trsm, B ** 3 / 3.0 - chol_panel
 
 
 def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
@@ -205,7 +207,8 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
     lines = T / max(1, every)                    # factorisations per step
     ffp = ff_peak_tflops(mhz)
     for name, (n, tot) in prof.items():
-        if n == 0 or name not in ("factor", "factor_form", "factor_panel", "factor_update", "syrk", "whiten_score"):
+        if n == 0 or name not in ("factor", "factor_form", "factor_diag", "factor_panel", "factor_update", "syrk",
+                                   "whiten_score"):
             continue
         ms = tot / prof_steps
         r = None
@@ -221,17 +224,20 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
                  "peak_source": "derived: 152 SMs x %.0f MHz x 128 FP32 lanes x 2 flop / 12 FP32 instructions "
                                 "per float-float multiply-subtract" % mhz,
                  "fp64_peak_derived": fp64_peak_tflops(mhz), "frac_of_fp64_peak": ach / fp64_peak_tflops(mhz)}
-        elif name == "factor_panel":
-            work = lines * factor_parts_per_line(B)[0]
+        elif name in ("factor_diag", "factor_panel"):
+            diag = name == "factor_diag"
+            work = lines * factor_parts_per_line(B)[0 if diag else 1]
             ach = work / (ms / 1e3) / 1e12
             r = {"bound": "alu", "achieved": ach, "peak": ffp, "unit": "TFLOP/s", "frac": ach / ffp,
-                 "kernel": "factor panels (64 x 64 diagonal block Cholesky + inverse, rows' triangular solve; "
-                           "float-float on the CUDA cores)",
-                 "work_per_step": f"{lines:.0f} lines x sum over panels (2 kb^3/3 + r kb^2) flop",
+                 "kernel": ("factor diagonal blocks (64 x 64 Cholesky + inverse, float-float on the CUDA cores)"
+                            if diag else "factor panels (rows' triangular solve as a float-float product with "
+                            "the diagonal block's inverse, six-digit split)"),
+                 "work_per_step": (f"{lines:.0f} lines x sum over panels 2 kb^3/3 flop" if diag
+                                   else f"{lines:.0f} lines x sum over panels r kb^2 flop"),
                  "peak_source": "derived: 152 SMs x %.0f MHz x 128 FP32 lanes x 2 flop / 12 FP32 instructions "
                                 "per float-float multiply-subtract" % mhz}
         elif name == "factor_update":
-            work = lines * factor_parts_per_line(B)[1]
+            work = lines * factor_parts_per_line(B)[2]
             ach = work / (ms / 1e3) / 1e12
             pk = peaks["bf16_tflops"]
             r = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,

@@ -782,9 +782,9 @@ int factor_lines(hsad_ctx* ctx, double* sigma, double* inv, const double* m, int
                  float* inv_s2, int32_t* status, int64_t n0, int W, int incl, const int64_t* n0_dev, int every,
                  int q_off, const double* n_line) {
   if (ctx->tc_factor) {
-    static const char* names[3] = {"factor_form", "factor_panel", "factor_update"};
+    static const char* names[4] = {"factor_form", "factor_diag", "factor_panel", "factor_update"};
     for (int s = 0; s < factor_tc_steps(ctx->B); ++s)
-      KL(names[s == 0 ? 0 : (s & 1) ? 1 : 2],
+      KL(names[factor_tc_step_kind(s)],
          launch_factor_tc_step(s, sigma, inv, m, L, ctx->B, ctx->prec, wmat, y0, inv_s2, status, n0, W, incl,
                                ctx->stream, &ctx->lc, n0_dev, every, q_off, n_line, ctx->dev_err));
     return HSAD_OK;

@@ -167,6 +167,7 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
 // and the trailing update of 64-column panel k (the last panel has no update).
 bool factor_tc_supported(int B, int prec);
 int factor_tc_steps(int B);
+int factor_tc_step_kind(int step);  // 0 covariance, 1 diagonal block, 2 rows below, 3 update
 cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, const double* m, int L, int B, int prec,
                                   void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
                                   int incl, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev, int every,

@@ -7,16 +7,16 @@
 // Blocked right-looking Cholesky in 64-column panels, one launch per step for a whole
 // batch of lines:
 //   tcf_form_kernel      S = (S2 - n m m^T) / (n - 1) as float-float, in place;
-//   tcf_panel_kernel(k)  one CTA per line: the 64 x 64 diagonal block factored and inverted
-//                        in 16-column sub-panels (float-float, pivots by Newton steps), the
-//                        rows below solved
-//                        as L_ik = A_ik L_kk^{-T} (float-float product with the inverse), the
-//                        whitening operand's block column k written (L_kk^{-1} on the diagonal,
-//                        L_ik below), and every panel row split into six signed base-256
-//                        digits with a per-row power of two: L_ik[r][c] = 2^e_r
-//                        sum_t d_t[r][c] 256^-(t+1) up to 2^e_r 256^-6 / 2 (the error-free
-//                        splitting of Ozaki et al., 2012, with BF16 digits: every digit is an
-//                        integer of magnitude <= 256, exact in BF16);
+//   tcf_diag_kernel(k)   one CTA per line: the 64 x 64 diagonal block factored and inverted
+//                        together (float-float, right-looking, pivots by a Newton step), the
+//                        whitening operand's diagonal block written (L_kk^{-1});
+//   tcf_trsm_kernel(k)   one CTA per line: the rows below solved as L_ik = A_ik L_kk^{-T}
+//                        (float-float product with the inverse), written to the whitening
+//                        operand, and every row split into six signed base-256 digits with a
+//                        per-row power of two: L_ik[r][c] = 2^e_r sum_t d_t[r][c] 256^-(t+1)
+//                        up to 2^e_r 256^-6 / 2 (the error-free splitting of Ozaki et al.,
+//                        2012, with BF16 digits: every digit is an integer of magnitude <= 256,
+//                        exact in BF16);
 //   tcf_update_kernel(k) A_ij -= sum_c L_ic L_jc over the trailing lower triangle in
 //                        128 x 64 tiles: for each digit level l = t + u <= 5 the products
 //                        d_t(i) d_u(j)^T are summed by tcgen05.mma (BF16 in, FP32 in TMEM).
@@ -28,8 +28,9 @@
 // about 2^-45 of the row scales per update, the order of float-float's 2^-48 (a CPU
 // emulation of this update on a 1024 x 448 stream covariance: score error 2e-12; at
 // condition number 1e10: 5e-7). Operand slices live in the context's inverse scratch
-// ([6][Bp + 64][64] BF16 per line, 128-byte swizzled rows, then the exponents, from the
-// first 1024-byte boundary of the line's slot), which is large enough from B = 192 on.
+// ([6][Bp + 64][64] BF16 per line, 128-byte swizzled rows, then the exponents and the
+// diagonal block's float-float inverse, from the first 1024-byte boundary of the line's
+// slot), which is large enough from B = 192 on.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -57,9 +58,13 @@ constexpr uint32_t TU_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + TU_TILE +
 // Byte layout of one line's slice region (in the inverse scratch): NDIG planes of
 // (Bp + 64) rows x 128 bytes, then (Bp + 64) int32 exponents.
 __host__ __device__ inline size_t plane_bytes(int Bp) { return (size_t)(Bp + 64) * 128; }
-__host__ __device__ inline size_t slice_region_bytes(int Bp) {
-  return NDIG * plane_bytes(Bp) + (size_t)(Bp + 64) * 4;
-}
+// the diagonal block's inverse X (float-float, [64][64]) follows the exponents
+__host__ __device__ inline size_t xinv_offset(int Bp) { return NDIG * plane_bytes(Bp) + (size_t)(Bp + 64) * 4; }
+__host__ __device__ inline size_t slice_region_bytes(int Bp) { return xinv_offset(Bp) + 64 * 64 * 8; }
+constexpr int TD_T = 128;            // threads per line of the diagonal-block kernel
+constexpr int TRI64 = 64 * 65 / 2;   // a packed 64 x 64 lower triangle
+__host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
+
 // Line t's slice region: its inverse-scratch slot rounded up to 1024 bytes (bulk copies
 // and the swizzled operand tiles need aligned rows).
 __host__ __device__ inline uint8_t* slice_base(uint8_t* all, size_t stride, int t) {
@@ -166,169 +171,128 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
   }
 }
 
-// ---- panel ------------------------------------------------------------------------------
+// ---- diagonal block -----------------------------------------------------------------------
+// One CTA of TD_T threads per line: the 64 x 64 diagonal block of panel k, as packed lower
+// triangles in shared memory, factored and inverted together, right-looking, a column at a
+// time: the pivot l = sqrt(A_jj) and r = 1 / l (float-float Newton step from the FP32 rsqrt
+// seed, computed by every thread), column j of L = A_.j r, row j of X = R_j. r (R: the
+// running right-hand sides, I at the start), then the rank-1 updates A_ic -= L_ij L_cj
+// (j < c <= i) and R_ic -= L_ij X_jc (i > j, c <= j) over the flattened trapezoid of rows
+// j + 1 .. kb - 1. Writes X (float-float, [64][64]) to the line's slice region for the
+// triangular solve, and the whitening operand's diagonal block (L_kk^{-1}).
 template <int PREC>
-__global__ void __launch_bounds__(TP_T, 3) tcf_panel_kernel(double* __restrict__ sigma_all,
-                                                            uint8_t* __restrict__ slice_all, size_t slice_stride,
-                                                            const double* __restrict__ m_all, int B, int k,
-                                                            int32_t* __restrict__ status, int every, int q_off,
-                                                            void* __restrict__ wmat, float* __restrict__ y0_all,
-                                                            float* __restrict__ inv_s2_all) {
+__global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sigma_all,
+                                                        uint8_t* __restrict__ slice_all, size_t slice_stride,
+                                                        const double* __restrict__ m_all, int B, int k,
+                                                        int32_t* __restrict__ status, int every, int q_off,
+                                                        void* __restrict__ wmat, float* __restrict__ y0_all,
+                                                        float* __restrict__ inv_s2_all) {
+  __shared__ float2 Dg[TRI64];  // L_kk, packed: (i, c) at tri(i) + c
+  __shared__ float2 X[TRI64];   // R, then X = L_kk^{-1}, packed
+  __shared__ uint8_t row_of[TRI64];
+  const int t = blockIdx.x, tid = threadIdx.x;
+  if (skip_line(status, t, every, q_off)) return;  // the same for the whole CTA
+  const int Bp = pad64(B), p = 64 * k, kb = min(64, B - p);
+  const float2* A = reinterpret_cast<const float2*>(sigma_all + (int64_t)t * B * B);
+  uint8_t* sl = slice_base(slice_all, slice_stride, t);
+  float2* Xg = reinterpret_cast<float2*>(sl + xinv_offset(Bp));
+  const int64_t plane = (int64_t)Bp * Bp;
+  void* w = (char*)wmat + (size_t)t * plane * 4;
+  if (k == 0) {  // the means of the triangular-solve form and the unit score scale
+    for (int n = tid; n < Bp; n += TD_T) y0_all[(int64_t)t * Bp + n] = n < B ? (float)m_all[(int64_t)t * B + n] : 0.f;
+    if (tid == 0) inv_s2_all[t] = 1.0f;
+  }
+  for (int e = tid; e < TRI64; e += TD_T) {
+    int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    while (tri(i + 1) <= e) ++i;
+    while (tri(i) > e) --i;
+    const int c = e - tri(i);
+    row_of[e] = (uint8_t)i;
+    Dg[e] = i < kb ? A[(int64_t)(p + i) * B + p + c] : make_float2(0.f, 0.f);
+    X[e] = make_float2(i == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    const float2 a = Dg[tri(j) + j];
+    if (!(a.x > 0.f) || !isfinite(a.x)) {  // the same value in every thread
+      if (tid == 0) status[t] = LS_NOT_PD;
+      return;
+    }
+    // r = 1 / sqrt(a): FP32 seed, one Newton step r += r (1 - a r^2) / 2 in float-float (the
+    // seed's relative error, below 2^-22, squares to below 2^-44: the order of the six-digit
+    // updates' 2^-45); l = a r
+    float2 r = make_float2(rsqrtf(a.x), 0.f);
+    {
+      const float2 ee = ff_sub(make_float2(1.f, 0.f), ff_mul(a, ff_mul(r, r)));
+      r = ff_sub(r, ff_mul(r, make_float2(-0.5f * ee.x, -0.5f * ee.y)));
+    }
+    __syncthreads();  // every thread has read the pivot
+    // column j of L below the pivot, row j of X
+    const int nl = kb - 1 - j;
+    if (tid < nl) {
+      const int i = j + 1 + tid;
+      Dg[tri(i) + j] = ff_mul(Dg[tri(i) + j], r);
+    } else if (tid - nl <= j) {
+      const int c = tid - nl;
+      X[tri(j) + c] = ff_mul(X[tri(j) + c], r);
+    } else if (tid == 127) {
+      Dg[tri(j) + j] = ff_mul(a, r);
+    }
+    __syncthreads();
+    // rank-1 update of rows j + 1 .. kb - 1: X columns c <= j, L columns c > j
+    const int e0 = tri(j + 1), e1 = tri(kb);
+    for (int e = e0 + tid; e < e1; e += TD_T) {
+      const int i = row_of[e], c = e - tri(i);
+      const bool inx = c <= j;
+      float2* base = inx ? X : Dg;
+      const float2 lij = Dg[tri(i) + j];
+      const float2 y = inx ? X[tri(j) + c] : Dg[tri(c) + j];
+      float2 v = base[e];
+      ff_fms(v.x, v.y, lij, y);
+      base[e] = ff_norm(v.x, v.y);
+    }
+    __syncthreads();
+  }
+  // X for the triangular solve (full 64 x 64, zero above the diagonal and past kb) and the
+  // operand's diagonal block, threads on consecutive addresses
+  constexpr bool TR = PREC == P_FP32T;
+  for (int e = tid; e < 64 * 64; e += TD_T) {
+    const int i = e >> 6, c = e & 63;
+    Xg[e] = (c <= i && i < kb) ? X[tri(i) + c] : make_float2(0.f, 0.f);
+  }
+  for (int e = tid; e < 64 * 64; e += TD_T) {
+    const int n = TR ? e & 63 : e >> 6, c = TR ? e >> 6 : e & 63;  // row n, column c of the block
+    const int64_t idx = fk::h_index<PREC>(p + n, p + c, Bp);
+    if (c <= n && n < kb) fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(X[tri(n) + c]));
+    else fk::WOut<PREC>::zero(w, plane, idx);
+  }
+}
+
+// ---- rows below the diagonal block ----------------------------------------------------------
+// One CTA per line: L_ik = A_ik X^T for the 64-row chunks below panel k's diagonal block
+// (float-float products with the inverse from the diagonal-block kernel), written to the
+// whitening operand and split into six base-256 digits with a per-row power of two.
+template <int PREC>
+__global__ void __launch_bounds__(TP_T, 3) tcf_trsm_kernel(double* __restrict__ sigma_all,
+                                                           uint8_t* __restrict__ slice_all, size_t slice_stride,
+                                                           int B, int k, const int32_t* __restrict__ status,
+                                                           int every, int q_off, void* __restrict__ wmat) {
   const int t = blockIdx.x;
   if (skip_line(status, t, every, q_off)) return;  // the same for the whole CTA
   extern __shared__ __align__(16) float2 psm[];
-  float2* Dg = psm;             // [64][DS] the diagonal block, then L_kk
-  float2* Iv = Dg + 64 * DS;    // [64][DS] L_kk^{-1}
-  float2* Ch = Dg;              // [64][DS] a chunk of 64 rows below: A_ik, then L_ik (L_kk is dead by then)
-  __shared__ float2 rdg[64];
-  __shared__ int notpd;
+  float2* Ch = psm;             // [64][DS] a chunk of 64 rows below: A_ik, then L_ik
+  float2* Iv = Ch + 64 * DS;    // [64][DS] X = L_kk^{-1}
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Bp = pad64(B), p = 64 * k, kb = min(64, B - p);
   float2* A = reinterpret_cast<float2*>(sigma_all + (int64_t)t * B * B);
   uint8_t* sl = slice_base(slice_all, slice_stride, t);
   int32_t* expo = reinterpret_cast<int32_t*>(sl + NDIG * plane_bytes(Bp));
+  const float2* Xg = reinterpret_cast<const float2*>(sl + xinv_offset(Bp));
   const int64_t plane = (int64_t)Bp * Bp;
   void* w = (char*)wmat + (size_t)t * plane * 4;
-
-  if (k == 0) {  // the means of the triangular-solve form and the unit score scale
-    for (int n = tid; n < Bp; n += TP_T) y0_all[(int64_t)t * Bp + n] = n < B ? (float)m_all[(int64_t)t * B + n] : 0.f;
-    if (tid == 0) inv_s2_all[t] = 1.0f;
-  }
-  if (tid == 0) notpd = 0;
-  for (int e = tid; e < 64 * 64; e += TP_T) {
-    const int r = e >> 6, c = e & 63;
-    Dg[r * DS + c] = (r < kb && c <= r) ? A[(int64_t)(p + r) * B + p + c] : make_float2(0.f, 0.f);
-    Iv[r * DS + c] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-
-  // ---- L_kk and X = L_kk^{-1}, in 16-column sub-panels ------------------------------------
-  // Per sub-panel at p0: one warp factors its 16 x 16 diagonal block and inverts it (X16),
-  // with warp-level syncs only (pivots by float-float Newton steps from FP32 seeds); then
-  // the whole CTA solves the rows below it, L[r][p0 + c] = sum_q A[r][p0 + q] X16[c][q],
-  // forms block row p0 of X from the running right-hand sides R (I at the start; Iv holds R,
-  // then X), and applies the rank-16 updates to the rest of the block (A) and of R.
-  __shared__ float2 X16[16][17];
-  for (int e = tid; e < 64; e += TP_T) Iv[e * DS + e] = make_float2(1.f, 0.f);
-  __syncthreads();
-  for (int p0 = 0; p0 < kb; p0 += 16) {
-    const int nb = min(16, kb - p0);
-    if (warp == 0) {
-      for (int e = lane; e < 256; e += 32) X16[e >> 4][e & 15] = make_float2((e >> 4) == (e & 15) ? 1.f : 0.f, 0.f);
-      __syncwarp();
-      for (int j = 0; j < nb; ++j) {
-        if (lane == 0) {
-          const float2 a = Dg[(p0 + j) * DS + p0 + j];
-          if (!(a.x > 0.f) || !isfinite(a.x)) {
-            notpd = 1;
-          } else {
-            // r = 1 / sqrt(a) from the FP32 seed by a Newton step r += r (1 - a r^2) / 2 in
-            // float-float; then l = a r (= sqrt(a)) and 1 / l = r
-            // (the seed's relative error, below 2^-22, squares to below 2^-44 in one step: the
-            // order of the six-digit updates' 2^-45)
-            float2 r = make_float2(rsqrtf(a.x), 0.f);
-            {
-              const float2 e = ff_sub(make_float2(1.f, 0.f), ff_mul(a, ff_mul(r, r)));
-              r = ff_sub(r, ff_mul(r, make_float2(-0.5f * e.x, -0.5f * e.y)));
-            }
-            Dg[(p0 + j) * DS + p0 + j] = ff_mul(a, r);
-            rdg[p0 + j] = r;
-          }
-        }
-        __syncwarp();
-        if (notpd) break;  // shared, the same for the whole warp
-        const float2 rj = rdg[p0 + j];
-        if (lane > j && lane < nb) Dg[(p0 + lane) * DS + p0 + j] = ff_mul(Dg[(p0 + lane) * DS + p0 + j], rj);
-        if (lane >= 16 && lane - 16 <= j) X16[j][lane - 16] = ff_mul(X16[j][lane - 16], rj);
-        __syncwarp();
-        for (int e = lane; e < 256; e += 32) {
-          const int r = e >> 4, c = e & 15;
-          if (r <= j || r >= nb) continue;
-          if (c > j && c <= r) {
-            float2 v = Dg[(p0 + r) * DS + p0 + c];
-            ff_fms(v.x, v.y, Dg[(p0 + r) * DS + p0 + j], Dg[(p0 + c) * DS + p0 + j]);
-            Dg[(p0 + r) * DS + p0 + c] = ff_norm(v.x, v.y);
-          } else if (c <= j) {
-            float2 v = X16[r][c];
-            ff_fms(v.x, v.y, Dg[(p0 + r) * DS + p0 + j], X16[j][c]);
-            X16[r][c] = ff_norm(v.x, v.y);
-          }
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (notpd) {
-      if (tid == 0) status[t] = LS_NOT_PD;
-      return;
-    }
-    // rows below the sub-panel (o < nbel * 16) and block row p0 of X for columns < p0
-    // (o >= nbel * 16), computed into registers, written after a barrier
-    const int nbel = kb - p0 - nb;
-    const int n_l = nbel * 16, n_x = 16 * p0;
-    float2 res[6];
-    int cnt = 0;
-    for (int o = tid; o < n_l + n_x; o += TP_T, ++cnt) {
-      float s = 0.f, cc = 0.f;
-      if (o < n_l) {
-        const int r = p0 + nb + (o >> 4), c = o & 15;
-        for (int q = 0; q <= c && q < nb; ++q) {
-          const float2 x = X16[c][q];
-          ff_fms(s, cc, Dg[r * DS + p0 + q], make_float2(-x.x, -x.y));  // s += A X16^T
-        }
-      } else {
-        const int f = o - n_l, r = f / p0, c = f % p0;  // X[p0 + r][c], c < p0
-        for (int q = 0; q <= r && q < nb; ++q) {
-          const float2 x = X16[r][q];
-          ff_fms(s, cc, Iv[(p0 + q) * DS + c], make_float2(-x.x, -x.y));  // s += X16 R
-        }
-      }
-      res[cnt] = ff_norm(s, cc);
-    }
-    __syncthreads();
-    cnt = 0;
-    for (int o = tid; o < n_l + n_x; o += TP_T, ++cnt) {
-      if (o < n_l) {
-        Dg[(p0 + nb + (o >> 4)) * DS + p0 + (o & 15)] = res[cnt];
-      } else {
-        const int f = o - n_l;
-        Iv[(p0 + f / p0) * DS + f % p0] = res[cnt];
-      }
-    }
-    for (int e = tid; e < 256; e += TP_T)  // the diagonal part of block row p0 of X
-      if ((e >> 4) < nb && (e & 15) < nb) Iv[(p0 + (e >> 4)) * DS + p0 + (e & 15)] = X16[e >> 4][e & 15];
-    __syncthreads();
-    // rank-nb updates: A[r][c] -= sum_q L[r][p0 + q] L[c][p0 + q] (p0 + nb <= c <= r < kb) and
-    // R[r][c] -= sum_q L[r][p0 + q] X[p0 + q][c] (r >= p0 + nb, c < p0 + nb)
-    const int nr = nbel * (p0 + nb);
-    for (int e = tid; e < 64 * nbel + nr; e += TP_T) {
-      if (e < 64 * nbel) {  // (r, c) on a 64-wide grid, the lower triangle only
-        const int r = e >> 6, c = e & 63;
-        if (c > r) continue;
-        const int ri = p0 + nb + r, ci = p0 + nb + c;
-        float2 v = Dg[ri * DS + ci];
-        for (int q = 0; q < nb; ++q) ff_fms(v.x, v.y, Dg[ri * DS + p0 + q], Dg[ci * DS + p0 + q]);
-        Dg[ri * DS + ci] = ff_norm(v.x, v.y);
-      } else {
-        const int f = e - 64 * nbel, ri = p0 + nb + f / (p0 + nb), c = f % (p0 + nb);
-        float2 v = Iv[ri * DS + c];
-        for (int q = 0; q < nb; ++q) ff_fms(v.x, v.y, Dg[ri * DS + p0 + q], Iv[(p0 + q) * DS + c]);
-        Iv[ri * DS + c] = ff_norm(v.x, v.y);
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---- whitening operand, block column k: zero above the diagonal block, L_kk^{-1} on it
   constexpr bool TR = PREC == P_FP32T;  // transposed operand: consecutive threads on consecutive rows n
-  for (int e = tid; e < 64 * 64; e += TP_T) {  // rows p .. p + 63 (those above stay zero from creation)
-    const int n = p + (TR ? e & 63 : e >> 6), c = TR ? e >> 6 : e & 63;
-    const int64_t idx = fk::h_index<PREC>(n, p + c, Bp);
-    if (c <= n - p && n - p < kb && c < kb)
-      fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Iv[(n - p) * DS + c]));
-    else
-      fk::WOut<PREC>::zero(w, plane, idx);
-  }
+  for (int e = tid; e < 64 * 64; e += TP_T) Iv[(e >> 6) * DS + (e & 63)] = Xg[e];
+  __syncthreads();
 
   // ---- rows below: L_ik = A_ik L_kk^{-T}, written to the operand and split into digits ----
   const int tr = tid >> 4, tcg = tid & 15;  // rows 4 tr .. 4 tr + 3, columns 4 tcg .. 4 tcg + 3
@@ -551,7 +515,10 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
 
 bool factor_tc_supported(int B, int prec) { return is_trsm(prec) && B >= 192; }
 
-int factor_tc_steps(int B) { return 2 * (pad64(B) / 64); }
+// Steps: 0 forms the covariance; then per panel k the diagonal block, and, for every panel
+// but the last, the rows below and the trailing update: 1 + 3 nb - 2 launches.
+int factor_tc_steps(int B) { return 3 * (pad64(B) / 64) - 1; }
+int factor_tc_step_kind(int step) { return step == 0 ? 0 : 1 + (step - 1) % 3; }
 
 cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, const double* m, int L, int B, int prec,
                                   void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
@@ -564,18 +531,20 @@ cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, cons
   if (slice_region_bytes(Bp) + 1024 > stride) return cudaErrorInvalidValue;
   uint8_t* slices = reinterpret_cast<uint8_t*>(scratch);
   cudaError_t e = cudaSuccess;
-  if (step == 0) {
+  const int kind = factor_tc_step_kind(step), k = (step - 1) / 3;
+  if (kind == 0) {
     tcf_form_kernel<<<dim3((B + 7) / 8, L), 256, 0, st>>>(sigma, m, B, status, n0, W, incl, n0_dev, every, q_off,
                                                            n_line);
-  } else if (step & 1) {
-    const int k = step / 2;
+  } else if (kind == 1) {
+    auto diag = prec == P_BF16T ? tcf_diag_kernel<P_BF16T> : tcf_diag_kernel<P_FP32T>;
+    diag<<<L, TD_T, 0, st>>>(sigma, slices, stride, m, B, k, status, every, q_off, wmat, y0, inv_s2);
+  } else if (kind == 2) {
     const size_t psmem = (size_t)2 * 64 * DS * sizeof(float2);
-    auto panel = prec == P_BF16T ? tcf_panel_kernel<P_BF16T> : tcf_panel_kernel<P_FP32T>;
-    e = cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    auto trsm = prec == P_BF16T ? tcf_trsm_kernel<P_BF16T> : tcf_trsm_kernel<P_FP32T>;
+    e = cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     if (e != cudaSuccess) return e;
-    panel<<<L, TP_T, psmem, st>>>(sigma, slices, stride, m, B, k, status, every, q_off, wmat, y0, inv_s2);
+    trsm<<<L, TP_T, psmem, st>>>(sigma, slices, stride, B, k, status, every, q_off, wmat);
   } else {
-    const int k = step / 2 - 1;
     const long long limit = 4000000000LL;  // ~2 s of clock cycles
     e = cudaFuncSetAttribute(tcf_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TU_SMEM);
     if (e != cudaSuccess) return e;

@@ -62,11 +62,14 @@ def test_kernel_rooflines_from_a_profile():
     wb = bench.kernel_rooflines(prof, 2, T, W, B, 1, "bf16", 1, peaks, 2070.0)["whiten_score"]
     assert wb["bound"] == "tensor" and wb["peak"] == 1849.2
     # the tensor-core factor's three classes: their algorithmic parts add up to the Cholesky
-    panel, upd = bench.factor_parts_per_line(B)
+    diag, trsm, upd = bench.factor_parts_per_line(B)
     blocks = [min(64, B - p) for p in range(0, B, 64)]
-    assert abs((upd + panel - sum(b ** 3 / 3 for b in blocks)) - B ** 3 / 3) < 1e-3
-    prof2 = {"factor_form": (8, 8.0), "factor_panel": (56, 40.0), "factor_update": (48, 30.0)}
+    assert abs((upd + diag + trsm - sum(b ** 3 / 3 for b in blocks)) - B ** 3 / 3) < 1e-3
+    prof2 = {"factor_form": (8, 8.0), "factor_diag": (56, 10.0), "factor_panel": (48, 30.0),
+             "factor_update": (48, 30.0)}
     r2 = bench.kernel_rooflines(prof2, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)
     assert r2["factor_update"]["bound"] == "tensor" and r2["factor_panel"]["bound"] == "alu"
+    assert abs(r2["factor_diag"]["achieved"] - 8000 * diag / 0.005 / 1e12) < 1e-9
+    assert abs(r2["factor_panel"]["achieved"] - 8000 * trsm / 0.015 / 1e12) < 1e-9
     assert abs(r2["factor_update"]["achieved"] - 8000 * upd / 0.015 / 1e12) < 1e-9
     assert abs(r2["factor_form"]["achieved"] - 8000 * B * (B + 1) / 2 * 16 / 0.004 / 1e9) < 1e-6
