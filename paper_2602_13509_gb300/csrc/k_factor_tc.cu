@@ -44,8 +44,6 @@ namespace hsad {
 
 namespace {
 
-constexpr int TP_T = 256;          // threads of the panel kernel
-constexpr int DS = 65;             // padded row stride (8-byte slots) of the 64 x 64 blocks in shared memory
 constexpr int NDIG = 6;            // base-256 digits per value
 constexpr int TU_M = 128, TU_N = 64, TU_K = 64;
 constexpr int TU_T = 160;          // 4 epilogue warps + 1 copy / MMA warp
@@ -58,9 +56,11 @@ constexpr uint32_t TU_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + TU_TILE +
 // Byte layout of one line's slice region (in the inverse scratch): NDIG planes of
 // (Bp + 64) rows x 128 bytes, then (Bp + 64) int32 exponents.
 __host__ __device__ inline size_t plane_bytes(int Bp) { return (size_t)(Bp + 64) * 128; }
-// the diagonal block's inverse X (float-float, [64][64]) follows the exponents
-__host__ __device__ inline size_t xinv_offset(int Bp) { return NDIG * plane_bytes(Bp) + (size_t)(Bp + 64) * 4; }
-__host__ __device__ inline size_t slice_region_bytes(int Bp) { return xinv_offset(Bp) + 64 * 64 * 8; }
+// then the digits of the diagonal block's inverse X (NDIG planes of [64][64] BF16, swizzled
+// like the panel rows) and X's 64 row exponents
+__host__ __device__ inline size_t xdig_offset(int Bp) { return NDIG * plane_bytes(Bp) + (size_t)(Bp + 64) * 4; }
+constexpr uint32_t XDIG_BYTES = NDIG * TU_B_PLANE + 64 * 4;
+__host__ __device__ inline size_t slice_region_bytes(int Bp) { return xdig_offset(Bp) + XDIG_BYTES; }
 constexpr int TD_T = 128;            // threads per line of the diagonal-block kernel
 constexpr int TRI64 = 64 * 65 / 2;   // a packed 64 x 64 lower triangle
 __host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
@@ -75,7 +75,6 @@ using fk::ff_fms;
 using fk::ff_mul;
 using fk::ff_norm;
 
-__device__ __forceinline__ double ffd(float2 v) { return (double)v.x + (double)v.y; }
 __device__ __forceinline__ float2 dff(double d) {
   const float h = __double2float_rn(d);
   return make_float2(h, __double2float_rn(d - (double)h));
@@ -86,6 +85,46 @@ __device__ __forceinline__ float2 ff_sub(float2 a, float2 b) {
   const float z = __fsub_rn(s, a.x);
   const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, z)), __fsub_rn(-b.x, z));
   return ff_norm(s, __fadd_rn(e, __fsub_rn(a.y, b.y)));
+}
+
+// The six signed base-256 digits of v * sc (|v * sc| < 1): v * sc = sum_d dg[d] 256^-(d+1)
+// up to 256^-6 / 2; every digit an integer of magnitude <= 256 (exact in BF16).
+__device__ __forceinline__ void split_digits(float2 v, float sc, float (&dg)[NDIG]) {
+  float xh = __fmul_rn(v.x, sc), xl = __fmul_rn(v.y, sc);  // exact: a power of two
+#pragma unroll
+  for (int d = 0; d < NDIG; ++d) {
+    xh = __fmul_rn(xh, 256.f);
+    xl = __fmul_rn(xl, 256.f);
+    dg[d] = rintf(xh);
+    const float2 rem = ff_norm(__fsub_rn(xh, dg[d]), xl);  // xh - dg is exact
+    xh = rem.x;
+    xl = rem.y;
+  }
+}
+// Exponent e with |v| <= mx < 2^e (0 for an all-zero row).
+__device__ __forceinline__ int row_exponent(float mx) {
+  int e = 0;
+  if (mx > 0.f) frexpf(mx, &e);
+  return e;
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+// 2^(-16) sum_l S_l 256^-l in float-float times 2^e: the digit levels (exact FP32 integers)
+// of one accumulator column combined.
+__device__ __forceinline__ float2 combine_levels(const float (&lev)[NDIG][16], int c, int e) {
+  float hs = lev[0][c], hc = 0.f;
+#pragma unroll
+  for (int l = 1; l < NDIG; ++l) {
+    const float p = __fmul_rn(lev[l][c], ldexpf(1.f, -8 * l));
+    const float s2 = __fadd_rn(hs, p);
+    const float z = __fsub_rn(s2, hs);
+    hc = __fadd_rn(hc, __fadd_rn(__fsub_rn(hs, __fsub_rn(s2, z)), __fsub_rn(p, z)));
+    hs = s2;
+  }
+  const float sc = ldexpf(1.f, e - 16);
+  return ff_norm(__fmul_rn(hs, sc), __fmul_rn(hc, sc));
 }
 
 __device__ __forceinline__ bool skip_line(const int32_t* status, int t, int every, int q_off) {
@@ -178,8 +217,8 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
 // seed, computed by every thread), column j of L = A_.j r, row j of X = R_j. r (R: the
 // running right-hand sides, I at the start), then the rank-1 updates A_ic -= L_ij L_cj
 // (j < c <= i) and R_ic -= L_ij X_jc (i > j, c <= j) over the flattened trapezoid of rows
-// j + 1 .. kb - 1. Writes X (float-float, [64][64]) to the line's slice region for the
-// triangular solve, and the whitening operand's diagonal block (L_kk^{-1}).
+// j + 1 .. kb - 1. Writes X's digits (per-row power of two, six base-256 digits) to the
+// line's slice region for the triangular solve, and the operand's diagonal block (L_kk^{-1}).
 template <int PREC>
 __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sigma_all,
                                                         uint8_t* __restrict__ slice_all, size_t slice_stride,
@@ -195,7 +234,8 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
   const int Bp = pad64(B), p = 64 * k, kb = min(64, B - p);
   const float2* A = reinterpret_cast<const float2*>(sigma_all + (int64_t)t * B * B);
   uint8_t* sl = slice_base(slice_all, slice_stride, t);
-  float2* Xg = reinterpret_cast<float2*>(sl + xinv_offset(Bp));
+  uint8_t* xd = sl + xdig_offset(Bp);
+  int32_t* xe = reinterpret_cast<int32_t*>(xd + NDIG * TU_B_PLANE);
   const int64_t plane = (int64_t)Bp * Bp;
   void* w = (char*)wmat + (size_t)t * plane * 4;
   if (k == 0) {  // the means of the triangular-solve form and the unit score scale
@@ -253,13 +293,39 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
     }
     __syncthreads();
   }
-  // X for the triangular solve (full 64 x 64, zero above the diagonal and past kb) and the
-  // operand's diagonal block, threads on consecutive addresses
+  // X for the triangular solve, where rows lie below: per row c an exponent and six digit
+  // planes of X[c][q] (zero above the diagonal), the B operand of the tensor-core solve
   constexpr bool TR = PREC == P_FP32T;
-  for (int e = tid; e < 64 * 64; e += TD_T) {
-    const int i = e >> 6, c = e & 63;
-    Xg[e] = (c <= i && i < kb) ? X[tri(i) + c] : make_float2(0.f, 0.f);
+  if (p + 64 < Bp) {
+    __shared__ int xe_s[64];
+    if (tid < 64) {
+      float mx = 0.f;
+      for (int q = 0; q <= tid && tid < kb; ++q) mx = fmaxf(mx, fabsf(X[tri(tid) + q].x));
+      const int e = row_exponent(mx);
+      xe_s[tid] = e;
+      xe[tid] = e;
+    }
+    __syncthreads();
+    for (int it = tid; it < 64 * 8; it += TD_T) {  // (row c, 8-column group g)
+      const int c = it >> 3, g = it & 7;
+      const float sc = ldexpf(1.f, -xe_s[c]);
+      uint32_t pk[NDIG][4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float d0[NDIG], d1[NDIG];
+        const int q0 = 8 * g + 2 * h;
+        split_digits((q0 <= c && c < kb) ? X[tri(c) + q0] : make_float2(0.f, 0.f), sc, d0);
+        split_digits((q0 + 1 <= c && c < kb) ? X[tri(c) + q0 + 1] : make_float2(0.f, 0.f), sc, d1);
+#pragma unroll
+        for (int d = 0; d < NDIG; ++d) pk[d][h] = pack_bf16x2(d0[d], d1[d]);
+      }
+#pragma unroll
+      for (int d = 0; d < NDIG; ++d)
+        *reinterpret_cast<uint4*>(xd + d * TU_B_PLANE + c * 128 + (((g ^ c) & 7) << 4)) =
+            make_uint4(pk[d][0], pk[d][1], pk[d][2], pk[d][3]);
+    }
   }
+  // the operand's diagonal block, threads on consecutive addresses
   for (int e = tid; e < 64 * 64; e += TD_T) {
     const int n = TR ? e & 63 : e >> 6, c = TR ? e >> 6 : e & 63;  // row n, column c of the block
     const int64_t idx = fk::h_index<PREC>(p + n, p + c, Bp);
@@ -268,100 +334,165 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
   }
 }
 
-// ---- rows below the diagonal block ----------------------------------------------------------
-// One CTA per line: L_ik = A_ik X^T for the 64-row chunks below panel k's diagonal block
-// (float-float products with the inverse from the diagonal-block kernel), written to the
-// whitening operand and split into six base-256 digits with a per-row power of two.
+// ---- rows below the diagonal block on the tensor cores -------------------------------------
+// L_ik = A_ik X^T for a 128-row tile of the rows below panel k's diagonal block (grid: row
+// tiles x lines; 4 epilogue warps + 1 copy / MMA warp, like the update): the tile's rows of A
+// (float-float) are split into six digits with a per-row power of two straight into the
+// swizzled A operand while X's digits arrive by one bulk copy; the 21 digit-product MMAs sum
+// each level exactly in TMEM (the update's bound: a 64-term level sum stays below 2^24); the
+// epilogue combines the levels per row (one row per thread), writes the row to the whitening
+// operand, and splits it again into six digits for the trailing updates.
+constexpr uint32_t TT_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + 256 + 128 * 4 + 64;
 template <int PREC>
-__global__ void __launch_bounds__(TP_T, 3) tcf_trsm_kernel(double* __restrict__ sigma_all,
+__global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ sigma_all,
                                                            uint8_t* __restrict__ slice_all, size_t slice_stride,
                                                            int B, int k, const int32_t* __restrict__ status,
-                                                           int every, int q_off, void* __restrict__ wmat) {
-  const int t = blockIdx.x;
-  if (skip_line(status, t, every, q_off)) return;  // the same for the whole CTA
-  extern __shared__ __align__(16) float2 psm[];
-  float2* Ch = psm;             // [64][DS] a chunk of 64 rows below: A_ik, then L_ik
-  float2* Iv = Ch + 64 * DS;    // [64][DS] X = L_kk^{-1}
+                                                           int every, int q_off, void* __restrict__ wmat,
+                                                           int32_t* __restrict__ err, long long limit) {
+  const int t = blockIdx.y;
+  const int Bp = pad64(B), p = 64 * k, i0 = p + 64 + TU_M * blockIdx.x;
+  if (i0 >= Bp || skip_line(status, t, every, q_off)) return;  // uniform for the CTA
+  extern __shared__ uint8_t tsm_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = sm;                          // NDIG planes of 128 x 64 BF16 (swizzled); later the L rows
+  uint8_t* sX = sm + NDIG * TU_A_PLANE;      // NDIG planes of 64 x 64 BF16, then X's 64 row exponents
+  const int* fx = (const int*)(sX + NDIG * TU_B_PLANE);
+  int* ea = (int*)(sX + XDIG_BYTES);         // exponents of the tile's rows of A
+  uint64_t* bars = (uint64_t*)(ea + 128);
+  uint32_t* tslot = (uint32_t*)(bars + 4);
+  const uint32_t full = tc::smem_u32(bars), done = full + 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int Bp = pad64(B), p = 64 * k, kb = min(64, B - p);
-  float2* A = reinterpret_cast<float2*>(sigma_all + (int64_t)t * B * B);
   uint8_t* sl = slice_base(slice_all, slice_stride, t);
   int32_t* expo = reinterpret_cast<int32_t*>(sl + NDIG * plane_bytes(Bp));
-  const float2* Xg = reinterpret_cast<const float2*>(sl + xinv_offset(Bp));
-  const int64_t plane = (int64_t)Bp * Bp;
-  void* w = (char*)wmat + (size_t)t * plane * 4;
-  constexpr bool TR = PREC == P_FP32T;  // transposed operand: consecutive threads on consecutive rows n
-  for (int e = tid; e < 64 * 64; e += TP_T) Iv[(e >> 6) * DS + (e & 63)] = Xg[e];
-  __syncthreads();
 
-  // ---- rows below: L_ik = A_ik L_kk^{-T}, written to the operand and split into digits ----
-  const int tr = tid >> 4, tcg = tid & 15;  // rows 4 tr .. 4 tr + 3, columns 4 tcg .. 4 tcg + 3
-  for (int c0 = p + 64; c0 < Bp; c0 += 64) {
-    for (int e = tid; e < 64 * 64; e += TP_T) {
-      const int r = e >> 6, c = e & 63;
-      Ch[r * DS + c] = (c0 + r < B && c < kb) ? A[(int64_t)(c0 + r) * B + p + c] : make_float2(0.f, 0.f);
+  if (tid == 0) {
+    tc::mbar_init(full, 1);
+    tc::mbar_init(done, 1);
+    tc::mbar_init_fence();
+  }
+  if (warp == 4) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const float2* A = reinterpret_cast<const float2*>(sigma_all + (int64_t)t * B * B);
+
+  if (warp == 4) {
+    if (lane == 0) {
+      tc::mbar_arrive_expect_tx(full, XDIG_BYTES);
+      tc::bulk_load(tc::smem_u32(sX), sl + xdig_offset(Bp), XDIG_BYTES, full);
     }
-    __syncthreads();
-    float s[4][4], cc[4][4];
+  } else {
+    // the A operand: rows of the tile split into digits (16 rows per round, lanes across the
+    // 64 columns: coalesced loads, conflict-free 2-byte stores within a swizzled row)
+    for (int rr = warp * 32; rr < warp * 32 + 32; rr += 16) {
+      float2 v[16][2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int q = 0; q < 16; ++q) {
+        const int i = i0 + rr + q;
 #pragma unroll
-      for (int b = 0; b < 4; ++b) s[a][b] = cc[a][b] = 0.f;
-    const int qmax = min(kb, 4 * tcg + 4);  // X[c][q] = 0 for q > c
-    for (int q = 0; q < qmax; ++q) {
-      float2 av[4], xv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        av[a] = Ch[(4 * tr + a) * DS + q];
-        const float2 x = Iv[(4 * tcg + a) * DS + q];  // X[c][q]: zero for q > c
-        xv[a] = make_float2(-x.x, -x.y);
+        for (int h = 0; h < 2; ++h)
+          v[q][h] = i < B ? A[(int64_t)i * B + p + lane + 32 * h] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int q = 0; q < 16; ++q) {
+        float mx = fmaxf(fabsf(v[q][0].x), fabsf(v[q][1].x));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int e = row_exponent(mx);
+        if (lane == 0) ea[rr + q] = e;
+        const float sc = ldexpf(1.f, -e);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) ff_fms(s[a][b], cc[a][b], av[a], xv[b]);  // s += A X^T
-    }
-    __syncthreads();  // every thread has read Ch
+        for (int h = 0; h < 2; ++h) {
+          float dg[NDIG];
+          split_digits(v[q][h], sc, dg);
+          const uint32_t off = tc::sw128_offset(rr + q, lane + 32 * h);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) Ch[(4 * tr + a) * DS + 4 * tcg + b] = ff_norm(s[a][b], cc[a][b]);
-    __syncthreads();
-    // the operand's rows c0 .. c0 + 63 of block column k
-    for (int e = tid; e < 64 * 64; e += TP_T) {
-      const int r = TR ? e & 63 : e >> 6, c = TR ? e >> 6 : e & 63;
-      const int64_t idx = fk::h_index<PREC>(c0 + r, p + c, Bp);
-      if (c0 + r < B && c < kb) fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Ch[r * DS + c]));
-      else fk::WOut<PREC>::zero(w, plane, idx);
-    }
-    // digits: one warp per row, two columns per lane
-    for (int r = warp; r < 64; r += TP_T / 32) {
-      const int row = c0 + r;
-      float2 v[2] = {Ch[r * DS + lane], Ch[r * DS + lane + 32]};
-      float mx = fmaxf(fabsf(v[0].x), fabsf(v[1].x));
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      int e = 0;
-      if (mx > 0.f) frexpf(mx, &e);  // |value| <= mx < 2^e
-      if (lane == 0) expo[row] = e;
-      const float sc = ldexpf(1.f, -e);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float xh = __fmul_rn(v[h].x, sc), xl = __fmul_rn(v[h].y, sc);  // exact: a power of two
-        const int col = lane + 32 * h;
-        const uint32_t off = tc::sw128_offset(row, col);
-#pragma unroll
-        for (int d = 0; d < NDIG; ++d) {
-          xh = __fmul_rn(xh, 256.f);
-          xl = __fmul_rn(xl, 256.f);
-          const float dg = rintf(xh);
-          const float2 rem = ff_norm(__fsub_rn(xh, dg), xl);  // xh - dg is exact
-          xh = rem.x;
-          xl = rem.y;
-          *(__nv_bfloat16*)(sl + d * plane_bytes(Bp) + off) = __float2bfloat16_rn(dg);  // |dg| <= 256: exact
+          for (int d = 0; d < NDIG; ++d) *(__nv_bfloat16*)(sA + d * TU_A_PLANE + off) = __float2bfloat16_rn(dg[d]);
         }
       }
     }
-    __syncthreads();  // before the next chunk overwrites Ch
+    tc::fence_proxy_async();  // the digits written by these threads, visible to the tensor cores
+  }
+  __syncthreads();
+  bool ok = true;
+  if (warp == 4) {
+    if (lane == 0) {
+      if (!tc::mbar_wait(full, 0, limit)) ok = false;
+      tc::fence_after_sync();
+      if (ok) {
+        const uint32_t idesc = tc::idesc_f16(1, TU_M, TU_N);
+        for (int l = 0; l < NDIG; ++l)
+          for (int dt = 0; dt <= l; ++dt) {
+            const uint32_t aop = tc::smem_u32(sA + dt * TU_A_PLANE), bop = tc::smem_u32(sX + (l - dt) * TU_B_PLANE);
+#pragma unroll
+            for (int ks = 0; ks < TU_K / 16; ++ks)
+              tc::mma_f16(tbase + (uint32_t)(64 * l), tc::desc_sw128(aop + ks * 32), tc::desc_sw128(bop + ks * 32),
+                          idesc, (dt > 0 || ks > 0) ? 1u : 0u);
+          }
+        tc::mma_commit(done);
+      } else {
+        tc::mbar_arrive(done);
+        atomicExch(err, 1);
+        tc::mbar_wait(full, 0, limit);  // a copy still in flight lands before the CTA may exit
+      }
+    }
+  } else {
+    const bool dok = tc::mbar_wait(done, 0, limit);
+    __syncwarp();
+    tc::fence_after_sync();
+    if (!dok) atomicExch(err, 1);
+    const int row = 32 * warp + lane, i = i0 + row;
+    const int ei = ea[row];
+    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    float2* Ls = reinterpret_cast<float2*>(sA) + row * TU_AS;  // this thread's row (the MMAs are done)
+    float mx = 0.f;
+    for (int c0 = 0; c0 < TU_N; c0 += 16) {
+      float lev[NDIG][16];
+#pragma unroll
+      for (int l = 0; l < NDIG; ++l) tc::tmem_ld16(taddr + (uint32_t)(64 * l + c0), lev[l]);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float2 v = (dok && i < B) ? combine_levels(lev, c, ei + fx[c0 + c]) : make_float2(0.f, 0.f);
+        Ls[c0 + c] = v;
+        mx = fmaxf(mx, fabsf(v.x));
+      }
+    }
+    if (dok && i < Bp) {
+      // the whitening operand's rows (zero past B)
+      const int64_t plane = (int64_t)Bp * Bp;
+      void* w = (char*)wmat + (size_t)t * plane * 4;
+      for (int c = 0; c < TU_N; ++c) {
+        const int64_t idx = fk::h_index<PREC>(i, p + c, Bp);
+        if (i < B) fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Ls[c]));
+        else fk::WOut<PREC>::zero(w, plane, idx);
+      }
+      // the row's digits for the trailing updates: 16-byte stores into the swizzled planes
+      const int e = row_exponent(mx);
+      expo[i] = e;
+      const float sc = ldexpf(1.f, -e);
+      for (int g = 0; g < 8; ++g) {
+        uint32_t pk[NDIG][4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          float d0[NDIG], d1[NDIG];
+          split_digits(Ls[8 * g + 2 * h], sc, d0);
+          split_digits(Ls[8 * g + 2 * h + 1], sc, d1);
+#pragma unroll
+          for (int d = 0; d < NDIG; ++d) pk[d][h] = pack_bf16x2(d0[d], d1[d]);
+        }
+#pragma unroll
+        for (int d = 0; d < NDIG; ++d)
+          *reinterpret_cast<uint4*>(sl + d * plane_bytes(Bp) + (size_t)i * 128 + (((g ^ i) & 7) << 4)) =
+              make_uint4(pk[d][0], pk[d][1], pk[d][2], pk[d][3]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 4) {
+    __syncwarp();
+    tc::tmem_dealloc(tbase, 512);
   }
 }
 
@@ -476,18 +607,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
         for (int c = 0; c < 16; ++c) {
           const int j = j0 + c0 + c;
           if (j <= i && j < B) {
-            // sum_l S_l 2^(-8 l) in float-float (each term an exact FP32 integer times a power of two)
-            float hs = lev[0][c], hc = 0.f;
-#pragma unroll
-            for (int l = 1; l < NDIG; ++l) {
-              const float p = __fmul_rn(lev[l][c], ldexpf(1.f, -8 * l));
-              const float s2 = __fadd_rn(hs, p);
-              const float z = __fsub_rn(s2, hs);
-              hc = __fadd_rn(hc, __fadd_rn(__fsub_rn(hs, __fsub_rn(s2, z)), __fsub_rn(p, z)));
-              hs = s2;
-            }
-            const float sc = ldexpf(1.f, ei + ej[c0 + c] - 16);
-            const float2 upd = ff_norm(__fmul_rn(hs, sc), __fmul_rn(hc, sc));
+            const float2 upd = combine_levels(lev, c, ei + ej[c0 + c]);
             As[row * TU_AS + c0 + c] = ff_sub(As[row * TU_AS + c0 + c], upd);
           }
         }
@@ -539,11 +659,12 @@ cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, cons
     auto diag = prec == P_BF16T ? tcf_diag_kernel<P_BF16T> : tcf_diag_kernel<P_FP32T>;
     diag<<<L, TD_T, 0, st>>>(sigma, slices, stride, m, B, k, status, every, q_off, wmat, y0, inv_s2);
   } else if (kind == 2) {
-    const size_t psmem = (size_t)2 * 64 * DS * sizeof(float2);
+    const long long limit = 4000000000LL;  // ~2 s of clock cycles
     auto trsm = prec == P_BF16T ? tcf_trsm_kernel<P_BF16T> : tcf_trsm_kernel<P_FP32T>;
-    e = cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    e = cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM);
     if (e != cudaSuccess) return e;
-    trsm<<<L, TP_T, psmem, st>>>(sigma, slices, stride, B, k, status, every, q_off, wmat);
+    const int tiles = (Bp - 64 * (k + 1) + TU_M - 1) / TU_M;
+    trsm<<<dim3(tiles, L), TU_T, TT_SMEM, st>>>(sigma, slices, stride, B, k, status, every, q_off, wmat, err, limit);
   } else {
     const long long limit = 4000000000LL;  // ~2 s of clock cycles
     e = cudaFuncSetAttribute(tcf_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TU_SMEM);
