@@ -197,7 +197,12 @@ def factor_parts_per_line(B):
     return diag, trsm, B ** 3 / 3.0 - chol_panel
 
 
-def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
+def whitening_label(form, tc):
+    """How the arm whitens: the form (Sec. 3.3) and the units its contraction runs on."""
+    return ("triangular solve" if form else "explicit inverse") + (", tensor cores" if tc else ", SIMT cores")
+
+
+def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, tc_whiten=None):
     """Roofline entries of the factor (whole, or its covariance, panel and update kernels),
     covariance (SYRK) and whitening kernels of one arm: algorithmic work per step (per-unit
     figures x units per step) over the kernel class's CUDA-event time per step, against the
@@ -255,7 +260,8 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
             flops = px_step * B * (B + 1)               # B(B+1)/2 multiply-adds per pixel
             byts = px_step * (2 * B + (5 if name == "whiten_score" else 0))
             ach = flops / (ms / 1e3) / 1e12
-            if name == "whiten_score" and prec == "fp32":
+            tcw = (prec != "fp32") if tc_whiten is None else tc_whiten
+            if name == "whiten_score" and not tcw:
                 pk, bound, src = fp32_peak_tflops(mhz), "alu", "derived: 152 SMs x %.0f MHz x 128 FFMA x 2" % mhz
             else:
                 pk, bound, src = peaks["bf16_tflops"], "tensor", f"{peaks['source']} bf16 burst"
@@ -263,6 +269,10 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz):
                  "traffic_algorithmic": byts, "kernel": name, "work_per_step": f"{px_step} px x B(B+1) flop",
                  "peak_source": src, "hbm_achieved_gbs": byts / (ms / 1e3) / 1e9,
                  "hbm_frac": byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+            if name == "whiten_score" and tcw:  # BF16 operand-term products per algorithmic one
+                terms = 6 if prec == "fp32" else 3
+                r["operand_terms"] = terms
+                r["issued_tflops"] = terms * ach
         r["traffic"] = None
         r["ms_per_step"] = ms
         r["launches_per_step"] = n / prof_steps
@@ -812,6 +822,7 @@ def main():
         pass) and the scores of the accuracy sample line. Leaves the detector open."""
         det = detector(prec, factor)
         form = det.whitening_form
+        tcw = det.whitening_tensor_cores
         if clocks:
             with ClockSampler(local) as clk:
                 ms, launches = timed(det)
@@ -827,13 +838,14 @@ def main():
         prof = det.profile_totals()
         det.profile(False)
         sample = s_dev[t_acc].cpu().numpy().copy(), m_dev[t_acc].cpu().numpy().copy()
-        return det, dict(value=weak_value(px_step, world, ms), ms=ms, launches=launches, form=form, prof=prof,
+        return det, dict(value=weak_value(px_step, world, ms), ms=ms, launches=launches, form=form, tc=tcw, prof=prof,
                          sample=sample, clocks=clk_summary)
 
     prof_steps = 2
     t_acc = T // 2   # the accuracy sample: scored by the oracle once, compared with every arm
     det, head = measure(args.precision, args.factor_precision, clocks=True)
     ms, launches, form, prof = head["ms"], head["launches"], head["form"], head["prof"]
+    tcw = head["tc"]
     value = head["value"]
     per_kernel = {k: {"launches_per_step": n / prof_steps, "ms_per_step": t / prof_steps}
                   for k, (n, t) in prof.items()}
@@ -919,7 +931,8 @@ def main():
             arms["fp32_fp64_factor"] = arm3
 
     mhz = peaks["sm_max_mhz"]
-    head_roofs = kernel_rooflines(prof, prof_steps, T, W, B, form, args.precision, args.factor_every, peaks, mhz)
+    head_roofs = kernel_rooflines(prof, prof_steps, T, W, B, form, args.precision, args.factor_every, peaks, mhz,
+                                  tcw)
     roof = dict(head_roofs[dom]) if dom in head_roofs else None
 
     cpu, ref_line = None, None
@@ -940,10 +953,10 @@ def main():
               for k, (n, t) in arm["prof"].items()}
         return {"value": arm["value"], "unit": "pixel-spectra/s", "ms_per_step": arm["ms"], "dtype": prec,
                 "gpu_launches": arm["launches"], "e2e": arm.get("e2e"),
-                "whitening": "triangular solve" if arm["form"] else "explicit inverse",
+                "whitening": whitening_label(arm["form"], arm["tc"]),
                 "accuracy_vs_oracle": accuracy(arm, prec), "kernels": pk,
                 "rooflines": kernel_rooflines(arm["prof"], prof_steps, T, W, B, arm["form"], prec,
-                                              args.factor_every, peaks, mhz)}
+                                              args.factor_every, peaks, mhz, arm["tc"])}
 
     out = {
         "metric": "pixel-spectra scored/s", "value": value, "unit": "pixel-spectra/s", "n_gpus": world,
@@ -951,7 +964,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "width": W, "bands": B, "lines": T, "stats": "exclusive",
                    "input": "uint16 12-bit DN", "batch_lines": wl["batch"],
-                   "whitening": "triangular solve" if form else "explicit inverse",
+                   "whitening": whitening_label(form, tcw),
                    "factor": "FP64" if args.factor_precision == "fp64" else "float-float",
                    **({"factor_every": args.factor_every} if args.factor_every > 1 else {}),
                    **({"line_gain": "per-line gains U[0.8, 1.25] (hsad_push_lines_gain)"} if args.line_gain else {}),

@@ -66,8 +66,10 @@ enum { HSAD_FACTOR_FF = 0, HSAD_FACTOR_FP64 = 1 };
  * HSAD_FORM_TRIANGULAR_SOLVE   streamed statistics (EXCLUSIVE, INCLUSIVE: a factorisation
  *                              per line): L y = x' - m solved blockwise from L and the
  *                              inverses of its 64 x 64 diagonal blocks only, half the
- *                              factor work; on the tensor cores for BF16 (uint16 input), on
- *                              the SIMT cores for FP32. */
+ *                              factor work; on the tensor cores for uint16 input (BF16:
+ *                              two-term operands; FP32 with the float-float factor and
+ *                              B >= 192: three-term operands, FP32-accurate products), else
+ *                              on the SIMT cores (FP32). */
 enum { HSAD_FORM_INVERSE = 0, HSAD_FORM_TRIANGULAR_SOLVE = 1 };
 /* statistics window (which pixels form mu and Sigma for a scored line t) */
 enum {
@@ -297,6 +299,10 @@ int hsad_profile_reset(hsad_ctx* ctx);
 
 /* The context's whitening form (HSAD_FORM_*), or HSAD_E_INVALID for a null context. */
 int hsad_whitening_form(const hsad_ctx* ctx);
+/* 1 if the context's whitening contraction runs on the tensor cores (tcgen05), 0 if on the
+ * SIMT cores (FFMA), HSAD_E_INVALID for a null context. An implementation query with no
+ * counterpart in the method (Sec. 3.3 fixes what is computed, not on which units). */
+int hsad_whitening_tensor_cores(const hsad_ctx* ctx);
 
 /* Bytes of device memory the context holds. */
 int64_t hsad_device_bytes(const hsad_ctx* ctx);

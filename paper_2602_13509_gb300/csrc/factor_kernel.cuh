@@ -93,6 +93,26 @@ template <>
 struct WOut<P_BF16T> : WOut<P_BF16> {};
 template <>
 struct WOut<P_FP32T> : WOut<P_FP32> {};
+// three BF16 planes hi / mid / lo: an exact split of the FP32 value (each remainder is exact
+// in FP32 and holds at most 16, then 8, significant bits)
+template <>
+struct WOut<P_FP32X> {
+  __device__ static float store(void* w, int64_t plane, int64_t idx, float f) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const float r = f - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r);
+    ((__nv_bfloat16*)w)[idx] = hi;
+    ((__nv_bfloat16*)w)[plane + idx] = mid;
+    ((__nv_bfloat16*)w)[2 * plane + idx] = __float2bfloat16_rn(r - __bfloat162float(mid));
+    return f;
+  }
+  __device__ static void zero(void* w, int64_t plane, int64_t idx) {
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    ((__nv_bfloat16*)w)[idx] = z;
+    ((__nv_bfloat16*)w)[plane + idx] = z;
+    ((__nv_bfloat16*)w)[2 * plane + idx] = z;
+  }
+};
 
 // Element (n, k) of the triangular-solve operand H: row n = output band (n-major) for the
 // tensor-core form, whose TMA boxes are K-major rows; column k major (transposed) for the

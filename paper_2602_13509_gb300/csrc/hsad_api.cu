@@ -282,7 +282,7 @@ int64_t plan_bytes(const hsad_ctx* c) {
   b += Ls * B * 8 * 2;                                           // s1_line, m_line
   if (c->lam != 1.0) b += Ls * 8;                                // forgetting weights per line
   b += Lf * B * B * 8 * 2;                                       // sigma, inv
-  b += Lf * Bp * Bp * 4 + Lf * Bp * 4 + Lf * 4 + Ls * 4;        // wmat, y0, inv_s2, status
+  b += Lf * Bp * Bp * wmat_elem_bytes(c->prec) + Lf * Bp * 4 + Lf * 4 + Ls * 4;  // wmat, y0, inv_s2, status
   if (c->prec == P_FP32T) b += (int64_t)whiten_trsm_simt_scratch_bytes(c->B);  // FP32 solve scratch
   b += c->ring * c->W * 5 + c->ring * 4 + 64;                    // result ring
   b += c->ring * c->W * 2 + 64;                                  // transmit codes scratch
@@ -454,8 +454,9 @@ int hsad_autotune_factor(int32_t device, int32_t bands, int32_t precision, int32
     return ndev <= 0 ? HSAD_E_CUDA : HSAD_E_INVALID;
   }
   DeviceGuard dg(device);
-  // the form of a streamed uint16-input context (the case with a factorisation per line)
-  const int prec = precision == HSAD_FP32 ? fp32_form(false, false)
+  // the factor kernel's form for a streamed uint16-input context (the case with a
+  // factorisation per line; the tensor-core factor has no tuned shape)
+  const int prec = precision == HSAD_FP32 ? fp32_form(bands, IN_U16, false, false, false)
                    : precision == HSAD_BF16 ? bf16_form(bands, IN_U16, false, false)
                                             : P_FP16;
   factor_prepare(bands, prec);
@@ -527,7 +528,8 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->in_type = cfg->in_dtype == HSAD_U16 ? IN_U16 : IN_F32;
   const bool cube = cfg->stats_mode == HSAD_CUBE;
   const bool force_inverse = (cfg->flags & HSAD_FORCE_INVERSE) != 0;
-  ctx->prec = cfg->precision == HSAD_FP32 ? fp32_form(cube, force_inverse)
+  ctx->prec = cfg->precision == HSAD_FP32
+                  ? fp32_form(ctx->B, ctx->in_type, cube, force_inverse, cfg->factor_precision == HSAD_FACTOR_FF)
               : cfg->precision == HSAD_BF16 ? bf16_form(ctx->B, ctx->in_type, cube, force_inverse)
                                             : P_FP16;
   ctx->fprec = ctx->prec | (cfg->factor_precision == HSAD_FACTOR_FP64 ? kFactorF64 : 0);
@@ -609,7 +611,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->m_line = (double*)dalloc(ctx, Ls * B * 8, &ok);
   ctx->sigma = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
   ctx->inv = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
-  ctx->wmat = dalloc(ctx, Lf * Bp * Bp * 4, &ok);
+  ctx->wmat = dalloc(ctx, Lf * Bp * Bp * wmat_elem_bytes(ctx->prec), &ok);
   if (ctx->prec == P_FP32T) ctx->yscratch = (float*)dalloc(ctx, (int64_t)whiten_trsm_simt_scratch_bytes(B), &ok);
   ctx->y0 = (float*)dalloc(ctx, Lf * Bp * 4, &ok);
   ctx->inv_s2 = (float*)dalloc(ctx, Lf * 4, &ok);
@@ -660,7 +662,8 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   // affine map): validated above, not needed on the device
   // the tensor-core factor writes only the lower part of the whitening operand and never the
   // zero padding rows of its digit planes: both start (and stay) zero
-  if (ctx->tc_factor && (cudaMemsetAsync(ctx->wmat, 0, (size_t)Lf * Bp * Bp * 4, ctx->stream) != cudaSuccess ||
+  if (ctx->tc_factor && (cudaMemsetAsync(ctx->wmat, 0, (size_t)Lf * Bp * Bp * wmat_elem_bytes(ctx->prec),
+                                         ctx->stream) != cudaSuccess ||
                          cudaMemsetAsync(ctx->inv, 0, (size_t)Lf * B * B * 8, ctx->stream) != cudaSuccess)) {
     cudaGetLastError();
     release(ctx);
@@ -675,10 +678,11 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
     release(ctx);
     return fail(nullptr, HSAD_E_CUDA, "device initialisation failed");
   }
-  if (ctx->prec == P_BF16 || ctx->prec == P_FP16 || ctx->prec == P_BF16T) {
-    // G planes [Lf][2][Bp][Bp] 16-bit as a 2-D tensor of Lf*2*Bp rows, 64 x 64 boxes
-    const int64_t rows = Lf * 2 * Bp;
-    if (!encode_gmap(&ctx->gmap, ctx->wmat, Bp, rows, ctx->prec == P_BF16T ? 64 : 128)) {
+  if (ctx->prec == P_BF16 || ctx->prec == P_FP16 || ctx->prec == P_BF16T || ctx->prec == P_FP32X) {
+    // G (H) planes [Lf][2 or 3][Bp][Bp] 16-bit as a 2-D tensor of Lf*planes*Bp rows, 64 x 64
+    // boxes (the inverse form: 128-row boxes)
+    const int64_t rows = Lf * (ctx->prec == P_FP32X ? 3 : 2) * Bp;
+    if (!encode_gmap(&ctx->gmap, ctx->wmat, Bp, rows, trsm_planes(ctx->prec) ? 64 : 128)) {
       release(ctx);
       return fail(nullptr, HSAD_E_CUDA, "cuTensorMapEncodeTiled failed for the whitening operand");
     }
@@ -729,15 +733,16 @@ int add_record(hsad_ctx* ctx, uint64_t first, uint64_t n) {
 int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o, int gain_off = 0) {
   cudaStream_t st = ctx->stream;
   if (ctx->batch_gain) {
-    if (ctx->prec != P_BF16T && ctx->prec != P_FP32T) return fail(ctx, HSAD_E_INVALID, "gains need the triangular-solve form");
+    if (!is_trsm(ctx->prec)) return fail(ctx, HSAD_E_INVALID, "gains need the triangular-solve form");
     KL("gain_mean", launch_gain_mean(ctx->d_gain_cur + (size_t)kGainStride * gain_off, L, ctx->B, ctx->y0, ctx->c_int, factor_stride, o,
                                      ctx->d_mgain, ctx->d_gscale, st, &ctx->lc));
     o.m_line = ctx->d_mgain;
     o.line_scale = ctx->d_gscale;
   }
-  if (ctx->prec == P_BF16T) {
-    KL("whiten_score", launch_whiten_trsm((const uint16_t*)x, L, ctx->W, ctx->B, ctx->c_int, &ctx->gmap, ctx->y0,
-                                          ctx->inv_s2, ctx->status, factor_stride, o, ctx->dev_err, st, &ctx->lc));
+  if (trsm_planes(ctx->prec)) {
+    KL("whiten_score", launch_whiten_trsm((const uint16_t*)x, L, ctx->W, ctx->B, ctx->prec, ctx->c_int, &ctx->gmap,
+                                          ctx->y0, ctx->inv_s2, ctx->status, factor_stride, o, ctx->dev_err, st,
+                                          &ctx->lc));
   } else if (ctx->prec == P_FP32T) {
     KL("whiten_score", launch_whiten_trsm_simt(x, L, ctx->W, ctx->B, ctx->in_type, ctx->c_int, ctx->c_flt,
                                                (const float*)ctx->wmat, ctx->y0, ctx->inv_s2, ctx->status,
@@ -822,7 +827,7 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
                                      ctx->c_int, W, ctx->lam));
   {
     const int rc_f = factor_lines(ctx, ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L,
-                                    (char*)ctx->wmat + (size_t)Bp * Bp * 4, ctx->y0 + Bp, ctx->inv_s2 + 1, ctx->status + 1,
+                                    (char*)ctx->wmat + (size_t)Bp * Bp * wmat_elem_bytes(ctx->prec), ctx->y0 + Bp, ctx->inv_s2 + 1, ctx->status + 1,
                                     ctx->n_stats, W, 1, n0_dev, ctx->every, q0 + 1, n_line);
     if (rc_f != HSAD_OK) return rc_f;
   }
@@ -840,7 +845,7 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   // the batch holds none)
   const int c = L - (q0 + L) % ctx->every;
   if (c > 0) {
-    const size_t wb = (size_t)Bp * Bp * 4;
+    const size_t wb = (size_t)Bp * Bp * wmat_elem_bytes(ctx->prec);
     CK(cudaMemcpyAsync(ctx->wmat, (char*)ctx->wmat + (size_t)c * wb, wb, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ctx->y0, ctx->y0 + (size_t)c * Bp, (size_t)Bp * 4, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ctx->inv_s2, ctx->inv_s2 + c, 4, cudaMemcpyDeviceToDevice, st));
@@ -1032,7 +1037,7 @@ int hsad_push_lines_gain(hsad_ctx* ctx, const void* lines, const float* line_gai
   if (n_lines > 0 && !line_gain) return fail(ctx, HSAD_E_INVALID, "line_gain is NULL");
   if (ctx->mode == HSAD_CUBE) return fail(ctx, HSAD_E_INVALID, "per-line gains need streamed statistics");
   if (ctx->in_type != IN_U16) return fail(ctx, HSAD_E_INVALID, "per-line gains need uint16 input");
-  if (ctx->prec != P_BF16T && ctx->prec != P_FP32T)
+  if (!is_trsm(ctx->prec))
     return fail(ctx, HSAD_E_INVALID, "per-line gains need the triangular-solve whitening form (FP32 or BF16)");
   for (int64_t i = 0; i < n_lines; ++i) {
     const float g = line_gain[i];
@@ -1597,6 +1602,11 @@ int64_t hsad_device_bytes(const hsad_ctx* ctx) { return ctx ? ctx->dev_bytes : 0
 int hsad_whitening_form(const hsad_ctx* ctx) {
   if (!ctx) return HSAD_E_INVALID;
   return is_trsm(ctx->prec) ? HSAD_FORM_TRIANGULAR_SOLVE : HSAD_FORM_INVERSE;
+}
+
+int hsad_whitening_tensor_cores(const hsad_ctx* ctx) {
+  if (!ctx) return HSAD_E_INVALID;
+  return ctx->prec == P_FP32 || ctx->prec == P_FP32T ? 0 : 1;
 }
 
 int hsad_destroy(hsad_ctx* ctx) {

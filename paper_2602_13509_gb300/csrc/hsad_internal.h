@@ -26,8 +26,17 @@ enum Prec : int32_t { P_FP32 = 0, P_BF16 = 1, P_FP16 = 2,
                       // factor output for the triangular-solve whitening: L's off-diagonal
                       // 64 x 64 blocks and the inverses of its diagonal blocks, as BF16 hi / lo
                       // planes (tensor cores) or FP32 (SIMT)
-                      P_BF16T = 3, P_FP32T = 4 };
-__host__ __device__ constexpr bool is_trsm(int prec) { return prec == P_BF16T || prec == P_FP32T; }
+                      P_BF16T = 3, P_FP32T = 4,
+                      // the same operand as BF16 hi / mid / lo planes: the FP32 value split
+                      // into three BF16 terms for an FP32-accurate tensor-core solve
+                      P_FP32X = 5 };
+__host__ __device__ constexpr bool is_trsm(int prec) {
+  return prec == P_BF16T || prec == P_FP32T || prec == P_FP32X;
+}
+// BF16 planes of the tensor-core triangular-solve operand (0: not that form).
+__host__ __device__ constexpr int trsm_planes(int prec) { return prec == P_BF16T ? 2 : prec == P_FP32X ? 3 : 0; }
+// Bytes per element of one factor slot's whitening operand (Bp x Bp elements).
+__host__ __device__ constexpr int wmat_elem_bytes(int prec) { return prec == P_FP32X ? 6 : 4; }
 
 __host__ __device__ inline int pad64(int b) { return (b + 63) / 64 * 64; }
 
@@ -228,12 +237,13 @@ cudaError_t launch_whiten_tc(const void* x, int L, int W, int B, int in_type, co
                              const float* inv_s2, const int32_t* status, int factor_stride, ScoreOut out,
                              int32_t* err, cudaStream_t st, LaunchCounter* lc);
 
-// K6, triangular-solve form (P_BF16T factors, uint16 input): delta = ||L^{-1} (x' - m)||^2 by
-// blocked forward substitution on the tensor cores; hmap is the CUtensorMap over the BF16
-// hi / lo planes of H with 64 x 64 boxes, m the FP32 means (the y0 rows of the factor).
-cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, const int32_t* c_int, const void* hmap,
-                               const float* m, const float* inv_s2, const int32_t* status, int factor_stride,
-                               ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc);
+// K6, triangular-solve form (P_BF16T or P_FP32X factors, uint16 input): delta =
+// ||L^{-1} (x' - m)||^2 by blocked forward substitution on the tensor cores; hmap is the
+// CUtensorMap over the BF16 planes of H (trsm_planes(prec) of them) with 64 x 64 boxes, m the
+// FP32 means (the y0 rows of the factor).
+cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, int prec, const int32_t* c_int,
+                               const void* hmap, const float* m, const float* inv_s2, const int32_t* status,
+                               int factor_stride, ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc);
 // K6, triangular-solve form on the SIMT cores (P_FP32T factors): the same blocked forward
 // substitution in FP32 with H in FP32 (stored transposed, see h_index), 128 pixels per
 // item of a persistent grid; yscratch: whiten_trsm_simt_scratch_bytes(B) of device memory
@@ -243,18 +253,21 @@ cudaError_t launch_whiten_trsm_simt(const void* x, int L, int W, int B, int in_t
                                     const int32_t* status, int factor_stride, ScoreOut out, float* yscratch,
                                     cudaStream_t st, LaunchCounter* lc);
 size_t whiten_trsm_simt_scratch_bytes(int B);
-// Ring depth the triangular-solve whitening runs with for B bands; 0 if it does not fit.
-int whiten_trsm_stages(int B);
+// Ring depth the triangular-solve whitening runs with for B bands and an operand of
+// `planes` BF16 planes; 0 if it does not fit.
+int whiten_trsm_stages(int B, int planes);
 // Working form of a context. The triangular solve halves the factor work but its
 // whitening is a chain of dependent block steps: it pays where a factorisation per line
 // dominates (streamed statistics), not in CUBE mode (one factorisation per cube, the
 // whitening dominates), which keeps the explicit inverse.
 // BF16: P_BF16T for uint16 input, else P_BF16.
-// FP32: P_FP32T (triangular solve on the SIMT cores), else P_FP32.
+// FP32: P_FP32X (triangular solve on the tensor cores with three-term BF16 operands) for
+// uint16 input where the tensor-core factor runs (tc_factor), else P_FP32T (triangular
+// solve on the SIMT cores), else P_FP32.
 // force_inverse (the HSAD_FORCE_INVERSE configuration flag) keeps the explicit inverse
 // everywhere (comparisons).
 int bf16_form(int B, int in_type, bool cube, bool force_inverse);
-int fp32_form(bool cube, bool force_inverse);
+int fp32_form(int B, int in_type, bool cube, bool force_inverse, bool tc_factor);
 
 // K7: cube maximum of delta over n_lines ring lines, then optional normalisation and
 // the REL / ABS mask.

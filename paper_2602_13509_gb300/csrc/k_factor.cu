@@ -133,6 +133,7 @@ cudaError_t launch_factor_shape(int cl, int ft, double* sigma, double* scratch, 
                                 int W, int incl, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev,
                                 int every, int q_off, const double* n_line) {
   if (L <= 0) return cudaSuccess;
+  if ((fprec & 0xff) > P_FP32T) return cudaErrorInvalidValue;  // the three-plane form: tensor-core factor only
   const FactorArgs a{sigma, scratch, m, L, B, wmat, y0, inv_s2, status, n0, W, incl, st, n0_dev, every, q_off,
                      n_line};
   const cudaError_t e = instance(fprec).launch(cl, ft, a);

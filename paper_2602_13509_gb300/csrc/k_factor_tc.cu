@@ -127,6 +127,28 @@ __device__ __forceinline__ float2 combine_levels(const float (&lev)[NDIG][16], i
   return ff_norm(__fmul_rn(hs, sc), __fmul_rn(hc, sc));
 }
 
+// Eight consecutive operand values as NP BF16 planes (hi / lo, or hi / mid / lo: each the
+// BF16 rounding of the FP32 remainder of the ones before), one 16-byte store per plane.
+template <int NP>
+__device__ __forceinline__ void store_planes8(__nv_bfloat16* w, int64_t plane, int64_t idx, const float (&f)[8]) {
+  uint32_t pk[NP][4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(f[2 * h], f[2 * h + 1]);
+    const float r0 = f[2 * h] - __low2float(hi), r1 = f[2 * h + 1] - __high2float(hi);
+    const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+    pk[0][h] = *reinterpret_cast<const uint32_t*>(&hi);
+    pk[1][h] = *reinterpret_cast<const uint32_t*>(&m);
+    if constexpr (NP == 3) {
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(r0 - __low2float(m), r1 - __high2float(m));
+      pk[2][h] = *reinterpret_cast<const uint32_t*>(&lo);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+    *reinterpret_cast<uint4*>(w + q * plane + idx) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+}
+
 __device__ __forceinline__ bool skip_line(const int32_t* status, int t, int every, int q_off) {
   return status[t] != LS_OK || (every > 1 && (q_off + t) % every != 0);
 }
@@ -237,7 +259,7 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
   uint8_t* xd = sl + xdig_offset(Bp);
   int32_t* xe = reinterpret_cast<int32_t*>(xd + NDIG * TU_B_PLANE);
   const int64_t plane = (int64_t)Bp * Bp;
-  void* w = (char*)wmat + (size_t)t * plane * 4;
+  void* w = (char*)wmat + (size_t)t * plane * wmat_elem_bytes(PREC);
   if (k == 0) {  // the means of the triangular-solve form and the unit score scale
     for (int n = tid; n < Bp; n += TD_T) y0_all[(int64_t)t * Bp + n] = n < B ? (float)m_all[(int64_t)t * B + n] : 0.f;
     if (tid == 0) inv_s2_all[t] = 1.0f;
@@ -460,11 +482,18 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
     if (dok && i < Bp) {
       // the whitening operand's rows (zero past B)
       const int64_t plane = (int64_t)Bp * Bp;
-      void* w = (char*)wmat + (size_t)t * plane * 4;
-      for (int c = 0; c < TU_N; ++c) {
-        const int64_t idx = fk::h_index<PREC>(i, p + c, Bp);
-        if (i < B) fk::WOut<PREC>::store(w, plane, idx, fk::ArFF::to_f(Ls[c]));
-        else fk::WOut<PREC>::zero(w, plane, idx);
+      void* w = (char*)wmat + (size_t)t * plane * wmat_elem_bytes(PREC);
+      if constexpr (PREC == P_FP32T) {  // transposed: consecutive threads on consecutive rows
+        for (int c = 0; c < TU_N; ++c)
+          fk::WOut<PREC>::store(w, plane, fk::h_index<PREC>(i, p + c, Bp), fk::ArFF::to_f(Ls[c]));
+      } else {  // BF16 planes, row-major: this thread's row in 16-byte pieces
+        __nv_bfloat16* wb = (__nv_bfloat16*)w;
+        for (int g = 0; g < 8; ++g) {
+          float f[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) f[j] = fk::ArFF::to_f(Ls[8 * g + j]);
+          store_planes8<trsm_planes(PREC)>(wb, plane, fk::h_index<PREC>(i, p + 8 * g, Bp), f);
+        }
       }
       // the row's digits for the trailing updates: 16-byte stores into the swizzled planes
       const int e = row_exponent(mx);
@@ -656,11 +685,15 @@ cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, cons
     tcf_form_kernel<<<dim3((B + 7) / 8, L), 256, 0, st>>>(sigma, m, B, status, n0, W, incl, n0_dev, every, q_off,
                                                            n_line);
   } else if (kind == 1) {
-    auto diag = prec == P_BF16T ? tcf_diag_kernel<P_BF16T> : tcf_diag_kernel<P_FP32T>;
+    auto diag = prec == P_BF16T   ? tcf_diag_kernel<P_BF16T>
+                : prec == P_FP32X ? tcf_diag_kernel<P_FP32X>
+                                  : tcf_diag_kernel<P_FP32T>;
     diag<<<L, TD_T, 0, st>>>(sigma, slices, stride, m, B, k, status, every, q_off, wmat, y0, inv_s2);
   } else if (kind == 2) {
     const long long limit = 4000000000LL;  // ~2 s of clock cycles
-    auto trsm = prec == P_BF16T ? tcf_trsm_kernel<P_BF16T> : tcf_trsm_kernel<P_FP32T>;
+    auto trsm = prec == P_BF16T   ? tcf_trsm_kernel<P_BF16T>
+                : prec == P_FP32X ? tcf_trsm_kernel<P_FP32X>
+                                  : tcf_trsm_kernel<P_FP32T>;
     e = cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM);
     if (e != cudaSuccess) return e;
     const int tiles = (Bp - 64 * (k + 1) + TU_M - 1) / TU_M;

@@ -14,16 +14,20 @@
 // One CTA scores 128 pixels of one line; tensor memory holds a 128 x Bp FP32 matrix whose
 // 64-column block k holds first the accumulated sum for z_k and then y_k.
 //   warps 0-3          one pixel (TMEM lane) each: z_k = v_k - acc_k in FP32, split into
-//                      BF16 hi + lo and written as the A operand; y_k read back, its square
-//                      summed into the score, split and written as the A operand of the
-//                      updates. v = x' - m in FP32; the pixel's raw values of block k + 1
+//                      NT BF16 terms (hi + lo, or hi + mid + lo) and written as the A
+//                      operand; y_k read back, its square summed into the score, split and
+//                      written as the A operand of the updates. v = x' - m in FP32; the pixel's raw values of block k + 1
 //                      are loaded into registers while block k is solved.
-//   warp 4 (one lane)  TMA: the 64 x 64 blocks (j, k), j >= k, of the hi and lo planes of
-//                      H in the order the MMAs use them, through a ring of up to 10 stages
+//   warp 4 (one lane)  TMA: the 64 x 64 blocks (j, k), j >= k, of the NT planes of H in
+//                      the order the MMAs use them, through a ring of up to 10 stages
 //                      (the whole solve streams ~(Bp/64)^2/2 blocks of 16 KB per CTA from
 //                      L2, so the ring depth sets how much of that latency is hidden).
-//   warp 5 (one lane)  tcgen05.mma (M = 128, N = 64, K = 16), three products per block:
-//                      a_hi h_hi + a_hi h_lo + a_lo h_hi, FP32 accumulation in TMEM.
+//   warp 5 (one lane)  tcgen05.mma (M = 128, N = 64, K = 16), FP32 accumulation in TMEM;
+//                      NT = 2 (BF16 working precision): a0 h0 + a0 h1 + a1 h0, the terms
+//                      above 2^-16 of the product; NT = 3 (FP32 working precision, both
+//                      operands exact three-term splits of their FP32 values): the six terms
+//                      a_t h_u with t + u <= 2, dropping those of order 2^-24 and below, the
+//                      rounding of an FP32 product.
 // Every wait is bounded; a timeout sets *err and the CTA drains its copies and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -43,7 +47,6 @@ namespace {
 constexpr int TS_M = 128, TS_KB = 64, TS_THREADS = 192, TS_MAX_STAGES = 10;
 constexpr uint32_t TS_BLK = TS_M * TS_KB * 2;  // one 128 x 64 16-bit operand block: 16 KB
 constexpr uint32_t TS_HALF = 64 * TS_KB * 2;   // one 64 x 64 16-bit block of H: 8 KB
-constexpr uint32_t TS_STAGE = 2 * TS_HALF;     // hi + lo planes of one block of H
 constexpr uint32_t TS_BAR = 256;
 constexpr uint32_t TS_SMEM_MAX = 227 * 1024;
 
@@ -52,10 +55,10 @@ __host__ __device__ inline uint32_t ts_cols(int Bp) {
   while (c < (uint32_t)Bp) c <<= 1;
   return c;
 }
-// shared memory after 1024-byte alignment: Z (hi, lo), Y (hi, lo), ring, {c, m} per band,
-// barriers
-__host__ __device__ inline uint32_t ts_smem(int Bp, int stages) {
-  return 1024 + 4 * TS_BLK + (uint32_t)stages * TS_STAGE + (uint32_t)Bp * 8 + TS_BAR;
+// shared memory after 1024-byte alignment: Z (nt planes), Y (nt planes), ring of stages of
+// nt 64 x 64 blocks of H, {c, m} per band, barriers
+__host__ __device__ inline uint32_t ts_smem(int Bp, int stages, int nt) {
+  return 1024 + 2 * nt * TS_BLK + (uint32_t)stages * nt * TS_HALF + (uint32_t)Bp * 8 + TS_BAR;
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) { return *(const uint32_t*)&v; }
@@ -67,8 +70,46 @@ __device__ __forceinline__ void split2(float z0, float z1, uint32_t& hi, uint32_
   hi = bf16x2_bits(h);
   lo = bf16x2_bits(__floats2bfloat162_rn(z0 - h0, z1 - h1));
 }
+// hi = bf16(z), mid = bf16(z - hi), lo = bf16(z - hi - mid): an exact split of an FP32 value
+// (each difference is exact in FP32) for a pair of values
+__device__ __forceinline__ void split3(float z0, float z1, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(z0, z1);
+  const float r0 = z0 - __low2float(h), r1 = z1 - __high2float(h);
+  const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+  hi = bf16x2_bits(h);
+  mid = bf16x2_bits(m);
+  lo = bf16x2_bits(__floats2bfloat162_rn(r0 - __low2float(m), r1 - __high2float(m)));
+}
+// the term pairs (a_t, h_u) of one block product
+template <int NT>
+struct Terms;
+template <>
+struct Terms<2> {
+  static constexpr int n = 3;
+  __device__ static int a(int i) { return i == 2 ? 1 : 0; }
+  __device__ static int h(int i) { return i == 1 ? 1 : 0; }
+};
+template <>
+struct Terms<3> {
+  static constexpr int n = 6;  // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+  __device__ static int a(int i) { return i == 2 || i == 4 ? 1 : i == 5 ? 2 : 0; }
+  __device__ static int h(int i) { return i == 1 || i == 4 ? 1 : i == 3 ? 2 : 0; }
+};
+// the NT-term split of 8 values (one 16-byte row chunk per plane) into plane base p
+template <int NT>
+__device__ __forceinline__ void store_split(uint8_t* p, uint32_t off, const float* v) {
+  uint32_t w[NT][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if constexpr (NT == 2) split2(v[2 * j], v[2 * j + 1], w[0][j], w[1][j]);
+    else split3(v[2 * j], v[2 * j + 1], w[0][j], w[1][j], w[2][j]);
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) *(uint4*)(p + t * TS_BLK + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+}
 }  // namespace
 
+template <int NT>
 __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     const uint16_t* __restrict__ x, int W, int B, const int32_t* __restrict__ c_int,
     const __grid_constant__ CUtensorMap hmap, const float* __restrict__ m_all,
@@ -92,12 +133,13 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   const uint32_t tcols = ts_cols(Bp);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sZ = sm;                          // z_k: hi block, lo block
-  uint8_t* sY = sZ + 2 * TS_BLK;             // y_k: hi block, lo block
-  uint8_t* sR = sY + 2 * TS_BLK;             // ring: [stage][hi 64 x 64][lo 64 x 64]
+  constexpr uint32_t STAGE = NT * TS_HALF;   // the NT planes of one 64 x 64 block of H
+  uint8_t* sZ = sm;                          // z_k: NT term blocks
+  uint8_t* sY = sZ + NT * TS_BLK;            // y_k: NT term blocks
+  uint8_t* sR = sY + NT * TS_BLK;            // ring: [stage][plane][64 x 64]
   // per band n: {bits of 1.5 * 2^23 - c_n, m_n} (zero past B), read as one 16-byte load per
   // two bands
-  int2* cmS = (int2*)(sR + stages * TS_STAGE);
+  int2* cmS = (int2*)(sR + stages * STAGE);
   uint64_t* bars = (uint64_t*)(cmS + Bp);
   uint32_t* tslot = (uint32_t*)(bars + 2 * TS_MAX_STAGES + 8);
   const uint32_t b_full = tc::smem_u32(bars), b_empty = b_full + 8 * TS_MAX_STAGES;
@@ -147,11 +189,12 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
             ok = false;
             break;
           }
-          tc::mbar_arrive_expect_tx(b_full + 8 * s, TS_STAGE);
-          const uint32_t dst = tc::smem_u32(sR + s * TS_STAGE);
-          const int row = (f * 2) * Bp + j * TS_KB;
-          tc::tma_load_2d(dst, &hmap, k * TS_KB, row, b_full + 8 * s);
-          tc::tma_load_2d(dst + TS_HALF, &hmap, k * TS_KB, row + Bp, b_full + 8 * s);
+          tc::mbar_arrive_expect_tx(b_full + 8 * s, STAGE);
+          const uint32_t dst = tc::smem_u32(sR + s * STAGE);
+          const int row = (f * NT) * Bp + j * TS_KB;
+#pragma unroll
+          for (int pl = 0; pl < NT; ++pl)
+            tc::tma_load_2d(dst + pl * TS_HALF, &hmap, k * TS_KB, row + pl * Bp, b_full + 8 * s);
         }
       // drain: every copy issued here has landed before the CTA may exit
       const int issued = it;
@@ -165,7 +208,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_f16(1, TS_M, 64);
-      const uint32_t zhi = tc::smem_u32(sZ), zlo = zhi + TS_BLK, yhi = tc::smem_u32(sY), ylo = yhi + TS_BLK;
+      const uint32_t z0 = tc::smem_u32(sZ), y0 = tc::smem_u32(sY);
       int it = 0;
       bool issued_any = false;
       for (int k = 0; k < nkb && ok; ++k) {
@@ -179,13 +222,13 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
           const int s = it % stages;
           if (!tc::mbar_wait(b_full + 8 * s, (uint32_t)((it / stages) & 1), limit)) { ok = false; break; }
           tc::fence_after_sync();
-          const uint32_t hhi = tc::smem_u32(sR + s * TS_STAGE), hlo = hhi + TS_HALF;
+          const uint32_t h0 = tc::smem_u32(sR + s * STAGE);
           const uint32_t d = tbase + (uint32_t)(j * TS_KB);
-          const uint32_t ahi = j == k ? zhi : yhi, alo = j == k ? zlo : ylo;
+          const uint32_t a0 = j == k ? z0 : y0;
 #pragma unroll
-          for (int term = 0; term < 3; ++term) {
-            const uint32_t aop = term == 2 ? alo : ahi;
-            const uint32_t bop = term == 1 ? hlo : hhi;
+          for (int term = 0; term < Terms<NT>::n; ++term) {
+            const uint32_t aop = a0 + Terms<NT>::a(term) * TS_BLK;
+            const uint32_t bop = h0 + Terms<NT>::h(term) * TS_HALF;
 #pragma unroll
             for (int ks = 0; ks < TS_KB / 16; ++ks) {
               // y_k overwrites block k; the updates of block j start at k = 0
@@ -249,20 +292,17 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t w4[4] = {rw[4 * q], rw[4 * q + 1], rw[4 * q + 2], rw[4 * q + 3]};
-        uint32_t hi[4], lo[4];
+        float zv[8];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int n = k * TS_KB + 8 * q + 2 * j;
           const int4 cm = *(const int4*)&cmS[n];  // bands n, n + 1
           const float x0 = __int_as_float(cm.x + (int)(w4[j] & 0xffffu)) - 12582912.0f;
           const float x1 = __int_as_float(cm.z + (int)(w4[j] >> 16)) - 12582912.0f;
-          const float z0 = (x0 - __int_as_float(cm.y)) - a[8 * q + 2 * j];
-          const float z1 = (x1 - __int_as_float(cm.w)) - a[8 * q + 2 * j + 1];
-          split2(z0, z1, hi[j], lo[j]);
+          zv[2 * j] = (x0 - __int_as_float(cm.y)) - a[8 * q + 2 * j];
+          zv[2 * j + 1] = (x1 - __int_as_float(cm.w)) - a[8 * q + 2 * j + 1];
         }
-        const uint32_t off = tc::sw128_offset(r, 8 * q);
-        *(uint4*)(sZ + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *(uint4*)(sZ + TS_BLK + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        store_split<NT>(sZ, tc::sw128_offset(r, 8 * q), zv);
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
@@ -278,14 +318,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
       for (int i = 0; i < 64; ++i) dsum = fmaf(a[i], a[i], dsum);
       if (k + 1 < nkb) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          uint32_t hi[4], lo[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) split2(a[8 * q + 2 * j], a[8 * q + 2 * j + 1], hi[j], lo[j]);
-          const uint32_t off = tc::sw128_offset(r, 8 * q);
-          *(uint4*)(sY + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *(uint4*)(sY + TS_BLK + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        }
+        for (int q = 0; q < 8; ++q) store_split<NT>(sY, tc::sw128_offset(r, 8 * q), a + 8 * q);
         tc::fence_proxy_async();
         tc::fence_before_sync();
         tc::mbar_arrive(ya_full);
@@ -311,35 +344,40 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
 
 int bf16_form(int B, int in_type, bool cube, bool force_inverse) {
   if (cube || force_inverse) return P_BF16;
-  return in_type == IN_U16 && whiten_trsm_stages(B) > 0 ? P_BF16T : P_BF16;
+  return in_type == IN_U16 && whiten_trsm_stages(B, 2) > 0 ? P_BF16T : P_BF16;
 }
 
-int fp32_form(bool cube, bool force_inverse) {
-  return cube || force_inverse ? P_FP32 : P_FP32T;
+int fp32_form(int B, int in_type, bool cube, bool force_inverse, bool tc_factor) {
+  if (cube || force_inverse) return P_FP32;
+  if (tc_factor && in_type == IN_U16 && factor_tc_supported(B, P_FP32X) && whiten_trsm_stages(B, 3) > 0)
+    return P_FP32X;
+  return P_FP32T;
 }
 
-int whiten_trsm_stages(int B) {
+int whiten_trsm_stages(int B, int planes) {
   // no deeper than the blocks one CTA streams (small B: less shared memory, more CTAs per SM)
   const int nkb = pad64(B) / TS_KB, blocks = nkb * (nkb + 1) / 2;
   for (int s = std::min(TS_MAX_STAGES, blocks); s >= 1; --s)
-    if (ts_smem(pad64(B), s) <= TS_SMEM_MAX) return s;
+    if (ts_smem(pad64(B), s, planes) <= TS_SMEM_MAX) return s;
   return 0;
 }
 
-cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, const int32_t* c_int, const void* hmap,
-                               const float* m, const float* inv_s2, const int32_t* status, int factor_stride,
-                               ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc) {
+cudaError_t launch_whiten_trsm(const uint16_t* x, int L, int W, int B, int prec, const int32_t* c_int,
+                               const void* hmap, const float* m, const float* inv_s2, const int32_t* status,
+                               int factor_stride, ScoreOut out, int32_t* err, cudaStream_t st, LaunchCounter* lc) {
   if (L <= 0) return cudaSuccess;
-  const int Bp = pad64(B);
-  const int stages = whiten_trsm_stages(B);
+  const int Bp = pad64(B), nt = trsm_planes(prec);
+  if (nt == 0) return cudaErrorInvalidValue;
+  const int stages = whiten_trsm_stages(B, nt);
   if (stages == 0) return cudaErrorInvalidValue;
-  const uint32_t smem = ts_smem(Bp, stages);
+  const uint32_t smem = ts_smem(Bp, stages, nt);
   const long long limit = 4000000000LL;  // ~2 s of clock cycles
-  cudaError_t e = cudaFuncSetAttribute(whiten_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = nt == 3 ? whiten_trsm_kernel<3> : whiten_trsm_kernel<2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((W + TS_M - 1) / TS_M, L), block(TS_THREADS);
-  whiten_trsm_kernel<<<grid, block, smem, st>>>(x, W, B, c_int, *(const CUtensorMap*)hmap, m, inv_s2, status,
-                                                factor_stride, out, err, limit, stages);
+  kern<<<grid, block, smem, st>>>(x, W, B, c_int, *(const CUtensorMap*)hmap, m, inv_s2, status, factor_stride, out,
+                                  err, limit, stages);
   if (lc) lc->n += 1;
   return cudaGetLastError();
 }

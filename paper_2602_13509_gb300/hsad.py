@@ -78,6 +78,7 @@ def _load():
         "hsad_kernel_launches": (C.c_int64, [P]),
         "hsad_device_bytes": (C.c_int64, [P]),
         "hsad_whitening_form": (C.c_int, [P]),
+        "hsad_whitening_tensor_cores": (C.c_int, [P]),
         "hsad_set_device_budget": (C.c_int, [C.c_int, C.c_int64]),
         "hsad_device_budget_used": (C.c_int64, [C.c_int]),
         "hsad_profile_enable": (C.c_int, [P, C.c_int32]),
@@ -246,6 +247,10 @@ def hsad_device_bytes(ctx) -> int:
 
 def hsad_whitening_form(ctx) -> int:
     return int(_lib.hsad_whitening_form(ctx))
+
+
+def hsad_whitening_tensor_cores(ctx) -> int:
+    return int(_lib.hsad_whitening_tensor_cores(ctx))
 
 
 def hsad_set_device_budget(device: int, nbytes: int) -> int:
@@ -509,6 +514,10 @@ class Detector:
     @property
     def whitening_form(self) -> int:
         return hsad_whitening_form(self.ctx)
+
+    @property
+    def whitening_tensor_cores(self) -> bool:
+        return hsad_whitening_tensor_cores(self.ctx) == 1
 
     def close(self):
         if self.ctx is not None:

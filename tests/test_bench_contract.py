@@ -60,7 +60,12 @@ def test_kernel_rooflines_from_a_profile():
     assert w["bound"] == "alu" and abs(w["peak"] - bench.fp32_peak_tflops(2070.0)) < 1e-12
     assert abs(w["traffic_algorithmic"] - T * W * (2 * B + 5)) < 1e-6
     wb = bench.kernel_rooflines(prof, 2, T, W, B, 1, "bf16", 1, peaks, 2070.0)["whiten_score"]
-    assert wb["bound"] == "tensor" and wb["peak"] == 1849.2
+    assert wb["bound"] == "tensor" and wb["peak"] == 1849.2 and wb["operand_terms"] == 3
+    # FP32 on the tensor cores (three-term operands): tensor bound, six products per product
+    wx = bench.kernel_rooflines(prof, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0, True)["whiten_score"]
+    assert wx["bound"] == "tensor" and wx["operand_terms"] == 6
+    assert abs(wx["issued_tflops"] - 6 * wx["achieved"]) < 1e-9
+    assert bench.whitening_label(1, True) == "triangular solve, tensor cores"
     # the tensor-core factor's three classes: their algorithmic parts add up to the Cholesky
     diag, trsm, upd = bench.factor_parts_per_line(B)
     blocks = [min(64, B - p) for p in range(0, B, 64)]
