@@ -46,7 +46,9 @@ namespace {
 
 constexpr int NDIG = 6;            // base-256 digits per value
 constexpr int TU_M = 128, TU_N = 64, TU_K = 64;
-constexpr int TU_T = 160;          // 4 epilogue warps + 1 copy / MMA warp
+constexpr int TU_EW = 8;           // epilogue warps: TMEM lane group (w & 3) x column half (w >> 2)
+constexpr int TU_MW = TU_EW;       // the copy / MMA warp
+constexpr int TU_T = 32 * (TU_EW + 1);
 constexpr uint32_t TU_A_PLANE = TU_M * TU_K * 2;   // 16 KB
 constexpr uint32_t TU_B_PLANE = TU_N * TU_K * 2;   // 8 KB
 constexpr int TU_AS = TU_N + 1;    // row stride (float2) of the staged trailing tile
@@ -358,13 +360,13 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
 
 // ---- rows below the diagonal block on the tensor cores -------------------------------------
 // L_ik = A_ik X^T for a 128-row tile of the rows below panel k's diagonal block (grid: row
-// tiles x lines; 4 epilogue warps + 1 copy / MMA warp, like the update): the tile's rows of A
+// tiles x lines; 8 epilogue warps + 1 copy / MMA warp, like the update): the tile's rows of A
 // (float-float) are split into six digits with a per-row power of two straight into the
 // swizzled A operand while X's digits arrive by one bulk copy; the 21 digit-product MMAs sum
 // each level exactly in TMEM (the update's bound: a 64-term level sum stays below 2^24); the
 // epilogue combines the levels per row (one row per thread), writes the row to the whitening
 // operand, and splits it again into six digits for the trailing updates.
-constexpr uint32_t TT_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + 256 + 128 * 4 + 64;
+constexpr uint32_t TT_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + 256 + 128 * 4 + 2 * 128 * 4 + 64;
 template <int PREC>
 __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ sigma_all,
                                                            uint8_t* __restrict__ slice_all, size_t slice_stride,
@@ -380,7 +382,8 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
   uint8_t* sX = sm + NDIG * TU_A_PLANE;      // NDIG planes of 64 x 64 BF16, then X's 64 row exponents
   const int* fx = (const int*)(sX + NDIG * TU_B_PLANE);
   int* ea = (int*)(sX + XDIG_BYTES);         // exponents of the tile's rows of A
-  uint64_t* bars = (uint64_t*)(ea + 128);
+  float* rmax = (float*)(ea + 128);          // [2][128] row maxima of the two column halves of L
+  uint64_t* bars = (uint64_t*)(rmax + 256);
   uint32_t* tslot = (uint32_t*)(bars + 4);
   const uint32_t full = tc::smem_u32(bars), done = full + 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -392,22 +395,22 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
     tc::mbar_init(done, 1);
     tc::mbar_init_fence();
   }
-  if (warp == 4) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  if (warp == TU_MW) tc::tmem_alloc(tc::smem_u32(tslot), 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   const float2* A = reinterpret_cast<const float2*>(sigma_all + (int64_t)t * B * B);
 
-  if (warp == 4) {
+  if (warp == TU_MW) {
     if (lane == 0) {
       tc::mbar_arrive_expect_tx(full, XDIG_BYTES);
       tc::bulk_load(tc::smem_u32(sX), sl + xdig_offset(Bp), XDIG_BYTES, full);
     }
   } else {
-    // the A operand: rows of the tile split into digits (16 rows per round, lanes across the
+    // the A operand: rows of the tile split into digits (16 rows per warp, lanes across the
     // 64 columns: coalesced loads, conflict-free 2-byte stores within a swizzled row)
-    for (int rr = warp * 32; rr < warp * 32 + 32; rr += 16) {
+    for (int rr = warp * 16; rr < warp * 16 + 16; rr += 16) {
       float2 v[16][2];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
   }
   __syncthreads();
   bool ok = true;
-  if (warp == 4) {
+  if (warp == TU_MW) {
     if (lane == 0) {
       if (!tc::mbar_wait(full, 0, limit)) ok = false;
       tc::fence_after_sync();
@@ -463,12 +466,14 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
     __syncwarp();
     tc::fence_after_sync();
     if (!dok) atomicExch(err, 1);
-    const int row = 32 * warp + lane, i = i0 + row;
+    // thread (TMEM lane group lg, column half ch): row 32 lg + lane, columns 32 ch .. 32 ch + 31
+    const int lg = warp & 3, ch = warp >> 2, cs = 32 * ch;
+    const int row = 32 * lg + lane, i = i0 + row;
     const int ei = ea[row];
-    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    const uint32_t taddr = tbase + ((uint32_t)(32 * lg) << 16);
     float2* Ls = reinterpret_cast<float2*>(sA) + row * TU_AS;  // this thread's row (the MMAs are done)
     float mx = 0.f;
-    for (int c0 = 0; c0 < TU_N; c0 += 16) {
+    for (int c0 = cs; c0 < cs + 32; c0 += 16) {
       float lev[NDIG][16];
 #pragma unroll
       for (int l = 0; l < NDIG; ++l) tc::tmem_ld16(taddr + (uint32_t)(64 * l + c0), lev[l]);
@@ -479,16 +484,19 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
         mx = fmaxf(mx, fabsf(v.x));
       }
     }
+    rmax[ch * 128 + row] = mx;
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * TU_EW) : "memory");  // the epilogue warps only
+    mx = fmaxf(rmax[row], rmax[128 + row]);
     if (dok && i < Bp) {
       // the whitening operand's rows (zero past B)
       const int64_t plane = (int64_t)Bp * Bp;
       void* w = (char*)wmat + (size_t)t * plane * wmat_elem_bytes(PREC);
       if constexpr (PREC == P_FP32T) {  // transposed: consecutive threads on consecutive rows
-        for (int c = 0; c < TU_N; ++c)
+        for (int c = cs; c < cs + 32; ++c)
           fk::WOut<PREC>::store(w, plane, fk::h_index<PREC>(i, p + c, Bp), fk::ArFF::to_f(Ls[c]));
       } else {  // BF16 planes, row-major: this thread's row in 16-byte pieces
         __nv_bfloat16* wb = (__nv_bfloat16*)w;
-        for (int g = 0; g < 8; ++g) {
+        for (int g = 4 * ch; g < 4 * ch + 4; ++g) {
           float f[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) f[j] = fk::ArFF::to_f(Ls[8 * g + j]);
@@ -497,9 +505,9 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
       }
       // the row's digits for the trailing updates: 16-byte stores into the swizzled planes
       const int e = row_exponent(mx);
-      expo[i] = e;
+      if (ch == 0) expo[i] = e;
       const float sc = ldexpf(1.f, -e);
-      for (int g = 0; g < 8; ++g) {
+      for (int g = 4 * ch; g < 4 * ch + 4; ++g) {
         uint32_t pk[NDIG][4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -519,7 +527,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 4) {
+  if (warp == TU_MW) {
     __syncwarp();
     tc::tmem_dealloc(tbase, 512);
   }
@@ -563,14 +571,14 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
     tc::mbar_init_fence();
   }
   if (tid < 64) ej[tid] = expo[j0 + tid];
-  if (warp == 4) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  if (warp == TU_MW) tc::tmem_alloc(tc::smem_u32(tslot), 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   bool ok = true;
 
-  if (warp == 4) {
+  if (warp == TU_MW) {
     if (lane == 0) {
       tc::mbar_arrive_expect_tx(full, NDIG * (TU_A_PLANE + TU_B_PLANE));
       for (int d = 0; d < NDIG; ++d) {
@@ -600,34 +608,30 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
       }
     }
   } else {
-    // epilogue warps: stage the trailing tile (coalesced rows, while the digits load and the
-    // MMAs run), then one tile row per thread (= its TMEM lane), then store it back coalesced
+    // epilogue warps: each stages its 32 rows x 32 columns of the trailing tile (coalesced
+    // row pieces, while the digits load and the MMAs run), then takes one row (= its TMEM
+    // lane) of those columns per thread, then stores them back coalesced
     float2* A = reinterpret_cast<float2*>(sigma_all + (int64_t)t * B * B);
-    // 16 rows per round: 32 independent loads in flight per lane
-    for (int r0w = warp * 32; r0w < warp * 32 + 32; r0w += 16) {
-      float2 v[16][2];
+    const int lg = warp & 3, ch = warp >> 2, cs = 32 * ch;
+    // 16 rows per round: 16 independent loads in flight per lane
+    for (int r0w = lg * 32; r0w < lg * 32 + 32; r0w += 16) {
+      float2 v[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int i = i0 + r0w + q;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int j = j0 + lane + 32 * h;
-          v[q][h] = (i < B && j < B && j <= i) ? A[(int64_t)i * B + j] : make_float2(0.f, 0.f);
-        }
+        const int i = i0 + r0w + q, j = j0 + cs + lane;
+        v[q] = (i < B && j < B && j <= i) ? A[(int64_t)i * B + j] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) As[(r0w + q) * TU_AS + lane + 32 * h] = v[q][h];
+      for (int q = 0; q < 16; ++q) As[(r0w + q) * TU_AS + cs + lane] = v[q];
     }
     const bool dok = tc::mbar_wait(done, 0, limit);
     __syncwarp();
     tc::fence_after_sync();
     if (!dok) atomicExch(err, 1);
-    const int row = 32 * warp + lane, i = i0 + row;
+    const int row = 32 * lg + lane, i = i0 + row;
     const int ei = expo[i];  // i < Bp + 64: the region's exponent rows
-    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
-    for (int c0 = 0; c0 < TU_N; c0 += 16) {
+    const uint32_t taddr = tbase + ((uint32_t)(32 * lg) << 16);
+    for (int c0 = cs; c0 < cs + 32; c0 += 16) {
       float lev[NDIG][16];
 #pragma unroll
       for (int l = 0; l < NDIG; ++l) tc::tmem_ld16(taddr + (uint32_t)(64 * l + c0), lev[l]);
@@ -642,21 +646,18 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
         }
       }
     }
-    __syncwarp();  // the warp's 32 rows are complete
+    __syncwarp();  // the warp's 32 rows x 32 columns are complete
     if (dok) {
-      for (int r = warp * 32; r < warp * 32 + 32; ++r) {
-        const int i2 = i0 + r;
-        for (int c = lane; c < TU_N; c += 32) {
-          const int j = j0 + c;
-          if (i2 < B && j < B && j <= i2) A[(int64_t)i2 * B + j] = As[r * TU_AS + c];
-        }
+      for (int r = lg * 32; r < lg * 32 + 32; ++r) {
+        const int i2 = i0 + r, j = j0 + cs + lane;
+        if (i2 < B && j < B && j <= i2) A[(int64_t)i2 * B + j] = As[r * TU_AS + cs + lane];
       }
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 4) {
+  if (warp == TU_MW) {
     __syncwarp();
     tc::tmem_dealloc(tbase, 512);
   }
