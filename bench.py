@@ -213,7 +213,7 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, t
     ffp = ff_peak_tflops(mhz)
     for name, (n, tot) in prof.items():
         if n == 0 or name not in ("factor", "factor_form", "factor_diag", "factor_panel", "factor_update", "syrk",
-                                   "whiten_score"):
+                                   "syrk_split", "whiten_score"):
             continue
         ms = tot / prof_steps
         r = None
@@ -250,6 +250,14 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, t
                            "MMAs per algorithmic product)",
                  "work_per_step": f"{lines:.0f} lines x (B^3/3 - panel Cholesky flops) algorithmic flop",
                  "issued_tflops": 21 * ach, "peak_source": f"{peaks['source']} bf16 burst"}
+        elif name == "syrk_split":
+            byts = px_step * (2 * B + 4 * (-(-B // 128) * 128))
+            ach = byts / (ms / 1e3) / 1e9
+            r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": ach / peaks["hbm_gbs"], "kernel": "SYRK operand split (uint16 DN in, BF16 h and r "
+                 "blocks out in the tensor-core operand layout)",
+                 "work_per_step": f"{px_step} px x (2 B + 4 x B rounded up to 128) bytes",
+                 "peak_source": peaks["source"]}
         elif name == "factor_form":
             byts = lines * B * (B + 1) / 2 * 16
             ach = byts / (ms / 1e3) / 1e9

@@ -116,6 +116,8 @@ struct hsad_ctx {
   void* d_bin[2] = {nullptr, nullptr};
   int fe_idx = 0;
   int64_t syrk_max_pix = 4096;  // pixels one exact SYRK accumulation may hold
+  bool split_syrk = false;      // streamed uint16 lines: split once into hr, then contract per tile
+  uint8_t* hr = nullptr;        // the split operand blocks of a batch's lines
   int every = 1;                // factorisation cadence in lines (EXCLUSIVE)
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   // pinned caller buffers are copied straight to d_stage on h2d_stream: copy_ev marks the
@@ -284,6 +286,7 @@ int64_t plan_bytes(const hsad_ctx* c) {
   b += Lf * B * B * 8 * 2;                                       // sigma, inv
   b += Lf * Bp * Bp * wmat_elem_bytes(c->prec) + Lf * Bp * 4 + Lf * 4 + Ls * 4;  // wmat, y0, inv_s2, status
   if (c->prec == P_FP32T) b += (int64_t)whiten_trsm_simt_scratch_bytes(c->B);  // FP32 solve scratch
+  if (c->split_syrk) b += (int64_t)syrk_split_bytes(L, c->W, c->B);             // split SYRK operands
   b += c->ring * c->W * 5 + c->ring * 4 + 64;                    // result ring
   b += c->ring * c->W * 2 + 64;                                  // transmit codes scratch
   if (c->mode == HSAD_CUBE) b += (int64_t)c->cfg.cube_lines * c->line_bytes;
@@ -546,6 +549,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   // sums of bin 12-bit DN: |x'| < 2^(12 + ceil(log2 bin)); an exact accumulation holds
   // 2^24 / (|x'| / 64)^2 pixels: 4096 (bin 1), 1024 (bin 2), 256 (bin 3, 4)
   if (ctx->fe) ctx->syrk_max_pix = cfg->band_bin == 1 ? 4096 : (cfg->band_bin == 2 ? 1024 : 256);
+  ctx->split_syrk = cfg->stats_mode != HSAD_CUBE && ctx->in_type == IN_U16 && ctx->W <= ctx->syrk_max_pix;
   ctx->min_pix = std::max<int64_t>((int64_t)ctx->B + 1, cfg->warmup_pixels);
   ctx->tau = cfg->threshold > 0.f
                  ? cfg->threshold
@@ -613,6 +617,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->inv = (double*)dalloc(ctx, Lf * B * B * 8, &ok);
   ctx->wmat = dalloc(ctx, Lf * Bp * Bp * wmat_elem_bytes(ctx->prec), &ok);
   if (ctx->prec == P_FP32T) ctx->yscratch = (float*)dalloc(ctx, (int64_t)whiten_trsm_simt_scratch_bytes(B), &ok);
+  if (ctx->split_syrk) ctx->hr = (uint8_t*)dalloc(ctx, (int64_t)syrk_split_bytes(L, ctx->W, ctx->B), &ok);
   ctx->y0 = (float*)dalloc(ctx, Lf * Bp * 4, &ok);
   ctx->inv_s2 = (float*)dalloc(ctx, Lf * 4, &ok);
   ctx->status = (int32_t*)dalloc(ctx, std::max(Ls, Lf) * 4, &ok);
@@ -765,7 +770,12 @@ int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o, i
 int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* out, int64_t out_stride,
          bool accumulate) {
   cudaStream_t st = ctx->stream;
-  if (ctx->in_type == IN_U16) {
+  if (ctx->in_type == IN_U16 && ctx->split_syrk && !accumulate && pix == ctx->W && n_groups <= ctx->Lmax) {
+    // streamed lines: each line's DN split once, then one contraction per block pair
+    KL("syrk_split", launch_syrk_split((const uint16_t*)x, n_groups, pix, ctx->B, ctx->c_int, ctx->hr, st,
+                                       &ctx->lc));
+    KL("syrk", launch_syrk_pre(ctx->hr, n_groups, pix, ctx->B, out, out_stride, ctx->dev_err, st, &ctx->lc));
+  } else if (ctx->in_type == IN_U16) {
     bool acc = accumulate;
     if (!acc && pix > ctx->syrk_max_pix) {  // exactness bound of one accumulation: add slices atomically
       CK(cudaMemsetAsync(out, 0, (size_t)(n_groups * out_stride * 8), st));

@@ -103,6 +103,15 @@ cudaError_t launch_prefix_cov(double* buf, double* state_s2, int L, int B, int i
 cudaError_t launch_syrk_tc(const uint16_t* x, int64_t n_groups, int64_t pix_per_group, int B,
                            const int32_t* c_int, double* out, int64_t out_stride, int accumulate, int32_t* err,
                            cudaStream_t st, LaunchCounter* lc, int64_t max_pix = 4096);
+// K2 for streamed statistics in two launches: the integer split of every group's DN into the
+// BF16 operand blocks (scratch of syrk_split_bytes), then one tile contraction per block pair
+// and group from those blocks (groups of at most 4096 pixels, out as for launch_syrk_tc
+// without accumulation).
+size_t syrk_split_bytes(int64_t groups, int64_t pix, int B);
+cudaError_t launch_syrk_split(const uint16_t* x, int64_t n_groups, int64_t pix, int B, const int32_t* c_int,
+                              uint8_t* hr, cudaStream_t st, LaunchCounter* lc);
+cudaError_t launch_syrk_pre(const uint8_t* hr, int64_t n_groups, int64_t pix, int B, double* out,
+                            int64_t out_stride, int32_t* err, cudaStream_t st, LaunchCounter* lc);
 // Front end (Sec. 3.2): out[p][b] = sum_{i < bin} raw[p][first + bin * b + i].
 cudaError_t launch_frontend(const uint16_t* raw, int64_t n_px, int raw_bands, int first, int bin, int bands,
                             uint16_t* out, cudaStream_t st, LaunchCounter* lc);

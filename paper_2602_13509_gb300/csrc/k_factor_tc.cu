@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
   const int Bp = pad64(B), p = 64 * k, i0 = p + 64 + TU_M * blockIdx.x;
   if (i0 >= Bp || skip_line(status, t, every, q_off)) return;  // uniform for the CTA
   extern __shared__ uint8_t tsm_raw[];
-  uint8_t* sm = (uint8_t*)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(tsm_raw);
   uint8_t* sA = sm;                          // NDIG planes of 128 x 64 BF16 (swizzled); later the L rows
   uint8_t* sX = sm + NDIG * TU_A_PLANE;      // NDIG planes of 64 x 64 BF16, then X's 64 row exponents
   const int* fx = (const int*)(sX + NDIG * TU_B_PLANE);
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
   }
   if (a >= nbr || skip_line(status, t, every, q_off)) return;  // uniform for the CTA
   extern __shared__ uint8_t usm_raw[];
-  uint8_t* sm = (uint8_t*)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(usm_raw);
   uint8_t* sA = sm;                                  // NDIG planes of 128 x 64 BF16 (swizzled)
   uint8_t* sB = sm + NDIG * TU_A_PLANE;              // NDIG planes of 64 x 64 BF16
   float2* As = (float2*)(sB + NDIG * TU_B_PLANE);   // the trailing tile A[i0 ..][j0 ..], [128][TU_AS]

@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "hsad_internal.h"
 #include "tc_util.cuh"
 
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
 
   // shared memory: 2 operand stages | raw_bufs DN chunks of 64 pixels x B | barriers
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   const bool bulk = raw_bufs > 0;
   const uint32_t rawb = sk_raw_bytes(B);
   uint8_t* raw = sm + 2 * SK_STAGE;
@@ -168,10 +170,10 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
         ok = false;
         atomicExch(err, 1);
       }
-      // the chunk's DN: staged in shared memory by the bulk copy, else read from global
-      const uint16_t* src = bulk ? (const uint16_t*)(raw + r * rawb) : xg + pc * B;
+      // the chunk's DN: staged in shared memory by the bulk copy, else read from global (two
+      // instantiations, so that the shared path uses shared-memory loads)
       const int npx = (int)min((int64_t)SK_KC, p_end - pc);
-      if (ok) {
+      auto convert = [&](auto load, auto full) {  // full: a valid row and a whole chunk
         for (int gi = g_begin; gi < g_end; ++gi) {
           uint32_t hw[4], rw[4];
 #pragma unroll
@@ -180,8 +182,9 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               const int k = gi * 8 + 2 * q + u;
-              const int dn = (valid && k < npx) ? (int)src[k * B + band] : 0;
-              const float xv = (valid && k < npx) ? __int_as_float(magic_c + dn) - 12582912.0f : 0.f;
+              const bool in = decltype(full)::value || (valid && k < npx);
+              const int dn = in ? load(k * B + band) : 0;
+              const float xv = in ? __int_as_float(magic_c + dn) - 12582912.0f : 0.f;
               // h = rint(x'/64) (round to nearest even, exact: |x'/64| <= 64), r = x' - 64 h
               const float hf = __fmaf_rn(xv, 1.f / 64.f, 12582912.0f) - 12582912.0f;
               hv[u] = hf;
@@ -194,6 +197,20 @@ __global__ void __launch_bounds__(SK_THREADS, 1) syrk_tc_kernel(const uint16_t* 
           const uint32_t off = tc::sw128_offset(row, gi * 8);
           *(uint4*)(OH + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           *(uint4*)(OR + off) = make_uint4(rw[0], rw[1], rw[2], rw[3]);
+        }
+      };
+      if (ok) {
+        const bool whole = valid && npx == SK_KC;
+        if (bulk) {
+          const uint16_t* rs = (const uint16_t*)(raw + r * rawb);
+          auto ld = [&](int idx) { return (int)rs[idx]; };
+          if (whole) convert(ld, std::true_type{});
+          else convert(ld, std::false_type{});
+        } else {
+          const uint16_t* gs = xg + pc * B;
+          auto ld = [&](int idx) { return (int)__ldg(gs + idx); };
+          if (whole) convert(ld, std::true_type{});
+          else convert(ld, std::false_type{});
         }
       }
       tc::fence_proxy_async();

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(WT_THREADS, 1) whiten_tc_kernel(
   const int npx = min(WT_M, W - p0);
   const uint32_t tcols = tmem_cols_for(Bp);
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   uint8_t* sA = sm;                                  // [2 buf][2 op][128 x 64] swizzled
   uint8_t* sB = sm + SMEM_A;                         // [stage][2 plane][64 x 64] swizzled
   float* y0s = (float*)(sB + stages * 2 * B_TILE);

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   const int npx = min(TS_M, W - p0);
   const uint32_t tcols = ts_cols(Bp);
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   constexpr uint32_t STAGE = NT * TS_HALF;   // the NT planes of one 64 x 64 block of H
   uint8_t* sZ = sm;                          // z_k: NT term blocks
   uint8_t* sY = sZ + NT * TS_BLK;            // y_k: NT term blocks

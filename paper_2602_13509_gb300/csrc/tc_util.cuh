@@ -11,6 +11,10 @@ namespace tc {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
+// The first 1024-byte boundary (of the shared-window address) at or after p, a pointer into
+// dynamic shared memory, by an offset added to p: the compiler keeps the shared address
+// space (ld/st.shared instead of generic accesses), which an integer round trip loses.
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) { return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u); }
 
 // ---- mbarrier -----------------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {

@@ -66,6 +66,8 @@ def test_kernel_rooflines_from_a_profile():
     assert wx["bound"] == "tensor" and wx["operand_terms"] == 6
     assert abs(wx["issued_tflops"] - 6 * wx["achieved"]) < 1e-9
     assert bench.whitening_label(1, True) == "triangular solve, tensor cores"
+    sp = bench.kernel_rooflines({"syrk_split": (4, 8.0)}, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)["syrk_split"]
+    assert sp["bound"] == "hbm" and abs(sp["achieved"] - T * W * (2 * B + 4 * 128 * -(-B // 128)) / 0.004 / 1e9) < 1e-6
     # the tensor-core factor's three classes: their algorithmic parts add up to the Cholesky
     diag, trsm, upd = bench.factor_parts_per_line(B)
     blocks = [min(64, B - p) for p in range(0, B, 64)]
