@@ -9,9 +9,9 @@
 //                      blocks, written to a scratch in exactly the shared-memory operand
 //                      layout (per block: H then R, 128 rows x 64 pixels BF16, 128-byte
 //                      swizzle; rows past B and pixels past the line zero);
-//   syrk_pre_kernel    one CTA per (block pair, line): a copy warp streams the pair's
-//                      32 KB operand blocks per chunk with bulk copies through a 3-stage
-//                      ring, one thread issues the 4 MMAs per 16 pixels into the three
+//   syrk_pre_kernel    one CTA per (128-band row block, 64-band column block, line): a
+//                      copy warp streams the row block's 32 KB and the column block's 16 KB
+//                      of operands per chunk with bulk copies through a 2-stage ring, one thread issues the 4 MMAs per 16 pixels into the three
 //                      exact accumulators (TMEM), 4 warps read them out and store the exact
 //                      sums (int64 combination, FP64 store) to the lower triangle.
 // Every wait is bounded; a timeout sets *err and the CTA drains its copies and exits.
@@ -28,10 +28,13 @@ namespace {
 constexpr int SP_M = 128, SP_KC = 64;
 constexpr uint32_t SP_PLANE = SP_M * SP_KC * 2;  // 16 KB: 128 band rows x 64 pixels, 16-bit
 constexpr uint32_t SP_BLOCK = 2 * SP_PLANE;      // H then R of one band block
-constexpr int SP_STAGES = 3;
+constexpr int SP_STAGES = 2;
+constexpr int SP_N = 64;                         // output columns per tile: 3 accumulators in 256 TMEM columns
+constexpr uint32_t SP_HALF = SP_PLANE / 2;       // 64 band rows of a plane (the first or second 8 KB)
+constexpr uint32_t SP_STAGE = SP_BLOCK + 2 * SP_HALF;
 constexpr int SP_THREADS = 192;                  // 4 epilogue warps, copy warp, MMA warp
 constexpr int SP_COPY_WARP = 4, SP_MMA_WARP = 5;
-constexpr uint32_t SP_SMEM = 1024 + SP_STAGES * 2 * SP_BLOCK + 256;
+constexpr uint32_t SP_SMEM = 1024 + SP_STAGES * SP_STAGE + 256;
 
 __host__ __device__ inline int sp_blocks(int B) { return (B + SP_M - 1) / SP_M; }
 __host__ __device__ inline int64_t sp_chunks(int64_t pix) { return (pix + SP_KC - 1) / SP_KC; }
@@ -104,29 +107,32 @@ __global__ void __launch_bounds__(SS_T) syrk_split_kernel(const uint16_t* __rest
   }
 }
 
-// grid (block pairs ib <= jb, groups): the exact sums of one 128 x N block of S2 of one group.
-__global__ void __launch_bounds__(SP_THREADS, 1) syrk_pre_kernel(const uint8_t* __restrict__ hr, int64_t pix,
+// grid (tiles, groups): the exact sums of one 128 x 64 block of S2 of one group: 128-band row
+// block ib, 64-band column block jb >= 2 ib (two CTAs per SM: 96 KB of shared memory and 256
+// TMEM columns each, so that one CTA's epilogue overlaps the other's contraction).
+__global__ void __launch_bounds__(SP_THREADS, 2) syrk_pre_kernel(const uint8_t* __restrict__ hr, int64_t pix,
                                                                  int B, double* __restrict__ out,
                                                                  int64_t out_stride, int32_t* __restrict__ err,
                                                                  long long limit) {
-  const int nb = sp_blocks(B);
+  const int nb = sp_blocks(B), nc = (B + SP_N - 1) / SP_N;
   int tile = blockIdx.x, ib = 0;
-  while (tile >= nb - ib) {
-    tile -= nb - ib;
+  while (tile >= nc - 2 * ib) {
+    tile -= nc - 2 * ib;
     ++ib;
   }
-  const int jb = ib + tile;
-  const int i0 = ib * SP_M, j0 = jb * SP_M;
-  const int N = min(SP_M, ((B - j0) + 15) / 16 * 16);
-  const bool diag = ib == jb;
+  const int jb = 2 * ib + tile;                  // 64-band column block
+  const int i0 = ib * SP_M, j0 = jb * SP_N;
+  const int N = min(SP_N, ((B - j0) + 15) / 16 * 16);
+  const bool diag = (jb >> 1) == ib;             // the columns lie in the row block's own bands
   const int64_t g = blockIdx.y;
   const int nchunks = (int)sp_chunks(pix);
   const uint8_t* hg = hr + (size_t)g * nchunks * nb * SP_BLOCK;
-  const uint32_t stage_bytes = diag ? SP_BLOCK : 2 * SP_BLOCK;
+  const uint32_t stage_bytes = diag ? SP_BLOCK : SP_BLOCK + 2 * SP_HALF;
+  const uint32_t half_off = (uint32_t)(jb & 1) * SP_HALF;  // the column block's rows within its 128-band block
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = tc::align1024(smem_raw);
-  uint64_t* bars = (uint64_t*)(sm + SP_STAGES * 2 * SP_BLOCK);
+  uint64_t* bars = (uint64_t*)(sm + SP_STAGES * SP_STAGE);
   uint32_t* tslot = (uint32_t*)(bars + 2 * SP_STAGES + 2);
   const uint32_t full = tc::smem_u32(bars), empty = full + 8 * SP_STAGES, d_full = empty + 8 * SP_STAGES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -139,7 +145,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) syrk_pre_kernel(const uint8_t* 
     tc::mbar_init(d_full, 1);
     tc::mbar_init_fence();
   }
-  if (warp == SP_MMA_WARP) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  if (warp == SP_MMA_WARP) tc::tmem_alloc(tc::smem_u32(tslot), 256);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -157,10 +163,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1) syrk_pre_kernel(const uint8_t* 
         }
         tc::mbar_arrive_expect_tx(full + 8 * s, stage_bytes);
         const uint8_t* cb = hg + (size_t)c * nb * SP_BLOCK;
-        tc::bulk_load(tc::smem_u32(sm + s * 2 * SP_BLOCK), cb + (size_t)ib * SP_BLOCK, SP_BLOCK, full + 8 * s);
-        if (!diag)
-          tc::bulk_load(tc::smem_u32(sm + s * 2 * SP_BLOCK + SP_BLOCK), cb + (size_t)jb * SP_BLOCK, SP_BLOCK,
-                        full + 8 * s);
+        uint8_t* st_base = sm + s * SP_STAGE;
+        tc::bulk_load(tc::smem_u32(st_base), cb + (size_t)ib * SP_BLOCK, SP_BLOCK, full + 8 * s);
+        if (!diag) {  // H and R rows of the 64-band column block
+          const uint8_t* jbk = cb + (size_t)(jb >> 1) * SP_BLOCK + half_off;
+          tc::bulk_load(tc::smem_u32(st_base + SP_BLOCK), jbk, SP_HALF, full + 8 * s);
+          tc::bulk_load(tc::smem_u32(st_base + SP_BLOCK + SP_HALF), jbk + SP_PLANE, SP_HALF, full + 8 * s);
+        }
       }
       for (int s = 0; s < SP_STAGES && s < issued; ++s) {  // every copy landed before exit
         const int last = issued - 1 - ((issued - 1 - s) % SP_STAGES);
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) syrk_pre_kernel(const uint8_t* 
     }
   } else if (warp == SP_MMA_WARP) {
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_f16(1, SP_M, N);
+      const uint32_t idesc = tc::idesc_f16(1, SP_M, N);  // accumulators at columns 0, 64, 128
       bool any = false;
       for (int c = 0; c < nchunks; ++c) {
         const int s = c % SP_STAGES;
@@ -179,15 +188,16 @@ __global__ void __launch_bounds__(SP_THREADS, 1) syrk_pre_kernel(const uint8_t* 
           break;
         }
         tc::fence_after_sync();
-        const uint32_t aH = tc::smem_u32(sm + s * 2 * SP_BLOCK), aR = aH + SP_PLANE;
-        const uint32_t bH = diag ? aH : aH + SP_BLOCK, bR = bH + SP_PLANE;
+        const uint32_t aH = tc::smem_u32(sm + s * SP_STAGE), aR = aH + SP_PLANE;
+        // B: the column block's 64 rows of H and R (inside A's block on the diagonal)
+        const uint32_t bH = diag ? aH + half_off : aH + SP_BLOCK, bR = diag ? aR + half_off : bH + SP_HALF;
 #pragma unroll
         for (int ks = 0; ks < SP_KC / 16; ++ks) {
           const uint32_t o = ks * 32, acc = (c > 0 || ks > 0) ? 1u : 0u;
           tc::mma_f16(tbase + 0, tc::desc_sw128(aH + o), tc::desc_sw128(bH + o), idesc, acc);
-          tc::mma_f16(tbase + 128, tc::desc_sw128(aH + o), tc::desc_sw128(bR + o), idesc, acc);
-          tc::mma_f16(tbase + 128, tc::desc_sw128(aR + o), tc::desc_sw128(bH + o), idesc, 1u);
-          tc::mma_f16(tbase + 256, tc::desc_sw128(aR + o), tc::desc_sw128(bR + o), idesc, acc);
+          tc::mma_f16(tbase + 64, tc::desc_sw128(aH + o), tc::desc_sw128(bR + o), idesc, acc);
+          tc::mma_f16(tbase + 64, tc::desc_sw128(aR + o), tc::desc_sw128(bH + o), idesc, 1u);
+          tc::mma_f16(tbase + 128, tc::desc_sw128(aR + o), tc::desc_sw128(bR + o), idesc, acc);
         }
         tc::mma_commit(empty + 8 * s);
         any = true;
@@ -212,8 +222,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1) syrk_pre_kernel(const uint8_t* 
       float hh[32], xr[32], rr[32];
       __syncwarp();
       tc::tmem_ld32(taddr + (uint32_t)c0, hh);
-      tc::tmem_ld32(taddr + 128u + (uint32_t)c0, xr);
-      tc::tmem_ld32(taddr + 256u + (uint32_t)c0, rr);
+      tc::tmem_ld32(taddr + 64u + (uint32_t)c0, xr);
+      tc::tmem_ld32(taddr + 128u + (uint32_t)c0, rr);
       if (write) {
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) syrk_pre_kernel(const uint8_t* 
   tc::fence_after_sync();
   if (warp == SP_MMA_WARP) {
     __syncwarp();
-    tc::tmem_dealloc(tbase, 512);
+    tc::tmem_dealloc(tbase, 256);
   }
 }
 
@@ -256,10 +266,12 @@ cudaError_t launch_syrk_pre(const uint8_t* hr, int64_t n_groups, int64_t pix, in
                             int64_t out_stride, int32_t* err, cudaStream_t st, LaunchCounter* lc) {
   if (n_groups <= 0 || pix <= 0) return cudaSuccess;
   if (n_groups > 65535 || pix > 4096) return cudaErrorInvalidValue;  // one exact accumulation per group
-  const int nb = sp_blocks(B);
+  const int nb = sp_blocks(B), nc = (B + SP_N - 1) / SP_N;
+  int tiles = 0;
+  for (int ib = 0; ib < nb; ++ib) tiles += nc - 2 * ib;
   cudaError_t e = cudaFuncSetAttribute(syrk_pre_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM);
   if (e != cudaSuccess) return e;
-  syrk_pre_kernel<<<dim3(nb * (nb + 1) / 2, (unsigned)n_groups), SP_THREADS, SP_SMEM, st>>>(
+  syrk_pre_kernel<<<dim3(tiles, (unsigned)n_groups), SP_THREADS, SP_SMEM, st>>>(
       hr, pix, B, out, out_stride, err, 4000000000LL);
   if (lc) lc->n += 1;
   return cudaGetLastError();
