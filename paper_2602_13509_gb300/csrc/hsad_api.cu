@@ -118,6 +118,7 @@ struct hsad_ctx {
   int64_t syrk_max_pix = 4096;  // pixels one exact SYRK accumulation may hold
   bool split_syrk = false;      // streamed uint16 lines: split once into hr, then contract per tile
   uint8_t* hr = nullptr;        // the split operand blocks of a batch's lines
+  float2* ffm = nullptr;        // per-line float-float means, n m, 1/(n-1) (tensor-core factor)
   int every = 1;                // factorisation cadence in lines (EXCLUSIVE)
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   // pinned caller buffers are copied straight to d_stage on h2d_stream: copy_ev marks the
@@ -287,6 +288,7 @@ int64_t plan_bytes(const hsad_ctx* c) {
   b += Lf * Bp * Bp * wmat_elem_bytes(c->prec) + Lf * Bp * 4 + Lf * 4 + Ls * 4;  // wmat, y0, inv_s2, status
   if (c->prec == P_FP32T) b += (int64_t)whiten_trsm_simt_scratch_bytes(c->B);  // FP32 solve scratch
   if (c->split_syrk) b += (int64_t)syrk_split_bytes(L, c->W, c->B);             // split SYRK operands
+  if (c->tc_factor) b += (int64_t)tcf_form_scratch_bytes((int)Lf, c->B);         // formation inputs
   b += c->ring * c->W * 5 + c->ring * 4 + 64;                    // result ring
   b += c->ring * c->W * 2 + 64;                                  // transmit codes scratch
   if (c->mode == HSAD_CUBE) b += (int64_t)c->cfg.cube_lines * c->line_bytes;
@@ -618,6 +620,7 @@ int hsad_create(const hsad_config* cfg, hsad_ctx** out) {
   ctx->wmat = dalloc(ctx, Lf * Bp * Bp * wmat_elem_bytes(ctx->prec), &ok);
   if (ctx->prec == P_FP32T) ctx->yscratch = (float*)dalloc(ctx, (int64_t)whiten_trsm_simt_scratch_bytes(B), &ok);
   if (ctx->split_syrk) ctx->hr = (uint8_t*)dalloc(ctx, (int64_t)syrk_split_bytes(L, ctx->W, ctx->B), &ok);
+  if (ctx->tc_factor) ctx->ffm = (float2*)dalloc(ctx, (int64_t)tcf_form_scratch_bytes((int)Lf, ctx->B), &ok);
   ctx->y0 = (float*)dalloc(ctx, Lf * Bp * 4, &ok);
   ctx->inv_s2 = (float*)dalloc(ctx, Lf * 4, &ok);
   ctx->status = (int32_t*)dalloc(ctx, std::max(Ls, Lf) * 4, &ok);
@@ -795,10 +798,10 @@ int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* ou
 // context, so a line's factor does not depend on how lines are batched).
 int factor_lines(hsad_ctx* ctx, double* sigma, double* inv, const double* m, int L, void* wmat, float* y0,
                  float* inv_s2, int32_t* status, int64_t n0, int W, int incl, const int64_t* n0_dev, int every,
-                 int q_off, const double* n_line) {
+                 int q_off, const double* n_line, bool formed = false) {
   if (ctx->tc_factor) {
     static const char* names[4] = {"factor_form", "factor_diag", "factor_panel", "factor_update"};
-    for (int s = 0; s < factor_tc_steps(ctx->B); ++s)
+    for (int s = formed ? 1 : 0; s < factor_tc_steps(ctx->B); ++s)
       KL(names[factor_tc_step_kind(s)],
          launch_factor_tc_step(s, sigma, inv, m, L, ctx->B, ctx->prec, wmat, y0, inv_s2, status, n0, W, incl,
                                ctx->stream, &ctx->lc, n0_dev, every, q_off, n_line, ctx->dev_err));
@@ -833,12 +836,20 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, 1,
                                        ctx->min_pix, ctx->status + 1, st, &ctx->lc, n0_dev, gain, ctx->c_int,
                                        ctx->lam, n_line));
-  KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc, gain, ctx->s1_line,
-                                     ctx->c_int, W, ctx->lam));
+  // the tensor-core factor takes its covariances formed in the prefix pass (integer sums only)
+  const bool fused = ctx->tc_factor && !gain && !n_line;
+  if (fused) {
+    KL("prefix_cov", launch_tcf_prefix_form(ctx->sigma + BB, ctx->state_s2, L, B, 1, ctx->m_line, ctx->n_stats, W,
+                                            1, n0_dev, ctx->ffm, st, &ctx->lc));
+  } else {
+    KL("prefix_cov", launch_prefix_cov(ctx->sigma + BB, ctx->state_s2, L, B, 1, st, &ctx->lc, gain, ctx->s1_line,
+                                       ctx->c_int, W, ctx->lam));
+  }
   {
     const int rc_f = factor_lines(ctx, ctx->sigma + BB, ctx->inv + BB, ctx->m_line, L,
-                                    (char*)ctx->wmat + (size_t)Bp * Bp * wmat_elem_bytes(ctx->prec), ctx->y0 + Bp, ctx->inv_s2 + 1, ctx->status + 1,
-                                    ctx->n_stats, W, 1, n0_dev, ctx->every, q0 + 1, n_line);
+                                  (char*)ctx->wmat + (size_t)Bp * Bp * wmat_elem_bytes(ctx->prec), ctx->y0 + Bp,
+                                  ctx->inv_s2 + 1, ctx->status + 1, ctx->n_stats, W, 1, n0_dev, ctx->every, q0 + 1,
+                                  n_line, fused);
     if (rc_f != HSAD_OK) return rc_f;
   }
   if (L > 1) {
@@ -957,11 +968,17 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
   if (n_line) KL("forget_n", launch_forget_n(ctx->n_eff, ctx->lam, W, L, incl, ctx->d_nline, st, &ctx->lc));
   KL("prefix_mean", launch_prefix_mean(ctx->s1_line, ctx->m_line, ctx->state_s1, ctx->n_stats, W, L, B, incl,
                         ctx->min_pix, ctx->status, st, &ctx->lc, nullptr, gain, ctx->c_int, ctx->lam, n_line));
-  KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc, gain, ctx->s1_line,
-                                     ctx->c_int, W, ctx->lam));
+  const bool fused = ctx->tc_factor && !gain && !n_line;
+  if (fused) {
+    KL("prefix_cov", launch_tcf_prefix_form(ctx->sigma, ctx->state_s2, L, B, incl, ctx->m_line, ctx->n_stats, W,
+                                            incl, nullptr, ctx->ffm, st, &ctx->lc));
+  } else {
+    KL("prefix_cov", launch_prefix_cov(ctx->sigma, ctx->state_s2, L, B, incl, st, &ctx->lc, gain, ctx->s1_line,
+                                       ctx->c_int, W, ctx->lam));
+  }
   {
     const int rc_f = factor_lines(ctx, ctx->sigma, ctx->inv, ctx->m_line, L, ctx->wmat, ctx->y0, ctx->inv_s2,
-                                    ctx->status, ctx->n_stats, W, incl, nullptr, 1, 0, n_line);
+                                  ctx->status, ctx->n_stats, W, incl, nullptr, 1, 0, n_line, fused);
     if (rc_f != HSAD_OK) return rc_f;
   }
   {

@@ -186,6 +186,14 @@ cudaError_t launch_factor(double* sigma, double* scratch, const double* m,
 bool factor_tc_supported(int B, int prec);
 int factor_tc_steps(int B);
 int factor_tc_step_kind(int step);  // 0 covariance, 1 diagonal block, 2 rows below, 3 update
+// The prefix of a batch's integer covariance sums (as launch_prefix_cov without gains or
+// forgetting) with each line's covariance formed in place for the tensor-core factor (its
+// step 0, which is then skipped): m, n0, W, incl, n0_dev as for the factor; ffm scratch of
+// tcf_form_scratch_bytes(L, B).
+size_t tcf_form_scratch_bytes(int L, int B);
+cudaError_t launch_tcf_prefix_form(double* buf, double* state_s2, int L, int B, int inclusive, const double* m,
+                                   int64_t n0, int W, int incl, const int64_t* n0_dev, float2* ffm,
+                                   cudaStream_t st, LaunchCounter* lc);
 cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, const double* m, int L, int B, int prec,
                                   void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
                                   int incl, cudaStream_t st, LaunchCounter* lc, const int64_t* n0_dev, int every,

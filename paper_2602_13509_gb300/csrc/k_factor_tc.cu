@@ -234,6 +234,74 @@ __global__ void tcf_form_kernel(double* __restrict__ sigma_all, const double* __
   }
 }
 
+// ---- running sums and covariance formation in one pass ---------------------------------
+// Streamed statistics without gains or forgetting: the prefix over a batch's lines of the
+// integer sums (S2 of lines so far, FP64, exact) and the formation of each line's covariance
+// from it, (S2 - n m m^T) / (n - 1) as float-float, by one thread per lower-triangle entry
+// walking the lines, so that the FP64 prefix is never written and re-read. The per-line
+// float-float means, n m and 1 / (n - 1) come from a small pass first (FP64 conversions
+// are slow here): ffm[t] = {m_0 .. m_B-1, n m_0 .. n m_B-1, 1 / (n - 1)}.
+__global__ void tcf_form_prep_kernel(const double* __restrict__ m_all, int L, int B, int64_t n0_arg, int W,
+                                     int incl, const int64_t* __restrict__ n0_dev, float2* __restrict__ ffm) {
+  const int t = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L) return;
+  const double nn = (double)((n0_dev ? *n0_dev : n0_arg) + (int64_t)(t + incl) * W);
+  float2* f = ffm + (int64_t)t * (2 * B + 1);
+  if (i < B) {
+    const double mi = m_all[(int64_t)t * B + i];
+    f[i] = dff(mi);
+    f[B + i] = dff(nn * mi);
+  }
+  if (i == 0) f[2 * B] = dff(1.0 / (nn - 1.0));
+}
+
+// A double (normal in FP32's range, or zero) as a float-float pair by integer operations on
+// its bits (the FP64 pipe, and FP64 -> FP32 conversion, issue at 1/64 of the FP32 rate
+// here): hi = the value truncated to 24 significant bits (exact), lo = the remaining 29 bits
+// rounded to FP32, a relative error below 2^-47 of the value.
+__device__ __forceinline__ float2 double_to_ff_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+  if (((b >> 52) & 0x7ff) == 0 || ex < -126) return make_float2(0.f, 0.f);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFULL;
+  const float hi = __uint_as_float(sign | ((unsigned int)(ex + 127) << 23) | (unsigned int)(mant >> 29));
+  float lo = ldexpf((float)(int)(mant & 0x1FFFFFFFULL), ex - 52);
+  lo = sign ? -lo : lo;
+  return make_float2(hi, lo);
+}
+
+__global__ void tcf_prefix_form_kernel(double* __restrict__ buf, double* __restrict__ state_s2, int L, int B,
+                                       int inclusive, const float2* __restrict__ ffm) {
+  const int64_t BB = (int64_t)B * B;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // lower-triangle entry q = tri(i) + j
+  if (q >= B * (B + 1) / 2) return;
+  int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+  while (tri(i + 1) <= q) ++i;
+  while (tri(i) > q) --i;
+  const int j = q - tri(i);
+  const int64_t e = (int64_t)i * B + j;
+  double run = state_s2[e];
+  constexpr int U = 8;  // lines whose loads are in flight together
+  for (int t0 = 0; t0 < L; t0 += U) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = (t0 + u < L) ? buf[(int64_t)(t0 + u) * BB + e] : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u;
+      if (t >= L) break;
+      const double before = run;
+      run += v[u];
+      const double S = inclusive ? run : before;
+      const float2* f = ffm + (int64_t)t * (2 * B + 1);
+      const float2 out = ff_mul(ff_sub(double_to_ff_bits(S), ff_mul(f[B + i], f[j])), f[2 * B]);
+      reinterpret_cast<float2*>(buf)[(int64_t)t * BB + e] = out;
+    }
+  }
+  state_s2[e] = run;
+}
+
 // ---- diagonal block -----------------------------------------------------------------------
 // One CTA of TD_T threads per line: the 64 x 64 diagonal block of panel k, as packed lower
 // triangles in shared memory, factored and inverted together, right-looking, a column at a
@@ -669,6 +737,20 @@ bool factor_tc_supported(int B, int prec) { return is_trsm(prec) && B >= 192; }
 // but the last, the rows below and the trailing update: 1 + 3 nb - 2 launches.
 int factor_tc_steps(int B) { return 3 * (pad64(B) / 64) - 1; }
 int factor_tc_step_kind(int step) { return step == 0 ? 0 : 1 + (step - 1) % 3; }
+
+size_t tcf_form_scratch_bytes(int L, int B) { return (size_t)L * (2 * B + 1) * sizeof(float2); }
+
+cudaError_t launch_tcf_prefix_form(double* buf, double* state_s2, int L, int B, int inclusive, const double* m,
+                                   int64_t n0, int W, int incl, const int64_t* n0_dev, float2* ffm,
+                                   cudaStream_t st, LaunchCounter* lc) {
+  if (L <= 0) return cudaSuccess;
+  tcf_form_prep_kernel<<<dim3((B + 127) / 128, L), 128, 0, st>>>(m, L, B, n0, W, incl, n0_dev, ffm);
+  if (lc) lc->n += 1;
+  const int nq = B * (B + 1) / 2;
+  tcf_prefix_form_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(buf, state_s2, L, B, inclusive, ffm);
+  if (lc) lc->n += 1;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, const double* m, int L, int B, int prec,
                                   void* wmat, float* y0, float* inv_s2, int32_t* status, int64_t n0, int W,
