@@ -44,7 +44,10 @@
 namespace hsad {
 
 namespace {
-constexpr int TS_M = 128, TS_KB = 64, TS_THREADS = 192, TS_MAX_STAGES = 10;
+constexpr int TS_M = 128, TS_KB = 64, TS_MAX_STAGES = 10;
+// converter warps: TMEM lane group (w & 3, 32 pixels) x half (w >> 2) of each 64-band block
+constexpr int TS_CW = 8, TS_CONV = 32 * TS_CW;
+constexpr int TS_TMA_WARP = TS_CW, TS_MMA_WARP = TS_CW + 1, TS_THREADS = 32 * (TS_CW + 2);
 constexpr uint32_t TS_BLK = TS_M * TS_KB * 2;  // one 128 x 64 16-bit operand block: 16 KB
 constexpr uint32_t TS_HALF = 64 * TS_KB * 2;   // one 64 x 64 16-bit block of H: 8 KB
 constexpr uint32_t TS_BAR = 256;
@@ -153,9 +156,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
       tc::mbar_init(b_full + 8 * s, 1);
       tc::mbar_init(b_empty + 8 * s, 1);
     }
-    tc::mbar_init(z_full, TS_M);
+    tc::mbar_init(z_full, TS_CONV);
     tc::mbar_init(y_full, 1);
-    tc::mbar_init(ya_full, TS_M);
+    tc::mbar_init(ya_full, TS_CONV);
     tc::mbar_init(acc_full, 1);
     tc::mbar_init(done, 1);
     tc::mbar_init_fence();
@@ -164,14 +167,14 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   const float* mf = out.m_line ? out.m_line + (int64_t)t * Bp : m_all + (int64_t)f * Bp;
   for (int n = tid; n < Bp; n += TS_THREADS)
     cmS[n] = make_int2(0x4B400000 - (n < B ? c_int[n] : 0), __float_as_int(n < B ? mf[n] : 0.f));
-  if (warp == 5) tc::tmem_alloc(tc::smem_u32(tslot), tcols);
+  if (warp == TS_MMA_WARP) tc::tmem_alloc(tc::smem_u32(tslot), tcols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   bool ok = true;
 
-  if (warp == 4) {
+  if (warp == TS_TMA_WARP) {
     // ---------------- TMA: blocks (j, k) of H, j = k .. nkb - 1, k = 0 .. nkb - 1 ----------
     if (lane == 0) {
       // the tile's raw values (contiguous) into L2 at once: the converters then read each
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
       }
       if (!ok) atomicExch(err, 1);
     }
-  } else if (warp == 5) {
+  } else if (warp == TS_MMA_WARP) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_f16(1, TS_M, 64);
@@ -248,24 +251,25 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
       if (!tc::mbar_wait(done, 0, limit)) atomicExch(err, 1);  // MMAs finished before TMEM is freed
     }
   } else {
-    // ---------------- warps 0-3: one pixel each ----------------
-    const int r = tid;
+    // ---------------- converter warps: one pixel and 32 bands of each block each ----------------
+    const int lg = warp & 3, hh = warp >> 2, cs = 32 * hh;
+    const int r = 32 * lg + lane;
     const bool rv = r < npx;
-    const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
-    // this pixel's raw values of bands [64 k, 64 k + 64) as 32 packed pairs (zero past B and
-    // for pixels past the tile); 4-byte loads when every row starts 4-byte aligned
+    const uint32_t taddr = tbase + ((uint32_t)(lg * 32) << 16);
+    // this pixel's raw values of bands [64 k + cs, 64 k + cs + 32) as 16 packed pairs (zero
+    // past B and for pixels past the tile); 4-byte loads when every row starts 4-byte aligned
     const uint16_t* px = xt + (int64_t)r * B;
     const bool pairs = (B & 1) == 0 && ((uintptr_t)x & 3) == 0;
-    uint32_t rw[32];
+    uint32_t rw[16];
     auto load_raw = [&](int k) {
-      const int nb = rv ? min(TS_KB, B - k * TS_KB) : 0;
-      const uint16_t* pk = px + k * TS_KB;
+      const int nb = rv ? min(TS_KB, B - k * TS_KB) - cs : 0;
+      const uint16_t* pk = px + k * TS_KB + cs;
       if (pairs) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) rw[i] = 2 * i < nb ? __ldg((const uint32_t*)pk + i) : 0u;
+        for (int i = 0; i < 16; ++i) rw[i] = 2 * i < nb ? __ldg((const uint32_t*)pk + i) : 0u;
       } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < 16; ++i) {
           const uint32_t lo = 2 * i < nb ? __ldg(pk + 2 * i) : 0u;
           const uint32_t hi = 2 * i + 1 < nb ? __ldg(pk + 2 * i + 1) : 0u;
           rw[i] = lo | (hi << 16);
@@ -275,34 +279,33 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     load_raw(0);
     float dsum = 0.f;
     for (int k = 0; k < nkb; ++k) {
-      float a[64];
+      float a[32];
       if (k > 0) {
         if (ok && !tc::mbar_wait(acc_full, (uint32_t)((k - 1) & 1), limit)) ok = false;
         __syncwarp();
         tc::fence_after_sync();
-        tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB), a);
-        tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB + 32), a + 32);
+        tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB + cs), a);
       } else {
 #pragma unroll
-        for (int i = 0; i < 64; ++i) a[i] = 0.f;
+        for (int i = 0; i < 32; ++i) a[i] = 0.f;
       }
       // z_k = (x' - m) - acc, x' = DN - c exact in FP32: the bits of 1.5 * 2^23 + x' minus
       // 1.5 * 2^23 (integer add + float subtract, no conversion instruction). Bands past B
       // give 0 (raw 0, c = m = 0, acc 0); pixels past the tile give values never stored.
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < 4; ++q) {
         const uint32_t w4[4] = {rw[4 * q], rw[4 * q + 1], rw[4 * q + 2], rw[4 * q + 3]};
         float zv[8];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int n = k * TS_KB + 8 * q + 2 * j;
+          const int n = k * TS_KB + cs + 8 * q + 2 * j;
           const int4 cm = *(const int4*)&cmS[n];  // bands n, n + 1
           const float x0 = __int_as_float(cm.x + (int)(w4[j] & 0xffffu)) - 12582912.0f;
           const float x1 = __int_as_float(cm.z + (int)(w4[j] >> 16)) - 12582912.0f;
           zv[2 * j] = (x0 - __int_as_float(cm.y)) - a[8 * q + 2 * j];
           zv[2 * j + 1] = (x1 - __int_as_float(cm.w)) - a[8 * q + 2 * j + 1];
         }
-        store_split<NT>(sZ, tc::sw128_offset(r, 8 * q), zv);
+        store_split<NT>(sZ, tc::sw128_offset(r, cs + 8 * q), zv);
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
@@ -312,22 +315,31 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
       if (ok && !tc::mbar_wait(y_full, (uint32_t)(k & 1), limit)) ok = false;
       __syncwarp();
       tc::fence_after_sync();
-      tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB), a);
-      tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB + 32), a + 32);
+      tc::tmem_ld32(taddr + (uint32_t)(k * TS_KB + cs), a);
 #pragma unroll
-      for (int i = 0; i < 64; ++i) dsum = fmaf(a[i], a[i], dsum);
+      for (int i = 0; i < 32; ++i) dsum = fmaf(a[i], a[i], dsum);
       if (k + 1 < nkb) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) store_split<NT>(sY, tc::sw128_offset(r, 8 * q), a + 8 * q);
+        for (int q = 0; q < 4; ++q) store_split<NT>(sY, tc::sw128_offset(r, cs + 8 * q), a + 8 * q);
         tc::fence_proxy_async();
         tc::fence_before_sync();
         tc::mbar_arrive(ya_full);
       }
     }
     if (!ok) atomicExch(err, 1);
+    // the two halves' sums of squares (NaN where a wait gave up)
+    // sZ holds them: once `done` completes every MMA (the last ones waited for every
+    // converter's z) has finished reading the operand blocks
+    float* red = reinterpret_cast<float*>(sZ);
+    const bool dn = tc::mbar_wait(done, 0, limit);
+    tc::fence_after_sync();
+    if (!ok || !dn) dsum = __int_as_float(0x7fc00000);
+    red[hh * TS_M + r] = dsum;
+    asm volatile("bar.sync 1, %0;" ::"n"(TS_CONV) : "memory");
     const int p = p0 + r;
-    if (p < W) {
-      float dlt = ok ? dsum * inv_s2_all[f] : __int_as_float(0x7fc00000);
+    if (hh == 0 && p < W) {
+      const float tot = red[r] + red[TS_M + r];
+      float dlt = tot == tot ? tot * inv_s2_all[f] : __int_as_float(0x7fc00000);
       if (out.line_scale) dlt *= out.line_scale[t];
       out.scores[slot * W + p] = dlt;
       if (out.write_mask) out.mask[slot * W + p] = dlt > out.tau ? 1 : 0;
@@ -336,7 +348,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 5) {
+  if (warp == TS_MMA_WARP) {
     __syncwarp();
     tc::tmem_dealloc(tbase, tcols);
   }
