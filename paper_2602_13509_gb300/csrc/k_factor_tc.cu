@@ -63,7 +63,7 @@ __host__ __device__ inline size_t plane_bytes(int Bp) { return (size_t)(Bp + 64)
 __host__ __device__ inline size_t xdig_offset(int Bp) { return NDIG * plane_bytes(Bp) + (size_t)(Bp + 64) * 4; }
 constexpr uint32_t XDIG_BYTES = NDIG * TU_B_PLANE + 64 * 4;
 __host__ __device__ inline size_t slice_region_bytes(int Bp) { return xdig_offset(Bp) + XDIG_BYTES; }
-constexpr int TD_T = 128;            // threads per line of the diagonal-block kernel
+constexpr int TD_T = 256;            // threads per line of the diagonal-block kernel
 constexpr int TRI64 = 64 * 65 / 2;   // a packed 64 x 64 lower triangle
 __host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
 
@@ -306,7 +306,7 @@ __global__ void tcf_prefix_form_kernel(double* __restrict__ buf, double* __restr
 // One CTA of TD_T threads per line: the 64 x 64 diagonal block of panel k, as packed lower
 // triangles in shared memory, factored and inverted together, right-looking, a column at a
 // time: the pivot l = sqrt(A_jj) and r = 1 / l (float-float Newton step from the FP32 rsqrt
-// seed, computed by every thread), column j of L = A_.j r, row j of X = R_j. r (R: the
+// seed, computed by one thread), column j of L = A_.j r, row j of X = R_j. r (R: the
 // running right-hand sides, I at the start), then the rank-1 updates A_ic -= L_ij L_cj
 // (j < c <= i) and R_ic -= L_ij X_jc (i > j, c <= j) over the flattened trapezoid of rows
 // j + 1 .. kb - 1. Writes X's digits (per-row power of two, six base-256 digits) to the
@@ -318,9 +318,12 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
                                                         int32_t* __restrict__ status, int every, int q_off,
                                                         void* __restrict__ wmat, float* __restrict__ y0_all,
                                                         float* __restrict__ inv_s2_all) {
-  __shared__ float2 Dg[TRI64];  // L_kk, packed: (i, c) at tri(i) + c
-  __shared__ float2 X[TRI64];   // R, then X = L_kk^{-1}, packed
+  __shared__ float2 S[2 * TRI64];  // L_kk then R (later X = L_kk^{-1}), packed: (i, c) at tri(i) + c
   __shared__ uint8_t row_of[TRI64];
+  __shared__ float2 rs;            // 1 / l_jj of the current column
+  __shared__ int not_pd;
+  float2* Dg = S;
+  float2* X = S + TRI64;
   const int t = blockIdx.x, tid = threadIdx.x;
   if (skip_line(status, t, every, q_off)) return;  // the same for the whole CTA
   const int Bp = pad64(B), p = 64 * k, kb = min(64, B - p);
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
     for (int n = tid; n < Bp; n += TD_T) y0_all[(int64_t)t * Bp + n] = n < B ? (float)m_all[(int64_t)t * B + n] : 0.f;
     if (tid == 0) inv_s2_all[t] = 1.0f;
   }
+  if (tid == 0) not_pd = 0;
   for (int e = tid; e < TRI64; e += TD_T) {
     int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
     while (tri(i + 1) <= e) ++i;
@@ -345,20 +349,26 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
   }
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    const float2 a = Dg[tri(j) + j];
-    if (!(a.x > 0.f) || !isfinite(a.x)) {  // the same value in every thread
+    if (tid < 32) {  // the pivot, by one warp: r = 1 / sqrt(a), l_jj = a r
+      const float2 a = Dg[tri(j) + j];
+      if (!(a.x > 0.f) || !isfinite(a.x)) {
+        if (tid == 0) not_pd = 1;
+      } else if (tid == 0) {
+        // FP32 seed, one Newton step r += r (1 - a r^2) / 2 in float-float (the seed's relative
+        // error, below 2^-22, squares to below 2^-44: the order of the six-digit updates' 2^-45)
+        float2 r = make_float2(rsqrtf(a.x), 0.f);
+        const float2 ee = ff_sub(make_float2(1.f, 0.f), ff_mul(a, ff_mul(r, r)));
+        r = ff_sub(r, ff_mul(r, make_float2(-0.5f * ee.x, -0.5f * ee.y)));
+        rs = r;
+        Dg[tri(j) + j] = ff_mul(a, r);  // read by nobody during this step
+      }
+    }
+    __syncthreads();
+    if (not_pd) {  // the same value in every thread
       if (tid == 0) status[t] = LS_NOT_PD;
       return;
     }
-    // r = 1 / sqrt(a): FP32 seed, one Newton step r += r (1 - a r^2) / 2 in float-float (the
-    // seed's relative error, below 2^-22, squares to below 2^-44: the order of the six-digit
-    // updates' 2^-45); l = a r
-    float2 r = make_float2(rsqrtf(a.x), 0.f);
-    {
-      const float2 ee = ff_sub(make_float2(1.f, 0.f), ff_mul(a, ff_mul(r, r)));
-      r = ff_sub(r, ff_mul(r, make_float2(-0.5f * ee.x, -0.5f * ee.y)));
-    }
-    __syncthreads();  // every thread has read the pivot
+    const float2 r = rs;
     // column j of L below the pivot, row j of X
     const int nl = kb - 1 - j;
     if (tid < nl) {
@@ -367,21 +377,20 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
     } else if (tid - nl <= j) {
       const int c = tid - nl;
       X[tri(j) + c] = ff_mul(X[tri(j) + c], r);
-    } else if (tid == 127) {
-      Dg[tri(j) + j] = ff_mul(a, r);
     }
     __syncthreads();
-    // rank-1 update of rows j + 1 .. kb - 1: X columns c <= j, L columns c > j
+    // rank-1 update of rows j + 1 .. kb - 1: X columns c <= j, L columns c > j (one shared
+    // array indexed by offset, so that every access is a shared-memory one)
     const int e0 = tri(j + 1), e1 = tri(kb);
     for (int e = e0 + tid; e < e1; e += TD_T) {
       const int i = row_of[e], c = e - tri(i);
       const bool inx = c <= j;
-      float2* base = inx ? X : Dg;
-      const float2 lij = Dg[tri(i) + j];
-      const float2 y = inx ? X[tri(j) + c] : Dg[tri(c) + j];
-      float2 v = base[e];
+      const int off = inx ? TRI64 : 0;
+      const float2 lij = S[tri(i) + j];
+      const float2 y = S[inx ? TRI64 + tri(j) + c : tri(c) + j];
+      float2 v = S[off + e];
       ff_fms(v.x, v.y, lij, y);
-      base[e] = ff_norm(v.x, v.y);
+      S[off + e] = ff_norm(v.x, v.y);
     }
     __syncthreads();
   }
