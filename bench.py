@@ -54,11 +54,34 @@ def load_peaks():
                 sm_max_mhz=2070.0)
 
 
-# DRAM bytes per line of the factor kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of a small launch divided by its lines), scaled to a launch by its
-# lines; keyed by (band count, whitening form: 1 = triangular solve). A form without a
-# capture of the current kernel reports null.
-FACTOR_DRAM_BYTES_PER_LINE = {}
+# DRAM bytes per unit (line or pixel) of a kernel class from one ncu capture of the same
+# kernels on a 256-line batch of the precision_1024x448 workload in the FP32 form
+# (dram__bytes_read.sum + dram__bytes_write.sum summed over the class's launches of one
+# batch, divided by its lines or pixels); per-launch traffic = that x units per step /
+# launches per step. Work and traffic per unit do not depend on the batch size. Only this
+# workload and form, and only kernels unchanged since the capture, have an entry; the rest
+# report null.
+DRAM_BYTES_PER_UNIT = {
+    ("precision_1024x448", "fp32"): {
+        "factor_update": ("line", 3.541e6),
+        "factor_panel": ("line", 1.940e6),
+        "syrk": ("px", 2768.0),
+        "syrk_split": ("px", 2716.0),
+        "whiten_score": ("px", 1661.0),
+    },
+}
+
+# BF16 tensor-core products issued per algorithmic product by each contraction's exact or
+# extended-precision scheme: the peak of that arithmetic on this GPU is the BF16 peak divided
+# by it (the kernel's own dtype; reported beside the plain BF16 fraction).
+TERMS = {
+    "factor_update": 21,    # six base-256 digits per operand, levels t + u <= 5
+    "factor_panel": 21,
+    "syrk": 4,              # x' = 64 h + r: HH, HR, RH, RR
+    "whiten_fp32": 6,       # three BF16 terms per operand, products with t + u <= 2
+    "whiten_bf16": 3,       # a_hi h_hi + a_hi h_lo + a_lo h_hi
+    "whiten_fp16": 2,
+}
 
 
 def factor_flops_per_line(B, form):
@@ -202,15 +225,27 @@ def whitening_label(form, tc):
     return ("triangular solve" if form else "explicit inverse") + (", tensor cores" if tc else ", SIMT cores")
 
 
-def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, tc_whiten=None):
-    """Roofline entries of the factor (whole, or its covariance, panel and update kernels),
-    covariance (SYRK) and whitening kernels of one arm: algorithmic work per step (per-unit
-    figures x units per step) over the kernel class's CUDA-event time per step, against the
-    peak of the unit that bounds it."""
+def tensor_peak(peaks, terms):
+    """Peak of a contraction whose scheme issues `terms` BF16 products per algorithmic product,
+    timed inside full steps: the measured sustained BF16 rate divided by `terms`."""
+    return peaks["bf16_tflops_sustained"] / terms
+
+
+def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, tc_whiten=None, workload=None):
+    """Roofline entries of the factor (whole, or its covariance, diagonal-block, panel and
+    update kernels), covariance (SYRK and its split) and whitening kernels of one arm:
+    algorithmic work per step (per-unit figures x units per step) over the kernel class's
+    CUDA-event time per step (measured inside full steps), against the peak of the unit and
+    dtype that bound it. A tensor-core contraction computing exact or extended-precision
+    products from BF16 terms takes the sustained BF16 peak divided by the BF16 products it
+    issues per algorithmic product; `frac_of_bf16_peak` gives the plain BF16 fraction."""
     out = {}
     px_step = T * W
     lines = T / max(1, every)                    # factorisations per step
     ffp = ff_peak_tflops(mhz)
+    sus = peaks["bf16_tflops_sustained"]
+    src_t = f"{peaks['source']} bf16 sustained"
+    dram = DRAM_BYTES_PER_UNIT.get((workload, prec), {})
     for name, (n, tot) in prof.items():
         if n == 0 or name not in ("factor", "factor_form", "factor_diag", "factor_panel", "factor_update", "syrk",
                                    "syrk_split", "whiten_score"):
@@ -229,27 +264,27 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, t
                  "peak_source": "derived: 152 SMs x %.0f MHz x 128 FP32 lanes x 2 flop / 12 FP32 instructions "
                                 "per float-float multiply-subtract" % mhz,
                  "fp64_peak_derived": fp64_peak_tflops(mhz), "frac_of_fp64_peak": ach / fp64_peak_tflops(mhz)}
-        elif name in ("factor_diag", "factor_panel"):
-            diag = name == "factor_diag"
-            work = lines * factor_parts_per_line(B)[0 if diag else 1]
+        elif name == "factor_diag":
+            work = lines * factor_parts_per_line(B)[0]
             ach = work / (ms / 1e3) / 1e12
             r = {"bound": "alu", "achieved": ach, "peak": ffp, "unit": "TFLOP/s", "frac": ach / ffp,
-                 "kernel": ("factor diagonal blocks (64 x 64 Cholesky + inverse, float-float on the CUDA cores)"
-                            if diag else "factor panels (rows' triangular solve as a float-float product with "
-                            "the diagonal block's inverse, six-digit split)"),
-                 "work_per_step": (f"{lines:.0f} lines x sum over panels 2 kb^3/3 flop" if diag
-                                   else f"{lines:.0f} lines x sum over panels r kb^2 flop"),
+                 "kernel": "factor diagonal blocks (64 x 64 Cholesky + inverse, float-float on the CUDA cores)",
+                 "work_per_step": f"{lines:.0f} lines x sum over panels 2 kb^3/3 flop",
                  "peak_source": "derived: 152 SMs x %.0f MHz x 128 FP32 lanes x 2 flop / 12 FP32 instructions "
                                 "per float-float multiply-subtract" % mhz}
-        elif name == "factor_update":
-            work = lines * factor_parts_per_line(B)[2]
+        elif name in ("factor_panel", "factor_update"):
+            upd = name == "factor_update"
+            work = lines * factor_parts_per_line(B)[2 if upd else 1]
             ach = work / (ms / 1e3) / 1e12
-            pk = peaks["bf16_tflops"]
+            pk = tensor_peak(peaks, TERMS[name])
             r = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                 "kernel": "factor trailing updates (tcgen05, six-digit exact BF16 split: 21 digit-product "
-                           "MMAs per algorithmic product)",
-                 "work_per_step": f"{lines:.0f} lines x (B^3/3 - panel Cholesky flops) algorithmic flop",
-                 "issued_tflops": 21 * ach, "peak_source": f"{peaks['source']} bf16 burst"}
+                 "kernel": ("factor trailing updates" if upd else "factor panels (rows below the diagonal blocks: "
+                            "L_ik = A_ik L_kk^-T)") + " on tcgen05, six-digit exact BF16 splits: 21 digit-product "
+                            "MMAs per float-float-accurate product",
+                 "work_per_step": (f"{lines:.0f} lines x (B^3/3 - panel Cholesky flops) algorithmic flop" if upd
+                                   else f"{lines:.0f} lines x sum over panels r kb^2 algorithmic flop"),
+                 "issued_tflops": TERMS[name] * ach, "frac_of_bf16_peak": ach / sus,
+                 "peak_source": f"{src_t} / {TERMS[name]} (BF16 products per product)"}
         elif name == "syrk_split":
             byts = px_step * (2 * B + 4 * (-(-B // 128) * 128))
             ach = byts / (ms / 1e3) / 1e9
@@ -270,18 +305,27 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, t
             ach = flops / (ms / 1e3) / 1e12
             tcw = (prec != "fp32") if tc_whiten is None else tc_whiten
             if name == "whiten_score" and not tcw:
-                pk, bound, src = fp32_peak_tflops(mhz), "alu", "derived: 152 SMs x %.0f MHz x 128 FFMA x 2" % mhz
+                pk, bound, src, terms = fp32_peak_tflops(mhz), "alu", \
+                    "derived: 152 SMs x %.0f MHz x 128 FFMA x 2" % mhz, None
             else:
-                pk, bound, src = peaks["bf16_tflops"], "tensor", f"{peaks['source']} bf16 burst"
+                terms = TERMS["syrk"] if name == "syrk" else TERMS["whiten_" + prec]
+                pk, bound = tensor_peak(peaks, terms), "tensor"
+                src = f"{src_t} / {terms} (BF16 products per product)"
             r = {"bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                  "traffic_algorithmic": byts, "kernel": name, "work_per_step": f"{px_step} px x B(B+1) flop",
                  "peak_source": src, "hbm_achieved_gbs": byts / (ms / 1e3) / 1e9,
                  "hbm_frac": byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
-            if name == "whiten_score" and tcw:  # BF16 operand-term products per algorithmic one
-                terms = 6 if prec == "fp32" else 3
+            if terms:
                 r["operand_terms"] = terms
                 r["issued_tflops"] = terms * ach
-        r["traffic"] = None
+                r["frac_of_bf16_peak"] = ach / sus
+        unit = dram.get(name)
+        if unit:
+            per_step = unit[1] * (lines if unit[0] == "line" else px_step)
+            r["traffic"] = per_step / (n / prof_steps)
+            r["traffic_source"] = f"ncu DRAM bytes per {unit[0]} of a 256-line batch x {unit[0]}s per launch"
+        else:
+            r["traffic"] = None
         r["ms_per_step"] = ms
         r["launches_per_step"] = n / prof_steps
         r["avg_launch_ms"] = tot / n
@@ -940,7 +984,7 @@ def main():
 
     mhz = peaks["sm_max_mhz"]
     head_roofs = kernel_rooflines(prof, prof_steps, T, W, B, form, args.precision, args.factor_every, peaks, mhz,
-                                  tcw)
+                                  tcw, args.workload)
     roof = dict(head_roofs[dom]) if dom in head_roofs else None
 
     cpu, ref_line = None, None
@@ -964,7 +1008,7 @@ def main():
                 "whitening": whitening_label(arm["form"], arm["tc"]),
                 "accuracy_vs_oracle": accuracy(arm, prec), "kernels": pk,
                 "rooflines": kernel_rooflines(arm["prof"], prof_steps, T, W, B, arm["form"], prec,
-                                              args.factor_every, peaks, mhz, arm["tc"])}
+                                              args.factor_every, peaks, mhz, arm["tc"], args.workload)}
 
     out = {
         "metric": "pixel-spectra scored/s", "value": value, "unit": "pixel-spectra/s", "n_gpus": world,

@@ -48,16 +48,21 @@ typedef enum {
 
 /* input element type */
 enum { HSAD_U16 = 0, HSAD_F32 = 1 };
-/* working precision of the whitening contraction (the covariance sums are exact
- * for HSAD_U16 input in every mode; the covariance, the Cholesky pivots and the 16 x 16
- * diagonal blocks are FP64 in every precision, and the O(B^3) factor work follows
- * factor_precision) */
+/* working precision of the whitening contraction (the covariance sums are exact for
+ * HSAD_U16 input in every mode; the factor's arithmetic follows factor_precision). HSAD_FP32
+ * with uint16 input, the float-float factor and B >= 192 on streamed statistics runs the
+ * contraction on the tensor cores with every FP32 operand split exactly into three BF16
+ * terms (the products kept to FP32 rounding); otherwise FP32 runs on the SIMT cores.
+ * HSAD_BF16 and HSAD_FP16 keep two-term operands (about 16 significant bits). */
 enum { HSAD_FP32 = 0, HSAD_BF16 = 1, HSAD_FP16 = 2 };
-/* arithmetic of the factor's O(B^3) work (trailing updates, row solves, inverse
- * substitutions; Sec. 3.3 needs Sigma^{-1}): float-float, pairs of FP32 values with about
- * 48 significant bits and FP32's exponent range, on the FP32 pipe (default); or FP64 (53
- * bits), at about half the factor throughput on this GPU, whose FP64 rate is 1/64 of its
- * FP32 rate. */
+/* arithmetic of the factor (Sec. 3.3 needs Sigma^{-1}): float-float, pairs of FP32 values
+ * with about 48 significant bits and FP32's exponent range (default). For streamed
+ * statistics at B >= 192 its O(B^3) products run on the tensor cores as exact six-digit
+ * BF16 splits (a relative error of about 2^-45 of the row scales per product) and its
+ * 64 x 64 diagonal blocks in float-float on the FP32 pipe; elsewhere the CUDA-core factor
+ * takes FP64 pivots and 16 x 16 diagonal blocks and float-float for the rest. FP64 (53
+ * bits) runs the CUDA-core factor in FP64 throughout, at a fraction of the throughput on
+ * this GPU, whose FP64 rate is 1/64 of its FP32 rate. */
 enum { HSAD_FACTOR_FF = 0, HSAD_FACTOR_FP64 = 1 };
 /* whitening form of a context (Eq. 1, Sec. 3.3), see hsad_whitening_form:
  * HSAD_FORM_INVERSE            y = G x' - y0 with G = s L^{-1}, the full triangular

@@ -39,10 +39,11 @@ def test_roofline_work_and_peaks():
 
 def test_kernel_rooflines_from_a_profile():
     """Per-kernel roofline entries: algorithmic work per step over the class's time per
-    step, against the peak of the unit that bounds each kernel."""
+    step, against the peak of the unit (and, for the tensor cores, the product scheme) that
+    bounds each kernel; measured traffic per launch where a capture exists."""
     sys.path.insert(0, ROOT)
     import bench
-    peaks = {"hbm_gbs": 6753.4, "bf16_tflops": 1849.2, "source": "measured"}
+    peaks = {"hbm_gbs": 6753.4, "bf16_tflops": 1849.2, "bf16_tflops_sustained": 1680.0, "source": "measured"}
     T, W, B = 8000, 1024, 448
     # two steps profiled: factor 4 launches of 2000 lines, syrk 4 launches, whitening 8
     prof = {"factor": (8, 8 * 30.0), "syrk": (8, 8 * 5.0), "whiten_score": (16, 16 * 2.0), "colsum": (8, 1.0)}
@@ -54,29 +55,39 @@ def test_kernel_rooflines_from_a_profile():
     assert f["bound"] == "alu" and abs(f["frac"] - f["achieved"] / bench.ff_peak_tflops(2070.0)) < 1e-12
     s = r["syrk"]
     assert s["bound"] == "tensor" and abs(s["achieved"] - T * W * B * (B + 1) / 0.020 / 1e12) < 1e-9
-    assert abs(s["frac"] - s["achieved"] / 1849.2) < 1e-12
-    assert abs(s["traffic_algorithmic"] - T * W * 2 * B) < 1e-6
+    # exact integer split: four BF16 products per product, against the sustained BF16 rate
+    assert abs(s["peak"] - 1680.0 / 4) < 1e-12 and abs(s["frac"] - s["achieved"] / 420.0) < 1e-12
+    assert abs(s["frac_of_bf16_peak"] - s["achieved"] / 1680.0) < 1e-12
+    assert abs(s["traffic_algorithmic"] - T * W * 2 * B) < 1e-6 and s["traffic"] is None
     w = r["whiten_score"]
     assert w["bound"] == "alu" and abs(w["peak"] - bench.fp32_peak_tflops(2070.0)) < 1e-12
     assert abs(w["traffic_algorithmic"] - T * W * (2 * B + 5)) < 1e-6
     wb = bench.kernel_rooflines(prof, 2, T, W, B, 1, "bf16", 1, peaks, 2070.0)["whiten_score"]
-    assert wb["bound"] == "tensor" and wb["peak"] == 1849.2 and wb["operand_terms"] == 3
+    assert wb["bound"] == "tensor" and abs(wb["peak"] - 560.0) < 1e-9 and wb["operand_terms"] == 3
     # FP32 on the tensor cores (three-term operands): tensor bound, six products per product
     wx = bench.kernel_rooflines(prof, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0, True)["whiten_score"]
-    assert wx["bound"] == "tensor" and wx["operand_terms"] == 6
+    assert wx["bound"] == "tensor" and wx["operand_terms"] == 6 and abs(wx["peak"] - 280.0) < 1e-9
     assert abs(wx["issued_tflops"] - 6 * wx["achieved"]) < 1e-9
     assert bench.whitening_label(1, True) == "triangular solve, tensor cores"
     sp = bench.kernel_rooflines({"syrk_split": (4, 8.0)}, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)["syrk_split"]
     assert sp["bound"] == "hbm" and abs(sp["achieved"] - T * W * (2 * B + 4 * 128 * -(-B // 128)) / 0.004 / 1e9) < 1e-6
+    # measured traffic: bytes per unit x units per step / launches per step, this workload only
+    wt = bench.kernel_rooflines(prof, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0, True,
+                                "precision_1024x448")["whiten_score"]
+    per_px = bench.DRAM_BYTES_PER_UNIT[("precision_1024x448", "fp32")]["whiten_score"][1]
+    assert abs(wt["traffic"] - per_px * T * W / 8) < 1e-3
     # the tensor-core factor's three classes: their algorithmic parts add up to the Cholesky
     diag, trsm, upd = bench.factor_parts_per_line(B)
     blocks = [min(64, B - p) for p in range(0, B, 64)]
     assert abs((upd + diag + trsm - sum(b ** 3 / 3 for b in blocks)) - B ** 3 / 3) < 1e-3
     prof2 = {"factor_form": (8, 8.0), "factor_diag": (56, 10.0), "factor_panel": (48, 30.0),
              "factor_update": (48, 30.0)}
-    r2 = bench.kernel_rooflines(prof2, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)
-    assert r2["factor_update"]["bound"] == "tensor" and r2["factor_panel"]["bound"] == "alu"
+    r2 = bench.kernel_rooflines(prof2, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0, True, "precision_1024x448")
+    assert r2["factor_update"]["bound"] == "tensor" and r2["factor_panel"]["bound"] == "tensor"
+    assert r2["factor_diag"]["bound"] == "alu" and abs(r2["factor_update"]["peak"] - 80.0) < 1e-9
     assert abs(r2["factor_diag"]["achieved"] - 8000 * diag / 0.005 / 1e12) < 1e-9
     assert abs(r2["factor_panel"]["achieved"] - 8000 * trsm / 0.015 / 1e12) < 1e-9
     assert abs(r2["factor_update"]["achieved"] - 8000 * upd / 0.015 / 1e12) < 1e-9
+    per_line = bench.DRAM_BYTES_PER_UNIT[("precision_1024x448", "fp32")]["factor_update"][1]
+    assert abs(r2["factor_update"]["traffic"] - per_line * 8000 / 24) < 1e-3
     assert abs(r2["factor_form"]["achieved"] - 8000 * B * (B + 1) / 2 * 16 / 0.004 / 1e9) < 1e-6
