@@ -103,11 +103,14 @@ __device__ __forceinline__ void split_digits(float2 v, float sc, float (&dg)[NDI
     xl = rem.y;
   }
 }
-// Exponent e with |v| <= mx < 2^e (0 for an all-zero row).
+// Exponent e with |v| <= mx < 2^e (0 for an all-zero row): the biased exponent field of mx
+// minus 126 (frexp's exponent for normal mx; -126, still a bound, for subnormal mx).
 __device__ __forceinline__ int row_exponent(float mx) {
-  int e = 0;
-  if (mx > 0.f) frexpf(mx, &e);
-  return e;
+  return mx > 0.f ? ((__float_as_int(mx) >> 23) & 0xff) - 126 : 0;
+}
+// 2^e as a float: the exponent field directly where 2^e is a normal float.
+__device__ __forceinline__ float pow2f(int e) {
+  return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.f, e);
 }
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -116,16 +119,17 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // 2^(-16) sum_l S_l 256^-l in float-float times 2^e: the digit levels (exact FP32 integers)
 // of one accumulator column combined.
 __device__ __forceinline__ float2 combine_levels(const float (&lev)[NDIG][16], int c, int e) {
+  constexpr float kLevel[NDIG] = {1.f, 0x1p-8f, 0x1p-16f, 0x1p-24f, 0x1p-32f, 0x1p-40f};
   float hs = lev[0][c], hc = 0.f;
 #pragma unroll
   for (int l = 1; l < NDIG; ++l) {
-    const float p = __fmul_rn(lev[l][c], ldexpf(1.f, -8 * l));
+    const float p = __fmul_rn(lev[l][c], kLevel[l]);
     const float s2 = __fadd_rn(hs, p);
     const float z = __fsub_rn(s2, hs);
     hc = __fadd_rn(hc, __fadd_rn(__fsub_rn(hs, __fsub_rn(s2, z)), __fsub_rn(p, z)));
     hs = s2;
   }
-  const float sc = ldexpf(1.f, e - 16);
+  const float sc = pow2f(e - 16);
   return ff_norm(__fmul_rn(hs, sc), __fmul_rn(hc, sc));
 }
 
@@ -266,7 +270,7 @@ __device__ __forceinline__ float2 double_to_ff_bits(double v) {
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
   const unsigned long long mant = b & 0xFFFFFFFFFFFFFULL;
   const float hi = __uint_as_float(sign | ((unsigned int)(ex + 127) << 23) | (unsigned int)(mant >> 29));
-  float lo = ldexpf((float)(int)(mant & 0x1FFFFFFFULL), ex - 52);
+  float lo = (float)(int)(mant & 0x1FFFFFFFULL) * pow2f(ex - 52);  // exact scaling (or flush below FP32's range)
   lo = sign ? -lo : lo;
   return make_float2(hi, lo);
 }
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
     __syncthreads();
     for (int it = tid; it < 64 * 8; it += TD_T) {  // (row c, 8-column group g)
       const int c = it >> 3, g = it & 7;
-      const float sc = ldexpf(1.f, -xe_s[c]);
+      const float sc = pow2f(-xe_s[c]);
       uint32_t pk[NDIG][4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         const int e = row_exponent(mx);
         if (lane == 0) ea[rr + q] = e;
-        const float sc = ldexpf(1.f, -e);
+        const float sc = pow2f(-e);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           float dg[NDIG];
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
       // the row's digits for the trailing updates: 16-byte stores into the swizzled planes
       const int e = row_exponent(mx);
       if (ch == 0) expo[i] = e;
-      const float sc = ldexpf(1.f, -e);
+      const float sc = pow2f(-e);
       for (int g = 4 * ch; g < 4 * ch + 4; ++g) {
         uint32_t pk[NDIG][4];
 #pragma unroll
