@@ -52,6 +52,8 @@ constexpr int TU_T = 32 * (TU_EW + 1);
 constexpr uint32_t TU_A_PLANE = TU_M * TU_K * 2;   // 16 KB
 constexpr uint32_t TU_B_PLANE = TU_N * TU_K * 2;   // 8 KB
 constexpr int TU_AS = TU_N + 1;    // row stride (float2) of the staged trailing tile
+// the update kernel: 16 epilogue warps (TMEM lane group w & 3 x 16-column quarter w >> 2)
+constexpr int UP_EW = 16, UP_MW = UP_EW, UP_T = 32 * (UP_EW + 1);
 constexpr uint32_t TU_TILE = TU_M * TU_AS * 8;
 constexpr uint32_t TU_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + TU_TILE + 256 + 64;
 
@@ -118,7 +120,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 // 2^(-16) sum_l S_l 256^-l in float-float times 2^e: the digit levels (exact FP32 integers)
 // of one accumulator column combined.
-__device__ __forceinline__ float2 combine_levels(const float (&lev)[NDIG][16], int c, int e) {
+template <int W>
+__device__ __forceinline__ float2 combine_levels(const float (&lev)[NDIG][W], int c, int e) {
   constexpr float kLevel[NDIG] = {1.f, 0x1p-8f, 0x1p-16f, 0x1p-24f, 0x1p-32f, 0x1p-40f};
   float hs = lev[0][c], hc = 0.f;
 #pragma unroll
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
 }
 
 // ---- trailing update on the tensor cores ------------------------------------------------
-__global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict__ sigma_all,
+__global__ void __launch_bounds__(UP_T, 1) tcf_update_kernel(double* __restrict__ sigma_all,
                                                              uint8_t* __restrict__ slice_all,
                                                              size_t slice_stride, int B, int k,
                                                              const int32_t* __restrict__ status, int every,
@@ -652,14 +655,14 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
     tc::mbar_init_fence();
   }
   if (tid < 64) ej[tid] = expo[j0 + tid];
-  if (warp == TU_MW) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  if (warp == UP_MW) tc::tmem_alloc(tc::smem_u32(tslot), 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   bool ok = true;
 
-  if (warp == TU_MW) {
+  if (warp == UP_MW) {
     if (lane == 0) {
       tc::mbar_arrive_expect_tx(full, NDIG * (TU_A_PLANE + TU_B_PLANE));
       for (int d = 0; d < NDIG; ++d) {
@@ -689,21 +692,22 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
       }
     }
   } else {
-    // epilogue warps: each stages its 32 rows x 32 columns of the trailing tile (coalesced
-    // row pieces, while the digits load and the MMAs run), then takes one row (= its TMEM
-    // lane) of those columns per thread, then stores them back coalesced
+    // epilogue warps: each stages its 32 rows x 16 columns of the trailing tile (two rows of
+    // 128 contiguous bytes per load instruction, while the digits load and the MMAs run),
+    // then takes one row (= its TMEM lane) of those columns per thread, then stores them
+    // back the way it loaded them
     float2* A = reinterpret_cast<float2*>(sigma_all + (int64_t)t * B * B);
-    const int lg = warp & 3, ch = warp >> 2, cs = 32 * ch;
-    // 16 rows per round: 16 independent loads in flight per lane
-    for (int r0w = lg * 32; r0w < lg * 32 + 32; r0w += 16) {
+    const int lg = warp & 3, cq = warp >> 2, cs = 16 * cq;
+    {
+      const int rr = lane >> 4, cc = cs + (lane & 15);
       float2 v[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int i = i0 + r0w + q, j = j0 + cs + lane;
+        const int i = i0 + 32 * lg + 2 * q + rr, j = j0 + cc;
         v[q] = (i < B && j < B && j <= i) ? A[(int64_t)i * B + j] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) As[(r0w + q) * TU_AS + cs + lane] = v[q];
+      for (int q = 0; q < 16; ++q) As[(32 * lg + 2 * q + rr) * TU_AS + cc] = v[q];
     }
     const bool dok = tc::mbar_wait(done, 0, limit);
     __syncwarp();
@@ -712,13 +716,13 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
     const int row = 32 * lg + lane, i = i0 + row;
     const int ei = expo[i];  // i < Bp + 64: the region's exponent rows
     const uint32_t taddr = tbase + ((uint32_t)(32 * lg) << 16);
-    for (int c0 = cs; c0 < cs + 32; c0 += 16) {
-      float lev[NDIG][16];
+    for (int c0 = cs; c0 < cs + 16; c0 += 8) {
+      float lev[NDIG][8];
 #pragma unroll
-      for (int l = 0; l < NDIG; ++l) tc::tmem_ld16(taddr + (uint32_t)(64 * l + c0), lev[l]);
+      for (int l = 0; l < NDIG; ++l) tc::tmem_ld8(taddr + (uint32_t)(64 * l + c0), lev[l]);
       if (dok && i < B) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < 8; ++c) {
           const int j = j0 + c0 + c;
           if (j <= i && j < B) {
             const float2 upd = combine_levels(lev, c, ei + ej[c0 + c]);
@@ -727,18 +731,20 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_update_kernel(double* __restrict_
         }
       }
     }
-    __syncwarp();  // the warp's 32 rows x 32 columns are complete
+    __syncwarp();  // the warp's 32 rows x 16 columns are complete
     if (dok) {
-      for (int r = lg * 32; r < lg * 32 + 32; ++r) {
-        const int i2 = i0 + r, j = j0 + cs + lane;
-        if (i2 < B && j < B && j <= i2) A[(int64_t)i2 * B + j] = As[r * TU_AS + cs + lane];
+      const int rr = lane >> 4, cc = cs + (lane & 15);
+#pragma unroll 4
+      for (int q = 0; q < 16; ++q) {
+        const int r = 32 * lg + 2 * q + rr, i2 = i0 + r, j = j0 + cc;
+        if (i2 < B && j < B && j <= i2) A[(int64_t)i2 * B + j] = As[r * TU_AS + cc];
       }
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == TU_MW) {
+  if (warp == UP_MW) {
     __syncwarp();
     tc::tmem_dealloc(tbase, 512);
   }
@@ -801,7 +807,7 @@ cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, cons
     const int r0 = 64 * (k + 1), nbr = (Bp - r0 + TU_M - 1) / TU_M, nbc = (Bp - r0) / TU_N;
     int tiles = 0;
     for (int a = 0; a < nbr; ++a) tiles += (2 * a + 2 < nbc) ? 2 * a + 2 : nbc;
-    tcf_update_kernel<<<dim3(tiles, L), TU_T, TU_SMEM, st>>>(sigma, slices, stride, B, k, status, every, q_off, err,
+    tcf_update_kernel<<<dim3(tiles, L), UP_T, TU_SMEM, st>>>(sigma, slices, stride, B, k, status, every, q_off, err,
                                                                limit);
   }
   if (lc) lc->n += 1;
