@@ -46,13 +46,11 @@ namespace {
 
 constexpr int NDIG = 6;            // base-256 digits per value
 constexpr int TU_M = 128, TU_N = 64, TU_K = 64;
-constexpr int TU_EW = 8;           // epilogue warps: TMEM lane group (w & 3) x column half (w >> 2)
-constexpr int TU_MW = TU_EW;       // the copy / MMA warp
-constexpr int TU_T = 32 * (TU_EW + 1);
 constexpr uint32_t TU_A_PLANE = TU_M * TU_K * 2;   // 16 KB
 constexpr uint32_t TU_B_PLANE = TU_N * TU_K * 2;   // 8 KB
 constexpr int TU_AS = TU_N + 1;    // row stride (float2) of the staged trailing tile
-// the update kernel: 16 epilogue warps (TMEM lane group w & 3 x 16-column quarter w >> 2)
+// the update and panel kernels: 16 epilogue warps (TMEM lane group w & 3 x 16-column quarter
+// w >> 2) and one copy / MMA warp
 constexpr int UP_EW = 16, UP_MW = UP_EW, UP_T = 32 * (UP_EW + 1);
 constexpr uint32_t TU_TILE = TU_M * TU_AS * 8;
 constexpr uint32_t TU_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + TU_TILE + 256 + 64;
@@ -444,15 +442,15 @@ __global__ void __launch_bounds__(TD_T) tcf_diag_kernel(double* __restrict__ sig
 
 // ---- rows below the diagonal block on the tensor cores -------------------------------------
 // L_ik = A_ik X^T for a 128-row tile of the rows below panel k's diagonal block (grid: row
-// tiles x lines; 8 epilogue warps + 1 copy / MMA warp, like the update): the tile's rows of A
+// tiles x lines; 16 epilogue warps + 1 copy / MMA warp, like the update): the tile's rows of A
 // (float-float) are split into six digits with a per-row power of two straight into the
 // swizzled A operand while X's digits arrive by one bulk copy; the 21 digit-product MMAs sum
 // each level exactly in TMEM (the update's bound: a 64-term level sum stays below 2^24); the
 // epilogue combines the levels per row (one row per thread), writes the row to the whitening
 // operand, and splits it again into six digits for the trailing updates.
-constexpr uint32_t TT_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + 256 + 128 * 4 + 2 * 128 * 4 + 64;
+constexpr uint32_t TT_SMEM = 1024 + NDIG * (TU_A_PLANE + TU_B_PLANE) + 256 + 128 * 4 + 4 * 128 * 4 + 64;
 template <int PREC>
-__global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ sigma_all,
+__global__ void __launch_bounds__(UP_T, 1) tcf_trsm_kernel(double* __restrict__ sigma_all,
                                                            uint8_t* __restrict__ slice_all, size_t slice_stride,
                                                            int B, int k, const int32_t* __restrict__ status,
                                                            int every, int q_off, void* __restrict__ wmat,
@@ -466,8 +464,8 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
   uint8_t* sX = sm + NDIG * TU_A_PLANE;      // NDIG planes of 64 x 64 BF16, then X's 64 row exponents
   const int* fx = (const int*)(sX + NDIG * TU_B_PLANE);
   int* ea = (int*)(sX + XDIG_BYTES);         // exponents of the tile's rows of A
-  float* rmax = (float*)(ea + 128);          // [2][128] row maxima of the two column halves of L
-  uint64_t* bars = (uint64_t*)(rmax + 256);
+  float* rmax = (float*)(ea + 128);          // [4][128] row maxima of the four column quarters of L
+  uint64_t* bars = (uint64_t*)(rmax + 512);
   uint32_t* tslot = (uint32_t*)(bars + 4);
   const uint32_t full = tc::smem_u32(bars), done = full + 8;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -479,32 +477,32 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
     tc::mbar_init(done, 1);
     tc::mbar_init_fence();
   }
-  if (warp == TU_MW) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  if (warp == UP_MW) tc::tmem_alloc(tc::smem_u32(tslot), 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   const float2* A = reinterpret_cast<const float2*>(sigma_all + (int64_t)t * B * B);
 
-  if (warp == TU_MW) {
+  if (warp == UP_MW) {
     if (lane == 0) {
       tc::mbar_arrive_expect_tx(full, XDIG_BYTES);
       tc::bulk_load(tc::smem_u32(sX), sl + xdig_offset(Bp), XDIG_BYTES, full);
     }
   } else {
-    // the A operand: rows of the tile split into digits (16 rows per warp, lanes across the
+    // the A operand: rows of the tile split into digits (8 rows per warp, lanes across the
     // 64 columns: coalesced loads, conflict-free 2-byte stores within a swizzled row)
-    for (int rr = warp * 16; rr < warp * 16 + 16; rr += 16) {
-      float2 v[16][2];
+    for (int rr = warp * 8; rr < warp * 8 + 8; rr += 8) {
+      float2 v[8][2];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < 8; ++q) {
         const int i = i0 + rr + q;
 #pragma unroll
         for (int h = 0; h < 2; ++h)
           v[q][h] = i < B ? A[(int64_t)i * B + p + lane + 32 * h] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
+      for (int q = 0; q < 8; ++q) {
         float mx = fmaxf(fabsf(v[q][0].x), fabsf(v[q][1].x));
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         const int e = row_exponent(mx);
@@ -524,7 +522,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
   }
   __syncthreads();
   bool ok = true;
-  if (warp == TU_MW) {
+  if (warp == UP_MW) {
     if (lane == 0) {
       if (!tc::mbar_wait(full, 0, limit)) ok = false;
       tc::fence_after_sync();
@@ -550,37 +548,37 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
     __syncwarp();
     tc::fence_after_sync();
     if (!dok) atomicExch(err, 1);
-    // thread (TMEM lane group lg, column half ch): row 32 lg + lane, columns 32 ch .. 32 ch + 31
-    const int lg = warp & 3, ch = warp >> 2, cs = 32 * ch;
+    // thread (TMEM lane group lg, column quarter ch): row 32 lg + lane, columns 16 ch .. 16 ch + 15
+    const int lg = warp & 3, ch = warp >> 2, cs = 16 * ch;
     const int row = 32 * lg + lane, i = i0 + row;
     const int ei = ea[row];
     const uint32_t taddr = tbase + ((uint32_t)(32 * lg) << 16);
     float2* Ls = reinterpret_cast<float2*>(sA) + row * TU_AS;  // this thread's row (the MMAs are done)
     float mx = 0.f;
-    for (int c0 = cs; c0 < cs + 32; c0 += 16) {
-      float lev[NDIG][16];
+    for (int c0 = cs; c0 < cs + 16; c0 += 8) {
+      float lev[NDIG][8];
 #pragma unroll
-      for (int l = 0; l < NDIG; ++l) tc::tmem_ld16(taddr + (uint32_t)(64 * l + c0), lev[l]);
+      for (int l = 0; l < NDIG; ++l) tc::tmem_ld8(taddr + (uint32_t)(64 * l + c0), lev[l]);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < 8; ++c) {
         const float2 v = (dok && i < B) ? combine_levels(lev, c, ei + fx[c0 + c]) : make_float2(0.f, 0.f);
         Ls[c0 + c] = v;
         mx = fmaxf(mx, fabsf(v.x));
       }
     }
     rmax[ch * 128 + row] = mx;
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * TU_EW) : "memory");  // the epilogue warps only
-    mx = fmaxf(rmax[row], rmax[128 + row]);
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * UP_EW) : "memory");  // the epilogue warps only
+    mx = fmaxf(fmaxf(rmax[row], rmax[128 + row]), fmaxf(rmax[256 + row], rmax[384 + row]));
     if (dok && i < Bp) {
       // the whitening operand's rows (zero past B)
       const int64_t plane = (int64_t)Bp * Bp;
       void* w = (char*)wmat + (size_t)t * plane * wmat_elem_bytes(PREC);
       if constexpr (PREC == P_FP32T) {  // transposed: consecutive threads on consecutive rows
-        for (int c = cs; c < cs + 32; ++c)
+        for (int c = cs; c < cs + 16; ++c)
           fk::WOut<PREC>::store(w, plane, fk::h_index<PREC>(i, p + c, Bp), fk::ArFF::to_f(Ls[c]));
       } else {  // BF16 planes, row-major: this thread's row in 16-byte pieces
         __nv_bfloat16* wb = (__nv_bfloat16*)w;
-        for (int g = 4 * ch; g < 4 * ch + 4; ++g) {
+        for (int g = 2 * ch; g < 2 * ch + 2; ++g) {
           float f[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) f[j] = fk::ArFF::to_f(Ls[8 * g + j]);
@@ -591,7 +589,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
       const int e = row_exponent(mx);
       if (ch == 0) expo[i] = e;
       const float sc = pow2f(-e);
-      for (int g = 4 * ch; g < 4 * ch + 4; ++g) {
+      for (int g = 2 * ch; g < 2 * ch + 2; ++g) {
         uint32_t pk[NDIG][4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -611,7 +609,7 @@ __global__ void __launch_bounds__(TU_T, 1) tcf_trsm_kernel(double* __restrict__ 
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == TU_MW) {
+  if (warp == UP_MW) {
     __syncwarp();
     tc::tmem_dealloc(tbase, 512);
   }
@@ -799,7 +797,7 @@ cudaError_t launch_factor_tc_step(int step, double* sigma, double* scratch, cons
     e = cudaFuncSetAttribute(trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM);
     if (e != cudaSuccess) return e;
     const int tiles = (Bp - 64 * (k + 1) + TU_M - 1) / TU_M;
-    trsm<<<dim3(tiles, L), TU_T, TT_SMEM, st>>>(sigma, slices, stride, B, k, status, every, q_off, wmat, err, limit);
+    trsm<<<dim3(tiles, L), UP_T, TT_SMEM, st>>>(sigma, slices, stride, B, k, status, every, q_off, wmat, err, limit);
   } else {
     const long long limit = 4000000000LL;  // ~2 s of clock cycles
     e = cudaFuncSetAttribute(tcf_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TU_SMEM);
