@@ -63,10 +63,13 @@ def load_peaks():
 # report null.
 DRAM_BYTES_PER_UNIT = {
     ("precision_1024x448", "fp32"): {
-        "factor_update": ("line", 3.541e6),
-        "factor_panel": ("line", 1.940e6),
+        "factor_update": ("line", 3.548e6),
+        "factor_panel": ("line", 1.976e6),
+        "factor_diag": ("line", 0.1496e6),
+        "prefix_cov": ("line", 1.434e6),
         "syrk": ("px", 2768.0),
-        "syrk_split": ("px", 2716.0),
+        "syrk_split": ("px", 2717.0),
+        "colsum": ("px", 909.0),
         "whiten_score": ("px", 1661.0),
     },
 }
@@ -248,7 +251,7 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, t
     dram = DRAM_BYTES_PER_UNIT.get((workload, prec), {})
     for name, (n, tot) in prof.items():
         if n == 0 or name not in ("factor", "factor_form", "factor_diag", "factor_panel", "factor_update", "syrk",
-                                   "syrk_split", "whiten_score"):
+                                   "syrk_split", "whiten_score", "prefix_cov", "colsum"):
             continue
         ms = tot / prof_steps
         r = None
@@ -293,6 +296,19 @@ def kernel_rooflines(prof, prof_steps, T, W, B, form, prec, every, peaks, mhz, t
                  "blocks out in the tensor-core operand layout)",
                  "work_per_step": f"{px_step} px x (2 B + 4 x B rounded up to 128) bytes",
                  "peak_source": peaks["source"]}
+        elif name == "prefix_cov":
+            byts = T * B * (B + 1) / 2 * 16
+            ach = byts / (ms / 1e3) / 1e9
+            r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": ach / peaks["hbm_gbs"], "kernel": "running covariance sums per line (FP64 in; FP64, or "
+                 "for the tensor-core factor the formed float-float covariance, out)",
+                 "work_per_step": f"{T} lines x B(B+1)/2 x 16 bytes", "peak_source": peaks["source"]}
+        elif name == "colsum":
+            byts = px_step * 2 * B
+            ach = byts / (ms / 1e3) / 1e9
+            r = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": ach / peaks["hbm_gbs"], "kernel": "per-line band sums (uint16 DN in)",
+                 "work_per_step": f"{px_step} px x 2 B bytes", "peak_source": peaks["source"]}
         elif name == "factor_form":
             byts = lines * B * (B + 1) / 2 * 16
             ach = byts / (ms / 1e3) / 1e9

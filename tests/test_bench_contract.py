@@ -48,7 +48,8 @@ def test_kernel_rooflines_from_a_profile():
     # two steps profiled: factor 4 launches of 2000 lines, syrk 4 launches, whitening 8
     prof = {"factor": (8, 8 * 30.0), "syrk": (8, 8 * 5.0), "whiten_score": (16, 16 * 2.0), "colsum": (8, 1.0)}
     r = bench.kernel_rooflines(prof, 2, T, W, B, 1, "fp32", 1, peaks, 2070.0)
-    assert set(r) == {"factor", "syrk", "whiten_score"}
+    assert set(r) == {"factor", "syrk", "whiten_score", "colsum"}
+    assert r["colsum"]["bound"] == "hbm" and abs(r["colsum"]["achieved"] - T * W * 2 * B / 0.0005 / 1e9) < 1e-6
     f = r["factor"]
     assert f["launches_per_step"] == 4 and abs(f["avg_launch_ms"] - 30.0) < 1e-12 and abs(f["ms_per_step"] - 120) < 1e-9
     assert abs(f["achieved"] - 8000 * bench.factor_flops_per_line(B, 1) / 0.120 / 1e12) < 1e-9
