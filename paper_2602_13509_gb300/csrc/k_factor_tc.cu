@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "factor_kernel.cuh"
 #include "hsad_internal.h"
 #include "tc_util.cuh"
@@ -276,26 +278,55 @@ __device__ __forceinline__ float2 double_to_ff_bits(double v) {
   return make_float2(hi, lo);
 }
 
-__global__ void tcf_prefix_form_kernel(double* __restrict__ buf, double* __restrict__ state_s2, int L, int B,
-                                       int inclusive, const float2* __restrict__ ffm) {
-  const int64_t BB = (int64_t)B * B;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // lower-triangle entry q = tri(i) + j
-  if (q >= B * (B + 1) / 2) return;
+// The batch's lines are cut into S segments of `len` lines so that S threads share each
+// entry's walk: a first pass sums each segment (but the last) per entry, the second starts
+// each segment from the state plus the sums of the segments before it. The sums are exact
+// integers below 2^53 in FP64, so the running values do not depend on the segmentation.
+__device__ __forceinline__ int tri_row(int q) {
   int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
   while (tri(i + 1) <= q) ++i;
   while (tri(i) > q) --i;
-  const int j = q - tri(i);
+  return i;
+}
+
+__global__ void tcf_segsum_kernel(const double* __restrict__ buf, int L, int B, int len,
+                                  double* __restrict__ segsum) {
+  const int nq = B * (B + 1) / 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, sg = blockIdx.y;
+  if (q >= nq) return;
+  const int i = tri_row(q), j = q - tri(i);
+  const int64_t BB = (int64_t)B * B, e = (int64_t)i * B + j;
+  const int t1 = min(L, (sg + 1) * len);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int t = sg * len;
+  for (; t + 4 <= t1; t += 4)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += buf[(int64_t)(t + u) * BB + e];
+  for (; t < t1; ++t) acc[0] += buf[(int64_t)t * BB + e];
+  segsum[(int64_t)sg * nq + q] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+__global__ void tcf_prefix_form_kernel(double* __restrict__ buf, double* __restrict__ state_s2, int L, int B,
+                                       int inclusive, const float2* __restrict__ ffm, int nseg, int len,
+                                       const double* __restrict__ segsum) {
+  const int64_t BB = (int64_t)B * B;
+  const int nq = B * (B + 1) / 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, sg = blockIdx.y;  // entry q = tri(i) + j
+  if (q >= nq) return;
+  const int i = tri_row(q), j = q - tri(i);
   const int64_t e = (int64_t)i * B + j;
   double run = state_s2[e];
+  for (int s2 = 0; s2 < sg; ++s2) run += segsum[(int64_t)s2 * nq + q];
+  const int tb = sg * len, te = min(L, tb + len);
   constexpr int U = 8;  // lines whose loads are in flight together
-  for (int t0 = 0; t0 < L; t0 += U) {
+  for (int t0 = tb; t0 < te; t0 += U) {
     double v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = (t0 + u < L) ? buf[(int64_t)(t0 + u) * BB + e] : 0.0;
+    for (int u = 0; u < U; ++u) v[u] = (t0 + u < te) ? buf[(int64_t)(t0 + u) * BB + e] : 0.0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int t = t0 + u;
-      if (t >= L) break;
+      if (t >= te) break;
       const double before = run;
       run += v[u];
       const double S = inclusive ? run : before;
@@ -304,7 +335,7 @@ __global__ void tcf_prefix_form_kernel(double* __restrict__ buf, double* __restr
       reinterpret_cast<float2*>(buf)[(int64_t)t * BB + e] = out;
     }
   }
-  state_s2[e] = run;
+  if (sg == nseg - 1) state_s2[e] = run;
 }
 
 // ---- diagonal block -----------------------------------------------------------------------
@@ -755,7 +786,13 @@ bool factor_tc_supported(int B, int prec) { return is_trsm(prec) && B >= 192; }
 int factor_tc_steps(int B) { return 3 * (pad64(B) / 64) - 1; }
 int factor_tc_step_kind(int step) { return step == 0 ? 0 : 1 + (step - 1) % 3; }
 
-size_t tcf_form_scratch_bytes(int L, int B) { return (size_t)L * (2 * B + 1) * sizeof(float2); }
+constexpr int kSegMax = 32;  // segments of the prefix pass
+__host__ __device__ inline size_t ffm_bytes(int L, int B) {
+  return ((size_t)L * (2 * B + 1) * sizeof(float2) + 255) / 256 * 256;
+}
+size_t tcf_form_scratch_bytes(int L, int B) {
+  return ffm_bytes(L, B) + (size_t)kSegMax * (B * (B + 1) / 2) * sizeof(double);
+}
 
 cudaError_t launch_tcf_prefix_form(double* buf, double* state_s2, int L, int B, int inclusive, const double* m,
                                    int64_t n0, int W, int incl, const int64_t* n0_dev, float2* ffm,
@@ -764,7 +801,19 @@ cudaError_t launch_tcf_prefix_form(double* buf, double* state_s2, int L, int B, 
   tcf_form_prep_kernel<<<dim3((B + 127) / 128, L), 128, 0, st>>>(m, L, B, n0, W, incl, n0_dev, ffm);
   if (lc) lc->n += 1;
   const int nq = B * (B + 1) / 2;
-  tcf_prefix_form_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(buf, state_s2, L, B, inclusive, ffm);
+  // segments so that the walk is spread over about 600 k threads (four per FP32 lane of the
+  // GPU), of at least 32 lines each
+  int nseg = (int)std::min<int64_t>({(int64_t)kSegMax, std::max<int64_t>(1, L / 32), (600000 + nq - 1) / nq});
+  nseg = std::max(nseg, 1);
+  const int len = (L + nseg - 1) / nseg;
+  nseg = (L + len - 1) / len;
+  double* segsum = reinterpret_cast<double*>(reinterpret_cast<char*>(ffm) + ffm_bytes(L, B));
+  const unsigned gx = (unsigned)((nq + 255) / 256);
+  if (nseg > 1) {
+    tcf_segsum_kernel<<<dim3(gx, nseg - 1), 256, 0, st>>>(buf, L, B, len, segsum);
+    if (lc) lc->n += 1;
+  }
+  tcf_prefix_form_kernel<<<dim3(gx, nseg), 256, 0, st>>>(buf, state_s2, L, B, inclusive, ffm, nseg, len, segsum);
   if (lc) lc->n += 1;
   return cudaGetLastError();
 }
