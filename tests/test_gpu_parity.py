@@ -109,6 +109,20 @@ def test_stream_ragged_shapes(hs, W, B):
     assert emax <= TOL["fp32"], emax
 
 
+@pytest.mark.parametrize("W,B,mode", [(70, 200, "exclusive"), (33, 270, "inclusive"), (9, 448, "exclusive")])
+def test_float_stream_tensor_core_factor_simt_solve(hs, W, B, mode):
+    """Float input at B >= 192: the tensor-core factor with the FP32 solve on the SIMT cores
+    (the transposed FP32 operand), against the oracle at the FP32 tolerance."""
+    from gen import IllConditionedScene
+    T = max(6, (B + 1) // W + 4)
+    lines = IllConditionedScene(W, B, seed=W * 7 + B, decades=2.0, dtype="f32").lines(0, T)  # kappa 1e4
+    rc, s, m, st, _ = _run(hs, lines, in_dtype="f32", stats_mode=mode)
+    ref, rst = orx.stream_rx(lines, oracle.EXCLUSIVE if mode == "exclusive" else oracle.INCLUSIVE)
+    np.testing.assert_array_equal(st, rst)
+    emax, _ = rel_err(s, ref)
+    assert emax <= TOL["fp32"], emax
+
+
 @pytest.mark.parametrize("W,B", [(1, 1), (7, 3), (129, 64), (65, 65), (33, 127), (300, 130), (130, 270),
                                  (640, 270), (130, 448), (40, 500), (21, 512)])
 def test_stream_bf16_ragged_shapes(hs, W, B):
@@ -125,21 +139,31 @@ def test_stream_bf16_ragged_shapes(hs, W, B):
     assert mask_mismatch(m, ref, tau, MARGIN["bf16"]) == 0
 
 
-@pytest.mark.parametrize("prec,dtype,B,mode,form", [("bf16", "u16", 270, "exclusive", 1),
-                                                     ("bf16", "u16", 448, "inclusive", 1),
-                                                     ("bf16", "u16", 512, "exclusive", 1),
-                                                     ("bf16", "f32", 270, "exclusive", 0),
-                                                     ("bf16", "u16", 270, "cube", 0),
-                                                     ("fp16", "u16", 270, "exclusive", 0),
-                                                     ("fp32", "u16", 270, "exclusive", 1),
-                                                     ("fp32", "f32", 270, "inclusive", 1),
-                                                     ("fp32", "u16", 512, "exclusive", 1),
-                                                     ("fp32", "f32", 270, "cube", 0)])
-def test_whitening_form_per_context(hs, prec, dtype, B, mode, form):
+@pytest.mark.parametrize("prec,dtype,B,mode,form,tcw", [("bf16", "u16", 270, "exclusive", 1, True),
+                                                         ("bf16", "u16", 448, "inclusive", 1, True),
+                                                         ("bf16", "u16", 512, "exclusive", 1, True),
+                                                         ("bf16", "f32", 270, "exclusive", 0, True),
+                                                         ("bf16", "u16", 270, "cube", 0, True),
+                                                         ("fp16", "u16", 270, "exclusive", 0, True),
+                                                         ("fp32", "u16", 270, "exclusive", 1, True),
+                                                         ("fp32", "u16", 128, "exclusive", 1, False),
+                                                         ("fp32", "f32", 270, "inclusive", 1, False),
+                                                         ("fp32", "u16", 512, "exclusive", 1, True),
+                                                         ("fp32", "f32", 270, "cube", 0, False)])
+def test_whitening_form_per_context(hs, prec, dtype, B, mode, form, tcw):
+    """Form (triangular solve or explicit inverse) and units (tensor or SIMT cores) of each
+    context kind: FP32 on the tensor cores needs uint16 input, streamed statistics and
+    B >= 192 (the tensor-core factor)."""
     kw = dict(cube_lines=16) if mode == "cube" else {}
     det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype, stats_mode=mode, **kw)
     assert det.whitening_form == form
+    assert det.whitening_tensor_cores == tcw
     det.close()
+    if prec == "fp32" and dtype == "u16" and mode != "cube":  # the FP64 factor keeps the SIMT solve
+        det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype, stats_mode=mode,
+                          factor_precision=hs.HSAD_FACTOR_FP64)
+        assert det.whitening_form == 1 and not det.whitening_tensor_cores
+        det.close()
     # HSAD_FORCE_INVERSE keeps the explicit inverse everywhere
     det = hs.Detector(width=32, bands=B, precision=prec, in_dtype=dtype, stats_mode=mode,
                       flags=hs.HSAD_FORCE_INVERSE, **kw)
