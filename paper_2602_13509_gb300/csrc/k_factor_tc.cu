@@ -559,13 +559,14 @@ __global__ void __launch_bounds__(UP_T, 1) tcf_trsm_kernel(double* __restrict__ 
       tc::fence_after_sync();
       if (ok) {
         const uint32_t idesc = tc::idesc_f16(1, TU_M, TU_N);
+        // descriptors by offset: a plane adds its size / 16, a 32-byte K step 2
+        const uint64_t dA = tc::desc_sw128(tc::smem_u32(sA)), dB = tc::desc_sw128(tc::smem_u32(sX));
         for (int l = 0; l < NDIG; ++l)
           for (int dt = 0; dt <= l; ++dt) {
-            const uint32_t aop = tc::smem_u32(sA + dt * TU_A_PLANE), bop = tc::smem_u32(sX + (l - dt) * TU_B_PLANE);
+            const uint64_t da = dA + (uint64_t)(dt * (TU_A_PLANE >> 4)), db = dB + (uint64_t)((l - dt) * (TU_B_PLANE >> 4));
 #pragma unroll
             for (int ks = 0; ks < TU_K / 16; ++ks)
-              tc::mma_f16(tbase + (uint32_t)(64 * l), tc::desc_sw128(aop + ks * 32), tc::desc_sw128(bop + ks * 32),
-                          idesc, (dt > 0 || ks > 0) ? 1u : 0u);
+              tc::mma_f16(tbase + (uint32_t)(64 * l), da + 2 * ks, db + 2 * ks, idesc, (dt > 0 || ks > 0) ? 1u : 0u);
           }
         tc::mma_commit(done);
       } else {
@@ -705,13 +706,13 @@ __global__ void __launch_bounds__(UP_T, 1) tcf_update_kernel(double* __restrict_
       if (ok) {
         const uint32_t idesc = tc::idesc_f16(1, TU_M, TU_N);
         // level l = t + u accumulates d_t(rows i) d_u(rows j)^T into columns 64 l .. 64 l + 63
+        const uint64_t dA = tc::desc_sw128(tc::smem_u32(sA)), dB = tc::desc_sw128(tc::smem_u32(sB));
         for (int l = 0; l < NDIG; ++l)
           for (int dt = 0; dt <= l; ++dt) {
-            const uint32_t aop = tc::smem_u32(sA + dt * TU_A_PLANE), bop = tc::smem_u32(sB + (l - dt) * TU_B_PLANE);
+            const uint64_t da = dA + (uint64_t)(dt * (TU_A_PLANE >> 4)), db = dB + (uint64_t)((l - dt) * (TU_B_PLANE >> 4));
 #pragma unroll
             for (int ks = 0; ks < TU_K / 16; ++ks)
-              tc::mma_f16(tbase + (uint32_t)(64 * l), tc::desc_sw128(aop + ks * 32), tc::desc_sw128(bop + ks * 32),
-                          idesc, (dt > 0 || ks > 0) ? 1u : 0u);
+              tc::mma_f16(tbase + (uint32_t)(64 * l), da + 2 * ks, db + 2 * ks, idesc, (dt > 0 || ks > 0) ? 1u : 0u);
           }
         tc::mma_commit(done);
       } else {

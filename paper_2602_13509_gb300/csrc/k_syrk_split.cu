@@ -191,13 +191,17 @@ __global__ void __launch_bounds__(SP_THREADS, 2) syrk_pre_kernel(const uint8_t* 
         const uint32_t aH = tc::smem_u32(sm + s * SP_STAGE), aR = aH + SP_PLANE;
         // B: the column block's 64 rows of H and R (inside A's block on the diagonal)
         const uint32_t bH = diag ? aH + half_off : aH + SP_BLOCK, bR = diag ? aR + half_off : bH + SP_HALF;
+        // descriptors by offset: a 32-byte K step adds 2 to the start-address field (address / 16)
+        const uint64_t dAH = tc::desc_sw128(aH), dAR = tc::desc_sw128(aR), dBH = tc::desc_sw128(bH),
+                       dBR = tc::desc_sw128(bR);
 #pragma unroll
         for (int ks = 0; ks < SP_KC / 16; ++ks) {
-          const uint32_t o = ks * 32, acc = (c > 0 || ks > 0) ? 1u : 0u;
-          tc::mma_f16(tbase + 0, tc::desc_sw128(aH + o), tc::desc_sw128(bH + o), idesc, acc);
-          tc::mma_f16(tbase + 64, tc::desc_sw128(aH + o), tc::desc_sw128(bR + o), idesc, acc);
-          tc::mma_f16(tbase + 64, tc::desc_sw128(aR + o), tc::desc_sw128(bH + o), idesc, 1u);
-          tc::mma_f16(tbase + 128, tc::desc_sw128(aR + o), tc::desc_sw128(bR + o), idesc, acc);
+          const uint64_t o = 2 * ks;
+          const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+          tc::mma_f16(tbase + 0, dAH + o, dBH + o, idesc, acc);
+          tc::mma_f16(tbase + 64, dAH + o, dBR + o, idesc, acc);
+          tc::mma_f16(tbase + 64, dAR + o, dBH + o, idesc, 1u);
+          tc::mma_f16(tbase + 128, dAR + o, dBR + o, idesc, acc);
         }
         tc::mma_commit(empty + 8 * s);
         any = true;

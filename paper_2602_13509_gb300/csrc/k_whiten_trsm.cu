@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_f16(1, TS_M, 64);
-      const uint32_t z0 = tc::smem_u32(sZ), y0 = tc::smem_u32(sY);
+      const uint64_t dz = tc::desc_sw128(tc::smem_u32(sZ)), dy = tc::desc_sw128(tc::smem_u32(sY));
       int it = 0;
       bool issued_any = false;
       for (int k = 0; k < nkb && ok; ++k) {
@@ -225,18 +225,19 @@ __global__ void __launch_bounds__(TS_THREADS, 1) whiten_trsm_kernel(
           const int s = it % stages;
           if (!tc::mbar_wait(b_full + 8 * s, (uint32_t)((it / stages) & 1), limit)) { ok = false; break; }
           tc::fence_after_sync();
-          const uint32_t h0 = tc::smem_u32(sR + s * STAGE);
           const uint32_t d = tbase + (uint32_t)(j * TS_KB);
-          const uint32_t a0 = j == k ? z0 : y0;
+          // descriptors by offset: the start-address field holds the shared address / 16 (all
+          // of shared memory fits its 14 bits), so a 32-byte K step adds 2, a plane its size / 16
+          const uint64_t da0 = j == k ? dz : dy, dh0 = tc::desc_sw128(tc::smem_u32(sR + s * STAGE));
 #pragma unroll
           for (int term = 0; term < Terms<NT>::n; ++term) {
-            const uint32_t aop = a0 + Terms<NT>::a(term) * TS_BLK;
-            const uint32_t bop = h0 + Terms<NT>::h(term) * TS_HALF;
+            const uint64_t da = da0 + (uint64_t)(Terms<NT>::a(term) * (TS_BLK >> 4));
+            const uint64_t db = dh0 + (uint64_t)(Terms<NT>::h(term) * (TS_HALF >> 4));
 #pragma unroll
             for (int ks = 0; ks < TS_KB / 16; ++ks) {
               // y_k overwrites block k; the updates of block j start at k = 0
               const bool first = term == 0 && ks == 0 && (j == k || k == 0);
-              tc::mma_f16(d, tc::desc_sw128(aop + ks * 32), tc::desc_sw128(bop + ks * 32), idesc, first ? 0u : 1u);
+              tc::mma_f16(d, da + 2 * ks, db + 2 * ks, idesc, first ? 0u : 1u);
             }
           }
           issued_any = true;
