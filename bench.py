@@ -63,14 +63,14 @@ def load_peaks():
 # report null.
 DRAM_BYTES_PER_UNIT = {
     ("precision_1024x448", "fp32"): {
-        "factor_update": ("line", 3.548e6),
-        "factor_panel": ("line", 1.976e6),
-        "factor_diag": ("line", 0.1496e6),
-        "prefix_cov": ("line", 1.434e6),
-        "syrk": ("px", 2768.0),
-        "syrk_split": ("px", 2717.0),
-        "colsum": ("px", 909.0),
-        "whiten_score": ("px", 1661.0),
+        "factor_update": ("line", 3.552e6),
+        "factor_panel": ("line", 1.947e6),
+        "factor_diag": ("line", 0.1495e6),
+        "prefix_cov": ("line", 2.172e6),
+        "syrk": ("px", 2769.0),
+        "syrk_split": ("px", 2716.0),
+        "colsum": ("px", 910.0),
+        "whiten_score": ("px", 1655.0),
     },
 }
 
