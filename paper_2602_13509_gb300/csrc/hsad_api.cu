@@ -770,12 +770,21 @@ int whiten(hsad_ctx* ctx, const void* x, int L, int factor_stride, ScoreOut o, i
 // K2: exact covariance sums of n_groups groups of pix pixels into out (lower triangle).
 // uint16 input runs on the tensor cores (integer split, exact); float input accumulates
 // FP32 x FP32 products in FP64 on the SIMT cores.
+// Whether syrk() takes the split path for n_groups lines of pix pixels (which also forms the
+// lines' band sums, so that the column-sum launch is skipped).
+bool syrk_split_path(const hsad_ctx* ctx, int64_t n_groups, int64_t pix, bool accumulate) {
+  return ctx->in_type == IN_U16 && ctx->split_syrk && !accumulate && pix == ctx->W && n_groups <= ctx->Lmax;
+}
+
+// K1b + K2 for a batch of streamed lines: the per-line band sums (s1) and the exact covariance
+// sums, in one pass over the lines where the split path applies.
 int syrk(hsad_ctx* ctx, const void* x, int64_t n_groups, int64_t pix, double* out, int64_t out_stride,
-         bool accumulate) {
+         bool accumulate, double* s1 = nullptr) {
   cudaStream_t st = ctx->stream;
-  if (ctx->in_type == IN_U16 && ctx->split_syrk && !accumulate && pix == ctx->W && n_groups <= ctx->Lmax) {
-    // streamed lines: each line's DN split once, then one contraction per block pair
-    KL("syrk_split", launch_syrk_split((const uint16_t*)x, n_groups, pix, ctx->B, ctx->c_int, ctx->hr, st,
+  if (syrk_split_path(ctx, n_groups, pix, accumulate)) {
+    // streamed lines: each line's DN split once (band sums on the way), then one contraction
+    // per block pair
+    KL("syrk_split", launch_syrk_split((const uint16_t*)x, n_groups, pix, ctx->B, ctx->c_int, ctx->hr, s1, st,
                                        &ctx->lc));
     KL("syrk", launch_syrk_pre(ctx->hr, n_groups, pix, ctx->B, out, out_stride, ctx->dev_err, st, &ctx->lc));
   } else if (ctx->in_type == IN_U16) {
@@ -825,9 +834,11 @@ int excl_tail(hsad_ctx* ctx, const void* x, int L, uint64_t first, bool dev) {
   cudaStream_t st = ctx->stream;
   const int64_t* n0_dev = dev ? ctx->bdesc : nullptr;
   CK(cudaMemsetAsync(ctx->status + 1, 0, (size_t)L * 4, st));
-  KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
   {
-    int rc = syrk(ctx, x, L, W, ctx->sigma + BB, BB, false);
+    const bool fused = syrk_split_path(ctx, L, W, false);
+    if (!fused)
+      KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
+    int rc = syrk(ctx, x, L, W, ctx->sigma + BB, BB, false, fused ? ctx->s1_line : nullptr);
     if (rc != HSAD_OK) return rc;
   }
   const double* gain = ctx->batch_gain ? ctx->d_gain_cur : nullptr;
@@ -958,9 +969,11 @@ int stream_batch(hsad_ctx* ctx, const void* x, int L, uint64_t first) {
   if (!incl) return stream_batch_excl(ctx, x, L, first);
   if (ctx->n_stats == 0) KL("shift_init", launch_shift_init(x, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, st, &ctx->lc));
   CK(cudaMemsetAsync(ctx->status, 0, (size_t)L * 4, st));
-  KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
   {
-    int rc = syrk(ctx, x, L, W, ctx->sigma, (int64_t)B * B, false);
+    const bool fused = syrk_split_path(ctx, L, W, false);
+    if (!fused)
+      KL("colsum", launch_colsum(x, L, W, B, ctx->in_type, ctx->c_int, ctx->c_flt, ctx->s1_line, st, &ctx->lc));
+    int rc = syrk(ctx, x, L, W, ctx->sigma, (int64_t)B * B, false, fused ? ctx->s1_line : nullptr);
     if (rc != HSAD_OK) return rc;
   }
   const double* gain = ctx->batch_gain ? ctx->d_gain_cur : nullptr;

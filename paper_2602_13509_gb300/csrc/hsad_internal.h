@@ -108,8 +108,10 @@ cudaError_t launch_syrk_tc(const uint16_t* x, int64_t n_groups, int64_t pix_per_
 // and group from those blocks (groups of at most 4096 pixels, out as for launch_syrk_tc
 // without accumulation).
 size_t syrk_split_bytes(int64_t groups, int64_t pix, int B);
+// s1 (nullable): also the groups' band sums s1[g][b] = sum_p (x - c) (exact integers in FP64),
+// as launch_colsum writes them.
 cudaError_t launch_syrk_split(const uint16_t* x, int64_t n_groups, int64_t pix, int B, const int32_t* c_int,
-                              uint8_t* hr, cudaStream_t st, LaunchCounter* lc);
+                              uint8_t* hr, double* s1, cudaStream_t st, LaunchCounter* lc);
 cudaError_t launch_syrk_pre(const uint8_t* hr, int64_t n_groups, int64_t pix, int B, double* out,
                             int64_t out_stride, int32_t* err, cudaStream_t st, LaunchCounter* lc);
 // Front end (Sec. 3.2): out[p][b] = sum_{i < bin} raw[p][first + bin * b + i].

@@ -52,7 +52,8 @@ constexpr int SS_T = 256;
 __host__ __device__ inline uint32_t ss_raw_bytes(int B) { return ((uint32_t)SP_KC * B * 2 + 15) / 16 * 16; }
 __global__ void __launch_bounds__(SS_T) syrk_split_kernel(const uint16_t* __restrict__ x, int64_t pix, int B,
                                                           const int32_t* __restrict__ c_int,
-                                                          uint8_t* __restrict__ hr, int vec) {
+                                                          uint8_t* __restrict__ hr, double* __restrict__ s1,
+                                                          int vec) {
   extern __shared__ __align__(16) uint8_t ssm[];
   uint8_t* blk = ssm;                                  // one staged operand block: H then R
   uint16_t* raw = reinterpret_cast<uint16_t*>(ssm + SP_BLOCK);
@@ -71,6 +72,14 @@ __global__ void __launch_bounds__(SS_T) syrk_split_kernel(const uint16_t* __rest
     for (int i = threadIdx.x; i < nval; i += SS_T) raw[i] = __ldg(src + i);
   }
   uint8_t* dst = hr + ((size_t)(g * sp_chunks(pix) + chunk) * nbb) * SP_BLOCK;
+  if (s1) {  // the chunk's band sums (exact integers; FP64 atomic adds of them are exact in any order)
+    __syncthreads();
+    for (int b = threadIdx.x; b < B; b += SS_T) {
+      int acc = 0;  // |x - c| < 2^16 over 64 pixels
+      for (int k = 0; k < npx; ++k) acc += (int)raw[k * B + b];
+      atomicAdd(s1 + g * B + b, (double)(acc - npx * c_int[b]));
+    }
+  }
   for (int bb = 0; bb < nbb; ++bb) {
     __syncthreads();  // the raw chunk is in place; the previous block's stores have read blk
     for (int it = threadIdx.x; it < SP_M * (SP_KC / 8); it += SS_T) {
@@ -252,8 +261,12 @@ __global__ void __launch_bounds__(SP_THREADS, 2) syrk_pre_kernel(const uint8_t* 
 }
 
 cudaError_t launch_syrk_split(const uint16_t* x, int64_t n_groups, int64_t pix, int B, const int32_t* c_int,
-                              uint8_t* hr, cudaStream_t st, LaunchCounter* lc) {
+                              uint8_t* hr, double* s1, cudaStream_t st, LaunchCounter* lc) {
   if (n_groups <= 0 || pix <= 0) return cudaSuccess;
+  if (s1) {
+    const cudaError_t e0 = cudaMemsetAsync(s1, 0, (size_t)n_groups * B * sizeof(double), st);
+    if (e0 != cudaSuccess) return e0;
+  }
   if (n_groups > 65535 || sp_chunks(pix) > 65535) return cudaErrorInvalidValue;
   const uint32_t smem = SP_BLOCK + ss_raw_bytes(B);
   cudaError_t e = cudaFuncSetAttribute(syrk_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -261,7 +274,7 @@ cudaError_t launch_syrk_split(const uint16_t* x, int64_t n_groups, int64_t pix, 
   // 16-byte loads: the input base and every chunk start (pixel multiples of 64 x B values)
   const int vec = ((uintptr_t)x % 16 == 0) && ((pix * B) % 8 == 0) && ((SP_KC * B) % 8 == 0);
   syrk_split_kernel<<<dim3((unsigned)sp_chunks(pix), (unsigned)n_groups), SS_T, smem, st>>>(x, pix, B, c_int, hr,
-                                                                                            vec);
+                                                                                            s1, vec);
   if (lc) lc->n += 1;
   return cudaGetLastError();
 }
