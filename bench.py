@@ -68,6 +68,7 @@ DRAM_BYTES_PER_UNIT = {
         "factor_diag": ("line", 0.1495e6),
         "prefix_cov": ("line", 2.172e6),
         "syrk": ("px", 2769.0),
+        "syrk_split": ("px", 2748.0),
         "whiten_score": ("px", 1655.0),
     },
 }
