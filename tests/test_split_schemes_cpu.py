@@ -46,7 +46,7 @@ def test_three_term_bf16_split_is_exact():
     # each term is a BF16 value
     for t in (hi, mid, lo):
         np.testing.assert_array_equal(t, bf16(t))
-    # (hi + mid) + lo in FP32 (the order the coupling reads use) is the value itself
+    # (hi + mid) + lo in FP32 is the value itself
     s = ((hi + mid).astype(np.float32) + lo).astype(np.float32)
     np.testing.assert_array_equal(s, v)
     # and exactly in FP64
